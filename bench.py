@@ -1,0 +1,344 @@
+"""Benchmark of the GB300 octree build: one JSON line on rank 0.
+
+Workload (one step): N = 2^27 particles, float64 coordinates from 1,000 Gaussian clumps
+(sigma log-uniform in 1e-4..1e-2 of the box) plus 20% uniform background, float32 log-normal
+masses, 63-bit Hilbert keys, Ncrit = 64. A step runs the whole path on the device: bounding cube,
+keys, radix sort with permutation, cornerstone leaf loop, linked octree, node-count upsweep and
+the FP32 compensated monopole/quadrupole upsweep. Inputs (3.5 GB) are larger than the 129 MB L2,
+so no explicit flush is needed between steps.
+
+``--impl reference`` times the plain CPU oracle instead (single thread, bounded sample of the
+same workload); under torchrun only rank 0 runs it.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_FULL = 1 << 27
+NCRIT = 64
+SEED = 20230626 + 2
+METRIC = "particles/s full octree build (keys->sort->leaves->tree) @1 GB300, % HBM roofline"
+WORKLOAD = "2^27 Gaussian clumps + 20% uniform, Hilbert keys, Ncrit=64, with count + multipole upsweep"
+CPU_SAMPLE = 1 << 21
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=N_FULL)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(n: int, rank: int = 0):
+    from paper_2307_06345_gb300 import workloads as w
+    x, y, z = w.clumps(n, SEED + 7919 * rank)
+    m = w.lognormal_masses(n, SEED + 1 + 7919 * rank)
+    return x, y, z, m
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_bytes(n: int, n_leaves: int, iter_leaves: int, n_nodes: int):
+    """Compulsory DRAM traffic of one step (bytes), by phase."""
+    return {
+        "bbox": 24 * n,
+        "keys": 32 * n,
+        "sort": (8 + 20 + 24 * 7) * n,          # digit histograms + 8 passes (first has no value read)
+        "leaves": 24 * iter_leaves + 8 * n,     # K + pos read/written per pass; P read by searches once
+        "link": 40 * n_nodes,
+        "counts": 8 * n_nodes,
+        "multipoles": 32 * n + 48 * n_nodes,    # xyz fp64 + m fp32 + perm; per-node outputs + scratch
+    }
+
+
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    import paper_2307_06345_gb300 as cs
+
+    cs.load()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    n = args.n
+    x, y, z, m = workload(n, rank)
+    X, Y, Z, M = (torch.from_numpy(a).to(dev) for a in (x, y, z, m))
+    stream = torch.cuda.current_stream()
+
+    # warm-up (also sizes the buffers)
+    out = cs.build_octree(X, Y, Z, curve=cs.HILBERT, ncrit=NCRIT, masses=M)
+    buffers = out["buffers"]
+    for _ in range(max(args.warmup - 1, 0)):
+        out = cs.build_octree(X, Y, Z, curve=cs.HILBERT, ncrit=NCRIT, masses=M, buffers=buffers)
+    torch.cuda.synchronize()
+    n_leaves, iters = out["n_leaves"], out["iters"]
+    n_nodes = cs.n_nodes(n_leaves)
+
+    # per-phase events recorded inside the timed steps (same stream as the library launches)
+    phases = ["bbox", "keys", "sort", "leaves", "link", "counts", "multipoles"]
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(phases) + 1)] for _ in range(K)]
+    b = buffers
+
+    def step(k):
+        e = ev[k]
+        e[0].record(stream)
+        cs.cstone_bbox(X, Y, Z, b.box, b.ws)
+        e[1].record(stream)
+        cs.cstone_keys(X, Y, Z, b.box, cs.HILBERT, b.keys)
+        e[2].record(stream)
+        cs.cstone_sort(b.keys, b.sorted_keys, b.perm, b.ws)
+        e[3].record(stream)
+        nl, _ = cs.cstone_build_leaves(b.sorted_keys, NCRIT, b.leaves, b.counts, b.offsets, 0, 64, b.ws)
+        e[4].record(stream)
+        t = b.tree_buffers(nl)
+        cs.cstone_link_tree(b.leaves, nl, t["NK"], t["CO"], t["LO"], t["leaf_to_node"], t["parent"], b.ws)
+        e[5].record(stream)
+        cs.cstone_upsweep_counts(b.counts, nl, t["leaf_to_node"], t["parent"], t["counts"], b.ws)
+        e[6].record(stream)
+        cs.cstone_upsweep_multipoles(X, Y, Z, M, b.perm, b.offsets, nl, t["leaf_to_node"], t["parent"], t["CO"],
+                                     t["mass"], t["com"], t["quad"], b.ws)
+        e[7].record(stream)
+        return nl
+
+    step(0)  # one more warm-up through the exact timed sequence
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        start.record(stream)
+        for k in range(K):
+            step(k)
+        stop.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    elapsed_ms = start.elapsed_time(stop)
+    if dist:
+        t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    phase_ms = {p: float(np.mean([ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(K)]))
+                for i, p in enumerate(phases)}
+    ms_per_step = elapsed_ms / K
+    value = world * n / (ms_per_step * 1e-3)
+
+    # roofline of the dominant kernel group: the radix sort (upfront histogram + 8 one-sweep passes)
+    hbm, peak_kind = peaks()
+    algo = algorithmic_bytes(n, n_leaves, int(n_leaves * 1.3), n_nodes)
+    dom = max(phase_ms, key=phase_ms.get)
+    achieved = algo[dom] / (phase_ms[dom] * 1e-3) / 1e9
+    step_bytes = sum(algo.values())
+
+    # end to end through the public API with host buffers: H2D inputs, build, D2H of the tree
+    e2e = None
+    if not args.no_e2e:
+        hx, hy, hz, hm = (torch.from_numpy(a).pin_memory() for a in (x, y, z, m))
+        Xe, Ye, Ze, Me = (torch.empty_like(t) for t in (X, Y, Z, M))
+        h2d = sum(t.numel() * t.element_size() for t in (hx, hy, hz, hm))
+
+        def e2e_step():
+            for src, dst in ((hx, Xe), (hy, Ye), (hz, Ze), (hm, Me)):
+                dst.copy_(src, non_blocking=True)
+            o = cs.build_octree(Xe, Ye, Ze, curve=cs.HILBERT, ncrit=NCRIT, masses=Me, buffers=buffers)
+            host = [o[k].cpu() for k in ("leaves", "leaf_counts", "NK", "CO", "LO", "node_counts", "mass", "com",
+                                         "quad")]
+            return sum(t.numel() * t.element_size() for t in host)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        s2, t2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ke = max(1, min(K, 5))
+        s2.record(stream)
+        d2h = 0
+        for _ in range(ke):
+            d2h = e2e_step()
+        t2.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = s2.elapsed_time(t2) / ke
+        if dist:
+            t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": world * n / (e2e_ms * 1e-3), "unit": "particles/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline:
+            cpu = cpu_baseline(CPU_SAMPLE)
+        launches_per_step = 3 + 1 + 10 + 1 + 4 + 1 + 1
+        line = {
+            "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_particles": n, "ncrit": NCRIT, "curve": "hilbert",
+                       "l2_flush": "inputs (3.5 GB) larger than L2", "parallelism": "replicas" if world > 1 else "1gpu",
+                       "n_leaves": n_leaves, "n_nodes": n_nodes, "leaf_iterations": iters,
+                       "arith": "f64 grid mapping, u64 keys/sort/tree, f32 compensated multipoles"},
+            "phase_ms": phase_ms,
+            "step_algorithmic_bytes": step_bytes,
+            "step_hbm_frac": step_bytes / (ms_per_step * 1e-3) / 1e9 / hbm,
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "peak_source": peak_kind, "traffic": None,
+                         "algorithmic_bytes_per_launch": algo[dom]},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clocks.summary(),
+            "gpu_launches": launches_per_step * K,
+        }
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return line
+
+
+def cpu_baseline(sample: int, rank_seed: int = 0):
+    """The oracle as it stands, single-threaded, on a bounded sample of the same workload."""
+    import oracle
+
+    oracle.build()
+    x, y, z, m = workload(sample, rank_seed)
+    t0 = time.perf_counter()
+    ref = oracle.full_build(x, y, z, oracle.HILBERT, NCRIT)
+    oracle.multipoles(x, y, z, m, ref["P"], ref["perm"], ref["NK"])
+    dt = time.perf_counter() - t0
+    return {"value": sample / dt, "unit": "particles/s", "cores": 1, "kind": "oracle",
+            "sample": f"{sample} particles of the same clump distribution, full path incl. multipoles, "
+                      f"{dt:.1f} s single-threaded"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    import oracle
+
+    oracle.build()
+    sample = CPU_SAMPLE
+    x, y, z, m = workload(sample)
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm state; warm-up steps would only repeat the timed work
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        ref = oracle.full_build(x, y, z, oracle.HILBERT, NCRIT)
+        oracle.multipoles(x, y, z, m, ref["P"], ref["perm"], ref["NK"])
+        times.append(time.perf_counter() - t0)
+    dt = sum(times) / len(times)
+    value = sample / dt
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64/u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_particles": sample, "ncrit": NCRIT, "curve": "hilbert"},
+            "cpu_baseline": {"value": value, "unit": "particles/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{sample} particles per step of the same clump distribution"},
+            "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+    else:
+        line = run_ours(args, rank, world, local)
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,183 @@
+/*
+ * cstone.h - C ABI of the GB300-native Cornerstone octree build.
+ *
+ * Method: S. Keller et al., "Cornerstone: Octree Construction Algorithms for Scalable Particle
+ * Simulations", PASC'23 (arXiv 2307.06345). Section references below are to that paper.
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers to arrays are DEVICE pointers (cudaMalloc / torch CUDA memory) owned by the caller,
+ *    unless the comment says "host". The library never allocates device memory: scratch space
+ *    comes from a caller-provided workspace `ws` of at least the size reported by the matching
+ *    *_workspace_size query, 256-byte aligned. A workspace may be reused by later calls on the
+ *    same stream but must not be shared by calls that can run concurrently.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream). Calls are
+ *    asynchronous on that stream unless a host out-parameter forces a synchronisation (stated).
+ *  - Every function returns a cstone_status. No C++ exception crosses the ABI. On failure a
+ *    human-readable detail is available from cstone_last_error_detail (per host thread).
+ *  - Keys are 63-bit space-filling-curve keys (L = 21 levels, Sec. 3) stored in uint64_t; the
+ *    end of the key space 8^L = 2^63 terminates cornerstone arrays (Eq. cstone).
+ *  - Particle counts n must satisfy 0 <= n < 2^30.
+ */
+#ifndef CSTONE_H
+#define CSTONE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define CSTONE_API __attribute__((visibility("default")))
+#else
+#define CSTONE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CSTONE_LEVELS 21
+#define CSTONE_MAX_PARTICLES ((int64_t)1 << 30)
+#define CSTONE_MAX_LEAVES ((int64_t)1 << 28)
+
+typedef enum {
+    CSTONE_OK = 0,
+    CSTONE_ERR_INVALID_ARG = 1,   /* bad size, NULL pointer, misaligned or too small workspace */
+    CSTONE_ERR_CUDA = 2,          /* a CUDA runtime call or kernel launch failed */
+    CSTONE_ERR_CAPACITY = 3,      /* an output array is too small; the required size is reported */
+    CSTONE_ERR_TIMEOUT = 4,       /* a bounded device-side wait gave up (results are invalid) */
+    CSTONE_ERR_NOT_CONVERGED = 5  /* the rebalance loop hit max_iters */
+} cstone_status;
+
+typedef enum { CSTONE_MORTON = 0, CSTONE_HILBERT = 1 } cstone_curve;
+
+/* Static description of a status code. Never NULL. */
+CSTONE_API const char* cstone_status_string(int status);
+
+/* Copies the detail message of the last failure on this host thread into buf (NUL-terminated,
+ * truncated to len). Returns CSTONE_OK. */
+CSTONE_API int cstone_last_error_detail(char* buf, size_t len);
+
+/* Library version as major * 10000 + minor * 100 + patch. */
+CSTONE_API int cstone_version(void);
+
+/* Reads the device error word kept in the header of any workspace filled by an asynchronous call
+ * (cstone_sort, cstone_link_tree) and stores the corresponding status in *status (host).
+ * Synchronises `stream`. The word is cleared by the next call that uses the workspace. */
+CSTONE_API int cstone_workspace_status(const void* ws, void* stream, int* status);
+
+/* ------------------------------------------------------------------------------------------
+ * Bounding cube (the paper is silent on the normalisation of coordinates to the key grid of
+ * Sec. 3; this library uses the cube anchored at the per-axis minimum whose side is the largest
+ * per-axis extent, side 1 when that extent is 0 or n == 0).
+ *   x, y, z  [n] float64 particle coordinates (finite).
+ *   box      [4] float64 output: {lo_x, lo_y, lo_z, side}.
+ * ------------------------------------------------------------------------------------------ */
+CSTONE_API int cstone_bbox_workspace_size(int64_t n, size_t* bytes);
+CSTONE_API int cstone_bbox(const double* x, const double* y, const double* z, int64_t n, double* box, void* ws, size_t ws_bytes,
+                void* stream);
+
+/* ------------------------------------------------------------------------------------------
+ * SFC keys (Sec. 3). Each coordinate is mapped to a grid cell of [0, 2^21) per axis by
+ * g = clamp(floor((x - lo) * s), 0, 2^21 - 1) with s = 2^21 / side, the subtraction and the
+ * product each rounded once in IEEE double precision (so results match any IEEE host bit for
+ * bit); points outside the box are clamped to its faces. The cell is then encoded as a Morton key
+ * (octal digit i holds bit 21-i of x, y, z, x most significant) or as a 3D Hilbert key
+ * (J. Skilling's formulation of the Hilbert curve, whose level-i prefix is the level-i octree
+ * node, Sec. 3).
+ *   box   [4] float64 device array {lo_x, lo_y, lo_z, side}, side > 0.
+ *   keys  [n] uint64 output.
+ * NaN coordinates give unspecified keys.
+ * ------------------------------------------------------------------------------------------ */
+CSTONE_API int cstone_keys(const double* x, const double* y, const double* z, int64_t n, const double* box, int curve,
+                uint64_t* keys, void* stream);
+
+/* ------------------------------------------------------------------------------------------
+ * Radix sort_by_key of the particle keys with the identity permutation as values (Sec. 4;
+ * Table 1 caption). Stable: equal keys keep ascending input index. LSD, one sweep per 8-bit
+ * digit with decoupled look-back between tiles.
+ *   keys_in   [n] uint64 input keys (may alias keys_out).
+ *   keys_out  [n] uint64 sorted keys P.
+ *   perm      [n] uint32 output: keys_out[j] = keys_in[perm[j]].
+ * Asynchronous; a look-back timeout is recorded in the workspace header
+ * (cstone_workspace_status).
+ * ------------------------------------------------------------------------------------------ */
+CSTONE_API int cstone_sort_workspace_size(int64_t n, size_t* bytes);
+CSTONE_API int cstone_sort(const uint64_t* keys_in, uint64_t* keys_out, uint32_t* perm, int64_t n, void* ws, size_t ws_bytes,
+                void* stream);
+
+/* ------------------------------------------------------------------------------------------
+ * Cornerstone leaf array (Sec. 4, Eqs. cstone, histogram, g1-g3): starting from the root
+ * {0, 8^L} (when *n_leaves == 0 on entry) or from the caller's array in `leaves` (when
+ * *n_leaves > 0: warm start from a previous step's leaves, Sec. 4), apply the histogram f and
+ * the rebalance g = g3 . g2 . g1 until g1 decides O_i = 1 for every leaf. Rules of g1: split when
+ * N_i > ncrit (unless the leaf is a single key at depth L); merge the 8 consecutive sibling
+ * leaves of a parent when their combined count is <= ncrit (the first octant keeps its key).
+ *   sorted_keys [n] uint64 sorted particle keys P (< 2^63).
+ *   leaves      [leaf_cap + 1] uint64 in/out cornerstone array K.
+ *   n_leaves    host in/out: leaves on entry (0 = root), final n_l on exit; on
+ *               CSTONE_ERR_CAPACITY the number of leaves that did not fit.
+ *   counts      [leaf_cap] uint32 output N_i of the final leaves.
+ *   offsets     [leaf_cap + 1] uint32 output (may be NULL): offsets[i] = first sorted particle of
+ *               leaf i, offsets[n_l] = n.
+ *   max_iters   bound on f/g passes (<= 256); iters (host, may be NULL) receives the number of
+ *               passes, including the last one that changed nothing.
+ * Synchronises `stream` (the host outputs need the converged size).
+ * ------------------------------------------------------------------------------------------ */
+CSTONE_API int cstone_leaves_workspace_size(int64_t n, int64_t leaf_cap, int32_t max_iters, size_t* bytes);
+CSTONE_API int cstone_build_leaves(const uint64_t* sorted_keys, int64_t n, uint32_t ncrit, uint64_t* leaves, int64_t leaf_cap,
+                        int64_t* n_leaves, uint32_t* counts, uint32_t* offsets, int32_t max_iters, int32_t* iters,
+                        void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------------------------
+ * Fully linked octree (Sec. 5): all nodes of the tree whose leaves are K, n = n_l + (n_l-1)/7
+ * of them, in breadth-first order (by level, then by key), each internal node with exactly 8
+ * children.
+ *   leaves        [n_leaves + 1] uint64 cornerstone array K.
+ *   node_keys     [n] uint64 NK: Warren-Salmon placeholder keys, (1 << 3*level) | key prefix.
+ *   child         [n] int32 CO: index of the first of the 8 children, 0 for a leaf.
+ *   level_offsets [23] int32 LO: first node of level l = 0..21; LO[22] = n.
+ *   leaf_to_node  [n_leaves] int32: node index of leaf i.
+ *   parent        [(n-1)/8] int32 (may be NULL): parent of the sibling group g, i.e. of the
+ *                 nodes 1+8g .. 8+8g.
+ * Asynchronous.
+ * ------------------------------------------------------------------------------------------ */
+CSTONE_API int cstone_link_workspace_size(int64_t n_leaves, size_t* bytes);
+CSTONE_API int cstone_link_tree(const uint64_t* leaves, int64_t n_leaves, uint64_t* node_keys, int32_t* child,
+                     int32_t* level_offsets, int32_t* leaf_to_node, int32_t* parent, void* ws, size_t ws_bytes,
+                     void* stream);
+
+/* ------------------------------------------------------------------------------------------
+ * Node-count upsweep (Sec. 5 node properties): a leaf holds its N_i, an internal node the sum of
+ * its 8 children. Inputs are the outputs of cstone_build_leaves and cstone_link_tree.
+ *   node_counts [n] uint32 output.
+ * Asynchronous.
+ * ------------------------------------------------------------------------------------------ */
+CSTONE_API int cstone_upsweep_workspace_size(int64_t n_leaves, size_t* bytes);
+CSTONE_API int cstone_upsweep_counts(const uint32_t* leaf_counts, int64_t n_leaves, const int32_t* leaf_to_node,
+                          const int32_t* parent, uint32_t* node_counts, void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------------------------
+ * Multipole upsweep (Sec. 5 node properties; Sec. 8 "cartesian multipoles with quadrupole
+ * corrections"): per node the mass M, the centre of mass (expansion centre) and the second
+ * moments about it Q_ab = sum m (x - com)_a (x - com)_b, components xx, xy, xz, yy, yz, zz.
+ * Accumulation is in FP32 with two-sum compensation (a sum/compensation pair per moment, carried
+ * up the tree); coordinate differences are rounded to FP32 once from their exact value, and the
+ * centre is stored in FP64. An empty node has M = 0, com = 0, Q = 0. The workspace holds the
+ * coordinates gathered into sorted order (28 bytes per particle) and the per-node sums.
+ *   x, y, z, m   [n] float64 coordinates and float32 masses in input order.
+ *   perm         [n] uint32 sort permutation (cstone_sort).
+ *   offsets      [n_leaves + 1] uint32 leaf particle offsets (cstone_build_leaves).
+ *   mass         [n] float32, com [3 * nn] float64 (SoA: x block, y block, z block),
+ *   quad         [6 * nn] float32 (SoA, component-major), nn = number of nodes.
+ * Asynchronous.
+ * ------------------------------------------------------------------------------------------ */
+CSTONE_API int cstone_multipole_workspace_size(int64_t n, int64_t n_leaves, size_t* bytes);
+CSTONE_API int cstone_upsweep_multipoles(const double* x, const double* y, const double* z, const float* m,
+                              const uint32_t* perm, int64_t n, const uint32_t* offsets, int64_t n_leaves,
+                              const int32_t* leaf_to_node, const int32_t* parent, const int32_t* child,
+                              float* mass, double* com, float* quad, void* ws, size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CSTONE_H */

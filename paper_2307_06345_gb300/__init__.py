@@ -1,0 +1,352 @@
+"""GB300-native Cornerstone octree build (Keller et al., PASC'23, arXiv 2307.06345).
+
+The compute path lives in the CUDA library ``libcstone.so`` (sources in ``csrc/``, C ABI in
+``include/cstone.h``). This module loads it with ctypes and marshals PyTorch CUDA tensors and
+streams into the C calls; the functions named ``cstone_*`` mirror the C entry points one to one.
+PyTorch only provides device memory and streams: every step of the build runs in the library's
+kernels, and nothing falls back to the CPU. If the library has not been built, ``load()`` raises.
+
+``build_octree`` strings the steps together in the paper's order (keys, sort, leaves, linked
+tree, count upsweep, optionally multipoles) and allocates the outputs.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass, field
+
+import torch
+
+from . import _build
+
+__all__ = [
+    "MORTON", "HILBERT", "CstoneError", "load", "build", "cstone_bbox", "cstone_keys", "cstone_sort",
+    "cstone_build_leaves", "cstone_link_tree", "cstone_upsweep_counts", "cstone_upsweep_multipoles",
+    "build_octree", "Workspace", "leaf_capacity", "n_nodes",
+]
+
+MORTON, HILBERT = 0, 1
+LEVELS = 21
+KEY_END = 1 << 63
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_CAPACITY, ERR_TIMEOUT, ERR_NOT_CONVERGED = range(6)
+
+_lib = None
+_lock = threading.Lock()
+
+
+class CstoneError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        super().__init__(f"{where}: {status_string(status)} ({detail})")
+        self.status = status
+
+
+def build(force: bool = False) -> str:
+    """Compile libcstone.so in-tree for sm_103a."""
+    return _build.build(force=force)
+
+
+def load():
+    """Load libcstone.so (raises if it is missing or stale: run ``build()``)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"CUDA library {_build.LIB} is missing: call paper_2307_06345_gb300.build() "
+                               "(the product has no CPU fallback)")
+        lib = ctypes.CDLL(_build.LIB)
+        P, i64, i32, u32, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32, ctypes.c_size_t
+        pi64, pi32, psz = ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_size_t)
+        sigs = {
+            "cstone_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+            "cstone_last_error_detail": (ctypes.c_int, [ctypes.c_char_p, sz]),
+            "cstone_version": (ctypes.c_int, []),
+            "cstone_workspace_status": (ctypes.c_int, [P, P, ctypes.POINTER(ctypes.c_int)]),
+            "cstone_bbox_workspace_size": (ctypes.c_int, [i64, psz]),
+            "cstone_bbox": (ctypes.c_int, [P, P, P, i64, P, P, sz, P]),
+            "cstone_keys": (ctypes.c_int, [P, P, P, i64, P, ctypes.c_int, P, P]),
+            "cstone_sort_workspace_size": (ctypes.c_int, [i64, psz]),
+            "cstone_sort": (ctypes.c_int, [P, P, P, i64, P, sz, P]),
+            "cstone_leaves_workspace_size": (ctypes.c_int, [i64, i64, i32, psz]),
+            "cstone_build_leaves": (ctypes.c_int, [P, i64, u32, P, i64, pi64, P, P, i32, pi32, P, sz, P]),
+            "cstone_link_workspace_size": (ctypes.c_int, [i64, psz]),
+            "cstone_link_tree": (ctypes.c_int, [P, i64, P, P, P, P, P, P, sz, P]),
+            "cstone_upsweep_workspace_size": (ctypes.c_int, [i64, psz]),
+            "cstone_upsweep_counts": (ctypes.c_int, [P, i64, P, P, P, P, sz, P]),
+            "cstone_multipole_workspace_size": (ctypes.c_int, [i64, i64, psz]),
+            "cstone_upsweep_multipoles": (ctypes.c_int, [P, P, P, P, P, i64, P, i64, P, P, P, P, P, P, P, sz, P]),
+        }
+        for name, (res, args) in sigs.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def status_string(status: int) -> str:
+    if _lib is None:
+        return f"status {status}"
+    return _lib.cstone_status_string(status).decode()
+
+
+def _detail() -> str:
+    buf = ctypes.create_string_buffer(512)
+    load().cstone_last_error_detail(buf, 512)
+    return buf.value.decode(errors="replace")
+
+
+def _check(rc: int, where: str):
+    if rc != OK:
+        raise CstoneError(rc, where, _detail())
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _size(fn, *args) -> int:
+    out = ctypes.c_size_t()
+    _check(fn(*args, ctypes.byref(out)), fn.__name__)
+    return int(out.value)
+
+
+class Workspace:
+    """Device scratch for the library calls, grown on demand (256-byte aligned torch buffer)."""
+
+    def __init__(self, device=None):
+        self.device = torch.device(device if device is not None else "cuda")
+        self.buf = None
+
+    def get(self, nbytes: int) -> torch.Tensor:
+        if self.buf is None or self.buf.numel() < nbytes:
+            self.buf = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
+        return self.buf
+
+    def status(self, stream=None) -> int:
+        st = ctypes.c_int()
+        _check(load().cstone_workspace_status(_ptr(self.buf), _stream(stream), ctypes.byref(st)), "workspace_status")
+        return st.value
+
+
+def _need(t: torch.Tensor, dtype, name):
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA tensor of {dtype}")
+
+
+# ------------------------------------------------------------------------- C entry points
+def cstone_bbox(x, y, z, box, ws: Workspace, stream=None):
+    lib = load()
+    n = x.numel()
+    for t, nm in ((x, "x"), (y, "y"), (z, "z")):
+        _need(t, torch.float64, nm)
+    _need(box, torch.float64, "box")
+    need = _size(lib.cstone_bbox_workspace_size, n)
+    buf = ws.get(need)
+    _check(lib.cstone_bbox(_ptr(x), _ptr(y), _ptr(z), n, _ptr(box), _ptr(buf), buf.numel(), _stream(stream)),
+           "cstone_bbox")
+
+
+def cstone_keys(x, y, z, box, curve: int, keys, stream=None):
+    lib = load()
+    for t, nm in ((x, "x"), (y, "y"), (z, "z"), (box, "box")):
+        _need(t, torch.float64, nm)
+    _need(keys, torch.int64, "keys")
+    _check(lib.cstone_keys(_ptr(x), _ptr(y), _ptr(z), x.numel(), _ptr(box), curve, _ptr(keys), _stream(stream)),
+           "cstone_keys")
+
+
+def cstone_sort(keys_in, keys_out, perm, ws: Workspace, stream=None):
+    lib = load()
+    n = keys_in.numel()
+    _need(keys_in, torch.int64, "keys_in")
+    _need(keys_out, torch.int64, "keys_out")
+    _need(perm, torch.int32, "perm")
+    buf = ws.get(_size(lib.cstone_sort_workspace_size, n))
+    _check(lib.cstone_sort(_ptr(keys_in), _ptr(keys_out), _ptr(perm), n, _ptr(buf), buf.numel(), _stream(stream)),
+           "cstone_sort")
+
+
+def cstone_build_leaves(sorted_keys, ncrit: int, leaves, counts, offsets=None, n_leaves: int = 0,
+                        max_iters: int = 64, ws: Workspace | None = None, stream=None):
+    """Returns (n_leaves, iterations). ``leaves`` holds the initial array when n_leaves > 0."""
+    lib = load()
+    n = sorted_keys.numel()
+    cap = counts.numel()
+    _need(sorted_keys, torch.int64, "sorted_keys")
+    _need(leaves, torch.int64, "leaves")
+    _need(counts, torch.int32, "counts")
+    if leaves.numel() < cap + 1:
+        raise ValueError("leaves needs leaf_cap + 1 entries")
+    if offsets is not None:
+        _need(offsets, torch.int32, "offsets")
+    ws = ws or Workspace(sorted_keys.device)
+    buf = ws.get(_size(lib.cstone_leaves_workspace_size, n, cap, max_iters))
+    nl = ctypes.c_int64(n_leaves)
+    it = ctypes.c_int32(0)
+    rc = lib.cstone_build_leaves(_ptr(sorted_keys), n, ncrit, _ptr(leaves), cap, ctypes.byref(nl), _ptr(counts),
+                                 _ptr(offsets), max_iters, ctypes.byref(it), _ptr(buf), buf.numel(), _stream(stream))
+    if rc == ERR_CAPACITY:
+        err = CstoneError(rc, "cstone_build_leaves", _detail())
+        err.required = int(nl.value)
+        raise err
+    _check(rc, "cstone_build_leaves")
+    return int(nl.value), int(it.value)
+
+
+def cstone_link_tree(leaves, n_leaves: int, node_keys, child, level_offsets, leaf_to_node, parent=None,
+                     ws: Workspace | None = None, stream=None):
+    lib = load()
+    ws = ws or Workspace(leaves.device)
+    buf = ws.get(_size(lib.cstone_link_workspace_size, n_leaves))
+    _check(lib.cstone_link_tree(_ptr(leaves), n_leaves, _ptr(node_keys), _ptr(child), _ptr(level_offsets),
+                                _ptr(leaf_to_node), _ptr(parent), _ptr(buf), buf.numel(), _stream(stream)),
+           "cstone_link_tree")
+
+
+def cstone_upsweep_counts(leaf_counts, n_leaves: int, leaf_to_node, parent, node_counts,
+                          ws: Workspace | None = None, stream=None):
+    lib = load()
+    ws = ws or Workspace(leaf_counts.device)
+    buf = ws.get(_size(lib.cstone_upsweep_workspace_size, n_leaves))
+    _check(lib.cstone_upsweep_counts(_ptr(leaf_counts), n_leaves, _ptr(leaf_to_node), _ptr(parent),
+                                     _ptr(node_counts), _ptr(buf), buf.numel(), _stream(stream)),
+           "cstone_upsweep_counts")
+
+
+def cstone_upsweep_multipoles(x, y, z, m, perm, offsets, n_leaves: int, leaf_to_node, parent, child, mass, com,
+                              quad, ws: Workspace | None = None, stream=None):
+    lib = load()
+    _need(m, torch.float32, "m")
+    ws = ws or Workspace(x.device)
+    buf = ws.get(_size(lib.cstone_multipole_workspace_size, x.numel(), n_leaves))
+    _check(lib.cstone_upsweep_multipoles(_ptr(x), _ptr(y), _ptr(z), _ptr(m), _ptr(perm), x.numel(), _ptr(offsets),
+                                         n_leaves, _ptr(leaf_to_node), _ptr(parent), _ptr(child), _ptr(mass),
+                                         _ptr(com), _ptr(quad), _ptr(buf), buf.numel(), _stream(stream)),
+           "cstone_upsweep_multipoles")
+
+
+# ------------------------------------------------------------------------- whole build
+def leaf_capacity(n: int, ncrit: int) -> int:
+    """A first guess for the leaf capacity; build_octree grows it if the tree needs more."""
+    return int(min(1 << 28, 16 * (n // (ncrit + 1)) + 4096))
+
+
+def n_nodes(n_leaves: int) -> int:
+    return n_leaves + (n_leaves - 1) // 7
+
+
+@dataclass
+class OctreeBuffers:
+    """Reusable device buffers for repeated builds of the same size (outputs and scratch)."""
+    device: torch.device
+    n: int
+    cap: int
+    keys: torch.Tensor = None
+    sorted_keys: torch.Tensor = None
+    perm: torch.Tensor = None
+    box: torch.Tensor = None
+    leaves: torch.Tensor = None
+    counts: torch.Tensor = None
+    offsets: torch.Tensor = None
+    ws: Workspace = None
+    tree: dict = field(default_factory=dict)
+
+    @classmethod
+    def allocate(cls, n: int, cap: int, device="cuda"):
+        d = torch.device(device)
+        b = cls(device=d, n=n, cap=cap)
+        b.keys = torch.empty(n, dtype=torch.int64, device=d)
+        b.sorted_keys = torch.empty(n, dtype=torch.int64, device=d)
+        b.perm = torch.empty(n, dtype=torch.int32, device=d)
+        b.box = torch.empty(4, dtype=torch.float64, device=d)
+        b.leaves = torch.empty(cap + 1, dtype=torch.int64, device=d)
+        b.counts = torch.empty(cap, dtype=torch.int32, device=d)
+        b.offsets = torch.empty(cap + 1, dtype=torch.int32, device=d)
+        b.ws = Workspace(d)
+        return b
+
+    def tree_buffers(self, n_leaves: int):
+        nn = n_nodes(n_leaves)
+        t = self.tree
+        if t.get("cap_nodes", 0) < nn:
+            d = self.device
+            cap_nodes = max(nn, int(1.25 * nn))
+            t.clear()
+            t["cap_nodes"] = cap_nodes
+            t["NK"] = torch.empty(cap_nodes, dtype=torch.int64, device=d)
+            t["CO"] = torch.empty(cap_nodes, dtype=torch.int32, device=d)
+            t["LO"] = torch.empty(LEVELS + 2, dtype=torch.int32, device=d)
+            t["leaf_to_node"] = torch.empty(max(self.cap, 1), dtype=torch.int32, device=d)
+            t["parent"] = torch.empty(max(cap_nodes // 8, 1), dtype=torch.int32, device=d)
+            t["counts"] = torch.empty(cap_nodes, dtype=torch.int32, device=d)
+        return t
+
+
+def build_octree(x, y, z, curve: int = HILBERT, ncrit: int = 64, box=None, masses=None, buffers=None,
+                 warm_leaves=None, max_iters: int = 64, stream=None, compute_bbox: bool | None = None):
+    """Full build: keys -> sort -> cornerstone leaves -> linked octree -> node counts
+    (-> multipoles when ``masses`` is given). Coordinates are float64 CUDA tensors.
+
+    ``box`` is a float64 tensor {lo_x, lo_y, lo_z, side} (CUDA); when None the bounding cube is
+    computed on the device. ``warm_leaves`` (int64 CUDA, n_l + 1 keys) warm-starts the leaf loop.
+    Returns a dict of device tensors sized to the built tree plus 'n_leaves' and 'iters'.
+    """
+    n = x.numel()
+    if buffers is None or buffers.n != n:
+        buffers = OctreeBuffers.allocate(n, leaf_capacity(n, ncrit), x.device)
+    b = buffers
+    if box is None:
+        cstone_bbox(x, y, z, b.box, b.ws, stream)
+        box = b.box
+    cstone_keys(x, y, z, box, curve, b.keys, stream)
+    cstone_sort(b.keys, b.sorted_keys, b.perm, b.ws, stream)
+    while True:
+        nl0 = 0
+        if warm_leaves is not None:
+            nl0 = warm_leaves.numel() - 1
+            if nl0 > b.cap:
+                b = _grow(b, nl0)
+            b.leaves[: nl0 + 1].copy_(warm_leaves)
+        try:
+            nl, iters = cstone_build_leaves(b.sorted_keys, ncrit, b.leaves, b.counts, b.offsets, nl0, max_iters,
+                                            b.ws, stream)
+            break
+        except CstoneError as e:
+            if e.status != ERR_CAPACITY:
+                raise
+            b = _grow(b, max(getattr(e, "required", 0), 2 * b.cap))
+    t = b.tree_buffers(nl)
+    nn = n_nodes(nl)
+    cstone_link_tree(b.leaves, nl, t["NK"], t["CO"], t["LO"], t["leaf_to_node"], t["parent"], b.ws, stream)
+    cstone_upsweep_counts(b.counts, nl, t["leaf_to_node"], t["parent"], t["counts"], b.ws, stream)
+    out = {
+        "buffers": b, "box": box, "keys": b.keys, "sorted_keys": b.sorted_keys, "perm": b.perm,
+        "leaves": b.leaves[: nl + 1], "leaf_counts": b.counts[:nl], "leaf_offsets": b.offsets[: nl + 1],
+        "n_leaves": nl, "iters": iters, "NK": t["NK"][:nn], "CO": t["CO"][:nn], "LO": t["LO"],
+        "leaf_to_node": t["leaf_to_node"][:nl], "parent": t["parent"][: (nn - 1) // 8], "node_counts": t["counts"][:nn],
+    }
+    if masses is not None:
+        if "mass" not in t or t["mass"].numel() < nn:
+            cap_nodes = t["cap_nodes"]
+            t["mass"] = torch.empty(cap_nodes, dtype=torch.float32, device=b.device)
+            t["com"] = torch.empty(3 * cap_nodes, dtype=torch.float64, device=b.device)
+            t["quad"] = torch.empty(6 * cap_nodes, dtype=torch.float32, device=b.device)
+        mass, com, quad = t["mass"][:nn], t["com"][: 3 * nn], t["quad"][: 6 * nn]
+        cstone_upsweep_multipoles(x, y, z, masses, b.perm, b.offsets, nl, t["leaf_to_node"], t["parent"], t["CO"],
+                                  mass, com, quad, b.ws, stream)
+        out.update({"mass": mass, "com": com.view(3, nn), "quad": quad.view(6, nn)})
+    return out
+
+
+def _grow(b: OctreeBuffers, want: int) -> OctreeBuffers:
+    cap = int(min(1 << 28, max(want, 2 * b.cap)))
+    nb = OctreeBuffers.allocate(b.n, cap, b.device)
+    nb.keys, nb.sorted_keys, nb.perm, nb.box, nb.ws = b.keys, b.sorted_keys, b.perm, b.box, b.ws
+    return nb

@@ -1,0 +1,79 @@
+// Internal helpers of the cstone library: status handling, workspace carving, bounded waits.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "cstone.h"
+
+namespace cst {
+
+using u64 = unsigned long long;
+using u32 = unsigned int;
+
+constexpr int kLevels = CSTONE_LEVELS;  // L
+constexpr u64 kKeyEnd = 1ULL << 63;     // 8^L
+
+// ---------------------------------------------------------------- host-side status plumbing
+int fail(int status, const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+int sm_count();
+
+#define CST_CUDA(call)                                          \
+    do {                                                        \
+        cudaError_t cst_e_ = (call);                            \
+        if (cst_e_ != cudaSuccess) return cst::cuda_fail(cst_e_, #call); \
+    } while (0)
+
+#define CST_LAUNCHED(name) CST_CUDA(cudaGetLastError())
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Every workspace starts with this header; err is the device error word of the call.
+struct WsHeader {
+    u32 err;        // 0 = ok, else a cstone_status (TIMEOUT, CAPACITY, ...)
+    u32 err_info;   // free-form detail (e.g. where a wait gave up)
+    u32 pad[62];
+};
+static_assert(sizeof(WsHeader) == 256, "header is one 256-byte slot");
+
+// Sequential carving of a workspace into 256-byte aligned arrays. With base == nullptr it only
+// measures, so the same code serves the size query and the call.
+struct Carver {
+    char* base;
+    size_t off;
+    explicit Carver(void* b) : base(static_cast<char*>(b)), off(sizeof(WsHeader)) {}
+    template <class T>
+    T* take(size_t count) {
+        size_t bytes = ((count * sizeof(T) + 255) / 256) * 256;
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += bytes;
+        return p;
+    }
+    size_t size() const { return off; }
+};
+
+inline bool aligned256(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 255u) == 0; }
+
+int check_ws(void* ws, size_t have, size_t need, const char* who);
+
+// ---------------------------------------------------------------- device helpers
+constexpr long long kSpinLimit = 1ll << 24;  // polls before a wait is declared timed out
+
+__device__ __forceinline__ u32 ld_volatile(const u32* p) { return *reinterpret_cast<const volatile u32*>(p); }
+__device__ __forceinline__ void st_volatile(u32* p, u32 v) { *reinterpret_cast<volatile u32*>(p) = v; }
+
+__device__ __forceinline__ u32 lanemask_lt() {
+    u32 m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Records the first error of a call (later ones keep the first).
+__device__ __forceinline__ void raise_error(WsHeader* h, u32 status, u32 info) {
+    if (atomicCAS(&h->err, 0u, status) == 0u) h->err_info = info;
+}
+
+}  // namespace cst

@@ -1,0 +1,416 @@
+// Bounding cube and space-filling-curve keys (Sec. 3).
+//
+// Keys are streaming work: 24 bytes of coordinates in, 8 bytes of key out per particle. The
+// kernel reads the three coordinate arrays with 16-byte vector loads (two particles per thread
+// per step), computes the grid cell in IEEE double precision with explicitly rounded operations
+// (no FMA contraction, so the cell matches any IEEE host bit for bit) and encodes it.
+//
+// Hilbert encoding uses a finite-state machine equivalent to J. Skilling's transpose formulation
+// of the Hilbert curve: walking the bit levels from the top, Skilling's per-level inversions and
+// exchanges act on all lower bits as a signed permutation of the axes, and the final Gray-code
+// flip of a level is the parity of the Gray-coded third axis above it. Tracking (permutation,
+// flips, parity) as a state gives 48 reachable states. The host builds a two-level table
+// (state, 6 input bits) -> (6 output bits, next state) once and passes it to the kernel as a
+// by-value parameter, so no device memory or symbol upload is involved.
+#include <mutex>
+
+#include "common.cuh"
+
+namespace cst {
+
+// ---------------------------------------------------------------------------------- bounding cube
+namespace {
+
+__device__ __forceinline__ u64 ordered_bits(double v) {
+    u64 b = static_cast<u64>(__double_as_longlong(v));
+    return (b >> 63) ? ~b : (b | (1ULL << 63));
+}
+
+__device__ __forceinline__ double from_ordered(u64 o) {
+    u64 b = (o >> 63) ? (o & ~(1ULL << 63)) : ~o;
+    return __longlong_as_double(static_cast<long long>(b));
+}
+
+struct BoxAcc {
+    u64 lo[3];  // ordered bits of the per-axis minimum
+    u64 hi[3];  // ordered bits of the per-axis maximum
+};
+
+__global__ void bbox_init_kernel(BoxAcc* acc) {
+    int t = threadIdx.x;
+    if (t < 3) {
+        acc->lo[t] = ~0ULL;
+        acc->hi[t] = 0ULL;
+    }
+}
+
+__global__ void __launch_bounds__(256) bbox_reduce_kernel(const double* __restrict__ x, const double* __restrict__ y,
+                                                          const double* __restrict__ z, long long n, BoxAcc* acc) {
+    u64 lo[3] = {~0ULL, ~0ULL, ~0ULL}, hi[3] = {0ULL, 0ULL, 0ULL};
+    const double* c[3] = {x, y, z};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            u64 o = ordered_bits(__ldg(c[d] + i));
+            lo[d] = o < lo[d] ? o : lo[d];
+            hi[d] = o > hi[d] ? o : hi[d];
+        }
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        for (int s = 16; s > 0; s >>= 1) {
+            u64 a = __shfl_xor_sync(0xffffffffu, lo[d], s);
+            u64 b = __shfl_xor_sync(0xffffffffu, hi[d], s);
+            lo[d] = a < lo[d] ? a : lo[d];
+            hi[d] = b > hi[d] ? b : hi[d];
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            atomicMin(&acc->lo[d], lo[d]);
+            atomicMax(&acc->hi[d], hi[d]);
+        }
+    }
+}
+
+__global__ void bbox_finalize_kernel(const BoxAcc* acc, long long n, double* box) {
+    if (threadIdx.x != 0) return;
+    if (n == 0) {
+        box[0] = box[1] = box[2] = 0.0;
+        box[3] = 1.0;
+        return;
+    }
+    double side = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        double lo = from_ordered(acc->lo[d]);
+        double hi = from_ordered(acc->hi[d]);
+        box[d] = lo;
+        double ext = __dsub_rn(hi, lo);
+        side = ext > side ? ext : side;
+    }
+    box[3] = side > 0.0 ? side : 1.0;
+}
+
+// ---------------------------------------------------------------------------------- grid + keys
+constexpr int kHilbertStates = 48;
+
+struct HilbertTable {
+    unsigned short two[kHilbertStates * 64];  // (state, 2 octants) -> 6 digit bits | next << 6
+    unsigned short one[kHilbertStates * 8];   // (state, 1 octant)  -> 3 digit bits | next << 3
+};
+
+// Cell index of one coordinate: floor((x - lo) * scale) clamped to [0, 2^21 - 1], with the
+// subtraction and the product rounded once each (explicit round-to-nearest intrinsics keep the
+// compiler from fusing them into an FMA).
+__device__ __forceinline__ u32 grid_cell(double x, double lo, double scale) {
+    double u = __dmul_rn(__dsub_rn(x, lo), scale);
+    if (!(u > 0.0)) return 0u;
+    if (u >= 2097152.0) return 2097151u;
+    return __double2uint_rz(u);
+}
+
+// Integer evaluation of grid_cell. Double-precision throughput is a small fraction of the integer
+// throughput on this GPU, so the cell is first computed in 64-bit fixed point:
+//   X = trunc(x * 2^F), LO = trunc(lo * 2^F), u * 2^R ~= ((X - LO) * S) >> 64, S = scale * 2^G,
+// with F chosen so |X| < 2^61 on [lo, lo + 2 side) and S holding scale's 53-bit mantissa at the
+// top of 64 bits. The truncations, the product and the two IEEE roundings of the reference
+// together move u by far less than 2^-24 cells, so whenever the fixed-point u is at least 2^-20
+// away from an integer its floor is the floor of the IEEE result. The remaining ~2^-19 of
+// coordinates, and boxes where the error bound does not hold, take the IEEE path.
+struct FixedGrid {
+    long long lo_fixed;   // LO
+    u64 scale_fixed;      // S
+    u64 lo_ord, hi_ord;   // order-preserving bits of lo and of lo + 2 side
+    double lo, scale;
+    int F, R;
+    int fast;
+};
+
+__device__ __forceinline__ u64 order_bits(double v) {
+    u64 b = static_cast<u64>(__double_as_longlong(v));
+    return (b >> 63) ? ~b : (b | (1ULL << 63));
+}
+
+__device__ __forceinline__ int exponent_of(double v) {  // unbiased exponent field (0 for zero/subnormal)
+    return static_cast<int>((static_cast<u64>(__double_as_longlong(v)) >> 52) & 0x7ffu);
+}
+
+// trunc(x * 2^F) for |x| * 2^F < 2^62
+__device__ __forceinline__ long long to_fixed(double x, int F) {
+    u64 b = static_cast<u64>(__double_as_longlong(x));
+    int e = static_cast<int>((b >> 52) & 0x7ffu);
+    u64 mant = b & ((1ULL << 52) - 1);
+    if (e != 0) mant |= (1ULL << 52);
+    int sh = (e == 0 ? 1 : e) - 1075 + F;
+    u64 mag = sh >= 0 ? (mant << sh) : (sh > -64 ? (mant >> (-sh)) : 0ULL);
+    return (b >> 63) ? -static_cast<long long>(mag) : static_cast<long long>(mag);
+}
+
+__device__ FixedGrid make_fixed_grid(double lo, double side) {
+    FixedGrid f;
+    f.lo = lo;
+    f.scale = __ddiv_rn(2097152.0, side);
+    const double hi = __dadd_rn(lo, __dmul_rn(2.0, side));
+    f.lo_ord = order_bits(lo);
+    f.hi_ord = order_bits(hi);
+    // 2^E > max(|lo|, |hi|)
+    const int e_max = max(exponent_of(lo), exponent_of(hi)) - 1023 + 1;
+    f.F = 61 - e_max;
+    const int es = exponent_of(f.scale) - 1023 - 52;  // scale = mantissa * 2^es
+    const int G = 11 - es;
+    f.R = f.F + G - 64;
+    u64 sb = static_cast<u64>(__double_as_longlong(f.scale));
+    f.scale_fixed = ((sb & ((1ULL << 52) - 1)) | (1ULL << 52)) << 11;
+    f.fast = (f.R >= 26 && f.R <= 62 && es + 78 <= f.F && f.F <= 1074 && exponent_of(f.scale) != 0 &&
+              exponent_of(f.scale) != 0x7ff && !(hi <= lo));
+    f.lo_fixed = f.fast ? to_fixed(lo, f.F) : 0;
+    return f;
+}
+
+__device__ __forceinline__ u32 grid_cell_fixed(double x, const FixedGrid& f) {
+    const u64 o = order_bits(x);
+    if (o <= f.lo_ord) return 0u;
+    if (o >= f.hi_ord) return 2097151u;
+    const u64 d = static_cast<u64>(to_fixed(x, f.F) - f.lo_fixed);
+    const u64 u = __umul64hi(d, f.scale_fixed);
+    const u32 frac20 = static_cast<u32>(u >> (f.R - 20)) & 0xfffffu;
+    if (frac20 == 0u || frac20 == 0xfffffu) return grid_cell(x, f.lo, f.scale);
+    const u64 g = u >> f.R;
+    return g > 2097151ULL ? 2097151u : static_cast<u32>(g);
+}
+
+// Spread the 21 bits of v to every third bit position (bit b -> bit 3b).
+__device__ __forceinline__ u64 spread3(u32 v) {
+    u64 x = v & 0x1fffffu;
+    x = (x | (x << 32)) & 0x001f00000000ffffULL;
+    x = (x | (x << 16)) & 0x001f0000ff0000ffULL;
+    x = (x | (x << 8)) & 0x100f00f00f00f00fULL;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ULL;
+    x = (x | (x << 2)) & 0x1249249249249249ULL;
+    return x;
+}
+
+__device__ __forceinline__ u64 morton_of(u32 gx, u32 gy, u32 gz) {
+    return (spread3(gx) << 2) | (spread3(gy) << 1) | spread3(gz);
+}
+
+// Hilbert key from the Morton interleave: the top level through the one-level table, then the
+// remaining 20 levels two at a time.
+__device__ __forceinline__ u64 hilbert_of(u64 m, const unsigned short* t1, const unsigned short* t2) {
+    u32 e = t1[(m >> 60) & 7u];  // initial state 0
+    u64 key = e & 7u;
+    u32 state = e >> 3;
+#pragma unroll
+    for (int sh = 54; sh >= 0; sh -= 6) {
+        u32 e2 = t2[state * 64u + static_cast<u32>((m >> sh) & 63u)];
+        key = (key << 6) | (e2 & 63u);
+        state = e2 >> 6;
+    }
+    return key;
+}
+
+template <int CURVE, bool VEC>
+__global__ void __launch_bounds__(256) keys_kernel(const double* __restrict__ x, const double* __restrict__ y,
+                                                   const double* __restrict__ z, long long n,
+                                                   const double* __restrict__ box, u64* __restrict__ keys,
+                                                   const __grid_constant__ HilbertTable table) {
+    __shared__ unsigned short s_t2[kHilbertStates * 64];
+    __shared__ unsigned short s_t1[kHilbertStates * 8];
+    __shared__ FixedGrid s_grid[3];
+    if (CURVE == CSTONE_HILBERT) {
+        for (int i = threadIdx.x; i < kHilbertStates * 64; i += blockDim.x) s_t2[i] = table.two[i];
+        for (int i = threadIdx.x; i < kHilbertStates * 8; i += blockDim.x) s_t1[i] = table.one[i];
+    }
+    if (threadIdx.x < 3) s_grid[threadIdx.x] = make_fixed_grid(box[threadIdx.x], box[3]);
+    __syncthreads();
+    const FixedGrid gx = s_grid[0], gy = s_grid[1], gz = s_grid[2];
+    const bool fast = gx.fast && gy.fast && gz.fast;
+
+    auto encode = [&](double px, double py, double pz) -> u64 {
+        u64 m;
+        if (fast)
+            m = morton_of(grid_cell_fixed(px, gx), grid_cell_fixed(py, gy), grid_cell_fixed(pz, gz));
+        else
+            m = morton_of(grid_cell(px, gx.lo, gx.scale), grid_cell(py, gy.lo, gy.scale),
+                          grid_cell(pz, gz.lo, gz.scale));
+        if (CURVE == CSTONE_HILBERT) return hilbert_of(m, s_t1, s_t2);
+        return m;
+    };
+
+    if (!VEC) {
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+            keys[i] = encode(__ldcs(x + i), __ldcs(y + i), __ldcs(z + i));
+        return;
+    }
+    const long long pairs = n >> 1;
+    const double2* x2 = reinterpret_cast<const double2*>(x);
+    const double2* y2 = reinterpret_cast<const double2*>(y);
+    const double2* z2 = reinterpret_cast<const double2*>(z);
+    ulonglong2* k2 = reinterpret_cast<ulonglong2*>(keys);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < pairs; i += (long long)gridDim.x * blockDim.x) {
+        double2 a = __ldcs(x2 + i), b = __ldcs(y2 + i), c = __ldcs(z2 + i);
+        ulonglong2 out;
+        out.x = encode(a.x, b.x, c.x);
+        out.y = encode(a.y, b.y, c.y);
+        __stcs(k2 + i, out);
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+        long long i = n - 1;
+        keys[i] = encode(x[i], y[i], z[i]);
+    }
+}
+
+// ------------------------------------------------------------------ host: Hilbert state machine
+// State of Skilling's walk seen from one bit level: perm[i] = input axis currently feeding
+// transposed axis i, flip[i] = inversion of that axis, gray = parity of the Gray-coded third
+// axis over the levels above (the final per-level flip of Skilling's algorithm).
+struct WalkState {
+    int perm[3];
+    int flip[3];
+    int gray;
+    bool operator==(const WalkState& o) const {
+        for (int i = 0; i < 3; ++i)
+            if (perm[i] != o.perm[i] || flip[i] != o.flip[i]) return false;
+        return gray == o.gray;
+    }
+};
+
+// One bit level: input octant bits (x high) -> output digit, state updated for the next level.
+int walk_level(WalkState& s, int octant) {
+    int in[3] = {(octant >> 2) & 1, (octant >> 1) & 1, octant & 1};
+    int e[3];
+    for (int i = 0; i < 3; ++i) e[i] = in[s.perm[i]] ^ s.flip[i];
+    for (int i = 0; i < 3; ++i) {
+        if (e[i]) {
+            s.flip[0] ^= 1;  // inversion of the first axis' lower bits
+        } else {             // exchange of the lower bits of the first axis and axis i
+            int tp = s.perm[0], tf = s.flip[0];
+            s.perm[0] = s.perm[i];
+            s.flip[0] = s.flip[i];
+            s.perm[i] = tp;
+            s.flip[i] = tf;
+        }
+    }
+    int g0 = e[0], g1 = e[1] ^ e[0], g2 = e[2] ^ g1;
+    int digit = ((g0 ^ s.gray) << 2) | ((g1 ^ s.gray) << 1) | (g2 ^ s.gray);
+    s.gray ^= g2;
+    return digit;
+}
+
+const HilbertTable& hilbert_table() {
+    static HilbertTable table;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        WalkState states[kHilbertStates];
+        int count = 1;
+        states[0] = WalkState{{0, 1, 2}, {0, 0, 0}, 0};
+        int next1[kHilbertStates][8], digit1[kHilbertStates][8];
+        for (int s = 0; s < count; ++s) {
+            for (int o = 0; o < 8; ++o) {
+                WalkState w = states[s];
+                digit1[s][o] = walk_level(w, o);
+                int id = -1;
+                for (int k = 0; k < count; ++k)
+                    if (states[k] == w) id = k;
+                if (id < 0) {
+                    id = count;
+                    if (count < kHilbertStates) states[count++] = w;
+                }
+                next1[s][o] = id;
+            }
+        }
+        for (int s = 0; s < kHilbertStates; ++s) {
+            for (int o = 0; o < 8; ++o)
+                table.one[s * 8 + o] = static_cast<unsigned short>(digit1[s][o] | (next1[s][o] << 3));
+            for (int hi = 0; hi < 8; ++hi)
+                for (int lo = 0; lo < 8; ++lo) {
+                    int mid = next1[s][hi];
+                    int digits = (digit1[s][hi] << 3) | digit1[mid][lo];
+                    table.two[s * 64 + hi * 8 + lo] = static_cast<unsigned short>(digits | (next1[mid][lo] << 6));
+                }
+        }
+    });
+    return table;
+}
+
+}  // namespace
+
+int launch_keys(const double* x, const double* y, const double* z, long long n, const double* box, int curve,
+                u64* keys, cudaStream_t st) {
+    if (n == 0) return CSTONE_OK;
+    const HilbertTable& tab = hilbert_table();
+    long long pairs = (n + 1) / 2;
+    long long want = (pairs + 255) / 256;
+    int grid = static_cast<int>(want < (long long)sm_count() * 8 ? (want > 0 ? want : 1) : (long long)sm_count() * 8);
+    bool vec = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y) | reinterpret_cast<uintptr_t>(z) |
+                 reinterpret_cast<uintptr_t>(keys)) & 15u) == 0;
+    if (curve == CSTONE_HILBERT) {
+        if (vec)
+            keys_kernel<CSTONE_HILBERT, true><<<grid, 256, 0, st>>>(x, y, z, n, box, keys, tab);
+        else
+            keys_kernel<CSTONE_HILBERT, false><<<grid, 256, 0, st>>>(x, y, z, n, box, keys, tab);
+    } else {
+        if (vec)
+            keys_kernel<CSTONE_MORTON, true><<<grid, 256, 0, st>>>(x, y, z, n, box, keys, tab);
+        else
+            keys_kernel<CSTONE_MORTON, false><<<grid, 256, 0, st>>>(x, y, z, n, box, keys, tab);
+    }
+    CST_LAUNCHED("keys_kernel");
+    return CSTONE_OK;
+}
+
+int launch_bbox(const double* x, const double* y, const double* z, long long n, double* box, void* ws,
+                cudaStream_t st) {
+    Carver c(ws);
+    BoxAcc* acc = c.take<BoxAcc>(1);
+    bbox_init_kernel<<<1, 32, 0, st>>>(acc);
+    CST_LAUNCHED("bbox_init_kernel");
+    if (n > 0) {
+        long long want = (n + 255) / 256;
+        int grid = static_cast<int>(want < (long long)sm_count() * 4 ? want : (long long)sm_count() * 4);
+        bbox_reduce_kernel<<<grid, 256, 0, st>>>(x, y, z, n, acc);
+        CST_LAUNCHED("bbox_reduce_kernel");
+    }
+    bbox_finalize_kernel<<<1, 32, 0, st>>>(acc, n, box);
+    CST_LAUNCHED("bbox_finalize_kernel");
+    return CSTONE_OK;
+}
+
+size_t bbox_ws_bytes() {
+    Carver c(nullptr);
+    c.take<BoxAcc>(1);
+    return c.size();
+}
+
+}  // namespace cst
+
+extern "C" {
+
+int cstone_bbox_workspace_size(int64_t n, size_t* bytes) {
+    if (!bytes || n < 0) return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_bbox_workspace_size: bad argument");
+    *bytes = cst::bbox_ws_bytes();
+    return CSTONE_OK;
+}
+
+int cstone_bbox(const double* x, const double* y, const double* z, int64_t n, double* box, void* ws, size_t ws_bytes,
+                void* stream) {
+    if (n < 0 || n >= CSTONE_MAX_PARTICLES || !box || (n > 0 && (!x || !y || !z)))
+        return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_bbox: bad argument (n=%lld)", (long long)n);
+    if (int rc = cst::check_ws(ws, ws_bytes, cst::bbox_ws_bytes(), "cstone_bbox")) return rc;
+    return cst::launch_bbox(x, y, z, n, box, ws, cst::as_stream(stream));
+}
+
+int cstone_keys(const double* x, const double* y, const double* z, int64_t n, const double* box, int curve,
+                uint64_t* keys, void* stream) {
+    if (n < 0 || n >= CSTONE_MAX_PARTICLES || !box || (n > 0 && (!x || !y || !z || !keys)))
+        return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_keys: bad argument (n=%lld)", (long long)n);
+    if (curve != CSTONE_MORTON && curve != CSTONE_HILBERT)
+        return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_keys: unknown curve %d", curve);
+    if (((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y) | reinterpret_cast<uintptr_t>(z) |
+          reinterpret_cast<uintptr_t>(keys)) & 7u) != 0)
+        return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_keys: arrays must be 8-byte aligned");
+    return cst::launch_keys(x, y, z, n, box, curve, reinterpret_cast<cst::u64*>(keys), cst::as_stream(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,268 @@
+// Fully linked octree from the cornerstone array (Sec. 5, steps 1-5), breadth-first.
+//
+// Node keys: every leaf i gives a node at level L - log8(K_{i+1} - K_i); every adjacent pair
+// (K_i, K_{i+1}) whose first differing bit is the leading bit of an octal digit (d % 3 == 0 with
+// d the number of equal leading bits of the 63-bit keys, step 2) gives the internal node at level
+// d / 3 that is the lowest common ancestor of the two leaves: the pair straddles the boundary
+// between its child 3 and child 4, so each internal node appears exactly once.
+//
+// Breadth-first order (step 3): taken in array order, leaf i followed by pair i is an in-order
+// walk of the tree, so the nodes of any one level already appear in key order. A stable
+// partition of that sequence by level therefore gives the breadth-first layout without sorting
+// 64-bit keys, and the offsets of the partition are the level offsets LO (step 4). This replaces
+// the paper's digit-weight slot mapping of step 2 followed by a radix sort of NK: the final NK
+// is the same. The partition is a counting sort with 22 buckets: per-tile level counts, one scan
+// over (level, tile), and a scatter that ranks items stably inside each tile.
+//
+// Step 5: the first child of an internal node is found by binary search for its key << 3 within
+// the next level's range of NK; the same pass fills the parent of every sibling group.
+#include "common.cuh"
+
+namespace cst {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kItems = 8;
+constexpr int kTile = kThreads * kItems;
+constexpr int kNumLevels = kLevels + 1;  // 0..21
+
+__device__ __forceinline__ int leaf_level(u64 delta) {  // delta is a power of 8
+    return kLevels - (__ffsll(static_cast<long long>(delta)) - 1) / 3;
+}
+
+// Level of the internal node implied by the pair (i, i+1), or -1 when d % 3 != 0.
+__device__ __forceinline__ int pair_level(u64 a, u64 b) {
+    int d = __clzll(static_cast<long long>(a ^ b)) - 1;  // equal leading bits of the 63-bit keys
+    return (d >= 0 && d % 3 == 0) ? d / 3 : -1;
+}
+
+__device__ __forceinline__ u64 placeholder(u64 key, int level) {
+    return (1ULL << (3 * level)) | (key >> (3 * (kLevels - level)));
+}
+
+__global__ void __launch_bounds__(kThreads) link_count_kernel(const u64* __restrict__ K, u32 nl, u32 ntiles,
+                                                              u32* __restrict__ counts) {
+    __shared__ u32 s_cnt[kNumLevels];
+    if (threadIdx.x < kNumLevels) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const u32 tile = blockIdx.x;
+    const u32 i0 = tile * kTile + threadIdx.x * kItems;
+    u32 local[kNumLevels];
+#pragma unroll
+    for (int l = 0; l < kNumLevels; ++l) local[l] = 0;
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+        u32 i = i0 + k;
+        if (i >= nl) break;
+        u64 a = K[i], b = K[i + 1];
+        int ll = leaf_level(b - a);
+#pragma unroll
+        for (int l = 0; l < kNumLevels; ++l) local[l] += (l == ll);
+        if (i + 1 < nl) {
+            int pl = pair_level(a, b);
+#pragma unroll
+            for (int l = 0; l < kNumLevels; ++l) local[l] += (l == pl);
+        }
+    }
+#pragma unroll
+    for (int l = 0; l < kNumLevels; ++l) {
+        u32 v = local[l];
+        for (int s = 16; s > 0; s >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(&s_cnt[l], v);
+    }
+    __syncthreads();
+    if (threadIdx.x < kNumLevels) counts[(size_t)threadIdx.x * ntiles + tile] = s_cnt[threadIdx.x];
+}
+
+// Exclusive scan of the level-major (level, tile) counts in one block; LO[l] = offset of (l, 0),
+// LO[22] = total. A total different from n_expected means the input was not a cornerstone array.
+__global__ void __launch_bounds__(1024) link_scan_kernel(u32* __restrict__ counts, u32 ntiles, int* __restrict__ LO,
+                                                         u32 n_expected, WsHeader* hdr) {
+    __shared__ u32 s_part[1024];
+    const u32 total_len = ntiles * kNumLevels;
+    const u32 per = (total_len + 1023) / 1024;
+    const u32 begin = threadIdx.x * per;
+    const u32 end = min(begin + per, total_len);
+    u32 sum = 0;
+    for (u32 i = begin; i < end; ++i) sum += counts[i];
+    s_part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int s = 1; s < 1024; s <<= 1) {
+        u32 v = threadIdx.x >= (unsigned)s ? s_part[threadIdx.x - s] : 0u;
+        __syncthreads();
+        s_part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    u32 run = s_part[threadIdx.x] - sum;
+    for (u32 i = begin; i < end; ++i) {
+        u32 c = counts[i];
+        counts[i] = run;
+        if (i % ntiles == 0) LO[i / ntiles] = static_cast<int>(run);
+        run += c;
+    }
+    if (threadIdx.x == 1023) {
+        u32 total = s_part[1023];
+        LO[kNumLevels] = static_cast<int>(total);
+        if (total != n_expected) raise_error(hdr, CSTONE_ERR_INVALID_ARG, total);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) link_scatter_kernel(const u64* __restrict__ K, u32 nl, u32 ntiles,
+                                                                const u32* __restrict__ offsets, u32 n_nodes,
+                                                                u64* __restrict__ NK, int* __restrict__ leaf_to_node) {
+    __shared__ u32 s_rank[kNumLevels][kThreads];  // per-thread counts, then per-thread slots
+    const int tid = threadIdx.x;
+    const u32 tile = blockIdx.x;
+    const u32 i0 = tile * kTile + tid * kItems;
+#pragma unroll
+    for (int l = 0; l < kNumLevels; ++l) s_rank[l][tid] = 0;
+    // count this thread's items per level (own column, no conflicts)
+    for (int k = 0; k < kItems; ++k) {
+        u32 i = i0 + k;
+        if (i >= nl) break;
+        u64 a = K[i], b = K[i + 1];
+        s_rank[leaf_level(b - a)][tid] += 1;
+        if (i + 1 < nl) {
+            int pl = pair_level(a, b);
+            if (pl >= 0) s_rank[pl][tid] += 1;
+        }
+    }
+    __syncthreads();
+    // exclusive scan of every level row across the threads, plus the tile's global offset
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int l = warp; l < kNumLevels; l += kThreads / 32) {
+        u32 v[kThreads / 32];
+        u32 sum = 0;
+#pragma unroll
+        for (int q = 0; q < kThreads / 32; ++q) {
+            v[q] = s_rank[l][lane * (kThreads / 32) + q];
+            sum += v[q];
+        }
+        u32 incl = sum;
+        for (int s = 1; s < 32; s <<= 1) {
+            u32 t = __shfl_up_sync(0xffffffffu, incl, s);
+            if (lane >= s) incl += t;
+        }
+        u32 run = offsets[(size_t)l * ntiles + tile] + incl - sum;
+#pragma unroll
+        for (int q = 0; q < kThreads / 32; ++q) {
+            s_rank[l][lane * (kThreads / 32) + q] = run;
+            run += v[q];
+        }
+    }
+    __syncthreads();
+    // emit in in-order sequence: leaf i, then the internal node of pair i
+    for (int k = 0; k < kItems; ++k) {
+        u32 i = i0 + k;
+        if (i >= nl) break;
+        u64 a = K[i], b = K[i + 1];
+        int ll = leaf_level(b - a);
+        u32 x = s_rank[ll][tid]++;
+        if (x < n_nodes) {
+            NK[x] = placeholder(a, ll);
+            leaf_to_node[i] = static_cast<int>(x);
+        }
+        if (i + 1 < nl) {
+            int pl = pair_level(a, b);
+            if (pl >= 0) {
+                u32 y = s_rank[pl][tid]++;
+                if (y < n_nodes) NK[y] = placeholder(a, pl);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) link_child_kernel(const u64* __restrict__ NK, u32 n_nodes,
+                                                              const int* __restrict__ LO, int* __restrict__ CO,
+                                                              int* __restrict__ parent) {
+    __shared__ int s_lo[kNumLevels + 1];
+    if (threadIdx.x <= kNumLevels) s_lo[threadIdx.x] = LO[threadIdx.x];
+    __syncthreads();
+    for (u32 x = blockIdx.x * kThreads + threadIdx.x; x < n_nodes; x += gridDim.x * kThreads) {
+        u64 k = NK[x];
+        int level = (63 - __clzll(static_cast<long long>(k))) / 3;
+        int c = 0;
+        if (level < kLevels) {
+            u64 want = k << 3;
+            u32 lo = min(static_cast<u32>(s_lo[level + 1]), n_nodes);
+            u32 hi = min(static_cast<u32>(s_lo[level + 2]), n_nodes);
+            const u32 end = hi;
+            while (lo < hi) {
+                u32 mid = lo + ((hi - lo) >> 1);
+                if (NK[mid] < want)
+                    lo = mid + 1;
+                else
+                    hi = mid;
+            }
+            if (lo < end && NK[lo] == want) c = static_cast<int>(lo);
+        }
+        CO[x] = c;
+        if (c > 0 && parent) parent[(c - 1) >> 3] = static_cast<int>(x);
+    }
+}
+
+struct LinkLayout {
+    u32* counts;
+    u32 ntiles;
+    size_t bytes;
+};
+
+LinkLayout link_layout(void* ws, long long nl) {
+    LinkLayout l;
+    Carver c(ws);
+    l.ntiles = static_cast<u32>((nl + kTile - 1) / kTile);
+    if (l.ntiles == 0) l.ntiles = 1;
+    l.counts = c.take<u32>((size_t)l.ntiles * kNumLevels);
+    l.bytes = c.size();
+    return l;
+}
+
+}  // namespace
+
+size_t link_ws_bytes(long long nl) { return link_layout(nullptr, nl).bytes; }
+
+int launch_link(const u64* K, long long nl, u64* NK, int* CO, int* LO, int* leaf_to_node, int* parent, void* ws,
+                cudaStream_t st) {
+    LinkLayout l = link_layout(ws, nl);
+    WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
+    CST_CUDA(cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st));
+    const u32 n_nodes = static_cast<u32>(nl + (nl - 1) / 7);
+    link_count_kernel<<<l.ntiles, kThreads, 0, st>>>(K, static_cast<u32>(nl), l.ntiles, l.counts);
+    CST_LAUNCHED("link_count_kernel");
+    link_scan_kernel<<<1, 1024, 0, st>>>(l.counts, l.ntiles, LO, n_nodes, hdr);
+    CST_LAUNCHED("link_scan_kernel");
+    link_scatter_kernel<<<l.ntiles, kThreads, 0, st>>>(K, static_cast<u32>(nl), l.ntiles, l.counts, n_nodes, NK,
+                                                       leaf_to_node);
+    CST_LAUNCHED("link_scatter_kernel");
+    long long want = (n_nodes + kThreads - 1) / kThreads;
+    int grid = static_cast<int>(want < (long long)sm_count() * 8 ? want : (long long)sm_count() * 8);
+    link_child_kernel<<<grid, kThreads, 0, st>>>(NK, n_nodes, LO, CO, parent);
+    CST_LAUNCHED("link_child_kernel");
+    return CSTONE_OK;
+}
+
+}  // namespace cst
+
+extern "C" {
+
+int cstone_link_workspace_size(int64_t n_leaves, size_t* bytes) {
+    if (!bytes || n_leaves < 1 || n_leaves > CSTONE_MAX_LEAVES)
+        return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_link_workspace_size: bad argument");
+    *bytes = cst::link_ws_bytes(n_leaves);
+    return CSTONE_OK;
+}
+
+int cstone_link_tree(const uint64_t* leaves, int64_t n_leaves, uint64_t* node_keys, int32_t* child,
+                     int32_t* level_offsets, int32_t* leaf_to_node, int32_t* parent, void* ws, size_t ws_bytes,
+                     void* stream) {
+    if (n_leaves < 1 || n_leaves > CSTONE_MAX_LEAVES || (n_leaves - 1) % 7 != 0 || !leaves || !node_keys || !child ||
+        !level_offsets || !leaf_to_node)
+        return cst::fail(CSTONE_ERR_INVALID_ARG,
+                         "cstone_link_tree: bad argument (n_leaves=%lld must be 1 + 7k, arrays non-NULL)",
+                         (long long)n_leaves);
+    if (int rc = cst::check_ws(ws, ws_bytes, cst::link_ws_bytes(n_leaves), "cstone_link_tree")) return rc;
+    return cst::launch_link(reinterpret_cast<const cst::u64*>(leaves), n_leaves, reinterpret_cast<cst::u64*>(node_keys),
+                            child, level_offsets, leaf_to_node, parent, ws, cst::as_stream(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,314 @@
+// Stable LSD radix sort_by_key of 64-bit keys with the identity permutation as values
+// (Sec. 4 and the caption of Table 1: the particle keys are sorted with a permutation that
+// records where each particle went).
+//
+// One-sweep design: a single upfront pass histograms all eight 8-bit digits at once, then each
+// digit pass reads a tile of keys (and values), ranks them within the tile with warp-level
+// match, publishes the tile's per-digit counts and resolves its global offsets by decoupled
+// look-back over the preceding tiles (tiles are claimed in order through an atomic counter, so
+// every tile a block waits for is already running), stages the tile in shared memory in digit
+// order and writes each digit's run contiguously. The first pass generates the identity values
+// instead of reading them.
+//
+// Look-back words are 32 bits: 2 flag bits (0 = not ready, 1 = tile aggregate, 2 = inclusive
+// prefix) and a 30-bit count, which bounds n below 2^30. Two look-back regions alternate between
+// passes; every tile clears its row of the other region (written by the previous pass) so that the
+// next pass finds it empty, and only the first region needs a memset per sort.
+#include "common.cuh"
+
+namespace cst {
+namespace {
+
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+constexpr int kPasses = 8;
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kItems = 16;
+constexpr int kTile = kThreads * kItems;  // 4096 keys per tile
+constexpr int kWindow = 8;  // look-back descriptors loaded per step
+constexpr u32 kFlagAggregate = 1u << 30;
+constexpr u32 kFlagPrefix = 2u << 30;
+constexpr u32 kValueMask = (1u << 30) - 1u;
+
+struct SortCtl {
+    u32 tile_counter[kPasses];
+    u32 pad[56];
+    u32 hist[kPasses][kRadix];     // digit counts of all keys, per pass
+    u32 offsets[kPasses][kRadix];  // exclusive scan of hist
+};
+
+// Histograms of all 8 digits in one read of the keys. Per-block shared histograms, one global
+// atomic per non-empty bin per block.
+__global__ void __launch_bounds__(kThreads) sort_hist_kernel(const u64* __restrict__ keys, long long n, SortCtl* ctl) {
+    __shared__ u32 sh[kPasses][kRadix];
+    for (int i = threadIdx.x; i < kPasses * kRadix; i += kThreads) (&sh[0][0])[i] = 0;
+    __syncthreads();
+    for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kThreads) {
+        u64 k = __ldg(keys + i);
+#pragma unroll
+        for (int p = 0; p < kPasses; ++p) atomicAdd(&sh[p][(k >> (p * kRadixBits)) & (kRadix - 1)], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kPasses * kRadix; i += kThreads) {
+        u32 v = (&sh[0][0])[i];
+        if (v) atomicAdd(&ctl->hist[0][0] + i, v);
+    }
+}
+
+// Exclusive scan of each pass's histogram: one warp per pass.
+__global__ void sort_scan_kernel(SortCtl* ctl) {
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp >= kPasses) return;
+    u32 carry = 0;
+    for (int base = 0; base < kRadix; base += 32) {
+        u32 v = ctl->hist[warp][base + lane];
+        u32 incl = v;
+        for (int s = 1; s < 32; s <<= 1) {
+            u32 t = __shfl_up_sync(0xffffffffu, incl, s);
+            if (lane >= s) incl += t;
+        }
+        ctl->offsets[warp][base + lane] = carry + incl - v;
+        carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+}
+
+struct PassSmem {
+    u64 keys[kTile];
+    u32 vals[kTile];
+    u32 warp_hist[kWarps][kRadix];  // per-warp digit counts, then per-warp exclusive offsets
+    u32 tile_start[kRadix];         // first slot of each digit in the staged tile
+    u32 global_base[kRadix];        // output position of the tile's first key of each digit
+    u32 scan_tmp[kWarps];
+    u32 tile;
+};
+
+template <bool FIRST>
+__global__ void __launch_bounds__(kThreads, 2)
+    sort_pass_kernel(const u64* __restrict__ kin, u64* __restrict__ kout, const u32* __restrict__ vin,
+                     u32* __restrict__ vout, long long n, int pass, SortCtl* ctl, u32* look, u32* look_other,
+                     WsHeader* hdr) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PassSmem& sm = *reinterpret_cast<PassSmem*>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int shift = pass * kRadixBits;
+
+    for (int i = tid; i < kWarps * kRadix; i += kThreads) (&sm.warp_hist[0][0])[i] = 0;
+    if (tid == 0) sm.tile = atomicAdd(&ctl->tile_counter[pass], 1u);
+    __syncthreads();
+    const u32 tile = sm.tile;
+    const long long base = (long long)tile * kTile;
+
+    // ---- load (warp-striped: warp w owns keys base + w*32*kItems + it*32 + lane)
+    u64 key[kItems];
+    u32 val[kItems];
+    u32 digit[kItems];
+    const long long wbase = base + (long long)warp * 32 * kItems + lane;
+#pragma unroll
+    for (int it = 0; it < kItems; ++it) {
+        long long idx = wbase + it * 32;
+        bool ok = idx < n;
+        key[it] = ok ? __ldcs(kin + idx) : ~0ULL;
+        if (FIRST)
+            val[it] = static_cast<u32>(idx);
+        else
+            val[it] = ok ? __ldcs(vin + idx) : 0u;
+        digit[it] = ok ? static_cast<u32>((key[it] >> shift) & (kRadix - 1)) : static_cast<u32>(kRadix);
+    }
+
+    // ---- rank within the warp, in memory order (stable)
+    u32 rank[kItems];
+    const u32 lt = lanemask_lt();
+#pragma unroll
+    for (int it = 0; it < kItems; ++it) {
+        u32 d = digit[it];
+        u32 peers = __match_any_sync(0xffffffffu, d);
+        int leader = __ffs(peers) - 1;
+        u32 before = 0;
+        if (lane == leader && d < kRadix) {
+            before = sm.warp_hist[warp][d];
+            sm.warp_hist[warp][d] = before + __popc(peers);
+        }
+        before = __shfl_sync(0xffffffffu, before, leader);
+        rank[it] = before + __popc(peers & lt);
+        __syncwarp();
+    }
+    __syncthreads();
+
+    // ---- per digit: tile total and per-warp exclusive offsets (thread t owns digit t)
+    const int d = tid;
+    u32 total = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+        u32 c = sm.warp_hist[w][d];
+        sm.warp_hist[w][d] = total;
+        total += c;
+    }
+    u32* my_look = look + (size_t)tile * kRadix + d;
+    if (tile == 0)
+        st_volatile(my_look, kFlagPrefix | total);
+    else
+        st_volatile(my_look, kFlagAggregate | total);
+
+    // block-wide exclusive scan of the totals over digits -> staging slots
+    {
+        u32 incl = total;
+        for (int s = 1; s < 32; s <<= 1) {
+            u32 t = __shfl_up_sync(0xffffffffu, incl, s);
+            if (lane >= s) incl += t;
+        }
+        if (lane == 31) sm.scan_tmp[warp] = incl;
+        __syncthreads();
+        u32 wpre = 0;
+        for (int w = 0; w < warp; ++w) wpre += sm.scan_tmp[w];
+        sm.tile_start[d] = wpre + incl - total;
+    }
+
+    // ---- decoupled look-back over preceding tiles for digit d, kWindow descriptors per step
+    u32 excl = 0;
+    if (tile > 0) {
+        long long j = (long long)tile - 1;
+        long long polls = 0;
+        for (;;) {
+            u32 v[kWindow];
+#pragma unroll
+            for (int w = 0; w < kWindow; ++w)
+                v[w] = (j - w >= 0) ? ld_volatile(look + (size_t)(j - w) * kRadix + d) : kFlagPrefix;
+            int used = 0;
+            bool done = false;
+#pragma unroll
+            for (int w = 0; w < kWindow; ++w) {
+                if (done || used < w) continue;
+                const u32 flag = v[w] & ~kValueMask;
+                if (flag == 0u) continue;  // not ready: stop consuming here
+                excl += v[w] & kValueMask;
+                used = w + 1;
+                if (flag == kFlagPrefix) done = true;
+            }
+            if (done) break;
+            j -= used;
+            if (used < kWindow) {
+                __nanosleep(32);
+                if (++polls > kSpinLimit || ld_volatile(&hdr->err) != 0u) {
+                    raise_error(hdr, CSTONE_ERR_TIMEOUT, 0x50000u + (u32)pass);
+                    break;
+                }
+            }
+        }
+        st_volatile(my_look, kFlagPrefix | ((excl + total) & kValueMask));
+    }
+    sm.global_base[d] = ctl->offsets[pass][d] + excl;
+    look_other[(size_t)tile * kRadix + d] = 0u;  // clear the previous pass's row for the next pass
+    __syncthreads();
+
+    // ---- stage in digit order
+#pragma unroll
+    for (int it = 0; it < kItems; ++it) {
+        u32 dd = digit[it];
+        if (dd < kRadix) {
+            u32 slot = sm.tile_start[dd] + sm.warp_hist[warp][dd] + rank[it];
+            sm.keys[slot] = key[it];
+            sm.vals[slot] = val[it];
+        }
+    }
+    __syncthreads();
+
+    // ---- write each digit's run contiguously
+    const long long remain = n - base;
+    const int count = remain < kTile ? static_cast<int>(remain) : kTile;
+    for (int s = tid; s < count; s += kThreads) {
+        u64 k = sm.keys[s];
+        u32 dd = static_cast<u32>((k >> shift) & (kRadix - 1));
+        u32 pos = sm.global_base[dd] + (static_cast<u32>(s) - sm.tile_start[dd]);
+        kout[pos] = k;
+        vout[pos] = sm.vals[s];
+    }
+}
+
+struct SortLayout {
+    SortCtl* ctl;
+    u32* look[2];
+    u64* keys_alt;
+    u32* vals_alt;
+    size_t bytes;
+    long long tiles;
+};
+
+SortLayout sort_layout(void* ws, long long n) {
+    SortLayout l;
+    Carver c(ws);
+    l.tiles = (n + kTile - 1) / kTile;
+    l.ctl = c.take<SortCtl>(1);
+    l.look[0] = c.take<u32>((size_t)l.tiles * kRadix);
+    l.look[1] = c.take<u32>((size_t)l.tiles * kRadix);
+    l.keys_alt = c.take<u64>((size_t)n);
+    l.vals_alt = c.take<u32>((size_t)n);
+    l.bytes = c.size();
+    return l;
+}
+
+}  // namespace
+
+size_t sort_ws_bytes(long long n) { return sort_layout(nullptr, n).bytes; }
+
+int launch_sort(const u64* keys_in, u64* keys_out, u32* perm, long long n, void* ws, cudaStream_t st) {
+    SortLayout l = sort_layout(ws, n);
+    WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
+    CST_CUDA(cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st));
+    if (n == 0) return CSTONE_OK;
+    CST_CUDA(cudaMemsetAsync(l.ctl, 0, sizeof(SortCtl), st));
+    CST_CUDA(cudaMemsetAsync(l.look[0], 0, (size_t)l.tiles * kRadix * sizeof(u32), st));
+
+    long long want = (n + kThreads - 1) / kThreads;
+    int hgrid = static_cast<int>(want < (long long)sm_count() * 4 ? want : (long long)sm_count() * 4);
+    sort_hist_kernel<<<hgrid, kThreads, 0, st>>>(keys_in, n, l.ctl);
+    CST_LAUNCHED("sort_hist_kernel");
+    sort_scan_kernel<<<1, 32 * kPasses, 0, st>>>(l.ctl);
+    CST_LAUNCHED("sort_scan_kernel");
+
+    const int smem = static_cast<int>(sizeof(PassSmem));
+    CST_CUDA(cudaFuncSetAttribute(sort_pass_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CST_CUDA(cudaFuncSetAttribute(sort_pass_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    // ping-pong: odd passes (1-based) write the workspace buffers, even passes the output, so the
+    // eighth pass lands in keys_out / perm.
+    const u64* ksrc = keys_in;
+    const u32* vsrc = nullptr;
+    for (int p = 0; p < kPasses; ++p) {
+        u64* kdst = (p % 2 == 0) ? l.keys_alt : keys_out;
+        u32* vdst = (p % 2 == 0) ? l.vals_alt : perm;
+        u32* look = l.look[p & 1];
+        u32* other = l.look[(p + 1) & 1];
+        if (p == 0)
+            sort_pass_kernel<true><<<(unsigned)l.tiles, kThreads, smem, st>>>(ksrc, kdst, vsrc, vdst, n, p, l.ctl, look,
+                                                                              other, hdr);
+        else
+            sort_pass_kernel<false><<<(unsigned)l.tiles, kThreads, smem, st>>>(ksrc, kdst, vsrc, vdst, n, p, l.ctl,
+                                                                               look, other, hdr);
+        CST_LAUNCHED("sort_pass_kernel");
+        ksrc = kdst;
+        vsrc = vdst;
+    }
+    return CSTONE_OK;
+}
+
+}  // namespace cst
+
+extern "C" {
+
+int cstone_sort_workspace_size(int64_t n, size_t* bytes) {
+    if (!bytes || n < 0 || n >= CSTONE_MAX_PARTICLES)
+        return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_sort_workspace_size: bad argument (n=%lld)", (long long)n);
+    *bytes = cst::sort_ws_bytes(n);
+    return CSTONE_OK;
+}
+
+int cstone_sort(const uint64_t* keys_in, uint64_t* keys_out, uint32_t* perm, int64_t n, void* ws, size_t ws_bytes,
+                void* stream) {
+    if (n < 0 || n >= CSTONE_MAX_PARTICLES || (n > 0 && (!keys_in || !keys_out || !perm)))
+        return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_sort: bad argument (n=%lld)", (long long)n);
+    if (int rc = cst::check_ws(ws, ws_bytes, cst::sort_ws_bytes(n), "cstone_sort")) return rc;
+    return cst::launch_sort(reinterpret_cast<const cst::u64*>(keys_in), reinterpret_cast<cst::u64*>(keys_out), perm,
+                            n, ws, cst::as_stream(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,73 @@
+"""The C-ABI library builds, loads and exports every entry point declared in include/cstone.h.
+Host-side argument checks and workspace-size queries run without a GPU (no kernel is launched)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "cstone.h")
+
+
+@pytest.fixture(scope="module")
+def clib():
+    import paper_2307_06345_gb300 as cs
+    cs.build()
+    return cs.load()
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"CSTONE_API\s+[\w\s\*]*?\b(cstone_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_path():
+    syms = declared_symbols()
+    for name in ("cstone_keys", "cstone_sort", "cstone_build_leaves", "cstone_link_tree", "cstone_upsweep_counts",
+                 "cstone_upsweep_multipoles", "cstone_bbox"):
+        assert name in syms
+
+
+def test_every_declared_symbol_is_exported(clib):
+    for name in declared_symbols():
+        assert hasattr(clib, name), name
+
+
+def test_status_strings(clib):
+    for code in range(6):
+        s = clib.cstone_status_string(code)
+        assert s and s.decode()
+    assert clib.cstone_status_string(99).decode() == "unknown status"
+    assert clib.cstone_version() >= 100
+
+
+def test_workspace_queries_and_argument_checks(clib):
+    sz = ctypes.c_size_t()
+    assert clib.cstone_sort_workspace_size(1 << 20, ctypes.byref(sz)) == 0
+    # the sort needs the alternate key/value buffers (12 bytes per key) plus look-back words
+    assert sz.value >= 12 * (1 << 20)
+    assert clib.cstone_sort_workspace_size(-1, ctypes.byref(sz)) == 1
+    assert clib.cstone_sort_workspace_size(1 << 30, ctypes.byref(sz)) == 1
+    assert clib.cstone_leaves_workspace_size(1000, 100, 64, ctypes.byref(sz)) == 0
+    assert clib.cstone_leaves_workspace_size(1000, 100, 0, ctypes.byref(sz)) == 1
+    assert clib.cstone_link_workspace_size(15, ctypes.byref(sz)) == 0
+    assert clib.cstone_link_workspace_size(0, ctypes.byref(sz)) == 1
+    # link: n_leaves must be 1 + 7k; rejected before any device work
+    dummy = ctypes.c_void_p(256)
+    rc = clib.cstone_link_tree(dummy, 3, dummy, dummy, dummy, dummy, None, dummy, 1 << 20, None)
+    assert rc == 1
+    buf = ctypes.create_string_buffer(512)
+    clib.cstone_last_error_detail(buf, 512)
+    assert b"n_leaves" in buf.value
+    # keys: unknown curve
+    rc = clib.cstone_keys(dummy, dummy, dummy, 10, dummy, 7, dummy, None)
+    assert rc == 1
+    # sort: workspace too small
+    rc = clib.cstone_sort(dummy, dummy, dummy, 1000, dummy, 16, None)
+    assert rc == 1
+    # leaves: initial leaf count beyond the capacity
+    nl = ctypes.c_int64(50)
+    rc = clib.cstone_build_leaves(dummy, 100, 8, dummy, 10, ctypes.byref(nl), dummy, None, 64, None, dummy, 1 << 20,
+                                  None)
+    assert rc == 1
