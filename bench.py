@@ -182,9 +182,9 @@ def run_ours(args, rank, world, local):
         t = b.tree_buffers(nl)
         cs.cstone_link_tree(b.leaves, nl, t["NK"], t["CO"], t["LO"], t["leaf_to_node"], t["parent"], b.ws)
         e[5].record(stream)
-        cs.cstone_upsweep_counts(b.counts, nl, t["leaf_to_node"], t["parent"], t["counts"], b.ws)
+        cs.cstone_upsweep_counts(b.counts, nl, t["leaf_to_node"], t["CO"], t["LO"], t["counts"], b.ws)
         e[6].record(stream)
-        cs.cstone_upsweep_multipoles(X, Y, Z, M, b.perm, b.offsets, nl, t["leaf_to_node"], t["parent"], t["CO"],
+        cs.cstone_upsweep_multipoles(X, Y, Z, M, b.perm, b.offsets, nl, t["leaf_to_node"], t["CO"], t["LO"], b.box,
                                      t["mass"], t["com"], t["quad"], b.ws)
         e[7].record(stream)
         return nl

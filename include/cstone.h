@@ -146,35 +146,43 @@ CSTONE_API int cstone_link_tree(const uint64_t* leaves, int64_t n_leaves, uint64
                      void* stream);
 
 /* ------------------------------------------------------------------------------------------
- * Node-count upsweep (Sec. 5 node properties): a leaf holds its N_i, an internal node the sum of
- * its 8 children. Inputs are the outputs of cstone_build_leaves and cstone_link_tree.
+ * Node-count upsweep (Sec. 5 node properties, computed by an upward pass as in Sec. 7): a leaf
+ * holds its N_i, an internal node the sum of its 8 children. Inputs are the outputs of
+ * cstone_build_leaves (counts) and cstone_link_tree (leaf_to_node, child, level_offsets).
  *   node_counts [n] uint32 output.
- * Asynchronous.
+ * One cooperative launch walking the levels from the deepest; asynchronous.
  * ------------------------------------------------------------------------------------------ */
 CSTONE_API int cstone_upsweep_workspace_size(int64_t n_leaves, size_t* bytes);
 CSTONE_API int cstone_upsweep_counts(const uint32_t* leaf_counts, int64_t n_leaves, const int32_t* leaf_to_node,
-                          const int32_t* parent, uint32_t* node_counts, void* ws, size_t ws_bytes, void* stream);
+                                     const int32_t* child, const int32_t* level_offsets, uint32_t* node_counts,
+                                     void* ws, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------------------------
  * Multipole upsweep (Sec. 5 node properties; Sec. 8 "cartesian multipoles with quadrupole
  * corrections"): per node the mass M, the centre of mass (expansion centre) and the second
  * moments about it Q_ab = sum m (x - com)_a (x - com)_b, components xx, xy, xz, yy, yz, zz.
  * Accumulation is in FP32 with two-sum compensation (a sum/compensation pair per moment, carried
- * up the tree); coordinate differences are rounded to FP32 once from their exact value, and the
- * centre is stored in FP64. An empty node has M = 0, com = 0, Q = 0. The workspace holds the
- * coordinates gathered into sorted order (28 bytes per particle) and the per-node sums.
+ * up the tree); positions are taken into 64-bit fixed point so that coordinate differences are
+ * exact before their single rounding to FP32, and the centre is written in FP64. An empty node has
+ * M = 0, com = 0, Q = 0. The workspace holds a 32-byte record per particle and the per-node sums.
  *   x, y, z, m   [n] float64 coordinates and float32 masses in input order.
  *   perm         [n] uint32 sort permutation (cstone_sort).
  *   offsets      [n_leaves + 1] uint32 leaf particle offsets (cstone_build_leaves).
- *   mass         [n] float32, com [3 * nn] float64 (SoA: x block, y block, z block),
+ *   leaf_to_node, child, level_offsets  from cstone_link_tree.
+ *   box          [4] float64 device array {lo_x, lo_y, lo_z, side}; it fixes the 64-bit
+ *                fixed-point frame of the positions. Every |coordinate| must stay below 2^E, the
+ *                smallest power of two above max(|lo|, |lo + 2 side|) (true for any point within
+ *                the box); otherwise the workspace error word reports CSTONE_ERR_INVALID_ARG.
+ *   mass         [nn] float32, com [3 * nn] float64 (SoA: x block, y block, z block),
  *   quad         [6 * nn] float32 (SoA, component-major), nn = number of nodes.
  * Asynchronous.
  * ------------------------------------------------------------------------------------------ */
 CSTONE_API int cstone_multipole_workspace_size(int64_t n, int64_t n_leaves, size_t* bytes);
 CSTONE_API int cstone_upsweep_multipoles(const double* x, const double* y, const double* z, const float* m,
-                              const uint32_t* perm, int64_t n, const uint32_t* offsets, int64_t n_leaves,
-                              const int32_t* leaf_to_node, const int32_t* parent, const int32_t* child,
-                              float* mass, double* com, float* quad, void* ws, size_t ws_bytes, void* stream);
+                                         const uint32_t* perm, int64_t n, const uint32_t* offsets, int64_t n_leaves,
+                                         const int32_t* leaf_to_node, const int32_t* child,
+                                         const int32_t* level_offsets, const double* box, float* mass, double* com,
+                                         float* quad, void* ws, size_t ws_bytes, void* stream);
 
 #ifdef __cplusplus
 }

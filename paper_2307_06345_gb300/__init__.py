@@ -73,9 +73,9 @@ def load():
             "cstone_link_workspace_size": (ctypes.c_int, [i64, psz]),
             "cstone_link_tree": (ctypes.c_int, [P, i64, P, P, P, P, P, P, sz, P]),
             "cstone_upsweep_workspace_size": (ctypes.c_int, [i64, psz]),
-            "cstone_upsweep_counts": (ctypes.c_int, [P, i64, P, P, P, P, sz, P]),
+            "cstone_upsweep_counts": (ctypes.c_int, [P, i64, P, P, P, P, P, sz, P]),
             "cstone_multipole_workspace_size": (ctypes.c_int, [i64, i64, psz]),
-            "cstone_upsweep_multipoles": (ctypes.c_int, [P, P, P, P, P, i64, P, i64, P, P, P, P, P, P, P, sz, P]),
+            "cstone_upsweep_multipoles": (ctypes.c_int, [P, P, P, P, P, i64, P, i64, P, P, P, P, P, P, P, P, sz, P]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(lib, name)
@@ -210,24 +210,25 @@ def cstone_link_tree(leaves, n_leaves: int, node_keys, child, level_offsets, lea
            "cstone_link_tree")
 
 
-def cstone_upsweep_counts(leaf_counts, n_leaves: int, leaf_to_node, parent, node_counts,
+def cstone_upsweep_counts(leaf_counts, n_leaves: int, leaf_to_node, child, level_offsets, node_counts,
                           ws: Workspace | None = None, stream=None):
     lib = load()
     ws = ws or Workspace(leaf_counts.device)
     buf = ws.get(_size(lib.cstone_upsweep_workspace_size, n_leaves))
-    _check(lib.cstone_upsweep_counts(_ptr(leaf_counts), n_leaves, _ptr(leaf_to_node), _ptr(parent),
-                                     _ptr(node_counts), _ptr(buf), buf.numel(), _stream(stream)),
+    _check(lib.cstone_upsweep_counts(_ptr(leaf_counts), n_leaves, _ptr(leaf_to_node), _ptr(child),
+                                     _ptr(level_offsets), _ptr(node_counts), _ptr(buf), buf.numel(), _stream(stream)),
            "cstone_upsweep_counts")
 
 
-def cstone_upsweep_multipoles(x, y, z, m, perm, offsets, n_leaves: int, leaf_to_node, parent, child, mass, com,
-                              quad, ws: Workspace | None = None, stream=None):
+def cstone_upsweep_multipoles(x, y, z, m, perm, offsets, n_leaves: int, leaf_to_node, child, level_offsets, box,
+                              mass, com, quad, ws: Workspace | None = None, stream=None):
     lib = load()
     _need(m, torch.float32, "m")
     ws = ws or Workspace(x.device)
     buf = ws.get(_size(lib.cstone_multipole_workspace_size, x.numel(), n_leaves))
     _check(lib.cstone_upsweep_multipoles(_ptr(x), _ptr(y), _ptr(z), _ptr(m), _ptr(perm), x.numel(), _ptr(offsets),
-                                         n_leaves, _ptr(leaf_to_node), _ptr(parent), _ptr(child), _ptr(mass),
+                                         n_leaves, _ptr(leaf_to_node), _ptr(child), _ptr(level_offsets), _ptr(box),
+                                         _ptr(mass),
                                          _ptr(com), _ptr(quad), _ptr(buf), buf.numel(), _stream(stream)),
            "cstone_upsweep_multipoles")
 
@@ -325,7 +326,7 @@ def build_octree(x, y, z, curve: int = HILBERT, ncrit: int = 64, box=None, masse
     t = b.tree_buffers(nl)
     nn = n_nodes(nl)
     cstone_link_tree(b.leaves, nl, t["NK"], t["CO"], t["LO"], t["leaf_to_node"], t["parent"], b.ws, stream)
-    cstone_upsweep_counts(b.counts, nl, t["leaf_to_node"], t["parent"], t["counts"], b.ws, stream)
+    cstone_upsweep_counts(b.counts, nl, t["leaf_to_node"], t["CO"], t["LO"], t["counts"], b.ws, stream)
     out = {
         "buffers": b, "box": box, "keys": b.keys, "sorted_keys": b.sorted_keys, "perm": b.perm,
         "leaves": b.leaves[: nl + 1], "leaf_counts": b.counts[:nl], "leaf_offsets": b.offsets[: nl + 1],
@@ -339,7 +340,7 @@ def build_octree(x, y, z, curve: int = HILBERT, ncrit: int = 64, box=None, masse
             t["com"] = torch.empty(3 * cap_nodes, dtype=torch.float64, device=b.device)
             t["quad"] = torch.empty(6 * cap_nodes, dtype=torch.float32, device=b.device)
         mass, com, quad = t["mass"][:nn], t["com"][: 3 * nn], t["quad"][: 6 * nn]
-        cstone_upsweep_multipoles(x, y, z, masses, b.perm, b.offsets, nl, t["leaf_to_node"], t["parent"], t["CO"],
+        cstone_upsweep_multipoles(x, y, z, masses, b.perm, b.offsets, nl, t["leaf_to_node"], t["CO"], t["LO"], box,
                                   mass, com, quad, b.ws, stream)
         out.update({"mass": mass, "com": com.view(3, nn), "quad": quad.view(6, nn)})
     return out

@@ -76,4 +76,39 @@ __device__ __forceinline__ void raise_error(WsHeader* h, u32 status, u32 info) {
     if (atomicCAS(&h->err, 0u, status) == 0u) h->err_info = info;
 }
 
+// Grid-wide barrier for cooperative launches (all blocks co-resident). The wait is bounded: after
+// kSpinLimit polls it records CSTONE_ERR_TIMEOUT and lets the block go on.
+struct GridBarrier {
+    u32 count;
+    u32 gen;
+};
+
+__device__ inline void grid_barrier(GridBarrier* bar, WsHeader* hdr) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const u32 gen = ld_volatile(&bar->gen);
+        __threadfence();
+        if (atomicAdd(&bar->count, 1u) == gridDim.x - 1) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            atomicAdd(&bar->gen, 1u);
+        } else {
+            long long polls = 0;
+            while (ld_volatile(&bar->gen) == gen) {
+                __nanosleep(64);
+                if (++polls > kSpinLimit) {
+                    raise_error(hdr, CSTONE_ERR_TIMEOUT, 0x1000u);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// Blocks of `threads` threads that fit on the device at once for `kernel` (cooperative grid size),
+// capped at `cap_per_sm` per SM.
+int cooperative_grid(const void* kernel, int threads, size_t smem, int cap_per_sm);
+
 }  // namespace cst

@@ -21,10 +21,11 @@ namespace cst {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kItems = 8;
+constexpr int kItems = 2;
 constexpr int kTile = kThreads * kItems;  // leaf indices per tile
 constexpr int kMaxIters = 256;
-constexpr u32 kLinearSplit = 4096;  // split ranges up to this many particles are counted, not searched
+constexpr int kSplitChunks = 16;                 // keys per lane loaded at once when counting a split
+constexpr u32 kLinearSplit = 32 * kSplitChunks;  // split ranges up to this size are counted, not searched
 constexpr u64 kLookAggregate = 1ULL << 62;
 constexpr u64 kLookPrefix = 2ULL << 62;
 constexpr u64 kLookValue = (1ULL << 62) - 1ULL;
@@ -33,8 +34,7 @@ struct LoopState {
     u32 nl[kMaxIters + 1];       // leaves entering pass t (nl[0] = initial)
     u32 changed[kMaxIters];      // pass t changed the array
     u32 tile_counter[kMaxIters]; // tile dispenser of pass t
-    u32 bar_count;               // grid barrier arrivals
-    u32 bar_gen;                 // grid barrier generation
+    GridBarrier bar;
     u32 iters;                   // passes executed (set at convergence)
     u32 converged;
     u32 required;                // leaves needed when the capacity was exceeded
@@ -48,31 +48,6 @@ struct LeafBufs {
 
 __device__ __forceinline__ u64 ld_volatile64(const u64* p) { return *reinterpret_cast<const volatile u64*>(p); }
 __device__ __forceinline__ void st_volatile64(u64* p, u64 v) { *reinterpret_cast<volatile u64*>(p) = v; }
-
-// Grid-wide barrier for a cooperative launch (all blocks co-resident), with a bounded wait.
-__device__ void grid_barrier(LoopState* ls, WsHeader* hdr) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        u32 gen = ld_volatile(&ls->bar_gen);
-        __threadfence();
-        if (atomicAdd(&ls->bar_count, 1u) == gridDim.x - 1) {
-            atomicExch(&ls->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&ls->bar_gen, 1u);
-        } else {
-            long long polls = 0;
-            while (ld_volatile(&ls->bar_gen) == gen) {
-                __nanosleep(64);
-                if (++polls > kSpinLimit) {
-                    raise_error(hdr, CSTONE_ERR_TIMEOUT, 0x1000u);
-                    break;
-                }
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
-}
 
 // First position in P[lo, hi) whose key is >= key.
 __device__ __forceinline__ u32 lower_bound_in(const u64* __restrict__ P, u32 lo, u32 hi, u64 key) {
@@ -131,7 +106,7 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const u64* __rest
         u32 nl0 = ls->nl[0];
         for (u32 i = gtid; i <= nl0; i += gthreads) b.pos[0][i] = lower_bound_in(P, 0u, n, b.K[0][i]);
     }
-    grid_barrier(ls, hdr);
+    grid_barrier(&ls->bar, hdr);
 
     int t = 0;
     for (; t < max_iters; ++t) {
@@ -284,12 +259,18 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const u64* __rest
                 const int child_shift = __ffsll(static_cast<long long>(delta)) - 1 - 3;
                 u32 below = 0;  // lane c in 1..7: particles whose child digit is < c
                 if (cnt_all <= kLinearSplit) {
-                    for (u32 b = 0; b < cnt_all; b += 32) {
-                        const u32 jj = b + lane;
-                        const u32 dg = jj < cnt_all ? static_cast<u32>((__ldg(P + lo + jj) >> child_shift) & 7ULL) : 8u;
+                    u32 dg[kSplitChunks];
+#pragma unroll
+                    for (int b = 0; b < kSplitChunks; ++b) {  // every load issued before any use
+                        const u32 jj = b * 32 + lane;
+                        dg[b] = jj < cnt_all ? static_cast<u32>((__ldg(P + lo + jj) >> child_shift) & 7ULL) : 8u;
+                    }
+#pragma unroll
+                    for (int b = 0; b < kSplitChunks; ++b) {
+                        if (b * 32 >= static_cast<int>(cnt_all)) break;
 #pragma unroll
                         for (u32 c = 1; c < 8; ++c) {
-                            const u32 bal = __ballot_sync(0xffffffffu, dg < c);
+                            const u32 bal = __ballot_sync(0xffffffffu, dg[b] < c);
                             if (lane == c) below += __popc(bal);
                         }
                     }
@@ -309,7 +290,7 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const u64* __rest
         if (any_change) s_any = 1;
         __syncthreads();
         if (tid == 0 && s_any) atomicOr(&ls->changed[t], 1u);
-        grid_barrier(ls, hdr);
+        grid_barrier(&ls->bar, hdr);
         if (ld_volatile(&hdr->err)) break;
         if (ld_volatile(&ls->changed[t]) == 0u) {
             ++t;  // this pass confirmed convergence; its output equals its input
@@ -357,20 +338,7 @@ LeavesLayout leaves_layout(void* ws, long long cap, int max_iters) {
     return l;
 }
 
-int leaves_grid() {
-    static thread_local int cached_dev = -1, cached = 0;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev != cached_dev) {
-        int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, leaves_loop_kernel, kThreads, 0) != cudaSuccess ||
-            per_sm < 1)
-            per_sm = 1;
-        cached = sm_count() * (per_sm < 2 ? per_sm : 2);
-        cached_dev = dev;
-    }
-    return cached;
-}
+int leaves_grid() { return cooperative_grid(reinterpret_cast<const void*>(leaves_loop_kernel), kThreads, 0, 8); }
 
 }  // namespace
 

@@ -84,7 +84,7 @@ struct PassSmem {
 };
 
 template <bool FIRST>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, 3)
     sort_pass_kernel(const u64* __restrict__ kin, u64* __restrict__ kout, const u32* __restrict__ vin,
                      u32* __restrict__ vout, long long n, int pass, SortCtl* ctl, u32* look, u32* look_other,
                      WsHeader* hdr) {
@@ -102,7 +102,6 @@ __global__ void __launch_bounds__(kThreads, 2)
     // ---- load (warp-striped: warp w owns keys base + w*32*kItems + it*32 + lane)
     u64 key[kItems];
     u32 val[kItems];
-    u32 digit[kItems];
     const long long wbase = base + (long long)warp * 32 * kItems + lane;
 #pragma unroll
     for (int it = 0; it < kItems; ++it) {
@@ -113,100 +112,114 @@ __global__ void __launch_bounds__(kThreads, 2)
             val[it] = static_cast<u32>(idx);
         else
             val[it] = ok ? __ldcs(vin + idx) : 0u;
-        digit[it] = ok ? static_cast<u32>((key[it] >> shift) & (kRadix - 1)) : static_cast<u32>(kRadix);
     }
+    auto digit_of = [&](int it) -> u32 {
+        return (wbase + it * 32 < n) ? static_cast<u32>((key[it] >> shift) & (kRadix - 1)) : static_cast<u32>(kRadix);
+    };
 
-    // ---- rank within the warp, in memory order (stable)
-    u32 rank[kItems];
+    // ---- rank within the warp, in memory order (stable); ranks packed two per register.
+    // Items are handled in groups: all matches of a group first, then the leaders' reservations
+    // (shared-memory atomics of one warp to one address take effect in program order, so earlier
+    // items keep lower ranks), then the broadcasts - so the round trips of a group overlap.
+    constexpr int kGroup = 8;
+    u32 rank2[kItems / 2];
     const u32 lt = lanemask_lt();
 #pragma unroll
-    for (int it = 0; it < kItems; ++it) {
-        u32 d = digit[it];
-        u32 peers = __match_any_sync(0xffffffffu, d);
-        int leader = __ffs(peers) - 1;
-        u32 before = 0;
-        if (lane == leader && d < kRadix) {
-            before = sm.warp_hist[warp][d];
-            sm.warp_hist[warp][d] = before + __popc(peers);
+    for (int g0 = 0; g0 < kItems; g0 += kGroup) {
+        u32 peers[kGroup], before[kGroup];
+#pragma unroll
+        for (int q = 0; q < kGroup; ++q) peers[q] = __match_any_sync(0xffffffffu, digit_of(g0 + q));
+#pragma unroll
+        for (int q = 0; q < kGroup; ++q) {
+            const u32 d = digit_of(g0 + q);
+            before[q] = 0;
+            if (lane == __ffs(peers[q]) - 1 && d < kRadix)
+                before[q] = atomicAdd(&sm.warp_hist[warp][d], static_cast<u32>(__popc(peers[q])));
         }
-        before = __shfl_sync(0xffffffffu, before, leader);
-        rank[it] = before + __popc(peers & lt);
-        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < kGroup; ++q) {
+            const u32 r = __shfl_sync(0xffffffffu, before[q], __ffs(peers[q]) - 1) + __popc(peers[q] & lt);
+            const int it = g0 + q;
+            if (it & 1)
+                rank2[it >> 1] |= r << 16;
+            else
+                rank2[it >> 1] = r;
+        }
     }
     __syncthreads();
 
-    // ---- per digit: tile total and per-warp exclusive offsets (thread t owns digit t)
-    const int d = tid;
-    u32 total = 0;
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) {
-        u32 c = sm.warp_hist[w][d];
-        sm.warp_hist[w][d] = total;
-        total += c;
-    }
+    // ---- per digit: tile total and per-warp exclusive offsets (thread t < 256 owns digit t)
+    const bool owner = tid < kRadix;
+    const int d = owner ? tid : 0;
+    u32 total = 0, incl = 0;
     u32* my_look = look + (size_t)tile * kRadix + d;
-    if (tile == 0)
-        st_volatile(my_look, kFlagPrefix | total);
-    else
-        st_volatile(my_look, kFlagAggregate | total);
-
-    // block-wide exclusive scan of the totals over digits -> staging slots
-    {
-        u32 incl = total;
+    if (owner) {
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            const u32 c = sm.warp_hist[w][d];
+            sm.warp_hist[w][d] = total;
+            total += c;
+        }
+        st_volatile(my_look, (tile == 0 ? kFlagPrefix : kFlagAggregate) | total);
+        // block-wide exclusive scan of the totals over digits -> staging slots
+        incl = total;
         for (int s = 1; s < 32; s <<= 1) {
-            u32 t = __shfl_up_sync(0xffffffffu, incl, s);
+            const u32 t = __shfl_up_sync(0xffffffffu, incl, s);
             if (lane >= s) incl += t;
         }
         if (lane == 31) sm.scan_tmp[warp] = incl;
-        __syncthreads();
+    }
+    __syncthreads();
+    if (owner) {
         u32 wpre = 0;
         for (int w = 0; w < warp; ++w) wpre += sm.scan_tmp[w];
         sm.tile_start[d] = wpre + incl - total;
-    }
 
-    // ---- decoupled look-back over preceding tiles for digit d, kWindow descriptors per step
-    u32 excl = 0;
-    if (tile > 0) {
-        long long j = (long long)tile - 1;
-        long long polls = 0;
-        for (;;) {
-            u32 v[kWindow];
+        // decoupled look-back over preceding tiles for digit d, kWindow descriptors per step
+        u32 excl = 0;
+        if (tile > 0) {
+            long long j = (long long)tile - 1;
+            long long polls = 0;
+            for (;;) {
+                u32 v[kWindow];
 #pragma unroll
-            for (int w = 0; w < kWindow; ++w)
-                v[w] = (j - w >= 0) ? ld_volatile(look + (size_t)(j - w) * kRadix + d) : kFlagPrefix;
-            int used = 0;
-            bool done = false;
+                for (int w = 0; w < kWindow; ++w)
+                    v[w] = (j - w >= 0) ? ld_volatile(look + (size_t)(j - w) * kRadix + d) : kFlagPrefix;
+                int used = 0;
+                bool done = false;
 #pragma unroll
-            for (int w = 0; w < kWindow; ++w) {
-                if (done || used < w) continue;
-                const u32 flag = v[w] & ~kValueMask;
-                if (flag == 0u) continue;  // not ready: stop consuming here
-                excl += v[w] & kValueMask;
-                used = w + 1;
-                if (flag == kFlagPrefix) done = true;
-            }
-            if (done) break;
-            j -= used;
-            if (used < kWindow) {
-                __nanosleep(32);
-                if (++polls > kSpinLimit || ld_volatile(&hdr->err) != 0u) {
-                    raise_error(hdr, CSTONE_ERR_TIMEOUT, 0x50000u + (u32)pass);
-                    break;
+                for (int w = 0; w < kWindow; ++w) {
+                    if (done || used < w) continue;
+                    const u32 flag = v[w] & ~kValueMask;
+                    if (flag == 0u) continue;  // not ready: stop consuming here
+                    excl += v[w] & kValueMask;
+                    used = w + 1;
+                    if (flag == kFlagPrefix) done = true;
+                }
+                if (done) break;
+                j -= used;
+                if (used < kWindow) {
+                    __nanosleep(32);
+                    if (++polls > kSpinLimit || ld_volatile(&hdr->err) != 0u) {
+                        raise_error(hdr, CSTONE_ERR_TIMEOUT, 0x50000u + (u32)pass);
+                        break;
+                    }
                 }
             }
+            st_volatile(my_look, kFlagPrefix | ((excl + total) & kValueMask));
         }
-        st_volatile(my_look, kFlagPrefix | ((excl + total) & kValueMask));
+        sm.global_base[d] = ctl->offsets[pass][d] + excl;
+        look_other[(size_t)tile * kRadix + d] = 0u;  // clear the previous pass's row for the next pass
     }
-    sm.global_base[d] = ctl->offsets[pass][d] + excl;
-    look_other[(size_t)tile * kRadix + d] = 0u;  // clear the previous pass's row for the next pass
     __syncthreads();
 
     // ---- stage in digit order
 #pragma unroll
     for (int it = 0; it < kItems; ++it) {
-        u32 dd = digit[it];
+        const u32 dd = digit_of(it);
         if (dd < kRadix) {
-            u32 slot = sm.tile_start[dd] + sm.warp_hist[warp][dd] + rank[it];
+            const u32 r = (rank2[it >> 1] >> ((it & 1) * 16)) & 0xffffu;
+            u32 slot = sm.tile_start[dd] + sm.warp_hist[warp][dd] + r;
             sm.keys[slot] = key[it];
             sm.vals[slot] = val[it];
         }

@@ -36,6 +36,14 @@ int sm_count() {
     return cached;
 }
 
+int cooperative_grid(const void* kernel, int threads, size_t smem, int cap_per_sm) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    if (per_sm > cap_per_sm) per_sm = cap_per_sm;
+    return sm_count() * per_sm;
+}
+
 int check_ws(void* ws, size_t have, size_t need, const char* who) {
     if (ws == nullptr || have < need)
         return fail(CSTONE_ERR_INVALID_ARG, "%s: workspace of %zu bytes given, %zu needed", who, have, need);

@@ -1,17 +1,18 @@
 // Upsweeps over the linked octree (Sec. 5 node properties; Sec. 7 computes node properties "by an
 // upward pass" where leaves depend on their particles and internal nodes on their children).
 //
-// Both upsweeps are single launches: one thread per leaf writes the leaf's value and climbs. At
-// every sibling group it increments the group's arrival counter; the eighth arrival computes the
-// parent from its 8 children (always in child order, so results do not depend on timing) and
-// continues upwards, the others stop. Breadth-first layout puts the 8 children of a node in one
-// aligned group, group g = nodes 1 + 8g .. 8 + 8g, whose parent is parent[g].
+// Both upsweeps walk the levels of the breadth-first tree from the deepest up in one cooperative
+// launch: the leaves' values are written first, then every internal node of a level combines its 8
+// children (in child order, so results do not depend on timing), with a bounded grid barrier
+// between levels. Level l occupies nodes [LO[l], LO[l+1]); a level whose next level is empty has no
+// internal node and is skipped.
 //
-// Multipoles (three launches: gather into sorted order, leaf sums, climb): FP32 accumulation with
-// compensation. Each sum is a pair (sum, compensation) updated with an exact two-sum step
-// (Neumaier), and the pairs of mass and second moments are carried up the tree in scratch so the
-// compensation survives all 21 levels. Coordinate differences are rounded to FP32 once from their
-// exact value; the expansion centre (centre of mass) is kept in FP64.
+// Multipoles (three launches: pack, leaf sums, climb): FP32 accumulation with compensation. Each
+// sum is a pair (sum, compensation) updated with an exact two-sum step (Neumaier), and the pairs of
+// mass and second moments are carried up the tree in scratch so the compensation survives all 21
+// levels. Positions are held in 64-bit fixed point, so coordinate differences are exact and are
+// rounded to FP32 once; the expansion centre (centre of mass) is kept in fixed point and written
+// out in FP64.
 // A leaf takes its first particle as the anchor for the differences, an internal node its first
 // non-empty child's centre; second moments of an internal node use the parallel-axis shift
 // Q = sum_c [Q_c + M_c (c_c - c)(c_c - c)^T].
@@ -23,26 +24,30 @@ namespace {
 constexpr int kThreads = 256;
 
 // ---------------------------------------------------------------------------- counts
+constexpr int kNumLevels = kLevels + 1;
+
 __global__ void __launch_bounds__(kThreads) upsweep_counts_kernel(const u32* __restrict__ leaf_counts, u32 nl,
                                                                   const int* __restrict__ leaf_to_node,
-                                                                  const int* __restrict__ parent,
-                                                                  u32* __restrict__ node_counts,
-                                                                  u32* __restrict__ arrive) {
-    u32 i = blockIdx.x * kThreads + threadIdx.x;
-    if (i >= nl) return;
-    int v = leaf_to_node[i];
-    node_counts[v] = leaf_counts[i];
-    while (v != 0) {
-        u32 g = static_cast<u32>(v - 1) >> 3;
-        __threadfence();
-        if (atomicAdd(&arrive[g], 1u) != 7u) return;
-        __threadfence();
-        const u32* kids = node_counts + 1 + 8 * g;
-        u32 s = 0;
+                                                                  const int* __restrict__ child,
+                                                                  const int* __restrict__ level_offsets,
+                                                                  u32* __restrict__ node_counts, GridBarrier* bar,
+                                                                  WsHeader* hdr) {
+    __shared__ int s_lo[kNumLevels + 1];
+    if (threadIdx.x <= kNumLevels) s_lo[threadIdx.x] = level_offsets[threadIdx.x];
+    const u32 gtid = blockIdx.x * kThreads + threadIdx.x, gthreads = gridDim.x * kThreads;
+    for (u32 i = gtid; i < nl; i += gthreads) node_counts[leaf_to_node[i]] = leaf_counts[i];
+    grid_barrier(bar, hdr);
+    for (int l = kLevels - 1; l >= 0; --l) {
+        if (s_lo[l + 2] == s_lo[l + 1]) continue;  // no internal node at level l
+        for (u32 x = s_lo[l] + gtid; x < static_cast<u32>(s_lo[l + 1]); x += gthreads) {
+            const int c = child[x];
+            if (c == 0) continue;
+            u32 sum = 0;
 #pragma unroll
-        for (int c = 0; c < 8; ++c) s += __ldcg(kids + c);
-        v = parent[g];
-        node_counts[v] = s;
+            for (int k = 0; k < 8; ++k) sum += __ldcg(node_counts + c + k);
+            node_counts[x] = sum;
+        }
+        grid_barrier(bar, hdr);
     }
 }
 
@@ -70,42 +75,77 @@ __device__ __forceinline__ ff ff_add(ff a, ff b) {
 
 __device__ __forceinline__ float ff_val(ff a) { return __fadd_rn(a.hi, a.lo); }
 
-// x - a rounded once to FP32. The exact difference is formed from the two 53-bit significands in
-// 64-bit integer arithmetic (aligned by the exponent gap, at most 9 bits here) and converted with
-// one rounding; the power-of-two scale is exact. Zero, subnormal or far-apart operands and
-// magnitudes outside the FP32 range of the scale take the FP64 path.
-__device__ __forceinline__ float diff_f32(double x, double a) {
-    const u64 bx = static_cast<u64>(__double_as_longlong(x));
-    const u64 ba = static_cast<u64>(__double_as_longlong(a));
-    const int ex = static_cast<int>((bx >> 52) & 0x7ffu), ea = static_cast<int>((ba >> 52) & 0x7ffu);
-    const int emin = min(ex, ea);
-    if (ex == 0 || ea == 0 || abs(ex - ea) > 9 || emin < 975 || max(ex, ea) > 1130)
-        return __double2float_rn(__dsub_rn(x, a));
-    constexpr u64 kMant = (1ULL << 52) - 1;
-    long long X = static_cast<long long>(((bx & kMant) | (1ULL << 52)) << (ex - emin));
-    long long A = static_cast<long long>(((ba & kMant) | (1ULL << 52)) << (ea - emin));
-    if (bx >> 63) X = -X;
-    if (ba >> 63) A = -A;
-    const float f = __ll2float_rn(X - A);
-    return __fmul_rn(f, __int_as_float((emin - 1075 + 127) << 23));
-}
-
-struct MpScratch {  // per node: compensated sums carried up the tree
-    ff* mass;       // [n]
-    ff* quad;       // [6 n], component-major
-    double* xs;     // [n_particles] coordinates and masses in sorted order
-    double* ys;
-    double* zs;
-    float* ms;
+// Coordinates in 64-bit fixed point: X = trunc(x * 2^F) with F chosen from the box so that
+// |X| < 2^61 for |x| < 2^E >= max(|lo|, |lo + 2 side|). Differences of fixed-point values are
+// exact; one conversion rounds them to FP32 and a power-of-two scale (split in two factors so
+// that each is a normal float) restores physical units.
+struct FixedFrame {
+    int F;
+    float s1, s2;  // 2^-F = s1 * s2
+    int e_lim;     // biased exponent bound: |x| < 2^(e_lim - 1023)
 };
 
-__device__ __forceinline__ void store_node(int v, u32 n_nodes, ff M, const double c[3], const ff q[6], MpScratch s,
-                                           float* __restrict__ mass, double* __restrict__ com,
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }
+
+__device__ FixedFrame make_frame(const double* box) {
+    FixedFrame f;
+    const double lo0 = fmin(fmin(box[0], box[1]), box[2]);
+    const double lo1 = fmax(fmax(box[0], box[1]), box[2]);
+    const double hi = __dadd_rn(lo1, __dmul_rn(2.0, box[3]));
+    const double big = fmax(fabs(lo0), fmax(fabs(lo1), fabs(hi)));
+    const int e = static_cast<int>((static_cast<u64>(__double_as_longlong(big)) >> 52) & 0x7ffu);
+    const int E = e - 1023 + 1;  // 2^E > big
+    f.F = 61 - E;
+    f.e_lim = E + 1023;
+    const int h = f.F / 2;
+    f.s1 = pow2f(-h);
+    f.s2 = pow2f(-(f.F - h));
+    return f;
+}
+
+__device__ __forceinline__ long long fixed_of(double x, int F) {
+    const u64 b = static_cast<u64>(__double_as_longlong(x));
+    const int e = static_cast<int>((b >> 52) & 0x7ffu);
+    u64 mant = b & ((1ULL << 52) - 1);
+    if (e != 0) mant |= (1ULL << 52);
+    const int sh = (e == 0 ? 1 : e) - 1075 + F;
+    const u64 mag = sh >= 0 ? (mant << sh) : (sh > -64 ? (mant >> (-sh)) : 0ULL);
+    return (b >> 63) ? -static_cast<long long>(mag) : static_cast<long long>(mag);
+}
+
+__device__ __forceinline__ float fixed_diff(long long a, long long b, const FixedFrame& f) {
+    return __fmul_rn(__fmul_rn(__ll2float_rn(a - b), f.s1), f.s2);
+}
+
+__device__ __forceinline__ double fixed_to_double(long long a, const FixedFrame& f) {
+    // exact power-of-two scaling of the (rounded) conversion
+    return __dmul_rn(__dmul_rn(__ll2double_rn(a), (double)f.s1), (double)f.s2);
+}
+
+struct __align__(16) Record {  // one particle, original order
+    long long x, y, z;
+    float m;
+    u32 pad;
+};
+
+struct MpScratch {  // per node: compensated sums and the fixed-point centre carried up the tree
+    ff* mass;           // [n]
+    ff* quad;           // [6 n], component-major
+    long long* cfix;    // [3 n], component-major
+    Record* rec;        // [n_particles]
+};
+
+__device__ __forceinline__ void store_node(int v, u32 n_nodes, ff M, const long long c[3], const ff q[6], MpScratch s,
+                                           const FixedFrame& f, float* __restrict__ mass, double* __restrict__ com,
                                            float* __restrict__ quad) {
     s.mass[v] = M;
     mass[v] = ff_val(M);
+    const bool empty = M.hi == 0.f && M.lo == 0.f;
 #pragma unroll
-    for (int d = 0; d < 3; ++d) com[(size_t)d * n_nodes + v] = c[d];
+    for (int d = 0; d < 3; ++d) {
+        s.cfix[(size_t)d * n_nodes + v] = c[d];
+        com[(size_t)d * n_nodes + v] = empty ? 0.0 : fixed_to_double(c[d], f);
+    }
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
         s.quad[(size_t)k * n_nodes + v] = q[k];
@@ -113,79 +153,111 @@ __device__ __forceinline__ void store_node(int v, u32 n_nodes, ff M, const doubl
     }
 }
 
-// The one random access of the upsweep: coordinates and masses gathered into sorted order,
-// several independent gathers in flight per thread.
-constexpr int kGather = 4;
-
-__global__ void __launch_bounds__(kThreads) multipole_gather_kernel(const double* __restrict__ x,
-                                                                    const double* __restrict__ y,
-                                                                    const double* __restrict__ z,
-                                                                    const float* __restrict__ m,
-                                                                    const u32* __restrict__ perm, u32 n, MpScratch s) {
-    const u32 stride = gridDim.x * kThreads * kGather;
-    for (u32 j0 = (blockIdx.x * kThreads) * kGather + threadIdx.x; j0 < n; j0 += stride) {
-        u32 p[kGather];
-#pragma unroll
-        for (int q = 0; q < kGather; ++q) {
-            const u32 j = j0 + q * kThreads;
-            p[q] = j < n ? __ldcs(perm + j) : 0u;
+// Coordinates and masses packed into 32-byte fixed-point records, in input order (coalesced).
+// A coordinate outside the fixed-point range raises CSTONE_ERR_INVALID_ARG.
+__global__ void __launch_bounds__(kThreads) multipole_pack_kernel(const double* __restrict__ x,
+                                                                  const double* __restrict__ y,
+                                                                  const double* __restrict__ z,
+                                                                  const float* __restrict__ m, u32 n,
+                                                                  const double* __restrict__ box, Record* rec,
+                                                                  WsHeader* hdr) {
+    __shared__ FixedFrame s_f;
+    if (threadIdx.x == 0) s_f = make_frame(box);
+    __syncthreads();
+    const FixedFrame f = s_f;
+    for (u32 p = blockIdx.x * kThreads + threadIdx.x; p < n; p += gridDim.x * kThreads) {
+        const double px = __ldcs(x + p), py = __ldcs(y + p), pz = __ldcs(z + p);
+        const int ex = static_cast<int>((static_cast<u64>(__double_as_longlong(px)) >> 52) & 0x7ffu);
+        const int ey = static_cast<int>((static_cast<u64>(__double_as_longlong(py)) >> 52) & 0x7ffu);
+        const int ez = static_cast<int>((static_cast<u64>(__double_as_longlong(pz)) >> 52) & 0x7ffu);
+        Record r;
+        if (max(ex, max(ey, ez)) >= f.e_lim) {
+            raise_error(hdr, CSTONE_ERR_INVALID_ARG, p);
+            r.x = r.y = r.z = 0;
+        } else {
+            r.x = fixed_of(px, f.F);
+            r.y = fixed_of(py, f.F);
+            r.z = fixed_of(pz, f.F);
         }
-        double px[kGather], py[kGather], pz[kGather];
-        float pm[kGather];
-#pragma unroll
-        for (int q = 0; q < kGather; ++q) {
-            px[q] = __ldg(x + p[q]);
-            py[q] = __ldg(y + p[q]);
-            pz[q] = __ldg(z + p[q]);
-            pm[q] = __ldg(m + p[q]);
-        }
-#pragma unroll
-        for (int q = 0; q < kGather; ++q) {
-            const u32 j = j0 + q * kThreads;
-            if (j < n) {
-                s.xs[j] = px[q];
-                s.ys[j] = py[q];
-                s.zs[j] = pz[q];
-                s.ms[j] = pm[q];
-            }
-        }
+        r.m = __ldcs(m + p);
+        r.pad = 0u;
+        rec[p] = r;
     }
 }
 
-// Leaf moments, one thread per leaf over its contiguous run of gathered particles: the centre of
-// mass from differences to the first particle, then the second moments about it.
-__global__ void __launch_bounds__(kThreads) multipole_leaf_kernel(const u32* __restrict__ offsets, u32 nl,
-                                                                  const int* __restrict__ leaf_to_node, u32 n_nodes,
-                                                                  MpScratch s, float* __restrict__ mass,
-                                                                  double* __restrict__ com,
-                                                                  float* __restrict__ quad) {
-    const u32 i = blockIdx.x * kThreads + threadIdx.x;
-    if (i >= nl) return;
-    const int v = leaf_to_node[i];
-    const u32 a = offsets[i], b = offsets[i + 1];
+// Leaf moments. A leaf is handled by a group of 8 lanes, each lane taking every 8th particle and
+// loading its 32-byte record through perm (the one random access of the upsweep; the second pass
+// over the same records hits L2), with the group's partial sums combined by shuffles: the centre
+// of mass from fixed-point differences to the leaf's first particle, then the second moments
+// about it.
+constexpr int kLeafThreads = 256;
+constexpr int kGroupLanes = 8;  // lanes per leaf
+
+__device__ __forceinline__ ff group_sum(ff v) {
+#pragma unroll
+    for (int s = kGroupLanes / 2; s >= 1; s >>= 1) {
+        ff o;
+        o.hi = __shfl_xor_sync(0xffffffffu, v.hi, s, kGroupLanes);
+        o.lo = __shfl_xor_sync(0xffffffffu, v.lo, s, kGroupLanes);
+        v = ff_add(v, o);
+    }
+    return v;
+}
+
+__global__ void __launch_bounds__(kLeafThreads) multipole_leaf_kernel(const u32* __restrict__ offsets, u32 nl,
+                                                                      const u32* __restrict__ perm,
+                                                                      const int* __restrict__ leaf_to_node,
+                                                                      u32 n_nodes, MpScratch s,
+                                                                      const double* __restrict__ box,
+                                                                      float* __restrict__ mass,
+                                                                      double* __restrict__ com,
+                                                                      float* __restrict__ quad) {
+    __shared__ FixedFrame s_f;
+    if (threadIdx.x == 0) s_f = make_frame(box);
+    __syncthreads();
+    const FixedFrame f = s_f;
+    const u32 gl = threadIdx.x % kGroupLanes;
+    const u32 i = (blockIdx.x * kLeafThreads + threadIdx.x) / kGroupLanes;
+    const bool active = i < nl;
+    const u32 a = active ? offsets[i] : 0u, b = active ? offsets[i + 1] : 0u;
+    u32 trips = (b - a + kGroupLanes - 1) / kGroupLanes;
+    for (int o = 16; o > 0; o >>= 1) trips = max(trips, __shfl_xor_sync(0xffffffffu, trips, o));
     ff M = ff_zero(), S[3] = {ff_zero(), ff_zero(), ff_zero()}, Q[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) Q[k] = ff_zero();
-    double c[3] = {0.0, 0.0, 0.0};
-    if (b > a) {
-        const double ax = s.xs[a], ay = s.ys[a], az = s.zs[a];
-        for (u32 j = a; j < b; ++j) {
-            const float mj = s.ms[j];
-            M = ff_add(M, mj);
-            S[0] = ff_add(S[0], __fmul_rn(mj, diff_f32(s.xs[j], ax)));
-            S[1] = ff_add(S[1], __fmul_rn(mj, diff_f32(s.ys[j], ay)));
-            S[2] = ff_add(S[2], __fmul_rn(mj, diff_f32(s.zs[j], az)));
+    Record r0{};
+    if (b > a) r0 = s.rec[__ldg(perm + a)];
+    for (u32 t = 0; t < trips; ++t) {
+        const u32 j = a + t * kGroupLanes + gl;
+        if (j < b) {
+            const Record r = s.rec[__ldg(perm + j)];
+            M = ff_add(M, r.m);
+            S[0] = ff_add(S[0], __fmul_rn(r.m, fixed_diff(r.x, r0.x, f)));
+            S[1] = ff_add(S[1], __fmul_rn(r.m, fixed_diff(r.y, r0.y, f)));
+            S[2] = ff_add(S[2], __fmul_rn(r.m, fixed_diff(r.z, r0.z, f)));
         }
+    }
+    M = group_sum(M);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) S[d] = group_sum(S[d]);
+    long long c[3] = {0, 0, 0};
+    if (b > a) {  // centre = anchor + S / M, rounded to the fixed-point grid
         const float Mv = ff_val(M);
-        c[0] = __dadd_rn(ax, (double)__fdiv_rn(ff_val(S[0]), Mv));
-        c[1] = __dadd_rn(ay, (double)__fdiv_rn(ff_val(S[1]), Mv));
-        c[2] = __dadd_rn(az, (double)__fdiv_rn(ff_val(S[2]), Mv));
-        for (u32 j = a; j < b; ++j) {
-            const float mj = s.ms[j];
-            const float e0 = diff_f32(s.xs[j], c[0]);
-            const float e1 = diff_f32(s.ys[j], c[1]);
-            const float e2 = diff_f32(s.zs[j], c[2]);
-            const float me0 = __fmul_rn(mj, e0), me1 = __fmul_rn(mj, e1), me2 = __fmul_rn(mj, e2);
+        const long long r0c[3] = {r0.x, r0.y, r0.z};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const float off = __fdiv_rn(ff_val(S[d]), Mv);
+            c[d] = r0c[d] + __float2ll_rn(__fmul_rn(__fmul_rn(off, 1.0f / f.s1), 1.0f / f.s2));
+        }
+    }
+    for (u32 t = 0; t < trips; ++t) {
+        const u32 j = a + t * kGroupLanes + gl;
+        if (j < b) {
+            const Record r = s.rec[__ldg(perm + j)];
+            const float e0 = fixed_diff(r.x, c[0], f);
+            const float e1 = fixed_diff(r.y, c[1], f);
+            const float e2 = fixed_diff(r.z, c[2], f);
+            const float me0 = __fmul_rn(r.m, e0), me1 = __fmul_rn(r.m, e1), me2 = __fmul_rn(r.m, e2);
             Q[0] = ff_add(Q[0], __fmul_rn(me0, e0));
             Q[1] = ff_add(Q[1], __fmul_rn(me0, e1));
             Q[2] = ff_add(Q[2], __fmul_rn(me0, e2));
@@ -194,85 +266,95 @@ __global__ void __launch_bounds__(kThreads) multipole_leaf_kernel(const u32* __r
             Q[5] = ff_add(Q[5], __fmul_rn(me2, e2));
         }
     }
-    store_node(v, n_nodes, M, c, Q, s, mass, com, quad);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) Q[k] = group_sum(Q[k]);
+    if (active && gl == 0) store_node(leaf_to_node[i], n_nodes, M, c, Q, s, f, mass, com, quad);
 }
 
-// Internal nodes: one thread per leaf climbs; the eighth arrival at a sibling group combines the
-// 8 children (in child order) into the parent with the parallel-axis shift.
-__global__ void __launch_bounds__(kThreads) multipole_climb_kernel(u32 nl, const int* __restrict__ leaf_to_node,
-                                                                   const int* __restrict__ parent, u32 n_nodes,
-                                                                   MpScratch s, float* __restrict__ mass,
-                                                                   double* __restrict__ com, float* __restrict__ quad,
-                                                                   u32* __restrict__ arrive) {
-    const u32 i = blockIdx.x * kThreads + threadIdx.x;
-    if (i >= nl) return;
-    int v = leaf_to_node[i];
-    while (v != 0) {
-        const u32 g = static_cast<u32>(v - 1) >> 3;
-        __threadfence();
-        if (atomicAdd(&arrive[g], 1u) != 7u) return;
-        __threadfence();
-        const int c0 = 1 + 8 * static_cast<int>(g);
-        ff Mc[8];
-        int anchor = -1;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const float2 mm = __ldcg(reinterpret_cast<const float2*>(s.mass) + c0 + k);
-            Mc[k] = {mm.x, mm.y};
-            if (anchor < 0 && (mm.x != 0.f || mm.y != 0.f)) anchor = k;
-        }
-        ff Mp = ff_zero(), Sp[3] = {ff_zero(), ff_zero(), ff_zero()}, Qp[6];
-#pragma unroll
-        for (int k = 0; k < 6; ++k) Qp[k] = ff_zero();
-        double cp[3] = {0.0, 0.0, 0.0};
-        if (anchor >= 0) {
-            double cc[8][3];
-#pragma unroll
-            for (int k = 0; k < 8; ++k)
-#pragma unroll
-                for (int d = 0; d < 3; ++d) cc[k][d] = __ldcg(com + (size_t)d * n_nodes + c0 + k);
-            double ca[3];
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                ca[d] = cc[0][d];
-#pragma unroll
-                for (int k = 1; k < 8; ++k)
-                    if (k == anchor) ca[d] = cc[k][d];
-            }
+// Internal nodes, level by level from the deepest: every internal node of a level combines its 8
+// children (in child order) with the parallel-axis shift; a grid barrier separates the levels.
+__global__ void __launch_bounds__(kThreads) multipole_level_kernel(const int* __restrict__ child,
+                                                                   const int* __restrict__ level_offsets, u32 n_nodes,
+                                                                   MpScratch s, const double* __restrict__ box,
+                                                                   float* __restrict__ mass, double* __restrict__ com,
+                                                                   float* __restrict__ quad, GridBarrier* bar,
+                                                                   WsHeader* hdr) {
+    __shared__ int s_lo[kNumLevels + 1];
+    __shared__ FixedFrame s_f;
+    if (threadIdx.x <= kNumLevels) s_lo[threadIdx.x] = level_offsets[threadIdx.x];
+    if (threadIdx.x == 0) s_f = make_frame(box);
+    __syncthreads();
+    const FixedFrame f = s_f;
+    const u32 gtid = blockIdx.x * kThreads + threadIdx.x, gthreads = gridDim.x * kThreads;
+    for (int l = kLevels - 1; l >= 0; --l) {
+        if (s_lo[l + 2] == s_lo[l + 1]) continue;  // no internal node at level l
+        for (u32 x = s_lo[l] + gtid; x < static_cast<u32>(s_lo[l + 1]); x += gthreads) {
+            const int c0 = child[x];
+            if (c0 == 0) continue;
+            ff Mc[8];
+            long long cc[8][3];
+            int anchor = -1;
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
-                Mp = ff_add(Mp, Mc[k]);
-                const float mk = ff_val(Mc[k]);
+                const float2 mm = __ldcg(reinterpret_cast<const float2*>(s.mass) + c0 + k);
+                Mc[k] = {mm.x, mm.y};
+                if (anchor < 0 && (mm.x != 0.f || mm.y != 0.f)) anchor = k;
 #pragma unroll
-                for (int d = 0; d < 3; ++d) Sp[d] = ff_add(Sp[d], __fmul_rn(mk, diff_f32(cc[k][d], ca[d])));
+                for (int d = 0; d < 3; ++d) cc[k][d] = __ldcg(s.cfix + (size_t)d * n_nodes + c0 + k);
             }
-            const float Mv = ff_val(Mp);
+            ff Mp = ff_zero(), Sp[3] = {ff_zero(), ff_zero(), ff_zero()}, Qp[6];
 #pragma unroll
-            for (int d = 0; d < 3; ++d) cp[d] = __dadd_rn(ca[d], (double)__fdiv_rn(ff_val(Sp[d]), Mv));
+            for (int k = 0; k < 6; ++k) Qp[k] = ff_zero();
+            long long cp[3] = {0, 0, 0};
+            if (anchor >= 0) {
+                long long ca[3];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                float e[3];
+                for (int d = 0; d < 3; ++d) {
+                    ca[d] = cc[0][d];
 #pragma unroll
-                for (int d = 0; d < 3; ++d) e[d] = diff_f32(cc[k][d], cp[d]);
-                const float mk = ff_val(Mc[k]);
-                const float me0 = __fmul_rn(mk, e[0]), me1 = __fmul_rn(mk, e[1]), me2 = __fmul_rn(mk, e[2]);
-                const float shift[6] = {__fmul_rn(me0, e[0]), __fmul_rn(me0, e[1]), __fmul_rn(me0, e[2]),
-                                        __fmul_rn(me1, e[1]), __fmul_rn(me1, e[2]), __fmul_rn(me2, e[2])};
+                    for (int k = 1; k < 8; ++k)
+                        if (k == anchor) ca[d] = cc[k][d];
+                }
 #pragma unroll
-                for (int q = 0; q < 6; ++q) {
-                    const float2 qq = __ldcg(reinterpret_cast<const float2*>(s.quad + (size_t)q * n_nodes) + c0 + k);
-                    Qp[q] = ff_add(Qp[q], ff{qq.x, qq.y});
-                    Qp[q] = ff_add(Qp[q], shift[q]);
+                for (int k = 0; k < 8; ++k) {
+                    Mp = ff_add(Mp, Mc[k]);
+                    const float mk = ff_val(Mc[k]);
+#pragma unroll
+                    for (int d = 0; d < 3; ++d)
+                        Sp[d] = ff_add(Sp[d], __fmul_rn(mk, fixed_diff(cc[k][d], ca[d], f)));
+                }
+                const float Mv = ff_val(Mp);
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    const float off = __fdiv_rn(ff_val(Sp[d]), Mv);
+                    cp[d] = ca[d] + __float2ll_rn(__fmul_rn(__fmul_rn(off, 1.0f / f.s1), 1.0f / f.s2));
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    float e[3];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) e[d] = fixed_diff(cc[k][d], cp[d], f);
+                    const float mk = ff_val(Mc[k]);
+                    const float me0 = __fmul_rn(mk, e[0]), me1 = __fmul_rn(mk, e[1]), me2 = __fmul_rn(mk, e[2]);
+                    const float shift[6] = {__fmul_rn(me0, e[0]), __fmul_rn(me0, e[1]), __fmul_rn(me0, e[2]),
+                                            __fmul_rn(me1, e[1]), __fmul_rn(me1, e[2]), __fmul_rn(me2, e[2])};
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) {
+                        const float2 qq =
+                            __ldcg(reinterpret_cast<const float2*>(s.quad + (size_t)q * n_nodes) + c0 + k);
+                        Qp[q] = ff_add(Qp[q], ff{qq.x, qq.y});
+                        Qp[q] = ff_add(Qp[q], shift[q]);
+                    }
                 }
             }
+            store_node(static_cast<int>(x), n_nodes, Mp, cp, Qp, s, f, mass, com, quad);
         }
-        v = parent[g];
-        store_node(v, n_nodes, Mp, cp, Qp, s, mass, com, quad);
+        grid_barrier(bar, hdr);
     }
 }
 
 struct UpLayout {
-    u32* arrive;
+    GridBarrier* bar;
     MpScratch mp;
     size_t bytes;
 };
@@ -280,17 +362,14 @@ struct UpLayout {
 UpLayout up_layout(void* ws, long long nl, long long n_particles, bool multipoles) {
     UpLayout l;
     Carver c(ws);
-    long long ni = (nl - 1) / 7;
-    long long nn = nl + ni;
-    l.arrive = c.take<u32>((size_t)(ni > 0 ? ni : 1));
+    const long long nn = nl + (nl - 1) / 7;
+    l.bar = c.take<GridBarrier>(1);
     l.mp = MpScratch{};
     if (multipoles) {
         l.mp.mass = c.take<ff>((size_t)nn);
         l.mp.quad = c.take<ff>((size_t)nn * 6);
-        l.mp.xs = c.take<double>((size_t)n_particles);
-        l.mp.ys = c.take<double>((size_t)n_particles);
-        l.mp.zs = c.take<double>((size_t)n_particles);
-        l.mp.ms = c.take<float>((size_t)n_particles);
+        l.mp.cfix = c.take<long long>((size_t)nn * 3);
+        l.mp.rec = c.take<Record>((size_t)(n_particles > 0 ? n_particles : 1));
     }
     l.bytes = c.size();
     return l;
@@ -301,41 +380,49 @@ UpLayout up_layout(void* ws, long long nl, long long n_particles, bool multipole
 size_t upsweep_ws_bytes(long long nl) { return up_layout(nullptr, nl, 0, false).bytes; }
 size_t multipole_ws_bytes(long long nl, long long n) { return up_layout(nullptr, nl, n, true).bytes; }
 
-int launch_upsweep_counts(const u32* leaf_counts, long long nl, const int* leaf_to_node, const int* parent,
-                          u32* node_counts, void* ws, cudaStream_t st) {
+int launch_upsweep_counts(const u32* leaf_counts, long long nl, const int* leaf_to_node, const int* child,
+                          const int* level_offsets, u32* node_counts, void* ws, cudaStream_t st) {
     UpLayout l = up_layout(ws, nl, 0, false);
-    long long ni = (nl - 1) / 7;
-    CST_CUDA(cudaMemsetAsync(ws, 0, sizeof(WsHeader), st));
-    if (ni > 0) CST_CUDA(cudaMemsetAsync(l.arrive, 0, (size_t)ni * sizeof(u32), st));
-    unsigned grid = static_cast<unsigned>((nl + kThreads - 1) / kThreads);
-    upsweep_counts_kernel<<<grid, kThreads, 0, st>>>(leaf_counts, static_cast<u32>(nl), leaf_to_node, parent,
-                                                     node_counts, l.arrive);
-    CST_LAUNCHED("upsweep_counts_kernel");
+    WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
+    CST_CUDA(cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st));
+    CST_CUDA(cudaMemsetAsync(l.bar, 0, sizeof(GridBarrier), st));
+    u32 nl_ = static_cast<u32>(nl);
+    GridBarrier* bar = l.bar;
+    void* args[] = {&leaf_counts, &nl_, &leaf_to_node, &child, &level_offsets, &node_counts, &bar, &hdr};
+    const int grid = cooperative_grid(reinterpret_cast<const void*>(upsweep_counts_kernel), kThreads, 0, 4);
+    CST_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(upsweep_counts_kernel), dim3(grid), dim3(kThreads),
+                                         args, 0, st));
     return CSTONE_OK;
 }
 
 int launch_upsweep_multipoles(const double* x, const double* y, const double* z, const float* m, const u32* perm,
-                              long long n, const u32* offsets, long long nl, const int* leaf_to_node, const int* parent,
-                              float* mass, double* com, float* quad, void* ws, cudaStream_t st) {
+                              long long n, const u32* offsets, long long nl, const int* leaf_to_node, const int* child,
+                              const int* level_offsets, const double* box, float* mass, double* com, float* quad,
+                              void* ws, cudaStream_t st) {
     UpLayout l = up_layout(ws, nl, n, true);
-    long long ni = (nl - 1) / 7;
-    CST_CUDA(cudaMemsetAsync(ws, 0, sizeof(WsHeader), st));
-    if (ni > 0) CST_CUDA(cudaMemsetAsync(l.arrive, 0, (size_t)ni * sizeof(u32), st));
-    unsigned grid = static_cast<unsigned>((nl + kThreads - 1) / kThreads);
-    const u32 nn = static_cast<u32>(nl + ni);
+    WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
+    CST_CUDA(cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st));
+    CST_CUDA(cudaMemsetAsync(l.bar, 0, sizeof(GridBarrier), st));
+    const u32 nn = static_cast<u32>(nl + (nl - 1) / 7);
     if (n > 0) {
-        long long want = (n + (long long)kThreads * kGather - 1) / ((long long)kThreads * kGather);
-        int ggrid = static_cast<int>(want < (long long)sm_count() * 16 ? want : (long long)sm_count() * 16);
-        multipole_gather_kernel<<<ggrid, kThreads, 0, st>>>(x, y, z, m, perm, static_cast<u32>(n), l.mp);
-        CST_LAUNCHED("multipole_gather_kernel");
+        long long want = (n + kThreads - 1) / kThreads;
+        int pgrid = static_cast<int>(want < (long long)sm_count() * 8 ? want : (long long)sm_count() * 8);
+        multipole_pack_kernel<<<pgrid, kThreads, 0, st>>>(x, y, z, m, static_cast<u32>(n), box, l.mp.rec, hdr);
+        CST_LAUNCHED("multipole_pack_kernel");
     }
-    multipole_leaf_kernel<<<grid, kThreads, 0, st>>>(offsets, static_cast<u32>(nl), leaf_to_node, nn, l.mp, mass, com,
-                                                     quad);
+    const long long groups_per_block = kLeafThreads / kGroupLanes;
+    unsigned lgrid = static_cast<unsigned>((nl + groups_per_block - 1) / groups_per_block);
+    multipole_leaf_kernel<<<lgrid, kLeafThreads, 0, st>>>(offsets, static_cast<u32>(nl), perm, leaf_to_node, nn, l.mp,
+                                                          box, mass, com, quad);
     CST_LAUNCHED("multipole_leaf_kernel");
-    if (ni > 0) {
-        multipole_climb_kernel<<<grid, kThreads, 0, st>>>(static_cast<u32>(nl), leaf_to_node, parent, nn, l.mp, mass,
-                                                          com, quad, l.arrive);
-        CST_LAUNCHED("multipole_climb_kernel");
+    if (nl > 1) {
+        u32 nn_ = nn;
+        MpScratch mp = l.mp;
+        GridBarrier* bar = l.bar;
+        void* args[] = {&child, &level_offsets, &nn_, &mp, &box, &mass, &com, &quad, &bar, &hdr};
+        const int grid = cooperative_grid(reinterpret_cast<const void*>(multipole_level_kernel), kThreads, 0, 4);
+        CST_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(multipole_level_kernel), dim3(grid),
+                                             dim3(kThreads), args, 0, st));
     }
     return CSTONE_OK;
 }
@@ -352,12 +439,13 @@ int cstone_upsweep_workspace_size(int64_t n_leaves, size_t* bytes) {
 }
 
 int cstone_upsweep_counts(const uint32_t* leaf_counts, int64_t n_leaves, const int32_t* leaf_to_node,
-                          const int32_t* parent, uint32_t* node_counts, void* ws, size_t ws_bytes, void* stream) {
+                          const int32_t* child, const int32_t* level_offsets, uint32_t* node_counts, void* ws,
+                          size_t ws_bytes, void* stream) {
     if (n_leaves < 1 || n_leaves > CSTONE_MAX_LEAVES || (n_leaves - 1) % 7 != 0 || !leaf_counts || !leaf_to_node ||
-        !node_counts || (n_leaves > 1 && !parent))
+        !child || !level_offsets || !node_counts)
         return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_upsweep_counts: bad argument");
     if (int rc = cst::check_ws(ws, ws_bytes, cst::upsweep_ws_bytes(n_leaves), "cstone_upsweep_counts")) return rc;
-    return cst::launch_upsweep_counts(leaf_counts, n_leaves, leaf_to_node, parent, node_counts, ws,
+    return cst::launch_upsweep_counts(leaf_counts, n_leaves, leaf_to_node, child, level_offsets, node_counts, ws,
                                       cst::as_stream(stream));
 }
 
@@ -370,17 +458,17 @@ int cstone_multipole_workspace_size(int64_t n, int64_t n_leaves, size_t* bytes) 
 
 int cstone_upsweep_multipoles(const double* x, const double* y, const double* z, const float* m,
                               const uint32_t* perm, int64_t n, const uint32_t* offsets, int64_t n_leaves,
-                              const int32_t* leaf_to_node, const int32_t* parent, const int32_t* child,
-                              float* mass, double* com, float* quad, void* ws, size_t ws_bytes, void* stream) {
-    (void)child;
+                              const int32_t* leaf_to_node, const int32_t* child, const int32_t* level_offsets,
+                              const double* box, float* mass, double* com, float* quad, void* ws, size_t ws_bytes,
+                              void* stream) {
     if (n < 0 || n >= CSTONE_MAX_PARTICLES || n_leaves < 1 || n_leaves > CSTONE_MAX_LEAVES ||
-        (n_leaves - 1) % 7 != 0 || !offsets || !leaf_to_node || !mass || !com || !quad ||
-        (n > 0 && (!x || !y || !z || !m || !perm)) || (n_leaves > 1 && !parent))
+        (n_leaves - 1) % 7 != 0 || !offsets || !leaf_to_node || !child || !level_offsets || !mass || !com || !quad ||
+        !box || (n > 0 && (!x || !y || !z || !m || !perm)))
         return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_upsweep_multipoles: bad argument");
     if (int rc = cst::check_ws(ws, ws_bytes, cst::multipole_ws_bytes(n_leaves, n), "cstone_upsweep_multipoles"))
         return rc;
-    return cst::launch_upsweep_multipoles(x, y, z, m, perm, n, offsets, n_leaves, leaf_to_node, parent, mass, com, quad,
-                                          ws, cst::as_stream(stream));
+    return cst::launch_upsweep_multipoles(x, y, z, m, perm, n, offsets, n_leaves, leaf_to_node, child, level_offsets,
+                                          box, mass, com, quad, ws, cst::as_stream(stream));
 }
 
 }  // extern "C"

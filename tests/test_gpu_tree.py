@@ -125,7 +125,7 @@ def test_link_and_counts_bit_exact(lib, oracle, kind, n, ncrit):
     nn = ref["NK"].size
     assert np.array_equal(i32(parent)[: (nn - 1) // 8], ref["parent"])
     counts = torch.empty(nn, dtype=torch.int32, device="cuda")
-    lib.cstone_upsweep_counts(dev(N.astype(np.uint32)), K.size - 1, l2n, parent, counts)
+    lib.cstone_upsweep_counts(dev(N.astype(np.uint32)), K.size - 1, l2n, CO, LO, counts)
     assert np.array_equal(u32(counts), oracle.node_counts(P, ref["NK"]))
 
 
