@@ -105,6 +105,26 @@ CSTONE_API int cstone_sort(const uint64_t* keys_in, uint64_t* keys_out, uint32_t
                 void* stream);
 
 /* ------------------------------------------------------------------------------------------
+ * Sort that allocates nothing (the paper has no counterpart; this is a deployment variant of
+ * cstone_sort with the same result). It is for callers that cannot call cudaMalloc and cannot
+ * hand out a workspace: code that runs inside a memory allocator's own callbacks, or inside a
+ * framework that owns and budgets all device memory of the process, where a new allocation is
+ * not allowed. Its scratch is a fixed static device array inside this library (about 13 MB,
+ * held on every GPU that loads the library until the process exits), so n is limited to
+ * CSTONE_SORT_STATIC_MAX_KEYS; a larger n returns CSTONE_ERR_INVALID_ARG without touching the
+ * GPU. The first call on a device looks up the array's device address (cudaGetSymbolAddress):
+ * make that first call before any stream capture. All calls share the one array, so calls that
+ * can overlap on the GPU (other streams, other host threads) race and must be serialised by the
+ * caller. Each call clears what has to start at zero; otherwise the array keeps the last call's
+ * contents. A look-back timeout, which only a GPU that cannot keep the launched tiles resident
+ * could cause, is not reported by this variant: the output is then invalid.
+ *   keys_in, keys_out, perm, n, stream: as for cstone_sort. Asynchronous.
+ * ------------------------------------------------------------------------------------------ */
+#define CSTONE_SORT_STATIC_MAX_KEYS ((int64_t)1 << 20)
+CSTONE_API int cstone_sort_static(const uint64_t* keys_in, uint64_t* keys_out, uint32_t* perm, int64_t n,
+                                  void* stream);
+
+/* ------------------------------------------------------------------------------------------
  * Cornerstone leaf array (Sec. 4, Eqs. cstone, histogram, g1-g3): starting from the root
  * {0, 8^L} (when *n_leaves == 0 on entry) or from the caller's array in `leaves` (when
  * *n_leaves > 0: warm start from a previous step's leaves, Sec. 4), apply the histogram f and

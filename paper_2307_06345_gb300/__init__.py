@@ -68,6 +68,7 @@ def load():
             "cstone_keys": (ctypes.c_int, [P, P, P, i64, P, ctypes.c_int, P, P]),
             "cstone_sort_workspace_size": (ctypes.c_int, [i64, psz]),
             "cstone_sort": (ctypes.c_int, [P, P, P, i64, P, sz, P]),
+            "cstone_sort_static": (ctypes.c_int, [P, P, P, i64, P]),
             "cstone_leaves_workspace_size": (ctypes.c_int, [i64, i64, i32, psz]),
             "cstone_build_leaves": (ctypes.c_int, [P, i64, u32, P, i64, pi64, P, P, i32, pi32, P, sz, P]),
             "cstone_link_workspace_size": (ctypes.c_int, [i64, psz]),
@@ -171,6 +172,17 @@ def cstone_sort(keys_in, keys_out, perm, ws: Workspace, stream=None):
     buf = ws.get(_size(lib.cstone_sort_workspace_size, n))
     _check(lib.cstone_sort(_ptr(keys_in), _ptr(keys_out), _ptr(perm), n, _ptr(buf), buf.numel(), _stream(stream)),
            "cstone_sort")
+
+
+def cstone_sort_static(keys_in, keys_out, perm, stream=None):
+    """Sort without any device allocation: scratch is a static array inside the library, so at most
+    2^20 keys, and calls must not overlap on the GPU (see include/cstone.h)."""
+    lib = load()
+    _need(keys_in, torch.int64, "keys_in")
+    _need(keys_out, torch.int64, "keys_out")
+    _need(perm, torch.int32, "perm")
+    _check(lib.cstone_sort_static(_ptr(keys_in), _ptr(keys_out), _ptr(perm), keys_in.numel(), _stream(stream)),
+           "cstone_sort_static")
 
 
 def cstone_build_leaves(sorted_keys, ncrit: int, leaves, counts, offsets=None, n_leaves: int = 0,

@@ -14,6 +14,8 @@
 // prefix) and a 30-bit count, which bounds n below 2^30. Two look-back regions alternate between
 // passes; every tile clears its row of the other region (written by the previous pass) so that the
 // next pass finds it empty, and only the first region needs a memset per sort.
+#include <mutex>
+
 #include "common.cuh"
 
 namespace cst {
@@ -264,6 +266,43 @@ SortLayout sort_layout(void* ws, long long n) {
 
 size_t sort_ws_bytes(long long n) { return sort_layout(nullptr, n).bytes; }
 
+// ---------------------------------------------------------------- sort without allocation
+// Scratch of cstone_sort_static: the same layout as the caller workspace of cstone_sort, sized for
+// CSTONE_SORT_STATIC_MAX_KEYS keys, held in a file-scope device array that every GPU loading the
+// library keeps until the process exits.
+namespace {
+constexpr size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+constexpr long long kStaticKeys = CSTONE_SORT_STATIC_MAX_KEYS;
+constexpr size_t kStaticTiles = static_cast<size_t>((kStaticKeys + kTile - 1) / kTile);
+constexpr size_t kStaticBytes = sizeof(WsHeader) + round256(sizeof(SortCtl)) + 2 * round256(kStaticTiles * kRadix * 4) +
+                                round256(static_cast<size_t>(kStaticKeys) * 8) +
+                                round256(static_cast<size_t>(kStaticKeys) * 4);
+
+__device__ __align__(256) unsigned char g_sort_scratch[kStaticBytes];
+
+std::mutex g_static_mutex;
+constexpr int kMaxDevices = 64;
+void* g_static_scratch[kMaxDevices] = {};
+
+// Device address of g_sort_scratch on the current device, looked up once per device. In host code
+// the array's name is only a host-side stand-in, never a device address.
+int static_sort_scratch(void** out) {
+    int dev = 0;
+    CST_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices)
+        return fail(CSTONE_ERR_INVALID_ARG, "cstone_sort_static: device ordinal %d not supported", dev);
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (g_static_scratch[dev] == nullptr) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_sort_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_sort_scratch)");
+        g_static_scratch[dev] = p;
+    }
+    *out = g_static_scratch[dev];
+    return CSTONE_OK;
+}
+}  // namespace
+
 int launch_sort(const u64* keys_in, u64* keys_out, u32* perm, long long n, void* ws, cudaStream_t st) {
     SortLayout l = sort_layout(ws, n);
     WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
@@ -320,6 +359,22 @@ int cstone_sort(const uint64_t* keys_in, uint64_t* keys_out, uint32_t* perm, int
     if (n < 0 || n >= CSTONE_MAX_PARTICLES || (n > 0 && (!keys_in || !keys_out || !perm)))
         return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_sort: bad argument (n=%lld)", (long long)n);
     if (int rc = cst::check_ws(ws, ws_bytes, cst::sort_ws_bytes(n), "cstone_sort")) return rc;
+    return cst::launch_sort(reinterpret_cast<const cst::u64*>(keys_in), reinterpret_cast<cst::u64*>(keys_out), perm,
+                            n, ws, cst::as_stream(stream));
+}
+
+int cstone_sort_static(const uint64_t* keys_in, uint64_t* keys_out, uint32_t* perm, int64_t n, void* stream) {
+    if (n < 0 || (n > 0 && (!keys_in || !keys_out || !perm)))
+        return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_sort_static: bad argument (n=%lld)", (long long)n);
+    if (n > CSTONE_SORT_STATIC_MAX_KEYS)
+        return cst::fail(CSTONE_ERR_INVALID_ARG,
+                         "cstone_sort_static: n=%lld exceeds the static scratch limit of %lld keys; use cstone_sort "
+                         "with a workspace",
+                         (long long)n, (long long)CSTONE_SORT_STATIC_MAX_KEYS);
+    if (cst::sort_ws_bytes(n) > cst::kStaticBytes)
+        return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_sort_static: static scratch too small");
+    void* ws = nullptr;
+    if (int rc = cst::static_sort_scratch(&ws)) return rc;
     return cst::launch_sort(reinterpret_cast<const cst::u64*>(keys_in), reinterpret_cast<cst::u64*>(keys_out), perm,
                             n, ws, cst::as_stream(stream));
 }
