@@ -204,6 +204,69 @@ CSTONE_API int cstone_upsweep_multipoles(const double* x, const double* y, const
                                          const int32_t* level_offsets, const double* box, float* mass, double* com,
                                          float* quad, void* ws, size_t ws_bytes, void* stream);
 
+/* ==========================================================================================
+ * Batched builds: S independent particle sets stored back to back (set s owns particles
+ * [set_offsets[s], set_offsets[s+1])), built with one launch per phase for all sets. The
+ * per-set results equal those of the single-set entry points on each set alone. Offsets arrays
+ * named *_offsets are DEVICE int64 arrays of S+1 entries.
+ * ========================================================================================== */
+
+/* Bounding cube of every set: boxes [S][4] float64 (device) output. Asynchronous. */
+CSTONE_API int cstone_bbox_batched(const double* x, const double* y, const double* z, const int64_t* set_offsets,
+                                   int32_t n_sets, double* boxes, void* stream);
+
+/* Keys of all particles, each with its own set's box (boxes [S][4], device). Asynchronous. */
+CSTONE_API int cstone_keys_batched_workspace_size(int32_t n_sets, size_t* bytes);
+CSTONE_API int cstone_keys_batched(const double* x, const double* y, const double* z, int64_t n,
+                                   const int64_t* set_offsets, int32_t n_sets, const double* boxes, int curve,
+                                   uint64_t* keys, void* ws, size_t ws_bytes, void* stream);
+
+/* Stable sort of every segment's keys (segments given by seg_offsets), one launch per digit pass
+ * for all segments: tiles are aligned to segments and the look-back stops at a segment's first
+ * tile. perm holds global input indices. keys_in must not alias keys_out. Asynchronous. */
+CSTONE_API int cstone_sort_segmented_workspace_size(int64_t n, int32_t n_segs, size_t* bytes);
+CSTONE_API int cstone_sort_segmented(const uint64_t* keys_in, uint64_t* keys_out, uint32_t* perm, int64_t n,
+                                     const int64_t* seg_offsets, int32_t n_segs, void* ws, size_t ws_bytes,
+                                     void* stream);
+
+/* Cornerstone arrays of all sets (Sec. 4) in one cooperative launch. The arrays are stored back to
+ * back as "elements": set s owns elements [element_offsets[s], element_offsets[s+1]), its leaves
+ * followed by its end key 8^L, so set s has element_offsets[s+1] - element_offsets[s] - 1 leaves.
+ *   sorted_keys   [n] keys sorted within each set (cstone_sort_segmented).
+ *   elements      [elem_cap] uint64 in/out: on entry the previous arrays when *n_elements > 0
+ *                 (warm start, with element_offsets filled in), else ignored (every set starts
+ *                 from its root).
+ *   element_offsets [S+1] int64 device in/out.
+ *   n_elements    host in/out: elements on entry (0 = cold), on exit; on CSTONE_ERR_CAPACITY the
+ *                 number of elements that did not fit.
+ *   counts        [elem_cap] uint32: leaf counts (0 at end keys); offsets [elem_cap] uint32 (may be
+ *                 NULL): first sorted particle (global index) of each element.
+ * Synchronises `stream`. */
+CSTONE_API int cstone_leaves_batched_workspace_size(int64_t elem_cap, int32_t max_iters, size_t* bytes);
+CSTONE_API int cstone_build_leaves_batched(const uint64_t* sorted_keys, int64_t n, const int64_t* set_offsets,
+                                           int32_t n_sets, uint32_t ncrit, uint64_t* elements, int64_t elem_cap,
+                                           int64_t* element_offsets, int64_t* n_elements, uint32_t* counts,
+                                           uint32_t* offsets, int32_t max_iters, int32_t* iters, void* ws,
+                                           size_t ws_bytes, void* stream);
+
+/* Linked octrees of all sets (Sec. 5), concatenated: set s's tree is one breadth-first block of
+ * the node arrays, from level_offsets[s][0] to level_offsets[s][22]. All indices (child,
+ * level_offsets [S][23], leaf_to_node [n_elements], -1 at end keys) are global node indices.
+ * n_nodes = sum over sets of n_l + (n_l - 1) / 7. A set whose node count disagrees (input not a
+ * cornerstone array) is reported through the workspace error word. Asynchronous. */
+CSTONE_API int cstone_link_batched_workspace_size(int64_t n_elements, int32_t n_sets, size_t* bytes);
+CSTONE_API int cstone_link_tree_batched(const uint64_t* elements, int64_t n_elements, const int64_t* element_offsets,
+                                        int32_t n_sets, int64_t n_nodes, uint64_t* node_keys, int32_t* child,
+                                        int32_t* level_offsets, int32_t* leaf_to_node, void* ws, size_t ws_bytes,
+                                        void* stream);
+
+/* Node counts of all sets' trees (at most 4096 sets); elem_counts from
+ * cstone_build_leaves_batched. Workspace: cstone_upsweep_workspace_size(1). Asynchronous. */
+CSTONE_API int cstone_upsweep_counts_batched(const uint32_t* elem_counts, int64_t n_elements,
+                                             const int32_t* leaf_to_node, const int32_t* child,
+                                             const int32_t* level_offsets, int32_t n_sets, uint32_t* node_counts,
+                                             void* ws, size_t ws_bytes, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

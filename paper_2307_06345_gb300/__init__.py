@@ -23,7 +23,9 @@ from . import _build
 __all__ = [
     "MORTON", "HILBERT", "CstoneError", "load", "build", "cstone_bbox", "cstone_keys", "cstone_sort",
     "cstone_build_leaves", "cstone_link_tree", "cstone_upsweep_counts", "cstone_upsweep_multipoles",
-    "build_octree", "Workspace", "leaf_capacity", "n_nodes",
+    "build_octree", "Workspace", "leaf_capacity", "n_nodes", "cstone_sort_static", "cstone_bbox_batched",
+    "cstone_keys_batched", "cstone_sort_segmented", "cstone_build_leaves_batched", "cstone_link_tree_batched",
+    "cstone_upsweep_counts_batched", "build_octrees_batched",
 ]
 
 MORTON, HILBERT = 0, 1
@@ -77,6 +79,17 @@ def load():
             "cstone_upsweep_counts": (ctypes.c_int, [P, i64, P, P, P, P, P, sz, P]),
             "cstone_multipole_workspace_size": (ctypes.c_int, [i64, i64, psz]),
             "cstone_upsweep_multipoles": (ctypes.c_int, [P, P, P, P, P, i64, P, i64, P, P, P, P, P, P, P, P, sz, P]),
+            "cstone_bbox_batched": (ctypes.c_int, [P, P, P, P, i32, P, P]),
+            "cstone_keys_batched_workspace_size": (ctypes.c_int, [i32, psz]),
+            "cstone_keys_batched": (ctypes.c_int, [P, P, P, i64, P, i32, P, ctypes.c_int, P, P, sz, P]),
+            "cstone_sort_segmented_workspace_size": (ctypes.c_int, [i64, i32, psz]),
+            "cstone_sort_segmented": (ctypes.c_int, [P, P, P, i64, P, i32, P, sz, P]),
+            "cstone_leaves_batched_workspace_size": (ctypes.c_int, [i64, i32, psz]),
+            "cstone_build_leaves_batched": (ctypes.c_int, [P, i64, P, i32, u32, P, i64, P, pi64, P, P, i32, pi32, P,
+                                                          sz, P]),
+            "cstone_link_batched_workspace_size": (ctypes.c_int, [i64, i32, psz]),
+            "cstone_link_tree_batched": (ctypes.c_int, [P, i64, P, i32, i64, P, P, P, P, P, sz, P]),
+            "cstone_upsweep_counts_batched": (ctypes.c_int, [P, i64, P, P, P, i32, P, P, sz, P]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(lib, name)
@@ -358,8 +371,166 @@ def build_octree(x, y, z, curve: int = HILBERT, ncrit: int = 64, box=None, masse
     return out
 
 
+# ------------------------------------------------------------------------- batched sets
+def cstone_bbox_batched(x, y, z, set_offsets, boxes, stream=None):
+    _check(load().cstone_bbox_batched(_ptr(x), _ptr(y), _ptr(z), _ptr(set_offsets), set_offsets.numel() - 1,
+                                      _ptr(boxes), _stream(stream)), "cstone_bbox_batched")
+
+
+def cstone_keys_batched(x, y, z, set_offsets, boxes, curve: int, keys, ws: Workspace, stream=None):
+    lib = load()
+    s = set_offsets.numel() - 1
+    buf = ws.get(_size(lib.cstone_keys_batched_workspace_size, s))
+    _check(lib.cstone_keys_batched(_ptr(x), _ptr(y), _ptr(z), x.numel(), _ptr(set_offsets), s, _ptr(boxes), curve,
+                                   _ptr(keys), _ptr(buf), buf.numel(), _stream(stream)), "cstone_keys_batched")
+
+
+def cstone_sort_segmented(keys_in, keys_out, perm, seg_offsets, ws: Workspace, stream=None):
+    lib = load()
+    n, s = keys_in.numel(), seg_offsets.numel() - 1
+    buf = ws.get(_size(lib.cstone_sort_segmented_workspace_size, n, s))
+    _check(lib.cstone_sort_segmented(_ptr(keys_in), _ptr(keys_out), _ptr(perm), n, _ptr(seg_offsets), s, _ptr(buf),
+                                     buf.numel(), _stream(stream)), "cstone_sort_segmented")
+
+
+def cstone_build_leaves_batched(sorted_keys, set_offsets, ncrit: int, elements, element_offsets, counts,
+                                offsets=None, n_elements: int = 0, max_iters: int = 64, ws: Workspace | None = None,
+                                stream=None):
+    """Returns (n_elements, iterations)."""
+    lib = load()
+    ws = ws or Workspace(sorted_keys.device)
+    cap = elements.numel()
+    buf = ws.get(_size(lib.cstone_leaves_batched_workspace_size, cap, max_iters))
+    ne = ctypes.c_int64(n_elements)
+    it = ctypes.c_int32(0)
+    rc = lib.cstone_build_leaves_batched(_ptr(sorted_keys), sorted_keys.numel(), _ptr(set_offsets),
+                                         set_offsets.numel() - 1, ncrit, _ptr(elements), cap, _ptr(element_offsets),
+                                         ctypes.byref(ne), _ptr(counts), _ptr(offsets), max_iters, ctypes.byref(it),
+                                         _ptr(buf), buf.numel(), _stream(stream))
+    if rc == ERR_CAPACITY:
+        err = CstoneError(rc, "cstone_build_leaves_batched", _detail())
+        err.required = int(ne.value)
+        raise err
+    _check(rc, "cstone_build_leaves_batched")
+    return int(ne.value), int(it.value)
+
+
+def cstone_link_tree_batched(elements, n_elements: int, element_offsets, n_nodes: int, node_keys, child,
+                             level_offsets, leaf_to_node, ws: Workspace | None = None, stream=None):
+    lib = load()
+    ws = ws or Workspace(elements.device)
+    s = element_offsets.numel() - 1
+    buf = ws.get(_size(lib.cstone_link_batched_workspace_size, n_elements, s))
+    _check(lib.cstone_link_tree_batched(_ptr(elements), n_elements, _ptr(element_offsets), s, n_nodes,
+                                        _ptr(node_keys), _ptr(child), _ptr(level_offsets), _ptr(leaf_to_node),
+                                        _ptr(buf), buf.numel(), _stream(stream)), "cstone_link_tree_batched")
+
+
+def cstone_upsweep_counts_batched(elem_counts, n_elements: int, leaf_to_node, child, level_offsets, n_sets: int,
+                                  node_counts, ws: Workspace | None = None, stream=None):
+    lib = load()
+    ws = ws or Workspace(elem_counts.device)
+    buf = ws.get(_size(lib.cstone_upsweep_workspace_size, 1))
+    _check(lib.cstone_upsweep_counts_batched(_ptr(elem_counts), n_elements, _ptr(leaf_to_node), _ptr(child),
+                                             _ptr(level_offsets), n_sets, _ptr(node_counts), _ptr(buf), buf.numel(),
+                                             _stream(stream)), "cstone_upsweep_counts_batched")
+
+
+def build_octrees_batched(x, y, z, set_offsets, curve: int = MORTON, ncrit: int = 32, boxes=None, warm=None,
+                          max_iters: int = 64, ws: Workspace | None = None, stream=None):
+    """Octrees of many independent sets stored back to back, one launch per phase for all sets.
+
+    ``set_offsets``: int64 CUDA tensor of S+1 particle offsets. ``boxes``: float64 CUDA tensor [S, 4]
+    (bounding cubes are computed when None). ``warm``: a previous result of this function for the
+    same sets (its elements and element offsets warm-start the leaf loop). Returns a dict with the
+    concatenated per-set outputs and host copies of the element and node offsets."""
+    dev = x.device
+    n = x.numel()
+    s = set_offsets.numel() - 1
+    ws = ws or Workspace(dev)
+    if boxes is None:
+        boxes = torch.empty((s, 4), dtype=torch.float64, device=dev)
+        cstone_bbox_batched(x, y, z, set_offsets, boxes, stream)
+    keys = torch.empty(n, dtype=torch.int64, device=dev)
+    cstone_keys_batched(x, y, z, set_offsets, boxes, curve, keys, ws, stream)
+    sorted_keys = torch.empty_like(keys)
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    cstone_sort_segmented(keys, sorted_keys, perm, set_offsets, ws, stream)
+    cap = max(4 * s, 16 * (n // (ncrit + 1)) + 2 * s + 4096)
+    if warm is not None:
+        cap = max(cap, 2 * warm["n_elements"])
+    while True:
+        elements = torch.empty(cap, dtype=torch.int64, device=dev)
+        element_offsets = torch.empty(s + 1, dtype=torch.int64, device=dev)
+        counts = torch.empty(cap, dtype=torch.int32, device=dev)
+        offsets = torch.empty(cap, dtype=torch.int32, device=dev)
+        ne0 = 0
+        if warm is not None:
+            ne0 = warm["n_elements"]
+            elements[:ne0].copy_(warm["elements"][:ne0])
+            element_offsets.copy_(warm["element_offsets"])
+        try:
+            ne, iters = cstone_build_leaves_batched(sorted_keys, set_offsets, ncrit, elements, element_offsets, counts,
+                                                    offsets, ne0, max_iters, ws, stream)
+            break
+        except CstoneError as e:
+            if e.status != ERR_CAPACITY:
+                raise
+            cap = max(2 * cap, getattr(e, "required", 0) + 1024)
+    eo_host = element_offsets.cpu().tolist()
+    nl = [eo_host[i + 1] - eo_host[i] - 1 for i in range(s)]
+    nn = [v + (v - 1) // 7 for v in nl]
+    node_offsets = [0]
+    for v in nn:
+        node_offsets.append(node_offsets[-1] + v)
+    n_nodes = node_offsets[-1]
+    NK = torch.empty(n_nodes, dtype=torch.int64, device=dev)
+    CO = torch.empty(n_nodes, dtype=torch.int32, device=dev)
+    LO = torch.empty((s, LEVELS + 2), dtype=torch.int32, device=dev)
+    l2n = torch.empty(ne, dtype=torch.int32, device=dev)
+    cstone_link_tree_batched(elements, ne, element_offsets, n_nodes, NK, CO, LO, l2n, ws, stream)
+    node_counts = torch.empty(n_nodes, dtype=torch.int32, device=dev)
+    cstone_upsweep_counts_batched(counts, ne, l2n, CO, LO, s, node_counts, ws, stream)
+    return {"boxes": boxes, "keys": keys, "sorted_keys": sorted_keys, "perm": perm, "elements": elements[:ne],
+            "n_elements": ne, "element_offsets": element_offsets, "element_offsets_host": eo_host,
+            "leaf_counts": counts[:ne], "leaf_offsets": offsets[:ne], "iters": iters, "NK": NK, "CO": CO, "LO": LO,
+            "leaf_to_node": l2n, "node_counts": node_counts, "node_offsets_host": node_offsets, "ws": ws}
+
+
 def _grow(b: OctreeBuffers, want: int) -> OctreeBuffers:
     cap = int(min(1 << 28, max(want, 2 * b.cap)))
     nb = OctreeBuffers.allocate(b.n, cap, b.device)
     nb.keys, nb.sorted_keys, nb.perm, nb.box, nb.ws = b.keys, b.sorted_keys, b.perm, b.box, b.ws
     return nb
+
+
+# ------------------------------------------------------------------------- time steps
+def padded_boxes(boxes, pad: float = 0.1):
+    """Each bounding cube grown by `pad` of its side on every side (boxes [S, 4], float64 CUDA)."""
+    out = boxes.clone()
+    out[:, :3] -= pad * boxes[:, 3:4]
+    out[:, 3] *= 1.0 + 2.0 * pad
+    return out
+
+
+class TimeStepper:
+    """Rebuilds the octrees of several independent runs after every step of a particle simulation.
+
+    The runs are stored back to back (``set_offsets``); each rebuild is one batched build of all
+    runs in a box fixed at step 0, warm-started from the previous step's leaf arrays (Sec. 4: a
+    single f/g update per step keeps a slowly moving distribution balanced)."""
+
+    def __init__(self, x, y, z, set_offsets, curve: int = HILBERT, ncrit: int = 64, pad: float = 0.1):
+        self.x, self.y, self.z, self.set_offsets = x, y, z, set_offsets
+        self.curve, self.ncrit = curve, ncrit
+        self.ws = Workspace(x.device)
+        cube = torch.empty((set_offsets.numel() - 1, 4), dtype=torch.float64, device=x.device)
+        cstone_bbox_batched(x, y, z, set_offsets, cube)
+        self.boxes = padded_boxes(cube, pad)
+        self.last = None
+
+    def rebuild(self, warm: bool = True):
+        out = build_octrees_batched(self.x, self.y, self.z, self.set_offsets, curve=self.curve, ncrit=self.ncrit,
+                                    boxes=self.boxes, warm=self.last if warm else None, ws=self.ws)
+        self.last = out
+        return out

@@ -334,7 +334,145 @@ const HilbertTable& hilbert_table() {
     return table;
 }
 
+// ------------------------------------------------------------------ batched sets
+// Set of particle p: the last set whose first particle is <= p (sets are stored back to back).
+__device__ __forceinline__ int set_of(const long long* __restrict__ set_offsets, int n_sets, long long p) {
+    int lo = 0, hi = n_sets;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(set_offsets + mid) <= p)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    while (lo + 1 < n_sets && __ldg(set_offsets + lo + 1) <= p) ++lo;  // skip empty sets
+    return lo;
+}
+
+// Bounding cube of every set, one block per set.
+__global__ void __launch_bounds__(256) bbox_batched_kernel(const double* __restrict__ x, const double* __restrict__ y,
+                                                           const double* __restrict__ z,
+                                                           const long long* __restrict__ set_offsets,
+                                                           double* __restrict__ boxes) {
+    __shared__ u64 s_lo[8][3], s_hi[8][3];
+    const long long a = set_offsets[blockIdx.x], b = set_offsets[blockIdx.x + 1];
+    u64 lo[3] = {~0ULL, ~0ULL, ~0ULL}, hi[3] = {0ULL, 0ULL, 0ULL};
+    const double* c[3] = {x, y, z};
+    for (long long i = a + threadIdx.x; i < b; i += blockDim.x) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const u64 o = ordered_bits(__ldg(c[d] + i));
+            lo[d] = o < lo[d] ? o : lo[d];
+            hi[d] = o > hi[d] ? o : hi[d];
+        }
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        for (int sft = 16; sft > 0; sft >>= 1) {
+            const u64 u = __shfl_xor_sync(0xffffffffu, lo[d], sft);
+            const u64 v = __shfl_xor_sync(0xffffffffu, hi[d], sft);
+            lo[d] = u < lo[d] ? u : lo[d];
+            hi[d] = v > hi[d] ? v : hi[d];
+        }
+    }
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0)
+        for (int d = 0; d < 3; ++d) {
+            s_lo[warp][d] = lo[d];
+            s_hi[warp][d] = hi[d];
+        }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double* box = boxes + 4 * blockIdx.x;
+    if (b <= a) {
+        box[0] = box[1] = box[2] = 0.0;
+        box[3] = 1.0;
+        return;
+    }
+    double side = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        u64 l = s_lo[0][d], h = s_hi[0][d];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            l = s_lo[w][d] < l ? s_lo[w][d] : l;
+            h = s_hi[w][d] > h ? s_hi[w][d] : h;
+        }
+        const double lod = from_ordered(l), hid = from_ordered(h);
+        box[d] = lod;
+        const double ext = __dsub_rn(hid, lod);
+        side = ext > side ? ext : side;
+    }
+    box[3] = side > 0.0 ? side : 1.0;
+}
+
+__global__ void keys_batched_setup_kernel(const double* __restrict__ boxes, int n_sets, FixedGrid* grids) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 3 * n_sets; i += gridDim.x * blockDim.x) {
+        const int sidx = i / 3, d = i % 3;
+        grids[i] = make_fixed_grid(boxes[4 * sidx + d], boxes[4 * sidx + 3]);
+    }
+}
+
+template <int CURVE>
+__global__ void __launch_bounds__(256) keys_batched_kernel(const double* __restrict__ x, const double* __restrict__ y,
+                                                           const double* __restrict__ z,
+                                                           const long long* __restrict__ set_offsets, int n_sets,
+                                                           long long n, const FixedGrid* __restrict__ grids,
+                                                           u64* __restrict__ keys,
+                                                           const __grid_constant__ HilbertTable table) {
+    __shared__ unsigned short s_t2[kHilbertStates * 64];
+    __shared__ unsigned short s_t1[kHilbertStates * 8];
+    if (CURVE == CSTONE_HILBERT) {
+        for (int i = threadIdx.x; i < kHilbertStates * 64; i += blockDim.x) s_t2[i] = table.two[i];
+        for (int i = threadIdx.x; i < kHilbertStates * 8; i += blockDim.x) s_t1[i] = table.one[i];
+    }
+    __syncthreads();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int sidx = set_of(set_offsets, n_sets, i);
+        const FixedGrid* g = grids + 3 * sidx;
+        const double px = __ldcs(x + i), py = __ldcs(y + i), pz = __ldcs(z + i);
+        u32 c[3];
+        const double pc[3] = {px, py, pz};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const FixedGrid f = g[d];
+            c[d] = f.fast ? grid_cell_fixed(pc[d], f) : grid_cell(pc[d], f.lo, f.scale);
+        }
+        const u64 m = morton_of(c[0], c[1], c[2]);
+        keys[i] = CURVE == CSTONE_HILBERT ? hilbert_of(m, s_t1, s_t2) : m;
+    }
+}
+
 }  // namespace
+
+size_t keys_batched_ws_bytes(int n_sets) {
+    Carver c(nullptr);
+    c.take<FixedGrid>((size_t)n_sets * 3);
+    return c.size();
+}
+
+int launch_bbox_batched(const double* x, const double* y, const double* z, const long long* set_offsets, int n_sets,
+                        double* boxes, cudaStream_t st) {
+    bbox_batched_kernel<<<n_sets, 256, 0, st>>>(x, y, z, set_offsets, boxes);
+    CST_LAUNCHED("bbox_batched_kernel");
+    return CSTONE_OK;
+}
+
+int launch_keys_batched(const double* x, const double* y, const double* z, const long long* set_offsets, int n_sets,
+                        long long n, const double* boxes, int curve, u64* keys, void* ws, cudaStream_t st) {
+    Carver c(ws);
+    FixedGrid* grids = c.take<FixedGrid>((size_t)n_sets * 3);
+    keys_batched_setup_kernel<<<(3 * n_sets + 127) / 128, 128, 0, st>>>(boxes, n_sets, grids);
+    CST_LAUNCHED("keys_batched_setup_kernel");
+    if (n == 0) return CSTONE_OK;
+    const HilbertTable& tab = hilbert_table();
+    const long long want = (n + 255) / 256;
+    const int grid = static_cast<int>(want < (long long)sm_count() * 8 ? want : (long long)sm_count() * 8);
+    if (curve == CSTONE_HILBERT)
+        keys_batched_kernel<CSTONE_HILBERT><<<grid, 256, 0, st>>>(x, y, z, set_offsets, n_sets, n, grids, keys, tab);
+    else
+        keys_batched_kernel<CSTONE_MORTON><<<grid, 256, 0, st>>>(x, y, z, set_offsets, n_sets, n, grids, keys, tab);
+    CST_LAUNCHED("keys_batched_kernel");
+    return CSTONE_OK;
+}
 
 int launch_keys(const double* x, const double* y, const double* z, long long n, const double* box, int curve,
                 u64* keys, cudaStream_t st) {
@@ -411,6 +549,34 @@ int cstone_keys(const double* x, const double* y, const double* z, int64_t n, co
           reinterpret_cast<uintptr_t>(keys)) & 7u) != 0)
         return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_keys: arrays must be 8-byte aligned");
     return cst::launch_keys(x, y, z, n, box, curve, reinterpret_cast<cst::u64*>(keys), cst::as_stream(stream));
+}
+
+int cstone_bbox_batched(const double* x, const double* y, const double* z, const int64_t* set_offsets, int32_t n_sets,
+                        double* boxes, void* stream) {
+    if (n_sets < 1 || n_sets > (1 << 20) || !set_offsets || !boxes || !x || !y || !z)
+        return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_bbox_batched: bad argument");
+    return cst::launch_bbox_batched(x, y, z, reinterpret_cast<const long long*>(set_offsets), n_sets, boxes,
+                                    cst::as_stream(stream));
+}
+
+int cstone_keys_batched_workspace_size(int32_t n_sets, size_t* bytes) {
+    if (!bytes || n_sets < 1 || n_sets > (1 << 20))
+        return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_keys_batched_workspace_size: bad argument");
+    *bytes = cst::keys_batched_ws_bytes(n_sets);
+    return CSTONE_OK;
+}
+
+int cstone_keys_batched(const double* x, const double* y, const double* z, int64_t n, const int64_t* set_offsets,
+                        int32_t n_sets, const double* boxes, int curve, uint64_t* keys, void* ws, size_t ws_bytes,
+                        void* stream) {
+    if (n < 0 || n >= CSTONE_MAX_PARTICLES || n_sets < 1 || n_sets > (1 << 20) || !set_offsets || !boxes ||
+        (n > 0 && (!x || !y || !z || !keys)))
+        return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_keys_batched: bad argument");
+    if (curve != CSTONE_MORTON && curve != CSTONE_HILBERT)
+        return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_keys_batched: unknown curve %d", curve);
+    if (int rc = cst::check_ws(ws, ws_bytes, cst::keys_batched_ws_bytes(n_sets), "cstone_keys_batched")) return rc;
+    return cst::launch_keys_batched(x, y, z, reinterpret_cast<const long long*>(set_offsets), n_sets, n, boxes, curve,
+                                    reinterpret_cast<cst::u64*>(keys), ws, cst::as_stream(stream));
 }
 
 }  // extern "C"

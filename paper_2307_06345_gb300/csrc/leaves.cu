@@ -8,13 +8,18 @@
 // parent's particle range [pos_i, pos_{i+1}) - the same lower bounds the paper's two binary
 // searches per bin give, found in a small window instead of the whole of P.
 //
-// One pass (g1 + g2 + g3) is a single sweep over tiles of the array: each thread decides O_i for
-// a run of leaves, the block scans the decisions, the tile's offset comes from decoupled
+// The array is handled as a list of elements: the leaves followed by the end key 8^L, which is
+// kept (O = 1) like any unchanged leaf. The same kernel then builds many independent arrays at
+// once (batched sets): they are stored back to back, each ending with its own 8^L, and every
+// element carries its set id so that a merge never reaches across two sets.
+//
+// One pass (g1 + g2 + g3) is a single sweep over tiles of the elements: the threads decide O for
+// the tile's elements, the block scans the decisions, the tile's offset comes from decoupled
 // look-back over the preceding tiles (claimed in order through an atomic counter), and every
-// leaf is copied, split into 8 or dropped at its scanned position. A bounded grid barrier closes
-// the pass; all blocks then read the "changed" flag and either start the next pass or, once a
-// pass changed nothing, write the converged array out. The whole loop is one launch and needs no
-// host round trip.
+// element is copied, split into 8 or dropped at its scanned position. A bounded grid barrier
+// closes the pass; all blocks then read the "changed" flag and either start the next pass or, once
+// a pass changed nothing, write the converged arrays out. The whole loop is one launch and needs
+// no host round trip.
 #include "common.cuh"
 
 namespace cst {
@@ -22,7 +27,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kItems = 2;
-constexpr int kTile = kThreads * kItems;  // leaf indices per tile
+constexpr int kTile = kThreads * kItems;  // elements per tile
 constexpr int kMaxIters = 256;
 constexpr int kSplitChunks = 16;                 // keys per lane loaded at once when counting a split
 constexpr u32 kLinearSplit = 32 * kSplitChunks;  // split ranges up to this size are counted, not searched
@@ -31,19 +36,26 @@ constexpr u64 kLookPrefix = 2ULL << 62;
 constexpr u64 kLookValue = (1ULL << 62) - 1ULL;
 
 struct LoopState {
-    u32 nl[kMaxIters + 1];       // leaves entering pass t (nl[0] = initial)
-    u32 changed[kMaxIters];      // pass t changed the array
-    u32 tile_counter[kMaxIters]; // tile dispenser of pass t
+    u32 ne[kMaxIters + 1];        // elements entering pass t (ne[0] = initial)
+    u32 changed[kMaxIters];       // pass t changed an array
+    u32 tile_counter[kMaxIters];  // tile dispenser of pass t
     GridBarrier bar;
-    u32 iters;                   // passes executed (set at convergence)
+    u32 iters;                    // passes executed (set at convergence)
     u32 converged;
-    u32 required;                // leaves needed when the capacity was exceeded
-    u32 final_buf;               // buffer holding the converged array
+    u32 required;                 // elements needed when the capacity was exceeded
+    u32 final_buf;                // buffer holding the converged arrays
 };
 
 struct LeafBufs {
     u64* K[2];
-    u32* pos[2];
+    u32* pos[2];   // lower bound of the element's key among its set's sorted keys (global index)
+    u32* set[2];   // set of the element (batched builds only)
+};
+
+struct SetView {  // batched builds
+    const long long* particle_offsets;  // [S+1] first particle of each set
+    long long* element_offsets;         // [S+1] in (warm start) / out: first element of each set
+    int n_sets;
 };
 
 __device__ __forceinline__ u64 ld_volatile64(const u64* p) { return *reinterpret_cast<const volatile u64*>(p); }
@@ -61,28 +73,35 @@ __device__ __forceinline__ u32 lower_bound_in(const u64* __restrict__ P, u32 lo,
     return lo;
 }
 
-// Eq. (g1) for leaf i < nl. Split when N_i > ncrit (a single key at depth L stays); merge away
-// the octants 1..7 of a parent whose 8 children are consecutive leaves holding <= ncrit in total
-// (octant 0 keeps its key, which is the parent's); keep otherwise.
-__device__ __forceinline__ u32 decide(const u64* __restrict__ K, const u32* __restrict__ pos, u32 i, u32 nl, u32 ncrit) {
-    u64 ki = K[i], delta = K[i + 1] - ki;
-    u32 cnt = pos[i + 1] - pos[i];
+// Eq. (g1) for element e of ne. The end key 8^L of a set is kept. A leaf splits when N > ncrit
+// (a single key at depth L stays); the octants 1..7 of a parent whose 8 children are consecutive
+// leaves of one set holding <= ncrit in total are merged away (octant 0 keeps its key, which is
+// the parent's); anything else is kept.
+template <bool BATCH>
+__device__ __forceinline__ u32 decide(const u64* __restrict__ K, const u32* __restrict__ pos,
+                                      const u32* __restrict__ set, u32 e, u32 ne, u32 ncrit) {
+    const u64 ke = K[e];
+    if (ke == kKeyEnd) return 1u;
+    const u64 delta = K[e + 1] - ke;
+    const u32 cnt = pos[e + 1] - pos[e];
     if (cnt > ncrit && delta > 1ULL) return 8u;
     if (delta < kKeyEnd) {
-        u32 j = static_cast<u32>((ki >> (__ffsll(static_cast<long long>(delta)) - 1)) & 7ULL);
-        if (j >= 1u && j <= i && i - j + 8u <= nl) {
-            u32 first = i - j;
-            if (K[first] + 8ULL * delta == K[first + 8] && pos[first + 8] - pos[first] <= ncrit) return 0u;
+        const u32 j = static_cast<u32>((ke >> (__ffsll(static_cast<long long>(delta)) - 1)) & 7ULL);
+        if (j >= 1u && j <= e && e - j + 8u < ne) {
+            const u32 first = e - j;
+            if (!BATCH || (set[first] == set[e] && set[first + 8] == set[e]))
+                if (K[first] + 8ULL * delta == K[first + 8] && pos[first + 8] - pos[first] <= ncrit) return 0u;
         }
     }
     return 1u;
 }
 
+template <bool BATCH>
 __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const u64* __restrict__ P, u32 n, u32 ncrit,
-                                                               LeafBufs b, u32 cap, int max_iters, int warm,
+                                                               LeafBufs b, u32 ecap, int max_iters, int warm,
                                                                u64* look, u32 max_tiles, LoopState* ls,
-                                                               WsHeader* hdr, u64* out_keys, u32* out_counts,
-                                                               u32* out_offsets) {
+                                                               WsHeader* hdr, SetView sv, u64* out_keys,
+                                                               u32* out_counts, u32* out_offsets) {
     __shared__ u32 s_warp[kThreads / 32];
     __shared__ unsigned char s_op[kTile];
     __shared__ unsigned short s_split[kTile];
@@ -94,17 +113,36 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const u64* __rest
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const u32 gtid = blockIdx.x * kThreads + tid, gthreads = gridDim.x * kThreads;
 
-    // ---- initial array in buffer 0 with the particle position of every key
-    if (!warm) {
-        if (gtid == 0) {
-            b.K[0][0] = 0ULL;
-            b.K[0][1] = kKeyEnd;
-            b.pos[0][0] = 0u;
-            b.pos[0][1] = n;
+    // ---- initial arrays in buffer 0, with the particle position of every key
+    if (!warm) {  // every set starts from its root {0, 8^L}
+        const int ns = BATCH ? sv.n_sets : 1;
+        for (u32 q = gtid; q < static_cast<u32>(ns); q += gthreads) {
+            b.K[0][2 * q] = 0ULL;
+            b.K[0][2 * q + 1] = kKeyEnd;
+            b.pos[0][2 * q] = BATCH ? static_cast<u32>(sv.particle_offsets[q]) : 0u;
+            b.pos[0][2 * q + 1] = BATCH ? static_cast<u32>(sv.particle_offsets[q + 1]) : n;
+            if (BATCH) b.set[0][2 * q] = b.set[0][2 * q + 1] = q;
         }
     } else {
-        u32 nl0 = ls->nl[0];
-        for (u32 i = gtid; i <= nl0; i += gthreads) b.pos[0][i] = lower_bound_in(P, 0u, n, b.K[0][i]);
+        const u32 ne0 = ls->ne[0];
+        for (u32 e = gtid; e < ne0; e += gthreads) {
+            u32 lo = 0, hi = n;
+            if (BATCH) {
+                int a = 0, c = sv.n_sets;  // last set whose first element is <= e
+                while (c - a > 1) {
+                    const int mid = (a + c) >> 1;
+                    if (sv.element_offsets[mid] <= e)
+                        a = mid;
+                    else
+                        c = mid;
+                }
+                b.set[0][e] = static_cast<u32>(a);
+                lo = static_cast<u32>(sv.particle_offsets[a]);
+                hi = static_cast<u32>(sv.particle_offsets[a + 1]);
+            }
+            const u64 k = b.K[0][e];
+            b.pos[0][e] = k == kKeyEnd ? hi : lower_bound_in(P, lo, hi, k);
+        }
     }
     grid_barrier(&ls->bar, hdr);
 
@@ -113,10 +151,12 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const u64* __rest
         if (ld_volatile(&hdr->err)) break;
         const u64* K = b.K[t & 1];
         const u32* pos = b.pos[t & 1];
+        const u32* set = b.set[t & 1];
         u64* Kn = b.K[(t + 1) & 1];
         u32* posn = b.pos[(t + 1) & 1];
-        const u32 nl = ld_volatile(&ls->nl[t]);
-        const u32 ntiles = (nl + 1 + kTile - 1) / kTile;  // indices 0..nl, nl is the end sentinel
+        u32* setn = b.set[(t + 1) & 1];
+        const u32 ne = ld_volatile(&ls->ne[t]);
+        const u32 ntiles = (ne + kTile - 1) / kTile;
         u64* look_t = look + (size_t)t * max_tiles;
         int any_change = 0;
 
@@ -130,14 +170,14 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const u64* __rest
             __syncthreads();
             if (tile >= ntiles) break;
 
-            // g1, striped: item j of the tile is leaf tile * kTile + j, handled by thread j % kThreads
+            // g1, striped: item j of the tile is element tile * kTile + j, handled by thread j % kThreads
             const u32 t0 = tile * kTile;
 #pragma unroll
             for (int k = 0; k < kItems; ++k) {
                 const u32 j = k * kThreads + tid;
-                const u32 i = t0 + j;
-                u32 o = (i < nl) ? decide(K, pos, i, nl, ncrit) : 0u;
-                if (i < nl && o != 1u) any_change = 1;
+                const u32 e = t0 + j;
+                const u32 o = (e < ne) ? decide<BATCH>(K, pos, set, e, ne, ncrit) : 0u;
+                if (e < ne && o != 1u) any_change = 1;
                 s_op[j] = static_cast<unsigned char>(o);
             }
             __syncthreads();
@@ -205,40 +245,40 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const u64* __rest
             }
             __syncthreads();
 
-            // g3, striped: copy, split or drop each leaf at its scanned position. A split writes its
-            // 8 child keys and queues itself; the child particle offsets are found below.
+            // g3, striped: copy, split or drop each element at its scanned position. A split writes
+            // its 8 child keys and queues itself; the child particle offsets are found below.
             const u64 prefix = s_prefix;
 #pragma unroll 1
             for (int k = 0; k < kItems; ++k) {
                 const u32 j = k * kThreads + tid;
-                const u32 i = t0 + j;
-                if (i > nl) break;
+                const u32 e = t0 + j;
+                if (e >= ne) break;
                 const u64 o_pos = prefix + s_off[j];
-                if (i == nl) {  // end sentinel: K'_{n_l'} = 8^L, and n_l' itself
-                    if (o_pos <= cap) {
-                        Kn[o_pos] = kKeyEnd;
-                        posn[o_pos] = n;
-                    }
-                    ls->nl[t + 1] = static_cast<u32>(o_pos > 0xffffffffULL ? 0xffffffffULL : o_pos);
-                    if (o_pos > cap) {
-                        ls->required = static_cast<u32>(o_pos > 0xffffffffULL ? 0xffffffffULL : o_pos);
-                        raise_error(hdr, CSTONE_ERR_CAPACITY, 0u);
-                    }
-                    break;
-                }
                 const u32 o = s_op[j];
                 if (o == 1u) {
-                    if (o_pos < cap) {
-                        Kn[o_pos] = K[i];
-                        posn[o_pos] = pos[i];
+                    if (o_pos < ecap) {
+                        Kn[o_pos] = K[e];
+                        posn[o_pos] = pos[e];
+                        if (BATCH) setn[o_pos] = set[e];
+                    }
+                    if (e == ne - 1) {  // the last element is an end key: the new element count
+                        const u64 ne_next = o_pos + 1;
+                        ls->ne[t + 1] = static_cast<u32>(ne_next > 0xffffffffULL ? 0xffffffffULL : ne_next);
+                        if (ne_next > ecap) {
+                            ls->required = static_cast<u32>(ne_next > 0xffffffffULL ? 0xffffffffULL : ne_next);
+                            raise_error(hdr, CSTONE_ERR_CAPACITY, 0u);
+                        }
                     }
                 } else if (o == 8u) {
-                    const u64 ki = K[i];
-                    const u64 step = (K[i + 1] - ki) >> 3;
-                    if (o_pos + 8 <= cap) {
+                    const u64 ke = K[e];
+                    const u64 step = (K[e + 1] - ke) >> 3;
+                    if (o_pos + 8 <= ecap) {
 #pragma unroll
-                        for (int c = 0; c < 8; ++c) Kn[o_pos + c] = ki + static_cast<u64>(c) * step;
-                        posn[o_pos] = pos[i];
+                        for (int c = 0; c < 8; ++c) {
+                            Kn[o_pos + c] = ke + static_cast<u64>(c) * step;
+                            if (BATCH) setn[o_pos + c] = set[e];
+                        }
+                        posn[o_pos] = pos[e];
                     }
                     s_split[atomicAdd(&s_nsplit, 1u)] = static_cast<unsigned short>(j);
                 }
@@ -251,37 +291,37 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const u64* __rest
             const u32 nsplit = s_nsplit;
             for (u32 q = warp; q < nsplit; q += kThreads / 32) {
                 const u32 j = s_split[q];
-                const u32 i = t0 + j;
+                const u32 e = t0 + j;
                 const u64 o_pos = prefix + s_off[j];
-                const u64 ki = K[i];
-                const u64 delta = K[i + 1] - ki;
-                const u32 lo = pos[i], cnt_all = pos[i + 1] - lo;
+                const u64 ke = K[e];
+                const u64 delta = K[e + 1] - ke;
+                const u32 lo = pos[e], cnt_all = pos[e + 1] - lo;
                 const int child_shift = __ffsll(static_cast<long long>(delta)) - 1 - 3;
                 u32 below = 0;  // lane c in 1..7: particles whose child digit is < c
                 if (cnt_all <= kLinearSplit) {
                     u32 dg[kSplitChunks];
 #pragma unroll
-                    for (int b = 0; b < kSplitChunks; ++b) {  // every load issued before any use
-                        const u32 jj = b * 32 + lane;
-                        dg[b] = jj < cnt_all ? static_cast<u32>((__ldg(P + lo + jj) >> child_shift) & 7ULL) : 8u;
+                    for (int c = 0; c < kSplitChunks; ++c) {  // every load issued before any use
+                        const u32 jj = c * 32 + lane;
+                        dg[c] = jj < cnt_all ? static_cast<u32>((__ldg(P + lo + jj) >> child_shift) & 7ULL) : 8u;
                     }
 #pragma unroll
-                    for (int b = 0; b < kSplitChunks; ++b) {
-                        if (b * 32 >= static_cast<int>(cnt_all)) break;
+                    for (int c = 0; c < kSplitChunks; ++c) {
+                        if (c * 32 >= static_cast<int>(cnt_all)) break;
 #pragma unroll
-                        for (u32 c = 1; c < 8; ++c) {
-                            const u32 bal = __ballot_sync(0xffffffffu, dg[b] < c);
-                            if (lane == c) below += __popc(bal);
+                        for (u32 d = 1; d < 8; ++d) {
+                            const u32 bal = __ballot_sync(0xffffffffu, dg[c] < d);
+                            if (lane == d) below += __popc(bal);
                         }
                     }
                 } else if (lane >= 1 && lane < 8) {
-                    const u64 key = ki + static_cast<u64>(lane) * (delta >> 3);
+                    const u64 key = ke + static_cast<u64>(lane) * (delta >> 3);
                     for (u32 st = 1u << (31 - __clz(cnt_all)); st > 0; st >>= 1) {
                         const u32 probe = below + st;
                         if (probe <= cnt_all && __ldg(P + lo + probe - 1) < key) below = probe;
                     }
                 }
-                if (lane >= 1 && lane < 8 && o_pos + 8 <= cap) posn[o_pos + lane] = lo + below;
+                if (lane >= 1 && lane < 8 && o_pos + 8 <= ecap) posn[o_pos + lane] = lo + below;
             }
             __syncthreads();  // s_op / s_off are rewritten by the next tile
         }
@@ -306,13 +346,21 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const u64* __rest
         ls->final_buf = static_cast<u32>(t & 1);
     }
     if (!converged) return;
-    const u32 nl = ld_volatile(&ls->nl[t]);
+    const u32 ne = ld_volatile(&ls->ne[t]);
     const u64* K = b.K[t & 1];
     const u32* pos = b.pos[t & 1];
-    for (u32 i = gtid; i <= nl; i += gthreads) {
-        out_keys[i] = K[i];
-        if (i < nl) out_counts[i] = pos[i + 1] - pos[i];
-        if (out_offsets) out_offsets[i] = pos[i];
+    const u32* set = b.set[t & 1];
+    for (u32 e = gtid; e < ne; e += gthreads) {
+        const u64 k = K[e];
+        out_keys[e] = k;
+        if (BATCH) {
+            out_counts[e] = k == kKeyEnd ? 0u : pos[e + 1] - pos[e];
+            if (e == 0 || K[e - 1] == kKeyEnd) sv.element_offsets[set[e]] = e;
+            if (e == 0) sv.element_offsets[sv.n_sets] = ne;
+        } else if (e + 1 < ne) {
+            out_counts[e] = pos[e + 1] - pos[e];
+        }
+        if (out_offsets) out_offsets[e] = pos[e];
     }
 }
 
@@ -324,42 +372,44 @@ struct LeavesLayout {
     size_t bytes;
 };
 
-LeavesLayout leaves_layout(void* ws, long long cap, int max_iters) {
+LeavesLayout leaves_layout(void* ws, long long ecap, int max_iters, bool batch) {
     LeavesLayout l;
     Carver c(ws);
     l.ls = c.take<LoopState>(1);
     for (int k = 0; k < 2; ++k) {
-        l.bufs.K[k] = c.take<u64>((size_t)cap + 1);
-        l.bufs.pos[k] = c.take<u32>((size_t)cap + 1);
+        l.bufs.K[k] = c.take<u64>((size_t)ecap);
+        l.bufs.pos[k] = c.take<u32>((size_t)ecap);
+        l.bufs.set[k] = batch ? c.take<u32>((size_t)ecap) : nullptr;
     }
-    l.max_tiles = static_cast<u32>((cap + 1 + kTile - 1) / kTile);
+    l.max_tiles = static_cast<u32>((ecap + kTile - 1) / kTile);
     l.look = c.take<u64>((size_t)l.max_tiles * (size_t)max_iters);
     l.bytes = c.size();
     return l;
 }
 
-int leaves_grid() { return cooperative_grid(reinterpret_cast<const void*>(leaves_loop_kernel), kThreads, 0, 8); }
+template <bool BATCH>
+int leaves_grid() {
+    return cooperative_grid(reinterpret_cast<const void*>(leaves_loop_kernel<BATCH>), kThreads, 0, 8);
+}
 
-}  // namespace
-
-size_t leaves_ws_bytes(long long cap, int max_iters) { return leaves_layout(nullptr, cap, max_iters).bytes; }
-
-int launch_build_leaves(const u64* P, long long n, u32 ncrit, u64* leaves, long long cap, long long* n_leaves,
-                        u32* counts, u32* offsets, int max_iters, int* iters, void* ws, cudaStream_t st) {
-    LeavesLayout l = leaves_layout(ws, cap, max_iters);
+// Runs the loop; on success *ne_out is the element count of the converged arrays.
+template <bool BATCH>
+int run_leaves(const u64* P, long long n, u32 ncrit, u64* leaves, long long ecap, long long ne0, long long* ne_out,
+               u32* counts, u32* offsets, int max_iters, int* iters, SetView sv, void* ws, cudaStream_t st,
+               const char* who) {
+    LeavesLayout l = leaves_layout(ws, ecap, max_iters, BATCH);
     WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
-    const long long nl0 = *n_leaves;
     CST_CUDA(cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st));
     CST_CUDA(cudaMemsetAsync(l.ls, 0, sizeof(LoopState), st));
     CST_CUDA(cudaMemsetAsync(l.look, 0, (size_t)l.max_tiles * max_iters * sizeof(u64), st));
-    int warm = nl0 > 0 ? 1 : 0;
-    u32 nl_start = warm ? static_cast<u32>(nl0) : 1u;
-    CST_CUDA(cudaMemcpyAsync(&l.ls->nl[0], &nl_start, sizeof(u32), cudaMemcpyHostToDevice, st));
+    int warm = ne0 > 0 ? 1 : 0;
+    const u32 ne_start = warm ? static_cast<u32>(ne0) : static_cast<u32>(2 * (BATCH ? sv.n_sets : 1));
+    CST_CUDA(cudaMemcpyAsync(&l.ls->ne[0], &ne_start, sizeof(u32), cudaMemcpyHostToDevice, st));
     if (warm)
-        CST_CUDA(cudaMemcpyAsync(l.bufs.K[0], leaves, (size_t)(nl0 + 1) * sizeof(u64), cudaMemcpyDeviceToDevice, st));
+        CST_CUDA(cudaMemcpyAsync(l.bufs.K[0], leaves, (size_t)ne0 * sizeof(u64), cudaMemcpyDeviceToDevice, st));
 
     const u64* P_ = P;
-    u32 n_ = static_cast<u32>(n), ncrit_ = ncrit, cap_ = static_cast<u32>(cap), max_tiles = l.max_tiles;
+    u32 n_ = static_cast<u32>(n), ncrit_ = ncrit, ecap_ = static_cast<u32>(ecap), max_tiles = l.max_tiles;
     int max_iters_ = max_iters;
     LeafBufs bufs = l.bufs;
     u64* look = l.look;
@@ -367,9 +417,9 @@ int launch_build_leaves(const u64* P, long long n, u32 ncrit, u64* leaves, long 
     u64* out_keys = leaves;
     u32* out_counts = counts;
     u32* out_offsets = offsets;
-    void* args[] = {&P_, &n_, &ncrit_, &bufs, &cap_, &max_iters_, &warm, &look, &max_tiles, &ls, &hdr,
+    void* args[] = {&P_, &n_, &ncrit_, &bufs, &ecap_, &max_iters_, &warm, &look, &max_tiles, &ls, &hdr, &sv,
                     &out_keys, &out_counts, &out_offsets};
-    CST_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(leaves_loop_kernel), dim3(leaves_grid()),
+    CST_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(leaves_loop_kernel<BATCH>), dim3(leaves_grid<BATCH>()),
                                          dim3(kThreads), args, 0, st));
 
     WsHeader h;
@@ -379,15 +429,45 @@ int launch_build_leaves(const u64* P, long long n, u32 ncrit, u64* leaves, long 
     CST_CUDA(cudaStreamSynchronize(st));
     if (iters) *iters = static_cast<int>(s.iters);
     if (h.err == CSTONE_ERR_CAPACITY) {
-        *n_leaves = s.required;
-        return fail(CSTONE_ERR_CAPACITY, "cstone_build_leaves: %u leaves needed, capacity %lld", s.required, cap);
+        *ne_out = s.required;
+        return fail(CSTONE_ERR_CAPACITY, "%s: %u array elements needed, capacity %lld", who, s.required, ecap);
     }
-    if (h.err) return fail(static_cast<int>(h.err), "cstone_build_leaves: device error %u (info 0x%x)", h.err,
-                           h.err_info);
-    if (!s.converged)
-        return fail(CSTONE_ERR_NOT_CONVERGED, "cstone_build_leaves: not converged after %d passes", max_iters);
-    *n_leaves = s.nl[s.iters];
+    if (h.err) return fail(static_cast<int>(h.err), "%s: device error %u (info 0x%x)", who, h.err, h.err_info);
+    if (!s.converged) return fail(CSTONE_ERR_NOT_CONVERGED, "%s: not converged after %d passes", who, max_iters);
+    *ne_out = s.ne[s.iters];
     return CSTONE_OK;
+}
+
+}  // namespace
+
+size_t leaves_ws_bytes(long long cap, int max_iters) { return leaves_layout(nullptr, cap + 1, max_iters, false).bytes; }
+size_t leaves_batched_ws_bytes(long long ecap, int max_iters) {
+    return leaves_layout(nullptr, ecap, max_iters, true).bytes;
+}
+
+int launch_build_leaves(const u64* P, long long n, u32 ncrit, u64* leaves, long long cap, long long* n_leaves,
+                        u32* counts, u32* offsets, int max_iters, int* iters, void* ws, cudaStream_t st) {
+    const long long ne0 = *n_leaves > 0 ? *n_leaves + 1 : 0;
+    long long ne = 0;
+    const int rc = run_leaves<false>(P, n, ncrit, leaves, cap + 1, ne0, &ne, counts, offsets, max_iters, iters,
+                                     SetView{nullptr, nullptr, 1}, ws, st, "cstone_build_leaves");
+    if (rc == CSTONE_ERR_CAPACITY) {
+        *n_leaves = ne - 1;
+        return rc;
+    }
+    if (rc == CSTONE_OK) *n_leaves = ne - 1;
+    return rc;
+}
+
+int launch_build_leaves_batched(const u64* P, long long n, const long long* particle_offsets, int n_sets, u32 ncrit,
+                                u64* leaves, long long ecap, long long* element_offsets, long long* n_elements,
+                                u32* counts, u32* offsets, int max_iters, int* iters, void* ws, cudaStream_t st) {
+    long long ne = 0;
+    const int rc = run_leaves<true>(P, n, ncrit, leaves, ecap, *n_elements, &ne, counts, offsets, max_iters, iters,
+                                    SetView{particle_offsets, element_offsets, n_sets}, ws, st,
+                                    "cstone_build_leaves_batched");
+    if (rc == CSTONE_OK || rc == CSTONE_ERR_CAPACITY) *n_elements = ne;
+    return rc;
 }
 
 }  // namespace cst
@@ -419,6 +499,39 @@ int cstone_build_leaves(const uint64_t* sorted_keys, int64_t n, uint32_t ncrit, 
                                       reinterpret_cast<cst::u64*>(leaves), leaf_cap, &nl, counts, offsets, max_iters,
                                       &it, ws, cst::as_stream(stream));
     *n_leaves = nl;
+    if (iters) *iters = it;
+    return rc;
+}
+
+int cstone_leaves_batched_workspace_size(int64_t elem_cap, int32_t max_iters, size_t* bytes) {
+    if (!bytes || elem_cap < 2 || elem_cap > CSTONE_MAX_LEAVES || max_iters < 1 || max_iters > 256)
+        return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_leaves_batched_workspace_size: bad argument");
+    *bytes = cst::leaves_batched_ws_bytes(elem_cap, max_iters);
+    return CSTONE_OK;
+}
+
+int cstone_build_leaves_batched(const uint64_t* sorted_keys, int64_t n, const int64_t* set_offsets, int32_t n_sets,
+                                uint32_t ncrit, uint64_t* elements, int64_t elem_cap, int64_t* element_offsets,
+                                int64_t* n_elements, uint32_t* counts, uint32_t* offsets, int32_t max_iters,
+                                int32_t* iters, void* ws, size_t ws_bytes, void* stream) {
+    if (n < 0 || n >= CSTONE_MAX_PARTICLES || n_sets < 1 || n_sets > (1 << 20) || !set_offsets || !elements ||
+        !element_offsets || !n_elements || !counts || elem_cap < 2 * (int64_t)n_sets || elem_cap > CSTONE_MAX_LEAVES ||
+        max_iters < 1 || max_iters > 256 || (n > 0 && !sorted_keys))
+        return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_build_leaves_batched: bad argument");
+    if (*n_elements < 0 || *n_elements > elem_cap || (*n_elements > 0 && *n_elements < 2 * (int64_t)n_sets))
+        return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_build_leaves_batched: initial n_elements %lld invalid",
+                         (long long)*n_elements);
+    if (int rc = cst::check_ws(ws, ws_bytes, cst::leaves_batched_ws_bytes(elem_cap, max_iters),
+                               "cstone_build_leaves_batched"))
+        return rc;
+    long long ne = *n_elements;
+    int it = 0;
+    int rc = cst::launch_build_leaves_batched(reinterpret_cast<const cst::u64*>(sorted_keys), n,
+                                              reinterpret_cast<const long long*>(set_offsets), n_sets, ncrit,
+                                              reinterpret_cast<cst::u64*>(elements), elem_cap,
+                                              reinterpret_cast<long long*>(element_offsets), &ne, counts, offsets,
+                                              max_iters, &it, ws, cst::as_stream(stream));
+    *n_elements = ne;
     if (iters) *iters = it;
     return rc;
 }

@@ -97,13 +97,16 @@ __global__ void __launch_bounds__(1024) link_scan_kernel(u32* __restrict__ count
     for (u32 i = begin; i < end; ++i) {
         u32 c = counts[i];
         counts[i] = run;
-        if (i % ntiles == 0) LO[i / ntiles] = static_cast<int>(run);
+        if (LO && i % ntiles == 0) LO[i / ntiles] = static_cast<int>(run);
         run += c;
     }
     if (threadIdx.x == 1023) {
         u32 total = s_part[1023];
-        LO[kNumLevels] = static_cast<int>(total);
-        if (total != n_expected) raise_error(hdr, CSTONE_ERR_INVALID_ARG, total);
+        counts[total_len] = total;
+        if (LO) {
+            LO[kNumLevels] = static_cast<int>(total);
+            if (total != n_expected) raise_error(hdr, CSTONE_ERR_INVALID_ARG, total);
+        }
     }
 }
 
@@ -212,11 +215,300 @@ LinkLayout link_layout(void* ws, long long nl) {
     Carver c(ws);
     l.ntiles = static_cast<u32>((nl + kTile - 1) / kTile);
     if (l.ntiles == 0) l.ntiles = 1;
-    l.counts = c.take<u32>((size_t)l.ntiles * kNumLevels);
+    l.counts = c.take<u32>((size_t)l.ntiles * kNumLevels + 1);
     l.bytes = c.size();
     return l;
 }
 
+// ------------------------------------------------------------------ batched sets
+// Several cornerstone arrays stored back to back as elements (each set's leaves followed by its end
+// key 8^L). Tiles are aligned to sets, so the per-tile level counts of set s are laid out at
+// [tile_first[s] * 22 + level * tiles_of_s + k]: one scan over everything then yields, set by set
+// and level by level, the node positions of a concatenated node array in which every set's tree is
+// one contiguous breadth-first block.
+struct LinkSets {
+    const long long* elem_offsets;  // [S+1] first element of each set
+    u32* n_tiles;                   // device scalar
+    u32* tile_first;                // [S+1] first tile of each set
+    u32* tile_set;                  // [max_tiles]
+    u32* tile_elem;                 // [max_tiles] first leaf element of the tile
+    u32* tile_count;                // [max_tiles]
+    u32* node_first;                // [S+1] expected first node of each set
+    int n_sets;
+};
+
+__global__ void __launch_bounds__(1024) link_b_setup_kernel(LinkSets ls) {
+    __shared__ u32 s_t[1024], s_n[1024];
+    const int per = (ls.n_sets + 1023) / 1024;
+    const int begin = threadIdx.x * per, end = min(begin + per, ls.n_sets);
+    u32 st = 0, sn = 0;
+    for (int q = begin; q < end; ++q) {
+        const long long nl = ls.elem_offsets[q + 1] - ls.elem_offsets[q] - 1;
+        st += static_cast<u32>((nl + kTile - 1) / kTile);
+        sn += static_cast<u32>(nl + (nl - 1) / 7);
+    }
+    s_t[threadIdx.x] = st;
+    s_n[threadIdx.x] = sn;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const u32 a = threadIdx.x >= (unsigned)o ? s_t[threadIdx.x - o] : 0u;
+        const u32 b = threadIdx.x >= (unsigned)o ? s_n[threadIdx.x - o] : 0u;
+        __syncthreads();
+        s_t[threadIdx.x] += a;
+        s_n[threadIdx.x] += b;
+        __syncthreads();
+    }
+    u32 rt = s_t[threadIdx.x] - st, rn = s_n[threadIdx.x] - sn;
+    for (int q = begin; q < end; ++q) {
+        ls.tile_first[q] = rt;
+        ls.node_first[q] = rn;
+        const long long nl = ls.elem_offsets[q + 1] - ls.elem_offsets[q] - 1;
+        rt += static_cast<u32>((nl + kTile - 1) / kTile);
+        rn += static_cast<u32>(nl + (nl - 1) / 7);
+    }
+    if (threadIdx.x == 1023) {
+        ls.tile_first[ls.n_sets] = s_t[1023];
+        ls.node_first[ls.n_sets] = s_n[1023];
+        *ls.n_tiles = s_t[1023];
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) link_b_tiles_kernel(LinkSets ls, u32 max_tiles) {
+    const u32 total = *ls.n_tiles;
+    for (u32 t = blockIdx.x * kThreads + threadIdx.x; t < max_tiles; t += gridDim.x * kThreads) {
+        if (t >= total) {
+            ls.tile_count[t] = 0;
+            continue;
+        }
+        int lo = 0, hi = ls.n_sets;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (ls.tile_first[mid] <= t)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        const long long e0 = ls.elem_offsets[lo] + (long long)(t - ls.tile_first[lo]) * kTile;
+        const long long last_leaf_end = ls.elem_offsets[lo + 1] - 1;  // the end key is not a leaf
+        ls.tile_set[t] = static_cast<u32>(lo);
+        ls.tile_elem[t] = static_cast<u32>(e0);
+        ls.tile_count[t] = static_cast<u32>(min((long long)kTile, last_leaf_end - e0));
+    }
+}
+
+__device__ __forceinline__ u32 count_index(const LinkSets& ls, u32 set, int level, u32 k) {
+    const u32 tf = ls.tile_first[set], nt = ls.tile_first[set + 1] - tf;
+    return tf * kNumLevels + static_cast<u32>(level) * nt + k;
+}
+
+__global__ void __launch_bounds__(kThreads) link_b_count_kernel(const u64* __restrict__ K, LinkSets ls,
+                                                                u32* __restrict__ counts) {
+    __shared__ u32 s_cnt[kNumLevels];
+    const u32 tile = blockIdx.x;
+    const u32 cnt = ls.tile_count[tile];
+    if (cnt == 0) return;
+    if (threadIdx.x < kNumLevels) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const u32 e0 = ls.tile_elem[tile];
+    for (u32 q = threadIdx.x; q < cnt; q += kThreads) {
+        const u32 e = e0 + q;
+        const u64 a = K[e], b = K[e + 1];
+        atomicAdd(&s_cnt[leaf_level(b - a)], 1u);
+        if (b != kKeyEnd) {
+            const int pl = pair_level(a, b);
+            if (pl >= 0) atomicAdd(&s_cnt[pl], 1u);
+        }
+    }
+    __syncthreads();
+    const u32 set = ls.tile_set[tile];
+    if (threadIdx.x < kNumLevels)
+        counts[count_index(ls, set, threadIdx.x, tile - ls.tile_first[set])] = s_cnt[threadIdx.x];
+}
+
+// Level offsets of every set (global node indices), a size check per set, and -1 for the
+// leaf_to_node entries of the end keys.
+__global__ void link_b_lo_kernel(const u32* __restrict__ counts, LinkSets ls, int* __restrict__ LO,
+                                 int* __restrict__ leaf_to_node, WsHeader* hdr) {
+    const u32 total_len = *ls.n_tiles * kNumLevels;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ls.n_sets * (kNumLevels + 1);
+         i += gridDim.x * blockDim.x) {
+        const int set = i / (kNumLevels + 1), l = i % (kNumLevels + 1);
+        u32 v;
+        if (l < kNumLevels)
+            v = counts[count_index(ls, set, l, 0)];
+        else
+            v = set + 1 < ls.n_sets ? counts[count_index(ls, set + 1, 0, 0)] : counts[total_len];
+        LO[i] = static_cast<int>(v);
+        if (l == kNumLevels) {
+            const u32 first = counts[count_index(ls, set, 0, 0)];
+            if (v - first != ls.node_first[set + 1] - ls.node_first[set])
+                raise_error(hdr, CSTONE_ERR_INVALID_ARG, static_cast<u32>(set));
+            leaf_to_node[ls.elem_offsets[set + 1] - 1] = -1;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) link_b_scatter_kernel(const u64* __restrict__ K, LinkSets ls,
+                                                                  const u32* __restrict__ offsets, u32 n_nodes,
+                                                                  u64* __restrict__ NK, int* __restrict__ leaf_to_node) {
+    __shared__ u32 s_rank[kNumLevels][kThreads];
+    const int tid = threadIdx.x;
+    const u32 tile = blockIdx.x;
+    const u32 cnt = ls.tile_count[tile];
+    if (cnt == 0) return;
+    const u32 e0 = ls.tile_elem[tile];
+    const u32 set = ls.tile_set[tile];
+    const u32 k_in_set = tile - ls.tile_first[set];
+    const u32 i0 = tid * kItems;
+#pragma unroll
+    for (int l = 0; l < kNumLevels; ++l) s_rank[l][tid] = 0;
+    for (int k = 0; k < kItems; ++k) {
+        const u32 q = i0 + k;
+        if (q >= cnt) break;
+        const u64 a = K[e0 + q], b = K[e0 + q + 1];
+        s_rank[leaf_level(b - a)][tid] += 1;
+        if (b != kKeyEnd) {
+            const int pl = pair_level(a, b);
+            if (pl >= 0) s_rank[pl][tid] += 1;
+        }
+    }
+    __syncthreads();
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int l = warp; l < kNumLevels; l += kThreads / 32) {
+        u32 v[kThreads / 32];
+        u32 sum = 0;
+#pragma unroll
+        for (int q = 0; q < kThreads / 32; ++q) {
+            v[q] = s_rank[l][lane * (kThreads / 32) + q];
+            sum += v[q];
+        }
+        u32 incl = sum;
+        for (int o = 1; o < 32; o <<= 1) {
+            const u32 t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        u32 run = offsets[count_index(ls, set, l, k_in_set)] + incl - sum;
+#pragma unroll
+        for (int q = 0; q < kThreads / 32; ++q) {
+            s_rank[l][lane * (kThreads / 32) + q] = run;
+            run += v[q];
+        }
+    }
+    __syncthreads();
+    for (int k = 0; k < kItems; ++k) {
+        const u32 q = i0 + k;
+        if (q >= cnt) break;
+        const u32 e = e0 + q;
+        const u64 a = K[e], b = K[e + 1];
+        const int ll = leaf_level(b - a);
+        const u32 x = s_rank[ll][tid]++;
+        if (x < n_nodes) {
+            NK[x] = placeholder(a, ll);
+            leaf_to_node[e] = static_cast<int>(x);
+        }
+        if (b != kKeyEnd) {
+            const int pl = pair_level(a, b);
+            if (pl >= 0) {
+                const u32 y = s_rank[pl][tid]++;
+                if (y < n_nodes) NK[y] = placeholder(a, pl);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) link_b_child_kernel(const u64* __restrict__ NK, u32 n_nodes, int n_sets,
+                                                                const int* __restrict__ LO, int* __restrict__ CO) {
+    for (u32 x = blockIdx.x * kThreads + threadIdx.x; x < n_nodes; x += gridDim.x * kThreads) {
+        int lo_s = 0, hi_s = n_sets;  // set whose node block contains x
+        while (hi_s - lo_s > 1) {
+            const int mid = (lo_s + hi_s) >> 1;
+            if (static_cast<u32>(LO[mid * (kNumLevels + 1)]) <= x)
+                lo_s = mid;
+            else
+                hi_s = mid;
+        }
+        const int* row = LO + lo_s * (kNumLevels + 1);
+        const u64 k = NK[x];
+        const int level = (63 - __clzll(static_cast<long long>(k))) / 3;
+        int c = 0;
+        if (level < kLevels) {
+            const u64 want = k << 3;
+            u32 lo = min(static_cast<u32>(row[level + 1]), n_nodes);
+            u32 hi = min(static_cast<u32>(row[level + 2]), n_nodes);
+            const u32 end = hi;
+            while (lo < hi) {
+                const u32 mid = lo + ((hi - lo) >> 1);
+                if (NK[mid] < want)
+                    lo = mid + 1;
+                else
+                    hi = mid;
+            }
+            if (lo < end && NK[lo] == want) c = static_cast<int>(lo);
+        }
+        CO[x] = c;
+    }
+}
+
+struct LinkBLayout {
+    LinkSets ls;
+    u32* counts;
+    u32 max_tiles;
+    size_t bytes;
+};
+
+LinkBLayout link_b_layout(void* ws, long long n_elements, int n_sets) {
+    LinkBLayout l;
+    Carver c(ws);
+    l.max_tiles = static_cast<u32>((n_elements + kTile - 1) / kTile + n_sets);
+    l.ls.n_tiles = c.take<u32>(1);
+    l.ls.tile_first = c.take<u32>((size_t)n_sets + 1);
+    l.ls.tile_set = c.take<u32>(l.max_tiles);
+    l.ls.tile_elem = c.take<u32>(l.max_tiles);
+    l.ls.tile_count = c.take<u32>(l.max_tiles);
+    l.ls.node_first = c.take<u32>((size_t)n_sets + 1);
+    l.ls.n_sets = n_sets;
+    l.ls.elem_offsets = nullptr;
+    l.counts = c.take<u32>((size_t)l.max_tiles * kNumLevels + 1);
+    l.bytes = c.size();
+    return l;
+}
+
+}  // namespace
+
+size_t link_batched_ws_bytes(long long n_elements, int n_sets) { return link_b_layout(nullptr, n_elements, n_sets).bytes; }
+
+int launch_link_batched(const u64* K, long long n_elements, const long long* elem_offsets, int n_sets, u64* NK,
+                        int* CO, int* LO, int* leaf_to_node, long long n_nodes, void* ws, cudaStream_t st) {
+    LinkBLayout l = link_b_layout(ws, n_elements, n_sets);
+    l.ls.elem_offsets = elem_offsets;
+    WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
+    CST_CUDA(cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st));
+    CST_CUDA(cudaMemsetAsync(l.counts, 0, ((size_t)l.max_tiles * kNumLevels + 1) * sizeof(u32), st));
+    link_b_setup_kernel<<<1, 1024, 0, st>>>(l.ls);
+    CST_LAUNCHED("link_b_setup_kernel");
+    const long long want = (l.max_tiles + kThreads - 1) / kThreads;
+    const int tgrid = static_cast<int>(want < (long long)sm_count() * 4 ? want : (long long)sm_count() * 4);
+    link_b_tiles_kernel<<<tgrid, kThreads, 0, st>>>(l.ls, l.max_tiles);
+    CST_LAUNCHED("link_b_tiles_kernel");
+    link_b_count_kernel<<<l.max_tiles, kThreads, 0, st>>>(K, l.ls, l.counts);
+    CST_LAUNCHED("link_b_count_kernel");
+    // one exclusive scan over all (set, level, tile) counts; unused tail entries are zero
+    link_scan_kernel<<<1, 1024, 0, st>>>(l.counts, l.max_tiles, nullptr, 0u, hdr);
+    CST_LAUNCHED("link_scan_kernel");
+    const int lo_threads = n_sets * (kNumLevels + 1);
+    link_b_lo_kernel<<<(lo_threads + 255) / 256, 256, 0, st>>>(l.counts, l.ls, LO, leaf_to_node, hdr);
+    CST_LAUNCHED("link_b_lo_kernel");
+    link_b_scatter_kernel<<<l.max_tiles, kThreads, 0, st>>>(K, l.ls, l.counts, static_cast<u32>(n_nodes), NK,
+                                                            leaf_to_node);
+    CST_LAUNCHED("link_b_scatter_kernel");
+    const long long wantc = (n_nodes + kThreads - 1) / kThreads;
+    const int cgrid = static_cast<int>(wantc < (long long)sm_count() * 8 ? (wantc > 0 ? wantc : 1) : (long long)sm_count() * 8);
+    link_b_child_kernel<<<cgrid, kThreads, 0, st>>>(NK, static_cast<u32>(n_nodes), n_sets, LO, CO);
+    CST_LAUNCHED("link_b_child_kernel");
+    return CSTONE_OK;
+}
+
+namespace {
 }  // namespace
 
 size_t link_ws_bytes(long long nl) { return link_layout(nullptr, nl).bytes; }
@@ -263,6 +555,30 @@ int cstone_link_tree(const uint64_t* leaves, int64_t n_leaves, uint64_t* node_ke
     if (int rc = cst::check_ws(ws, ws_bytes, cst::link_ws_bytes(n_leaves), "cstone_link_tree")) return rc;
     return cst::launch_link(reinterpret_cast<const cst::u64*>(leaves), n_leaves, reinterpret_cast<cst::u64*>(node_keys),
                             child, level_offsets, leaf_to_node, parent, ws, cst::as_stream(stream));
+}
+
+int cstone_link_batched_workspace_size(int64_t n_elements, int32_t n_sets, size_t* bytes) {
+    if (!bytes || n_sets < 1 || n_sets > (1 << 20) || n_elements < 2 * (int64_t)n_sets ||
+        n_elements > CSTONE_MAX_LEAVES)
+        return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_link_batched_workspace_size: bad argument");
+    *bytes = cst::link_batched_ws_bytes(n_elements, n_sets);
+    return CSTONE_OK;
+}
+
+int cstone_link_tree_batched(const uint64_t* elements, int64_t n_elements, const int64_t* element_offsets,
+                             int32_t n_sets, int64_t n_nodes, uint64_t* node_keys, int32_t* child,
+                             int32_t* level_offsets, int32_t* leaf_to_node, void* ws, size_t ws_bytes, void* stream) {
+    if (n_sets < 1 || n_sets > (1 << 20) || n_elements < 2 * (int64_t)n_sets || n_elements > CSTONE_MAX_LEAVES ||
+        n_nodes < n_sets || n_nodes > 2 * (int64_t)CSTONE_MAX_LEAVES || !elements || !element_offsets ||
+        !node_keys || !child || !level_offsets || !leaf_to_node)
+        return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_link_tree_batched: bad argument");
+    if (int rc = cst::check_ws(ws, ws_bytes, cst::link_batched_ws_bytes(n_elements, n_sets),
+                               "cstone_link_tree_batched"))
+        return rc;
+    return cst::launch_link_batched(reinterpret_cast<const cst::u64*>(elements), n_elements,
+                                    reinterpret_cast<const long long*>(element_offsets), n_sets,
+                                    reinterpret_cast<cst::u64*>(node_keys), child, level_offsets, leaf_to_node,
+                                    n_nodes, ws, cst::as_stream(stream));
 }
 
 }  // extern "C"

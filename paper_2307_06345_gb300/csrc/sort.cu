@@ -75,6 +75,128 @@ __global__ void sort_scan_kernel(SortCtl* ctl) {
     }
 }
 
+// Segmented sorts (many independent key sets stored back to back) use tiles aligned to the
+// segments: every tile holds keys of one segment only, digits are offset per segment, and the
+// look-back of a tile stops at its segment's first tile.
+struct SegTiles {
+    const u32* n_tiles;      // device scalar: tiles in use
+    const u32* tile_seg;     // segment of each tile
+    const u32* tile_base;    // first key (global index) of each tile
+    const u32* tile_count;   // keys in each tile (<= kTile)
+    const u32* seg_first;    // first tile of each segment
+    const u32* seg_offsets;  // [segment][pass][digit] output position of the digit's first key
+};
+
+struct SegBuild {  // writable view of the same tables
+    u32* n_tiles;
+    u32* tile_seg;
+    u32* tile_base;
+    u32* tile_count;
+    u32* seg_first;
+    u32* seg_hist;
+    u32* seg_offsets;
+};
+
+// Tiles per segment and their exclusive scan (one block).
+__global__ void __launch_bounds__(1024) seg_setup_kernel(const long long* __restrict__ seg_offsets_in, int n_segs,
+                                                         SegBuild b) {
+    __shared__ u32 s_part[1024];
+    const int per = (n_segs + 1023) / 1024;
+    const int begin = threadIdx.x * per, end = min(begin + per, n_segs);
+    u32 sum = 0;
+    for (int q = begin; q < end; ++q) {
+        const long long len = seg_offsets_in[q + 1] - seg_offsets_in[q];
+        sum += static_cast<u32>((len + kTile - 1) / kTile);
+    }
+    s_part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int st = 1; st < 1024; st <<= 1) {
+        const u32 v = threadIdx.x >= (unsigned)st ? s_part[threadIdx.x - st] : 0u;
+        __syncthreads();
+        s_part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    u32 run = s_part[threadIdx.x] - sum;
+    for (int q = begin; q < end; ++q) {
+        b.seg_first[q] = run;
+        const long long len = seg_offsets_in[q + 1] - seg_offsets_in[q];
+        run += static_cast<u32>((len + kTile - 1) / kTile);
+    }
+    if (threadIdx.x == 1023) {
+        b.seg_first[n_segs] = s_part[1023];
+        *b.n_tiles = s_part[1023];
+    }
+}
+
+// Tile table: segment, first key and key count of every tile.
+__global__ void __launch_bounds__(kThreads) seg_tiles_kernel(const long long* __restrict__ seg_offsets_in, int n_segs,
+                                                             u32 max_tiles, SegBuild b) {
+    const u32 total = *b.n_tiles;
+    for (u32 t = blockIdx.x * kThreads + threadIdx.x; t < max_tiles; t += gridDim.x * kThreads) {
+        if (t >= total) {
+            b.tile_count[t] = 0;
+            continue;
+        }
+        int lo = 0, hi = n_segs;  // last segment whose first tile is <= t
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (b.seg_first[mid] <= t)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        while (lo + 1 < n_segs && b.seg_first[lo + 1] <= t) ++lo;  // skip empty segments
+        const long long start = seg_offsets_in[lo] + (long long)(t - b.seg_first[lo]) * kTile;
+        const long long end = seg_offsets_in[lo + 1];
+        b.tile_seg[t] = static_cast<u32>(lo);
+        b.tile_base[t] = static_cast<u32>(start);
+        b.tile_count[t] = static_cast<u32>(min((long long)kTile, end - start));
+    }
+}
+
+// Per-segment digit histograms of all 8 passes, one block per tile.
+__global__ void __launch_bounds__(kThreads) seg_hist_kernel(const u64* __restrict__ keys, SegTiles st, u32* seg_hist) {
+    __shared__ u32 sh[kPasses][kRadix];
+    const u32 t = blockIdx.x;
+    const u32 count = st.tile_count[t];
+    if (count == 0) return;
+    for (int i = threadIdx.x; i < kPasses * kRadix; i += kThreads) (&sh[0][0])[i] = 0;
+    __syncthreads();
+    const u32 base = st.tile_base[t];
+    for (u32 i = threadIdx.x; i < count; i += kThreads) {
+        const u64 k = __ldg(keys + base + i);
+#pragma unroll
+        for (int p = 0; p < kPasses; ++p) atomicAdd(&sh[p][(k >> (p * kRadixBits)) & (kRadix - 1)], 1u);
+    }
+    __syncthreads();
+    u32* dst = seg_hist + (size_t)st.tile_seg[t] * kPasses * kRadix;
+    for (int i = threadIdx.x; i < kPasses * kRadix; i += kThreads) {
+        const u32 v = (&sh[0][0])[i];
+        if (v) atomicAdd(dst + i, v);
+    }
+}
+
+// Digit offsets per segment and pass: the segment start plus the exclusive scan of its histogram.
+__global__ void seg_scan_kernel(const long long* __restrict__ seg_offsets_in, const u32* __restrict__ seg_hist,
+                                u32* seg_offsets) {
+    const int seg = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp >= kPasses) return;
+    const u32* h = seg_hist + ((size_t)seg * kPasses + warp) * kRadix;
+    u32* o = seg_offsets + ((size_t)seg * kPasses + warp) * kRadix;
+    u32 carry = static_cast<u32>(seg_offsets_in[seg]);
+    for (int base = 0; base < kRadix; base += 32) {
+        const u32 v = h[base + lane];
+        u32 incl = v;
+        for (int sft = 1; sft < 32; sft <<= 1) {
+            const u32 t = __shfl_up_sync(0xffffffffu, incl, sft);
+            if (lane >= sft) incl += t;
+        }
+        o[base + lane] = carry + incl - v;
+        carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+}
+
 struct PassSmem {
     u64 keys[kTile];
     u32 vals[kTile];
@@ -85,11 +207,11 @@ struct PassSmem {
     u32 tile;
 };
 
-template <bool FIRST>
+template <bool FIRST, bool SEG>
 __global__ void __launch_bounds__(kThreads, 3)
     sort_pass_kernel(const u64* __restrict__ kin, u64* __restrict__ kout, const u32* __restrict__ vin,
                      u32* __restrict__ vout, long long n, int pass, SortCtl* ctl, u32* look, u32* look_other,
-                     WsHeader* hdr) {
+                     WsHeader* hdr, SegTiles seg) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PassSmem& sm = *reinterpret_cast<PassSmem*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -99,7 +221,22 @@ __global__ void __launch_bounds__(kThreads, 3)
     if (tid == 0) sm.tile = atomicAdd(&ctl->tile_counter[pass], 1u);
     __syncthreads();
     const u32 tile = sm.tile;
-    const long long base = (long long)tile * kTile;
+    long long base, end;
+    u32 first_tile;
+    const u32* digit_offsets;
+    if (SEG) {
+        if (tile >= *seg.n_tiles) return;
+        base = seg.tile_base[tile];
+        end = base + seg.tile_count[tile];
+        const u32 sg = seg.tile_seg[tile];
+        first_tile = seg.seg_first[sg];
+        digit_offsets = seg.seg_offsets + ((size_t)sg * kPasses + pass) * kRadix;
+    } else {
+        base = (long long)tile * kTile;
+        end = n;
+        first_tile = 0;
+        digit_offsets = ctl->offsets[pass];
+    }
 
     // ---- load (warp-striped: warp w owns keys base + w*32*kItems + it*32 + lane)
     u64 key[kItems];
@@ -108,7 +245,7 @@ __global__ void __launch_bounds__(kThreads, 3)
 #pragma unroll
     for (int it = 0; it < kItems; ++it) {
         long long idx = wbase + it * 32;
-        bool ok = idx < n;
+        bool ok = idx < end;
         key[it] = ok ? __ldcs(kin + idx) : ~0ULL;
         if (FIRST)
             val[it] = static_cast<u32>(idx);
@@ -116,7 +253,7 @@ __global__ void __launch_bounds__(kThreads, 3)
             val[it] = ok ? __ldcs(vin + idx) : 0u;
     }
     auto digit_of = [&](int it) -> u32 {
-        return (wbase + it * 32 < n) ? static_cast<u32>((key[it] >> shift) & (kRadix - 1)) : static_cast<u32>(kRadix);
+        return (wbase + it * 32 < end) ? static_cast<u32>((key[it] >> shift) & (kRadix - 1)) : static_cast<u32>(kRadix);
     };
 
     // ---- rank within the warp, in memory order (stable); ranks packed two per register.
@@ -162,7 +299,7 @@ __global__ void __launch_bounds__(kThreads, 3)
             sm.warp_hist[w][d] = total;
             total += c;
         }
-        st_volatile(my_look, (tile == 0 ? kFlagPrefix : kFlagAggregate) | total);
+        st_volatile(my_look, (tile == first_tile ? kFlagPrefix : kFlagAggregate) | total);
         // block-wide exclusive scan of the totals over digits -> staging slots
         incl = total;
         for (int s = 1; s < 32; s <<= 1) {
@@ -179,14 +316,15 @@ __global__ void __launch_bounds__(kThreads, 3)
 
         // decoupled look-back over preceding tiles for digit d, kWindow descriptors per step
         u32 excl = 0;
-        if (tile > 0) {
+        if (tile > first_tile) {
             long long j = (long long)tile - 1;
             long long polls = 0;
             for (;;) {
                 u32 v[kWindow];
 #pragma unroll
                 for (int w = 0; w < kWindow; ++w)
-                    v[w] = (j - w >= 0) ? ld_volatile(look + (size_t)(j - w) * kRadix + d) : kFlagPrefix;
+                    v[w] = (j - w >= (long long)first_tile) ? ld_volatile(look + (size_t)(j - w) * kRadix + d)
+                                                            : kFlagPrefix;
                 int used = 0;
                 bool done = false;
 #pragma unroll
@@ -210,7 +348,7 @@ __global__ void __launch_bounds__(kThreads, 3)
             }
             st_volatile(my_look, kFlagPrefix | ((excl + total) & kValueMask));
         }
-        sm.global_base[d] = ctl->offsets[pass][d] + excl;
+        sm.global_base[d] = digit_offsets[d] + excl;
         look_other[(size_t)tile * kRadix + d] = 0u;  // clear the previous pass's row for the next pass
     }
     __syncthreads();
@@ -229,7 +367,7 @@ __global__ void __launch_bounds__(kThreads, 3)
     __syncthreads();
 
     // ---- write each digit's run contiguously
-    const long long remain = n - base;
+    const long long remain = end - base;
     const int count = remain < kTile ? static_cast<int>(remain) : kTile;
     for (int s = tid; s < count; s += kThreads) {
         u64 k = sm.keys[s];
@@ -303,6 +441,34 @@ int static_sort_scratch(void** out) {
 }
 }  // namespace
 
+// The 8 digit passes. Ping-pong: odd passes (1-based) write the workspace buffers, even passes the
+// output, so the eighth pass lands in keys_out / perm.
+template <bool SEG>
+int run_passes(const u64* keys_in, u64* keys_out, u32* perm, long long n, long long tiles, SortCtl* ctl, u32* const look2[2],
+               u64* keys_alt, u32* vals_alt, WsHeader* hdr, SegTiles seg, cudaStream_t st) {
+    const int smem = static_cast<int>(sizeof(PassSmem));
+    CST_CUDA(cudaFuncSetAttribute(sort_pass_kernel<true, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CST_CUDA(cudaFuncSetAttribute(sort_pass_kernel<false, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    const u64* ksrc = keys_in;
+    const u32* vsrc = nullptr;
+    for (int p = 0; p < kPasses; ++p) {
+        u64* kdst = (p % 2 == 0) ? keys_alt : keys_out;
+        u32* vdst = (p % 2 == 0) ? vals_alt : perm;
+        u32* look = look2[p & 1];
+        u32* other = look2[(p + 1) & 1];
+        if (p == 0)
+            sort_pass_kernel<true, SEG><<<(unsigned)tiles, kThreads, smem, st>>>(ksrc, kdst, vsrc, vdst, n, p, ctl, look,
+                                                                                 other, hdr, seg);
+        else
+            sort_pass_kernel<false, SEG><<<(unsigned)tiles, kThreads, smem, st>>>(ksrc, kdst, vsrc, vdst, n, p, ctl,
+                                                                                  look, other, hdr, seg);
+        CST_LAUNCHED("sort_pass_kernel");
+        ksrc = kdst;
+        vsrc = vdst;
+    }
+    return CSTONE_OK;
+}
+
 int launch_sort(const u64* keys_in, u64* keys_out, u32* perm, long long n, void* ws, cudaStream_t st) {
     SortLayout l = sort_layout(ws, n);
     WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
@@ -318,29 +484,67 @@ int launch_sort(const u64* keys_in, u64* keys_out, u32* perm, long long n, void*
     sort_scan_kernel<<<1, 32 * kPasses, 0, st>>>(l.ctl);
     CST_LAUNCHED("sort_scan_kernel");
 
-    const int smem = static_cast<int>(sizeof(PassSmem));
-    CST_CUDA(cudaFuncSetAttribute(sort_pass_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    CST_CUDA(cudaFuncSetAttribute(sort_pass_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    // ping-pong: odd passes (1-based) write the workspace buffers, even passes the output, so the
-    // eighth pass lands in keys_out / perm.
-    const u64* ksrc = keys_in;
-    const u32* vsrc = nullptr;
-    for (int p = 0; p < kPasses; ++p) {
-        u64* kdst = (p % 2 == 0) ? l.keys_alt : keys_out;
-        u32* vdst = (p % 2 == 0) ? l.vals_alt : perm;
-        u32* look = l.look[p & 1];
-        u32* other = l.look[(p + 1) & 1];
-        if (p == 0)
-            sort_pass_kernel<true><<<(unsigned)l.tiles, kThreads, smem, st>>>(ksrc, kdst, vsrc, vdst, n, p, l.ctl, look,
-                                                                              other, hdr);
-        else
-            sort_pass_kernel<false><<<(unsigned)l.tiles, kThreads, smem, st>>>(ksrc, kdst, vsrc, vdst, n, p, l.ctl,
-                                                                               look, other, hdr);
-        CST_LAUNCHED("sort_pass_kernel");
-        ksrc = kdst;
-        vsrc = vdst;
-    }
-    return CSTONE_OK;
+    return run_passes<false>(keys_in, keys_out, perm, n, l.tiles, l.ctl, l.look, l.keys_alt, l.vals_alt, hdr, SegTiles{},
+                             st);
+}
+
+// ---------------------------------------------------------------- segmented sort
+namespace {
+struct SegLayout {
+    SortCtl* ctl;
+    SegBuild b;
+    u32* look[2];
+    u64* keys_alt;
+    u32* vals_alt;
+    size_t bytes;
+    long long max_tiles;
+};
+
+SegLayout seg_layout(void* ws, long long n, int n_segs) {
+    SegLayout l;
+    Carver c(ws);
+    l.max_tiles = (n + kTile - 1) / kTile + n_segs;
+    l.ctl = c.take<SortCtl>(1);
+    l.b.n_tiles = c.take<u32>(1);
+    l.b.tile_seg = c.take<u32>((size_t)l.max_tiles);
+    l.b.tile_base = c.take<u32>((size_t)l.max_tiles);
+    l.b.tile_count = c.take<u32>((size_t)l.max_tiles);
+    l.b.seg_first = c.take<u32>((size_t)n_segs + 1);
+    l.b.seg_hist = c.take<u32>((size_t)n_segs * kPasses * kRadix);
+    l.b.seg_offsets = c.take<u32>((size_t)n_segs * kPasses * kRadix);
+    l.look[0] = c.take<u32>((size_t)l.max_tiles * kRadix);
+    l.look[1] = c.take<u32>((size_t)l.max_tiles * kRadix);
+    l.keys_alt = c.take<u64>((size_t)n);
+    l.vals_alt = c.take<u32>((size_t)n);
+    l.bytes = c.size();
+    return l;
+}
+
+}  // namespace
+
+size_t sort_segmented_ws_bytes(long long n, int n_segs) { return seg_layout(nullptr, n, n_segs).bytes; }
+
+int launch_sort_segmented(const u64* keys_in, u64* keys_out, u32* perm, long long n, const long long* seg_offsets,
+                          int n_segs, void* ws, cudaStream_t st) {
+    SegLayout l = seg_layout(ws, n, n_segs);
+    WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
+    CST_CUDA(cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st));
+    if (n == 0) return CSTONE_OK;
+    CST_CUDA(cudaMemsetAsync(l.ctl, 0, sizeof(SortCtl), st));
+    CST_CUDA(cudaMemsetAsync(l.b.seg_hist, 0, (size_t)n_segs * kPasses * kRadix * sizeof(u32), st));
+    CST_CUDA(cudaMemsetAsync(l.look[0], 0, (size_t)l.max_tiles * kRadix * sizeof(u32), st));
+    seg_setup_kernel<<<1, 1024, 0, st>>>(seg_offsets, n_segs, l.b);
+    CST_LAUNCHED("seg_setup_kernel");
+    const long long want = (l.max_tiles + kThreads - 1) / kThreads;
+    const int tgrid = static_cast<int>(want < (long long)sm_count() * 4 ? want : (long long)sm_count() * 4);
+    seg_tiles_kernel<<<tgrid, kThreads, 0, st>>>(seg_offsets, n_segs, static_cast<u32>(l.max_tiles), l.b);
+    CST_LAUNCHED("seg_tiles_kernel");
+    const SegTiles view{l.b.n_tiles, l.b.tile_seg, l.b.tile_base, l.b.tile_count, l.b.seg_first, l.b.seg_offsets};
+    seg_hist_kernel<<<(unsigned)l.max_tiles, kThreads, 0, st>>>(keys_in, view, l.b.seg_hist);
+    CST_LAUNCHED("seg_hist_kernel");
+    seg_scan_kernel<<<(unsigned)n_segs, 32 * kPasses, 0, st>>>(seg_offsets, l.b.seg_hist, l.b.seg_offsets);
+    CST_LAUNCHED("seg_scan_kernel");
+    return run_passes<true>(keys_in, keys_out, perm, n, l.max_tiles, l.ctl, l.look, l.keys_alt, l.vals_alt, hdr, view, st);
 }
 
 }  // namespace cst
@@ -377,6 +581,28 @@ int cstone_sort_static(const uint64_t* keys_in, uint64_t* keys_out, uint32_t* pe
     if (int rc = cst::static_sort_scratch(&ws)) return rc;
     return cst::launch_sort(reinterpret_cast<const cst::u64*>(keys_in), reinterpret_cast<cst::u64*>(keys_out), perm,
                             n, ws, cst::as_stream(stream));
+}
+
+int cstone_sort_segmented_workspace_size(int64_t n, int32_t n_segs, size_t* bytes) {
+    if (!bytes || n < 0 || n >= CSTONE_MAX_PARTICLES || n_segs < 1 || n_segs > (1 << 20))
+        return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_sort_segmented_workspace_size: bad argument");
+    *bytes = cst::sort_segmented_ws_bytes(n, n_segs);
+    return CSTONE_OK;
+}
+
+int cstone_sort_segmented(const uint64_t* keys_in, uint64_t* keys_out, uint32_t* perm, int64_t n,
+                          const int64_t* seg_offsets, int32_t n_segs, void* ws, size_t ws_bytes, void* stream) {
+    if (n < 0 || n >= CSTONE_MAX_PARTICLES || n_segs < 1 || n_segs > (1 << 20) || !seg_offsets ||
+        (n > 0 && (!keys_in || !keys_out || !perm)))
+        return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_sort_segmented: bad argument (n=%lld, segments=%d)",
+                         (long long)n, n_segs);
+    if (keys_in == keys_out && n > 0)
+        return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_sort_segmented: keys_in must not alias keys_out");
+    if (int rc = cst::check_ws(ws, ws_bytes, cst::sort_segmented_ws_bytes(n, n_segs), "cstone_sort_segmented"))
+        return rc;
+    return cst::launch_sort_segmented(reinterpret_cast<const cst::u64*>(keys_in), reinterpret_cast<cst::u64*>(keys_out),
+                                      perm, n, reinterpret_cast<const long long*>(seg_offsets), n_segs, ws,
+                                      cst::as_stream(stream));
 }
 
 }  // extern "C"

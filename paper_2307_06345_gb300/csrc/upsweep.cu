@@ -51,6 +51,77 @@ __global__ void __launch_bounds__(kThreads) upsweep_counts_kernel(const u32* __r
     }
 }
 
+// Batched sets: the trees of all sets in one concatenated node array, level offsets per set
+// ([set][23], global node indices). Each level is processed for all sets at once: every block
+// scans the sets' level sizes in shared memory and maps a flat item index to (set, node).
+constexpr int kMaxBatchSets = 4096;
+
+__global__ void __launch_bounds__(kThreads) upsweep_counts_batched_kernel(
+    const u32* __restrict__ elem_counts, u32 n_elements, const int* __restrict__ leaf_to_node,
+    const int* __restrict__ child, const int* __restrict__ level_offsets, int n_sets, u32* __restrict__ node_counts,
+    GridBarrier* bar, WsHeader* hdr) {
+    __shared__ u32 s_prefix[kMaxBatchSets + 1];
+    __shared__ u32 s_warp[kThreads / 32];
+    const u32 gtid = blockIdx.x * kThreads + threadIdx.x, gthreads = gridDim.x * kThreads;
+    for (u32 e = gtid; e < n_elements; e += gthreads) {
+        const int v = leaf_to_node[e];
+        if (v >= 0) node_counts[v] = elem_counts[e];
+    }
+    grid_barrier(bar, hdr);
+    constexpr int kRow = kNumLevels + 1;
+    for (int l = kLevels - 1; l >= 0; --l) {
+        // exclusive prefix over sets of the number of level-l nodes that can have children
+        const int per = (n_sets + kThreads - 1) / kThreads;
+        const int b0 = threadIdx.x * per, b1 = min(b0 + per, n_sets);
+        u32 sum = 0;
+        for (int q = b0; q < b1; ++q) {
+            const int* row = level_offsets + q * kRow;
+            sum += (row[l + 2] > row[l + 1]) ? static_cast<u32>(row[l + 1] - row[l]) : 0u;
+        }
+        u32 incl = sum;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        for (int o = 1; o < 32; o <<= 1) {
+            const u32 t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) s_warp[warp] = incl;
+        __syncthreads();
+        u32 wpre = 0, total = 0;
+        for (int w = 0; w < kThreads / 32; ++w) {
+            if (w < warp) wpre += s_warp[w];
+            total += s_warp[w];
+        }
+        u32 run = wpre + incl - sum;
+        for (int q = b0; q < b1; ++q) {
+            s_prefix[q] = run;
+            const int* row = level_offsets + q * kRow;
+            run += (row[l + 2] > row[l + 1]) ? static_cast<u32>(row[l + 1] - row[l]) : 0u;
+        }
+        if (threadIdx.x == 0) s_prefix[n_sets] = total;
+        __syncthreads();
+        if (total == 0) continue;  // no internal node at level l in any set (uniform across blocks)
+        for (u32 k = gtid; k < total; k += gthreads) {
+            int a = 0, c = n_sets;  // last set whose prefix is <= k
+            while (c - a > 1) {
+                const int mid = (a + c) >> 1;
+                if (s_prefix[mid] <= k)
+                    a = mid;
+                else
+                    c = mid;
+            }
+            while (a + 1 < n_sets && s_prefix[a + 1] <= k) ++a;
+            const u32 x = static_cast<u32>(level_offsets[a * kRow + l]) + (k - s_prefix[a]);
+            const int cc = child[x];
+            if (cc == 0) continue;
+            u32 sm = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) sm += __ldcg(node_counts + cc + q);
+            node_counts[x] = sm;
+        }
+        grid_barrier(bar, hdr);
+    }
+}
+
 // ---------------------------------------------------------------------------- compensated sums
 // A running FP32 sum with Neumaier's compensation term (s, c): s + c tracks the exact sum with an
 // error independent of the number of terms. Explicit rounding intrinsics keep the compiler from
@@ -395,6 +466,22 @@ int launch_upsweep_counts(const u32* leaf_counts, long long nl, const int* leaf_
     return CSTONE_OK;
 }
 
+int launch_upsweep_counts_batched(const u32* elem_counts, long long n_elements, const int* leaf_to_node,
+                                  const int* child, const int* level_offsets, int n_sets, u32* node_counts, void* ws,
+                                  cudaStream_t st) {
+    UpLayout l = up_layout(ws, 1, 0, false);
+    WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
+    CST_CUDA(cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st));
+    CST_CUDA(cudaMemsetAsync(l.bar, 0, sizeof(GridBarrier), st));
+    u32 ne = static_cast<u32>(n_elements);
+    GridBarrier* bar = l.bar;
+    void* args[] = {&elem_counts, &ne, &leaf_to_node, &child, &level_offsets, &n_sets, &node_counts, &bar, &hdr};
+    const int grid = cooperative_grid(reinterpret_cast<const void*>(upsweep_counts_batched_kernel), kThreads, 0, 4);
+    CST_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(upsweep_counts_batched_kernel), dim3(grid),
+                                         dim3(kThreads), args, 0, st));
+    return CSTONE_OK;
+}
+
 int launch_upsweep_multipoles(const double* x, const double* y, const double* z, const float* m, const u32* perm,
                               long long n, const u32* offsets, long long nl, const int* leaf_to_node, const int* child,
                               const int* level_offsets, const double* box, float* mass, double* com, float* quad,
@@ -469,6 +556,18 @@ int cstone_upsweep_multipoles(const double* x, const double* y, const double* z,
         return rc;
     return cst::launch_upsweep_multipoles(x, y, z, m, perm, n, offsets, n_leaves, leaf_to_node, child, level_offsets,
                                           box, mass, com, quad, ws, cst::as_stream(stream));
+}
+
+int cstone_upsweep_counts_batched(const uint32_t* elem_counts, int64_t n_elements, const int32_t* leaf_to_node,
+                                  const int32_t* child, const int32_t* level_offsets, int32_t n_sets,
+                                  uint32_t* node_counts, void* ws, size_t ws_bytes, void* stream) {
+    if (n_sets < 1 || n_sets > cst::kMaxBatchSets || n_elements < 2 * (int64_t)n_sets ||
+        n_elements > CSTONE_MAX_LEAVES || !elem_counts || !leaf_to_node || !child || !level_offsets || !node_counts)
+        return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_upsweep_counts_batched: bad argument (at most %d sets)",
+                         cst::kMaxBatchSets);
+    if (int rc = cst::check_ws(ws, ws_bytes, cst::upsweep_ws_bytes(1), "cstone_upsweep_counts_batched")) return rc;
+    return cst::launch_upsweep_counts_batched(elem_counts, n_elements, leaf_to_node, child, level_offsets, n_sets,
+                                              node_counts, ws, cst::as_stream(stream));
 }
 
 }  // extern "C"
