@@ -34,12 +34,15 @@ CPU_SAMPLE = 1 << 21
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=N_FULL)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--no-timesteps", action="store_true")
+    p.add_argument("--ts-steps", type=int, default=100)
     return p.parse_args()
 
 
@@ -256,6 +259,13 @@ def run_ours(args, rank, world, local):
         e2e = {"value": world * n / (e2e_ms * 1e-3), "unit": "particles/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}
 
+    extra = {}
+    if rank == 0 and not args.no_batched:
+        extra["batched_512_sets"] = measure_batched(dev)
+    if rank == 0 and not args.no_timesteps and args.ts_steps > 0:
+        del X, Y, Z, M
+        torch.cuda.empty_cache()
+        extra["timesteps_8x2p26"] = measure_timesteps(dev, args.ts_steps)
     line = None
     if rank == 0:
         cpu = None
@@ -280,11 +290,110 @@ def run_ours(args, rank, world, local):
             "e2e": e2e,
             "clocks": clocks.summary(),
             "gpu_launches": launches_per_step * K,
+            "extra": extra,
         }
     if dist:
         dist.barrier()
         dist.destroy_process_group()
     return line
+
+
+def measure_batched(dev, reps: int = 5):
+    """512 independent sets (sizes log-uniform in [2^10, 2^20), uniform in the unit cube or Plummer in
+    its bounding cube), Morton keys, Ncrit 32: one batched build (one launch per phase for all sets)
+    against 512 plain single-set builds on the same GPU."""
+    import numpy as np
+    import torch
+
+    import paper_2307_06345_gb300 as cs
+    from paper_2307_06345_gb300 import workloads as w
+
+    sets = w.batched_sets(512, w.BASE_SEED + 3)
+    sizes = np.array([len(st[0]) for st in sets], np.int64)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    X, Y, Z = (torch.from_numpy(np.concatenate([st[k] for st in sets])).to(dev) for k in range(3))
+    OFF = torch.from_numpy(off).to(dev)
+    boxes = torch.empty((512, 4), dtype=torch.float64, device=dev)
+    cs.cstone_bbox_batched(X, Y, Z, OFF, boxes)
+    unit = torch.tensor([0.0, 0.0, 0.0, 1.0], dtype=torch.float64, device=dev)
+    for i, st in enumerate(sets):
+        if st[3] == "uniform":
+            boxes[i] = unit
+    ws = cs.Workspace(dev)
+    stream = torch.cuda.current_stream()
+    out = cs.build_octrees_batched(X, Y, Z, OFF, curve=cs.MORTON, ncrit=32, boxes=boxes, ws=ws)
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for _ in range(reps):
+        out = cs.build_octrees_batched(X, Y, Z, OFF, curve=cs.MORTON, ncrit=32, boxes=boxes, ws=ws)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    batched_ms = s0.elapsed_time(s1) / reps
+    # plain builds, one set after the other, buffers allocated beforehand
+    views = [(X[off[i]:off[i + 1]], Y[off[i]:off[i + 1]], Z[off[i]:off[i + 1]], boxes[i].contiguous())
+             for i in range(512)]
+    bufs = [cs.build_octree(*v[:3], curve=cs.MORTON, ncrit=32, box=v[3])["buffers"] for v in views]
+    torch.cuda.synchronize()
+    s0.record(stream)
+    for v, b in zip(views, bufs):
+        cs.build_octree(*v[:3], curve=cs.MORTON, ncrit=32, box=v[3], buffers=b)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = s0.elapsed_time(s1)
+    n = int(off[-1])
+    return {"sets": 512, "particles": n, "ncrit": 32, "curve": "morton", "batched_ms": batched_ms,
+            "batched_particles_per_s": n / (batched_ms * 1e-3), "plain_sequential_ms": seq_ms,
+            "speedup_vs_plain": seq_ms / batched_ms, "leaf_iterations": out["iters"]}
+
+
+def measure_timesteps(dev, steps: int, runs: int = 8, n: int = 1 << 26):
+    """8 runs of 2^26 Plummer particles, `steps` steps, Gaussian displacements of 1e-3 of the box
+    per step (drawn on the device), Hilbert keys, Ncrit 64: every step rebuilds all runs in one
+    batched build warm-started from the previous step's leaves, in the step-0 bounding cube padded
+    by 10% of its side on every side."""
+    import torch
+
+    import paper_2307_06345_gb300 as cs
+    from paper_2307_06345_gb300 import workloads as w
+
+    xs, ys, zs = [], [], []
+    for r in range(runs):
+        x, y, z = w.plummer_device(n, w.BASE_SEED + 5 + r, dev)
+        xs.append(x), ys.append(y), zs.append(z)
+    X, Y, Z = torch.cat(xs), torch.cat(ys), torch.cat(zs)
+    del xs, ys, zs
+    OFF = torch.arange(runs + 1, dtype=torch.int64, device=dev) * n
+    st = cs.TimeStepper(X, Y, Z, OFF, curve=cs.HILBERT, ncrit=64)
+    sigma = 1e-3 * float(st.boxes[0, 3]) / 1.2
+    g = torch.Generator(device=dev)
+    g.manual_seed(w.BASE_SEED + 6)
+    stream = torch.cuda.current_stream()
+    out = st.rebuild(warm=False)
+    torch.cuda.synchronize()
+    total_ms, iters = 0.0, []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for step in range(steps):
+        for c in (X, Y, Z):
+            c.add_(torch.randn(c.shape, dtype=torch.float64, device=dev, generator=g), alpha=sigma)
+        e0.record(stream)
+        out = st.rebuild(warm=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        iters.append(out["iters"])
+    cold = cs.build_octrees_batched(X, Y, Z, OFF, curve=cs.HILBERT, ncrit=64, boxes=st.boxes)
+    same = bool(torch.equal(cold["elements"], out["elements"]) and torch.equal(cold["NK"], out["NK"]))
+    lo, side = st.boxes[:, :3], st.boxes[:, 3:4]
+    clamped = 0
+    for r in range(runs):
+        sl = slice(r * n, (r + 1) * n)
+        pts = torch.stack([X[sl], Y[sl], Z[sl]], 1)
+        clamped += int(((pts < lo[r]) | (pts >= lo[r] + side[r])).any(1).sum())
+    return {"runs": runs, "particles_per_run": n, "steps": steps, "ms_per_step": total_ms / steps,
+            "particles_per_s": runs * n * steps / (total_ms * 1e-3), "leaf_iterations_max": max(iters),
+            "leaf_iterations_mean": sum(iters) / len(iters), "last_step_warm_equals_cold": same,
+            "clamped_particles": clamped}
 
 
 def cpu_baseline(sample: int, rank_seed: int = 0):

@@ -36,6 +36,7 @@ constexpr u64 kLookPrefix = 2ULL << 62;
 constexpr u64 kLookValue = (1ULL << 62) - 1ULL;
 
 struct LoopState {
+    unsigned long long stamp[kMaxIters + 1];  // %globaltimer at the start of pass t (ns), for profiling
     u32 ne[kMaxIters + 1];        // elements entering pass t (ne[0] = initial)
     u32 changed[kMaxIters];       // pass t changed an array
     u32 tile_counter[kMaxIters];  // tile dispenser of pass t
@@ -148,6 +149,11 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const u64* __rest
 
     int t = 0;
     for (; t < max_iters; ++t) {
+        if (gtid == 0) {
+            unsigned long long now;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+            ls->stamp[t] = now;
+        }
         if (ld_volatile(&hdr->err)) break;
         const u64* K = b.K[t & 1];
         const u32* pos = b.pos[t & 1];
@@ -341,6 +347,9 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const u64* __rest
     if (ld_volatile(&hdr->err)) return;
     const bool converged = (t <= max_iters) && ld_volatile(&ls->changed[t - 1]) == 0u;
     if (gtid == 0) {
+        unsigned long long now;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+        ls->stamp[t] = now;
         ls->iters = static_cast<u32>(t);
         ls->converged = converged ? 1u : 0u;
         ls->final_buf = static_cast<u32>(t & 1);

@@ -263,6 +263,7 @@ __global__ void __launch_bounds__(kThreads) multipole_pack_kernel(const double* 
 // about it.
 constexpr int kLeafThreads = 256;
 constexpr int kGroupLanes = 8;  // lanes per leaf
+constexpr int kCached = 4;      // records per lane kept in registers (leaves up to 32 particles)
 
 __device__ __forceinline__ ff group_sum(ff v) {
 #pragma unroll
@@ -296,16 +297,34 @@ __global__ void __launch_bounds__(kLeafThreads) multipole_leaf_kernel(const u32*
     ff M = ff_zero(), S[3] = {ff_zero(), ff_zero(), ff_zero()}, Q[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) Q[k] = ff_zero();
-    Record r0{};
-    if (b > a) r0 = s.rec[__ldg(perm + a)];
+    // the first kCached records of every lane stay in registers for both passes; their gathers are
+    // all issued before any use
+    Record cache[kCached];
+#pragma unroll
+    for (int t = 0; t < kCached; ++t) {
+        const u32 j = a + t * kGroupLanes + gl;
+        cache[t] = j < b ? s.rec[__ldg(perm + j)] : Record{};
+    }
+    Record anchor{};
+    anchor.x = __shfl_sync(0xffffffffu, cache[0].x, 0, kGroupLanes);
+    anchor.y = __shfl_sync(0xffffffffu, cache[0].y, 0, kGroupLanes);
+    anchor.z = __shfl_sync(0xffffffffu, cache[0].z, 0, kGroupLanes);
+    auto record = [&](u32 t) -> Record { return t < kCached ? cache[t] : s.rec[__ldg(perm + a + t * kGroupLanes + gl)]; };
     for (u32 t = 0; t < trips; ++t) {
         const u32 j = a + t * kGroupLanes + gl;
         if (j < b) {
-            const Record r = s.rec[__ldg(perm + j)];
+            Record r;
+            if (t < kCached) {
+#pragma unroll
+                for (int q = 0; q < kCached; ++q)
+                    if (q == static_cast<int>(t)) r = cache[q];
+            } else {
+                r = record(t);
+            }
             M = ff_add(M, r.m);
-            S[0] = ff_add(S[0], __fmul_rn(r.m, fixed_diff(r.x, r0.x, f)));
-            S[1] = ff_add(S[1], __fmul_rn(r.m, fixed_diff(r.y, r0.y, f)));
-            S[2] = ff_add(S[2], __fmul_rn(r.m, fixed_diff(r.z, r0.z, f)));
+            S[0] = ff_add(S[0], __fmul_rn(r.m, fixed_diff(r.x, anchor.x, f)));
+            S[1] = ff_add(S[1], __fmul_rn(r.m, fixed_diff(r.y, anchor.y, f)));
+            S[2] = ff_add(S[2], __fmul_rn(r.m, fixed_diff(r.z, anchor.z, f)));
         }
     }
     M = group_sum(M);
@@ -314,7 +333,7 @@ __global__ void __launch_bounds__(kLeafThreads) multipole_leaf_kernel(const u32*
     long long c[3] = {0, 0, 0};
     if (b > a) {  // centre = anchor + S / M, rounded to the fixed-point grid
         const float Mv = ff_val(M);
-        const long long r0c[3] = {r0.x, r0.y, r0.z};
+        const long long r0c[3] = {anchor.x, anchor.y, anchor.z};
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             const float off = __fdiv_rn(ff_val(S[d]), Mv);
@@ -324,7 +343,14 @@ __global__ void __launch_bounds__(kLeafThreads) multipole_leaf_kernel(const u32*
     for (u32 t = 0; t < trips; ++t) {
         const u32 j = a + t * kGroupLanes + gl;
         if (j < b) {
-            const Record r = s.rec[__ldg(perm + j)];
+            Record r;
+            if (t < kCached) {
+#pragma unroll
+                for (int q = 0; q < kCached; ++q)
+                    if (q == static_cast<int>(t)) r = cache[q];
+            } else {
+                r = record(t);
+            }
             const float e0 = fixed_diff(r.x, c[0], f);
             const float e1 = fixed_diff(r.y, c[1], f);
             const float e2 = fixed_diff(r.z, c[2], f);

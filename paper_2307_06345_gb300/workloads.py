@@ -98,3 +98,24 @@ def displacement(n: int, seed: int, sigma: float):
     """Per-step Gaussian displacement of every particle (time-step sequence)."""
     g = _rng(seed)
     return sigma * g.standard_normal(n), sigma * g.standard_normal(n), sigma * g.standard_normal(n)
+
+
+def plummer_device(n: int, seed: int, device, a: float = 1.0, r_max: float = 20.0):
+    """Plummer sphere drawn on the device with torch's generator (same recipe as ``plummer``), for
+    workloads too large to draw on the host quickly."""
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    r = torch.empty(n, dtype=torch.float64, device=device)
+    todo = torch.arange(n, device=device)
+    while todo.numel():
+        u = torch.rand(todo.numel(), dtype=torch.float64, device=device, generator=g).clamp_min(1e-300)
+        rr = a / torch.sqrt(u ** (-2.0 / 3.0) - 1.0)
+        ok = rr <= r_max
+        r[todo[ok]] = rr[ok]
+        todo = todo[~ok]
+    cos_t = 2.0 * torch.rand(n, dtype=torch.float64, device=device, generator=g) - 1.0
+    phi = 2.0 * torch.pi * torch.rand(n, dtype=torch.float64, device=device, generator=g)
+    sin_t = torch.sqrt(torch.clamp(1.0 - cos_t * cos_t, min=0.0))
+    return r * sin_t * torch.cos(phi), r * sin_t * torch.sin(phi), r * cos_t
