@@ -40,6 +40,7 @@ struct LoopState {
     u32 ne[kMaxIters + 1];        // elements entering pass t (ne[0] = initial)
     u32 changed[kMaxIters];       // pass t changed an array
     u32 tile_counter[kMaxIters];  // tile dispenser of pass t
+    u32 nsplit[kMaxIters];        // splits queued in pass t
     GridBarrier bar;
     u32 iters;                    // passes executed (set at convergence)
     u32 converged;
@@ -48,6 +49,8 @@ struct LoopState {
 };
 
 struct LeafBufs {
+    u32* split_elem;  // [ecap] element index of each queued split
+    u32* split_pos;   // [ecap] its first position in the new array
     u64* K[2];
     u32* pos[2];   // lower bound of the element's key among its set's sorted keys (global index)
     u32* set[2];   // set of the element (batched builds only)
@@ -107,6 +110,7 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const u64* __rest
     __shared__ unsigned char s_op[kTile];
     __shared__ unsigned short s_split[kTile];
     __shared__ u32 s_nsplit;
+    __shared__ u32 s_qbase;
     __shared__ u32 s_off[kTile];
     __shared__ u32 s_tile;
     __shared__ u64 s_prefix;
@@ -290,15 +294,27 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const u64* __rest
                 }
             }
             __syncthreads();
-            // particle offsets of the 7 inner children of every split leaf, one warp per split: the
-            // child of a particle is one octal digit of its key, so a short range is counted with
-            // ballots over coalesced loads; a long range (early passes) is binary-searched, one
-            // child boundary per lane
-            const u32 nsplit = s_nsplit;
-            for (u32 q = warp; q < nsplit; q += kThreads / 32) {
+            // queue the tile's splits for the grid-wide phase below (one reservation per tile)
+            if (tid == 0) s_qbase = s_nsplit ? atomicAdd(&ls->nsplit[t], s_nsplit) : 0u;
+            __syncthreads();
+            for (u32 q = tid; q < s_nsplit; q += kThreads) {
                 const u32 j = s_split[q];
-                const u32 e = t0 + j;
-                const u64 o_pos = prefix + s_off[j];
+                b.split_elem[s_qbase + q] = t0 + j;
+                b.split_pos[s_qbase + q] = static_cast<u32>(prefix + s_off[j]);
+            }
+            __syncthreads();  // s_op / s_off are rewritten by the next tile
+        }
+        // particle offsets of the 7 inner children of every split leaf, one warp of the whole grid per
+        // split (early passes have few leaves but long particle ranges): the child of a particle is
+        // one octal digit of its key, so a short range is counted with ballots over coalesced
+        // loads; a long range is binary-searched, one child boundary per lane
+        grid_barrier(&ls->bar, hdr);
+        {
+            const u32 nsplit = ld_volatile(&ls->nsplit[t]);
+            const u32 gwarp = gtid >> 5, nwarps = gthreads >> 5;
+            for (u32 q = gwarp; q < nsplit; q += nwarps) {
+                const u32 e = b.split_elem[q];
+                const u32 o_pos = b.split_pos[q];
                 const u64 ke = K[e];
                 const u64 delta = K[e + 1] - ke;
                 const u32 lo = pos[e], cnt_all = pos[e + 1] - lo;
@@ -327,9 +343,8 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const u64* __rest
                         if (probe <= cnt_all && __ldg(P + lo + probe - 1) < key) below = probe;
                     }
                 }
-                if (lane >= 1 && lane < 8 && o_pos + 8 <= ecap) posn[o_pos + lane] = lo + below;
+                if (lane >= 1 && lane < 8 && static_cast<u64>(o_pos) + 8 <= ecap) posn[o_pos + lane] = lo + below;
             }
-            __syncthreads();  // s_op / s_off are rewritten by the next tile
         }
         if (tid == 0) s_any = 0;
         __syncthreads();
@@ -385,6 +400,8 @@ LeavesLayout leaves_layout(void* ws, long long ecap, int max_iters, bool batch) 
     LeavesLayout l;
     Carver c(ws);
     l.ls = c.take<LoopState>(1);
+    l.bufs.split_elem = c.take<u32>((size_t)ecap);
+    l.bufs.split_pos = c.take<u32>((size_t)ecap);
     for (int k = 0; k < 2; ++k) {
         l.bufs.K[k] = c.take<u64>((size_t)ecap);
         l.bufs.pos[k] = c.take<u32>((size_t)ecap);

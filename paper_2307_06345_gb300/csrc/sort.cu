@@ -24,10 +24,22 @@ namespace {
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 constexpr int kPasses = 8;
-constexpr int kThreads = 256;
+// Tile shape (compile-time tuning knobs): threads per block, keys per thread, blocks per SM.
+#ifndef CSTONE_SORT_THREADS
+#define CSTONE_SORT_THREADS 256
+#endif
+#ifndef CSTONE_SORT_ITEMS
+#define CSTONE_SORT_ITEMS 12
+#endif
+#ifndef CSTONE_SORT_MIN_BLOCKS
+#define CSTONE_SORT_MIN_BLOCKS 4
+#endif
+constexpr int kThreads = CSTONE_SORT_THREADS;
 constexpr int kWarps = kThreads / 32;
-constexpr int kItems = 16;
-constexpr int kTile = kThreads * kItems;  // 4096 keys per tile
+constexpr int kItems = CSTONE_SORT_ITEMS;
+static_assert(kThreads >= 256 && kThreads % 32 == 0, "one thread per digit is needed");
+static_assert(kItems % 2 == 0, "ranks are packed two per register");
+constexpr int kTile = kThreads * kItems;  // keys per tile
 constexpr int kWindow = 8;  // look-back descriptors loaded per step
 constexpr u32 kFlagAggregate = 1u << 30;
 constexpr u32 kFlagPrefix = 2u << 30;
@@ -208,7 +220,7 @@ struct PassSmem {
 };
 
 template <bool FIRST, bool SEG>
-__global__ void __launch_bounds__(kThreads, 3)
+__global__ void __launch_bounds__(kThreads, CSTONE_SORT_MIN_BLOCKS)
     sort_pass_kernel(const u64* __restrict__ kin, u64* __restrict__ kout, const u32* __restrict__ vin,
                      u32* __restrict__ vout, long long n, int pass, SortCtl* ctl, u32* look, u32* look_other,
                      WsHeader* hdr, SegTiles seg) {
@@ -260,7 +272,7 @@ __global__ void __launch_bounds__(kThreads, 3)
     // Items are handled in groups: all matches of a group first, then the leaders' reservations
     // (shared-memory atomics of one warp to one address take effect in program order, so earlier
     // items keep lower ranks), then the broadcasts - so the round trips of a group overlap.
-    constexpr int kGroup = 8;
+    constexpr int kGroup = kItems % 8 == 0 ? 8 : (kItems % 4 == 0 ? 4 : 2);
     u32 rank2[kItems / 2];
     const u32 lt = lanemask_lt();
 #pragma unroll
