@@ -60,6 +60,17 @@ def workload(n: int, rank: int = 0):
     return x, y, z, m
 
 
+def max_over_ranks(value: float, dist, device=None) -> float:
+    """Largest value over all ranks (the job's time is its slowest rank's)."""
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -207,11 +218,7 @@ def run_ours(args, rank, world, local):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    elapsed_ms = start.elapsed_time(stop)
-    if dist:
-        t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(start.elapsed_time(stop), dist, dev)
     phase_ms = {p: float(np.mean([ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(K)]))
                 for i, p in enumerate(phases)}
     ms_per_step = elapsed_ms / K
@@ -251,11 +258,7 @@ def run_ours(args, rank, world, local):
             d2h = e2e_step()
         t2.record(stream)
         torch.cuda.synchronize()
-        e2e_ms = s2.elapsed_time(t2) / ke
-        if dist:
-            t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
+        e2e_ms = max_over_ranks(s2.elapsed_time(t2) / ke, dist, dev)
         e2e = {"value": world * n / (e2e_ms * 1e-3), "unit": "particles/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}
 

@@ -26,7 +26,7 @@ namespace cst {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kItems = 2;
+constexpr int kItems = 8;
 constexpr int kTile = kThreads * kItems;  // elements per tile
 constexpr int kMaxIters = 256;
 constexpr int kSplitChunks = 16;                 // keys per lane loaded at once when counting a split

@@ -1,0 +1,49 @@
+"""Host-side logic of multi-rank runs (torchrun launches one process per GPU; the octree build
+itself needs no collective): two gloo ranks on the CPU."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    import sys
+
+    import torch.distributed as dist
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        slowest = bench.max_over_ranks(10.0 + 5.0 * rank, dist)  # rank 1 is the slow one
+        args = type("A", (), {"steps": 1, "warmup": 0})()
+        ref = bench.run_reference(args, rank, world) if rank != 0 else "rank0"
+        q.put((rank, slowest, ref))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_time_by_slowest_and_reference_on_rank0_only():
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+    assert all(p.exitcode == 0 for p in procs)
+    got = dict((r, (v, ref)) for r, v, ref in (q.get(timeout=10) for _ in range(2)))
+    assert got[0][0] == got[1][0] == 15.0
+    assert got[1][1] is None  # non-zero ranks exit the reference arm without work
