@@ -238,13 +238,23 @@ def run_ours(args, rank, world, local):
         Xe, Ye, Ze, Me = (torch.empty_like(t) for t in (X, Y, Z, M))
         h2d = sum(t.numel() * t.element_size() for t in (hx, hy, hz, hm))
 
+        out_names = ("leaves", "leaf_counts", "NK", "CO", "LO", "node_counts", "mass", "com", "quad")
+        pinned_out = {}
+
         def e2e_step():
             for src, dst in ((hx, Xe), (hy, Ye), (hz, Ze), (hm, Me)):
                 dst.copy_(src, non_blocking=True)
             o = cs.build_octree(Xe, Ye, Ze, curve=cs.HILBERT, ncrit=NCRIT, masses=Me, buffers=buffers)
-            host = [o[k].cpu() for k in ("leaves", "leaf_counts", "NK", "CO", "LO", "node_counts", "mass", "com",
-                                         "quad")]
-            return sum(t.numel() * t.element_size() for t in host)
+            nbytes = 0
+            for k in out_names:  # the tree back into pinned host buffers, one synchronisation
+                t = o[k]
+                h = pinned_out.get(k)
+                if h is None or h.numel() < t.numel():
+                    h = pinned_out[k] = torch.empty(t.numel(), dtype=t.dtype, pin_memory=True)
+                h[: t.numel()].copy_(t.reshape(-1), non_blocking=True)
+                nbytes += t.numel() * t.element_size()
+            torch.cuda.current_stream().synchronize()
+            return nbytes
 
         e2e_step()
         torch.cuda.synchronize()

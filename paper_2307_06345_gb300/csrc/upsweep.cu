@@ -7,12 +7,12 @@
 // between levels. Level l occupies nodes [LO[l], LO[l+1]); a level whose next level is empty has no
 // internal node and is skipped.
 //
-// Multipoles (three launches: pack, leaf sums, climb): FP32 accumulation with compensation. Each
-// sum is a pair (sum, compensation) updated with an exact two-sum step (Neumaier), and the pairs of
-// mass and second moments are carried up the tree in scratch so the compensation survives all 21
-// levels. Positions are held in 64-bit fixed point, so coordinate differences are exact and are
-// rounded to FP32 once; the expansion centre (centre of mass) is kept in fixed point and written
-// out in FP64.
+// Multipoles (three launches: pack, leaf sums, level-by-level combination): FP32 accumulation with
+// compensation. Each sum is a pair (sum, compensation) updated with an exact two-sum step
+// (Neumaier), and the pairs of mass and second moments are carried up the tree in scratch so the
+// compensation survives all 21 levels. Positions are held in 64-bit fixed point, so coordinate
+// differences are exact and are rounded to FP32 once; the expansion centre (centre of mass) is kept
+// in fixed point and written out in FP64.
 // A leaf takes its first particle as the anchor for the differences, an internal node its first
 // non-empty child's centre; second moments of an internal node use the parallel-axis shift
 // Q = sum_c [Q_c + M_c (c_c - c)(c_c - c)^T].
@@ -236,8 +236,7 @@ __global__ void __launch_bounds__(kThreads) multipole_pack_kernel(const double* 
     if (threadIdx.x == 0) s_f = make_frame(box);
     __syncthreads();
     const FixedFrame f = s_f;
-    for (u32 p = blockIdx.x * kThreads + threadIdx.x; p < n; p += gridDim.x * kThreads) {
-        const double px = __ldcs(x + p), py = __ldcs(y + p), pz = __ldcs(z + p);
+    auto pack = [&](double px, double py, double pz, float pm, u32 p) {
         const int ex = static_cast<int>((static_cast<u64>(__double_as_longlong(px)) >> 52) & 0x7ffu);
         const int ey = static_cast<int>((static_cast<u64>(__double_as_longlong(py)) >> 52) & 0x7ffu);
         const int ez = static_cast<int>((static_cast<u64>(__double_as_longlong(pz)) >> 52) & 0x7ffu);
@@ -250,10 +249,34 @@ __global__ void __launch_bounds__(kThreads) multipole_pack_kernel(const double* 
             r.y = fixed_of(py, f.F);
             r.z = fixed_of(pz, f.F);
         }
-        r.m = __ldcs(m + p);
+        r.m = pm;
         r.pad = 0u;
-        rec[p] = r;
+        longlong2* dst = reinterpret_cast<longlong2*>(rec + p);
+        __stcs(dst, make_longlong2(r.x, r.y));
+        __stcs(dst + 1, make_longlong2(r.z, static_cast<long long>(__float_as_uint(r.m))));
+    };
+    const bool vec = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y) | reinterpret_cast<uintptr_t>(z) |
+                       reinterpret_cast<uintptr_t>(m)) & 15u) == 0;
+    u32 done = 0;
+    if (vec) {  // four particles per thread and step, 16-byte loads
+        const u32 quads = n >> 2;
+        for (u32 q = blockIdx.x * kThreads + threadIdx.x; q < quads; q += gridDim.x * kThreads) {
+            const double2 x0 = __ldcs(reinterpret_cast<const double2*>(x) + 2 * q);
+            const double2 x1 = __ldcs(reinterpret_cast<const double2*>(x) + 2 * q + 1);
+            const double2 y0 = __ldcs(reinterpret_cast<const double2*>(y) + 2 * q);
+            const double2 y1 = __ldcs(reinterpret_cast<const double2*>(y) + 2 * q + 1);
+            const double2 z0 = __ldcs(reinterpret_cast<const double2*>(z) + 2 * q);
+            const double2 z1 = __ldcs(reinterpret_cast<const double2*>(z) + 2 * q + 1);
+            const float4 mm = __ldcs(reinterpret_cast<const float4*>(m) + q);
+            pack(x0.x, y0.x, z0.x, mm.x, 4 * q);
+            pack(x0.y, y0.y, z0.y, mm.y, 4 * q + 1);
+            pack(x1.x, y1.x, z1.x, mm.z, 4 * q + 2);
+            pack(x1.y, y1.y, z1.y, mm.w, 4 * q + 3);
+        }
+        done = quads << 2;
     }
+    for (u32 p = done + blockIdx.x * kThreads + threadIdx.x; p < n; p += gridDim.x * kThreads)
+        pack(__ldcs(x + p), __ldcs(y + p), __ldcs(z + p), __ldcs(m + p), p);
 }
 
 // Leaf moments. A leaf is handled by a group of 8 lanes, each lane taking every 8th particle and
@@ -263,7 +286,6 @@ __global__ void __launch_bounds__(kThreads) multipole_pack_kernel(const double* 
 // about it.
 constexpr int kLeafThreads = 256;
 constexpr int kGroupLanes = 8;  // lanes per leaf
-constexpr int kCached = 4;      // records per lane kept in registers (leaves up to 32 particles)
 
 __device__ __forceinline__ ff group_sum(ff v) {
 #pragma unroll
@@ -297,34 +319,17 @@ __global__ void __launch_bounds__(kLeafThreads) multipole_leaf_kernel(const u32*
     ff M = ff_zero(), S[3] = {ff_zero(), ff_zero(), ff_zero()}, Q[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) Q[k] = ff_zero();
-    // the first kCached records of every lane stay in registers for both passes; their gathers are
-    // all issued before any use
-    Record cache[kCached];
-#pragma unroll
-    for (int t = 0; t < kCached; ++t) {
-        const u32 j = a + t * kGroupLanes + gl;
-        cache[t] = j < b ? s.rec[__ldg(perm + j)] : Record{};
-    }
-    Record anchor{};
-    anchor.x = __shfl_sync(0xffffffffu, cache[0].x, 0, kGroupLanes);
-    anchor.y = __shfl_sync(0xffffffffu, cache[0].y, 0, kGroupLanes);
-    anchor.z = __shfl_sync(0xffffffffu, cache[0].z, 0, kGroupLanes);
-    auto record = [&](u32 t) -> Record { return t < kCached ? cache[t] : s.rec[__ldg(perm + a + t * kGroupLanes + gl)]; };
+    Record r0{};
+    if (b > a) r0 = s.rec[__ldg(perm + a)];
+    auto acc = [](ff& sum, float v) { sum = ff_add(sum, v); };
     for (u32 t = 0; t < trips; ++t) {
         const u32 j = a + t * kGroupLanes + gl;
         if (j < b) {
-            Record r;
-            if (t < kCached) {
-#pragma unroll
-                for (int q = 0; q < kCached; ++q)
-                    if (q == static_cast<int>(t)) r = cache[q];
-            } else {
-                r = record(t);
-            }
-            M = ff_add(M, r.m);
-            S[0] = ff_add(S[0], __fmul_rn(r.m, fixed_diff(r.x, anchor.x, f)));
-            S[1] = ff_add(S[1], __fmul_rn(r.m, fixed_diff(r.y, anchor.y, f)));
-            S[2] = ff_add(S[2], __fmul_rn(r.m, fixed_diff(r.z, anchor.z, f)));
+            const Record r = s.rec[__ldg(perm + j)];
+            acc(M, r.m);
+            acc(S[0], __fmul_rn(r.m, fixed_diff(r.x, r0.x, f)));
+            acc(S[1], __fmul_rn(r.m, fixed_diff(r.y, r0.y, f)));
+            acc(S[2], __fmul_rn(r.m, fixed_diff(r.z, r0.z, f)));
         }
     }
     M = group_sum(M);
@@ -333,7 +338,7 @@ __global__ void __launch_bounds__(kLeafThreads) multipole_leaf_kernel(const u32*
     long long c[3] = {0, 0, 0};
     if (b > a) {  // centre = anchor + S / M, rounded to the fixed-point grid
         const float Mv = ff_val(M);
-        const long long r0c[3] = {anchor.x, anchor.y, anchor.z};
+        const long long r0c[3] = {r0.x, r0.y, r0.z};
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             const float off = __fdiv_rn(ff_val(S[d]), Mv);
@@ -343,24 +348,17 @@ __global__ void __launch_bounds__(kLeafThreads) multipole_leaf_kernel(const u32*
     for (u32 t = 0; t < trips; ++t) {
         const u32 j = a + t * kGroupLanes + gl;
         if (j < b) {
-            Record r;
-            if (t < kCached) {
-#pragma unroll
-                for (int q = 0; q < kCached; ++q)
-                    if (q == static_cast<int>(t)) r = cache[q];
-            } else {
-                r = record(t);
-            }
+            const Record r = s.rec[__ldg(perm + j)];
             const float e0 = fixed_diff(r.x, c[0], f);
             const float e1 = fixed_diff(r.y, c[1], f);
             const float e2 = fixed_diff(r.z, c[2], f);
             const float me0 = __fmul_rn(r.m, e0), me1 = __fmul_rn(r.m, e1), me2 = __fmul_rn(r.m, e2);
-            Q[0] = ff_add(Q[0], __fmul_rn(me0, e0));
-            Q[1] = ff_add(Q[1], __fmul_rn(me0, e1));
-            Q[2] = ff_add(Q[2], __fmul_rn(me0, e2));
-            Q[3] = ff_add(Q[3], __fmul_rn(me1, e1));
-            Q[4] = ff_add(Q[4], __fmul_rn(me1, e2));
-            Q[5] = ff_add(Q[5], __fmul_rn(me2, e2));
+            acc(Q[0], __fmul_rn(me0, e0));
+            acc(Q[1], __fmul_rn(me0, e1));
+            acc(Q[2], __fmul_rn(me0, e2));
+            acc(Q[3], __fmul_rn(me1, e1));
+            acc(Q[4], __fmul_rn(me1, e2));
+            acc(Q[5], __fmul_rn(me2, e2));
         }
     }
 #pragma unroll
@@ -518,7 +516,7 @@ int launch_upsweep_multipoles(const double* x, const double* y, const double* z,
     CST_CUDA(cudaMemsetAsync(l.bar, 0, sizeof(GridBarrier), st));
     const u32 nn = static_cast<u32>(nl + (nl - 1) / 7);
     if (n > 0) {
-        long long want = (n + kThreads - 1) / kThreads;
+        long long want = (n + 4 * kThreads - 1) / (4 * kThreads);
         int pgrid = static_cast<int>(want < (long long)sm_count() * 8 ? want : (long long)sm_count() * 8);
         multipole_pack_kernel<<<pgrid, kThreads, 0, st>>>(x, y, z, m, static_cast<u32>(n), box, l.mp.rec, hdr);
         CST_LAUNCHED("multipole_pack_kernel");
