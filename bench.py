@@ -43,6 +43,7 @@ def parse():
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--no-timesteps", action="store_true")
     p.add_argument("--ts-steps", type=int, default=100)
+    p.add_argument("--no-table1", action="store_true")
     return p.parse_args()
 
 
@@ -210,10 +211,12 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clocks:
+        launches0 = cs.cstone_kernel_launches()
         start.record(stream)
         for k in range(K):
             step(k)
         stop.record(stream)
+        launches = cs.cstone_kernel_launches() - launches0  # the library's own count of its launches
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -275,16 +278,19 @@ def run_ours(args, rank, world, local):
     extra = {}
     if rank == 0 and not args.no_batched:
         extra["batched_512_sets"] = measure_batched(dev)
-    if rank == 0 and not args.no_timesteps and args.ts_steps > 0:
-        del X, Y, Z, M
+    if rank == 0 and (not args.no_timesteps and args.ts_steps > 0 or not args.no_table1):
+        del X, Y, Z, M, buffers, b, out
         torch.cuda.empty_cache()
+    if rank == 0 and not args.no_timesteps and args.ts_steps > 0:
         extra["timesteps_8x2p26"] = measure_timesteps(dev, args.ts_steps)
+        torch.cuda.empty_cache()
+    if rank == 0 and not args.no_table1:
+        extra["table1_gaussian"] = measure_table1(dev)
     line = None
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
             cpu = cpu_baseline(CPU_SAMPLE)
-        launches_per_step = 3 + 1 + 10 + 1 + 4 + 1 + 1
         line = {
             "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -302,7 +308,7 @@ def run_ours(args, rank, world, local):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clocks.summary(),
-            "gpu_launches": launches_per_step * K,
+            "gpu_launches": launches,
             "extra": extra,
         }
     if dist:
@@ -364,7 +370,8 @@ def measure_timesteps(dev, steps: int, runs: int = 8, n: int = 1 << 26):
     """8 runs of 2^26 Plummer particles, `steps` steps, Gaussian displacements of 1e-3 of the box
     per step (drawn on the device), Hilbert keys, Ncrit 64: every step rebuilds all runs in one
     batched build warm-started from the previous step's leaves, in the step-0 bounding cube padded
-    by 10% of its side on every side."""
+    by 10% of its side on every side. The rebuild is one CUDA graph replayed per step; the same
+    steps launched one phase at a time are timed for comparison."""
     import torch
 
     import paper_2307_06345_gb300 as cs
@@ -377,24 +384,43 @@ def measure_timesteps(dev, steps: int, runs: int = 8, n: int = 1 << 26):
     X, Y, Z = torch.cat(xs), torch.cat(ys), torch.cat(zs)
     del xs, ys, zs
     OFF = torch.arange(runs + 1, dtype=torch.int64, device=dev) * n
-    st = cs.TimeStepper(X, Y, Z, OFF, curve=cs.HILBERT, ncrit=64)
+    st = cs.GraphTimeStepper(X, Y, Z, OFF, curve=cs.HILBERT, ncrit=64)
     sigma = 1e-3 * float(st.boxes[0, 3]) / 1.2
     g = torch.Generator(device=dev)
     g.manual_seed(w.BASE_SEED + 6)
     stream = torch.cuda.current_stream()
+
+    def move():
+        for c in (X, Y, Z):
+            c.add_(torch.randn(c.shape, dtype=torch.float64, device=dev, generator=g), alpha=sigma)
+
     out = st.rebuild(warm=False)
+    move()
+    out = st.rebuild(warm=True)  # captures the step's graph (not timed)
     torch.cuda.synchronize()
     total_ms, iters = 0.0, []
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for step in range(steps):
-        for c in (X, Y, Z):
-            c.add_(torch.randn(c.shape, dtype=torch.float64, device=dev, generator=g), alpha=sigma)
+        move()
         e0.record(stream)
-        out = st.rebuild(warm=True)
+        out = st.rebuild(warm=True)  # one graph replay + one read-back of the leaf loop's outcome
         e1.record(stream)
         torch.cuda.synchronize()
         total_ms += e0.elapsed_time(e1)
         iters.append(out["iters"])
+    # the same steps without the graph (launch by launch, host reads between phases), for comparison
+    eager = cs.TimeStepper(X, Y, Z, OFF, curve=cs.HILBERT, ncrit=64)
+    eager.boxes = st.boxes
+    eager.rebuild(warm=False)
+    eager_ms, eager_steps = 0.0, min(steps, 10)
+    for _ in range(eager_steps):
+        move()
+        e0.record(stream)
+        eager.rebuild(warm=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        eager_ms += e0.elapsed_time(e1)
+    out = st.rebuild(warm=True)
     cold = cs.build_octrees_batched(X, Y, Z, OFF, curve=cs.HILBERT, ncrit=64, boxes=st.boxes)
     same = bool(torch.equal(cold["elements"], out["elements"]) and torch.equal(cold["NK"], out["NK"]))
     lo, side = st.boxes[:, :3], st.boxes[:, 3:4]
@@ -403,10 +429,96 @@ def measure_timesteps(dev, steps: int, runs: int = 8, n: int = 1 << 26):
         sl = slice(r * n, (r + 1) * n)
         pts = torch.stack([X[sl], Y[sl], Z[sl]], 1)
         clamped += int(((pts < lo[r]) | (pts >= lo[r] + side[r])).any(1).sum())
-    return {"runs": runs, "particles_per_run": n, "steps": steps, "ms_per_step": total_ms / steps,
+    return {"runs": runs, "particles_per_run": n, "steps": steps, "graph": True, "ms_per_step": total_ms / steps,
+            "eager_ms_per_step": eager_ms / eager_steps,
             "particles_per_s": runs * n * steps / (total_ms * 1e-3), "leaf_iterations_max": max(iters),
             "leaf_iterations_mean": sum(iters) / len(iters), "last_step_warm_equals_cold": same,
             "clamped_particles": clamped}
+
+
+# Table 1 of the paper, NVIDIA A100 rows (ms), for context: another GPU, its own Gaussian width.
+TABLE1_A100_MS = {
+    "1M": {"keys_morton": 0.018, "keys_hilbert": 0.084, "sort": 0.483, "leaf_update": 0.11, "internal_nodes": 0.19},
+    "32M": {"keys_morton": 0.31, "keys_hilbert": 1.9, "sort": 5.0, "leaf_update": 0.51, "internal_nodes": 0.65},
+    "512M": {"keys_morton": 7.9, "keys_hilbert": 30.0, "sort": 73.0, "leaf_update": 2.5, "internal_nodes": 5.4},
+}
+
+
+def measure_table1(dev):
+    """Replay of the paper's Table 1 workload: one 3D Gaussian (sigma 0.1 of the unit box, drawn on
+    the device) of 2^20, 2^25 and 2^29 particles, Ncrit 64, each step of the build timed on its own
+    (median of several runs, CUDA events): Morton keys, Hilbert keys, the sort of the Hilbert keys,
+    the leaf update (one rebalance pass from the converged leaves, and the full convergence from
+    the root), and the internal nodes (linked octree from the leaves)."""
+    import torch
+
+    import paper_2307_06345_gb300 as cs
+    from paper_2307_06345_gb300 import workloads as w
+
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return sorted(ts)[len(ts) // 2]
+
+    res = {}
+    for label, n, reps in (("1M", 1 << 20, 20), ("32M", 1 << 25, 10), ("512M", 1 << 29, 5)):
+        X, Y, Z = w.gaussian_device(n, w.BASE_SEED + 7, dev)
+        ws = cs.Workspace(dev)
+        box = torch.empty(4, dtype=torch.float64, device=dev)
+        cs.cstone_bbox(X, Y, Z, box, ws)
+        keys = torch.empty(n, dtype=torch.int64, device=dev)
+        r = {"particles": n}
+        r["keys_morton"] = timed(lambda: cs.cstone_keys(X, Y, Z, box, cs.MORTON, keys), reps)
+        r["keys_hilbert"] = timed(lambda: cs.cstone_keys(X, Y, Z, box, cs.HILBERT, keys), reps)
+        del X, Y, Z
+        sk = torch.empty_like(keys)
+        perm = torch.empty(n, dtype=torch.int32, device=dev)
+        r["sort"] = timed(lambda: cs.cstone_sort(keys, sk, perm, ws), reps)
+        del keys
+        cap = cs.leaf_capacity(n, 64)
+        leaves = torch.empty(cap + 1, dtype=torch.int64, device=dev)
+        counts = torch.empty(cap, dtype=torch.int32, device=dev)
+        state = {}
+
+        def cold():
+            state["nl"], state["it"] = cs.cstone_build_leaves(sk, 64, leaves, counts, None, 0, 64, ws)
+
+        r["leaf_build_from_root"] = timed(cold, reps)
+        nl = state["nl"]
+        r["leaf_build_iterations"] = state["it"]
+        converged = leaves[: nl + 1].clone()
+
+        def warm():
+            leaves[: nl + 1].copy_(converged)
+            state["nl"], state["it"] = cs.cstone_build_leaves(sk, 64, leaves, counts, None, nl, 64, ws)
+
+        copy_ms = timed(lambda: leaves[: nl + 1].copy_(converged), reps)
+        r["leaf_update"] = max(timed(warm, reps) - copy_ms, 0.0)
+        r["leaf_update_iterations"] = state["it"]
+        nn = cs.n_nodes(nl)
+        NK = torch.empty(nn, dtype=torch.int64, device=dev)
+        CO = torch.empty(nn, dtype=torch.int32, device=dev)
+        LO = torch.empty(23, dtype=torch.int32, device=dev)
+        l2n = torch.empty(nl, dtype=torch.int32, device=dev)
+        r["internal_nodes"] = timed(lambda: cs.cstone_link_tree(leaves, nl, NK, CO, LO, l2n, None, ws), reps)
+        r["n_leaves"] = nl
+        res[label] = r
+        del sk, perm, leaves, counts, converged, NK, CO, LO, l2n, ws
+        torch.cuda.empty_cache()
+    res["paper_a100_ms"] = TABLE1_A100_MS
+    res["note"] = ("ms per step, median; leaf_update = one rebalance pass from the converged leaves; the paper's "
+                   "rows are an A100 with its own (unstated) Gaussian width, context only")
+    return res
 
 
 def cpu_baseline(sample: int, rank_seed: int = 0):

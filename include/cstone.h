@@ -59,6 +59,11 @@ CSTONE_API int cstone_last_error_detail(char* buf, size_t len);
 /* Library version as major * 10000 + minor * 100 + patch. */
 CSTONE_API int cstone_version(void);
 
+/* Number of kernels this library has launched in this process so far, over all threads and
+ * devices (instrumentation; the paper has no counterpart). A launch that failed to start is
+ * counted too. */
+CSTONE_API int64_t cstone_kernel_launches(void);
+
 /* Reads the device error word kept in the header of any workspace filled by an asynchronous call
  * (cstone_sort, cstone_link_tree) and stores the corresponding status in *status (host).
  * Synchronises `stream`. The word is cleared by the next call that uses the workspace. */
@@ -249,11 +254,37 @@ CSTONE_API int cstone_build_leaves_batched(const uint64_t* sorted_keys, int64_t 
                                            uint32_t* offsets, int32_t max_iters, int32_t* iters, void* ws,
                                            size_t ws_bytes, void* stream);
 
+/* The batched leaf loop without any host synchronisation, so that it can be captured in a CUDA
+ * graph together with the phases before and after it (the time-step driver replays one graph per
+ * step). Arguments as for cstone_build_leaves_batched, except:
+ *   warm      0: every set starts from its root; else the previous arrays are in `elements` and
+ *             `element_offsets`, and their element count is element_offsets[n_sets] (read on the
+ *             device).
+ * Nothing is returned to the host: the element count of the result is element_offsets[n_sets]
+ * on the device, and the outcome (passes, CSTONE_ERR_CAPACITY with the count needed,
+ * CSTONE_ERR_NOT_CONVERGED, a timeout) stays in the workspace until cstone_leaves_result reads it.
+ * On any failure every set's output is its root array {0, 8^L} (which needs elem_cap >= 2 S), so
+ * the phases queued after this call stay within their buffers. */
+CSTONE_API int cstone_build_leaves_batched_async(const uint64_t* sorted_keys, int64_t n, const int64_t* set_offsets,
+                                                 int32_t n_sets, uint32_t ncrit, uint64_t* elements, int64_t elem_cap,
+                                                 int64_t* element_offsets, int32_t warm, uint32_t* counts,
+                                                 uint32_t* offsets, int32_t max_iters, void* ws, size_t ws_bytes,
+                                                 void* stream);
+/* Outcome of the last cstone_build_leaves_batched_async on workspace `ws` (same elem_cap and
+ * max_iters): returns its status; *n_elements (host) = elements of the result, or on
+ * CSTONE_ERR_CAPACITY the count needed; *iters (host, may be NULL) = passes. Synchronises
+ * `stream`. */
+CSTONE_API int cstone_leaves_result(void* ws, int64_t elem_cap, int32_t max_iters, void* stream, int64_t* n_elements,
+                                    int32_t* iters);
+
 /* Linked octrees of all sets (Sec. 5), concatenated: set s's tree is one breadth-first block of
  * the node arrays, from level_offsets[s][0] to level_offsets[s][22]. All indices (child,
  * level_offsets [S][23], leaf_to_node [n_elements], -1 at end keys) are global node indices.
- * n_nodes = sum over sets of n_l + (n_l - 1) / 7. A set whose node count disagrees (input not a
- * cornerstone array) is reported through the workspace error word. Asynchronous. */
+ * n_nodes = sum over sets of n_l + (n_l - 1) / 7. n_elements and n_nodes may be capacities (upper
+ * bounds) instead of the exact counts: the element count is then taken from
+ * element_offsets[n_sets] on the device, leaf_to_node is -1 from there to n_elements, and only
+ * the exact node count is written. A set whose node count disagrees (input not a cornerstone
+ * array) is reported through the workspace error word. Asynchronous. */
 CSTONE_API int cstone_link_batched_workspace_size(int64_t n_elements, int32_t n_sets, size_t* bytes);
 CSTONE_API int cstone_link_tree_batched(const uint64_t* elements, int64_t n_elements, const int64_t* element_offsets,
                                         int32_t n_sets, int64_t n_nodes, uint64_t* node_keys, int32_t* child,
@@ -261,7 +292,9 @@ CSTONE_API int cstone_link_tree_batched(const uint64_t* elements, int64_t n_elem
                                         void* stream);
 
 /* Node counts of all sets' trees (at most 4096 sets); elem_counts from
- * cstone_build_leaves_batched. Workspace: cstone_upsweep_workspace_size(1). Asynchronous. */
+ * cstone_build_leaves_batched. n_elements may be the capacity that cstone_link_tree_batched was
+ * given (its leaf_to_node is -1 beyond the actual elements). Workspace:
+ * cstone_upsweep_workspace_size(1). Asynchronous. */
 CSTONE_API int cstone_upsweep_counts_batched(const uint32_t* elem_counts, int64_t n_elements,
                                              const int32_t* leaf_to_node, const int32_t* child,
                                              const int32_t* level_offsets, int32_t n_sets, uint32_t* node_counts,

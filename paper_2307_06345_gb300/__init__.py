@@ -25,7 +25,8 @@ __all__ = [
     "cstone_build_leaves", "cstone_link_tree", "cstone_upsweep_counts", "cstone_upsweep_multipoles",
     "build_octree", "Workspace", "leaf_capacity", "n_nodes", "cstone_sort_static", "cstone_bbox_batched",
     "cstone_keys_batched", "cstone_sort_segmented", "cstone_build_leaves_batched", "cstone_link_tree_batched",
-    "cstone_upsweep_counts_batched", "build_octrees_batched",
+    "cstone_upsweep_counts_batched", "build_octrees_batched", "cstone_build_leaves_batched_async",
+    "cstone_leaves_result", "cstone_kernel_launches", "TimeStepper", "GraphTimeStepper",
 ]
 
 MORTON, HILBERT = 0, 1
@@ -64,6 +65,7 @@ def load():
             "cstone_status_string": (ctypes.c_char_p, [ctypes.c_int]),
             "cstone_last_error_detail": (ctypes.c_int, [ctypes.c_char_p, sz]),
             "cstone_version": (ctypes.c_int, []),
+            "cstone_kernel_launches": (ctypes.c_int64, []),
             "cstone_workspace_status": (ctypes.c_int, [P, P, ctypes.POINTER(ctypes.c_int)]),
             "cstone_bbox_workspace_size": (ctypes.c_int, [i64, psz]),
             "cstone_bbox": (ctypes.c_int, [P, P, P, i64, P, P, sz, P]),
@@ -90,6 +92,9 @@ def load():
             "cstone_link_batched_workspace_size": (ctypes.c_int, [i64, i32, psz]),
             "cstone_link_tree_batched": (ctypes.c_int, [P, i64, P, i32, i64, P, P, P, P, P, sz, P]),
             "cstone_upsweep_counts_batched": (ctypes.c_int, [P, i64, P, P, P, i32, P, P, sz, P]),
+            "cstone_build_leaves_batched_async": (ctypes.c_int, [P, i64, P, i32, u32, P, i64, P, i32, P, P, i32, P,
+                                                                sz, P]),
+            "cstone_leaves_result": (ctypes.c_int, [P, i64, i32, P, pi64, pi32]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(lib, name)
@@ -155,6 +160,11 @@ def _need(t: torch.Tensor, dtype, name):
 
 
 # ------------------------------------------------------------------------- C entry points
+def cstone_kernel_launches() -> int:
+    """Kernels the library has launched in this process so far."""
+    return int(load().cstone_kernel_launches())
+
+
 def cstone_bbox(x, y, z, box, ws: Workspace, stream=None):
     lib = load()
     n = x.numel()
@@ -415,6 +425,38 @@ def cstone_build_leaves_batched(sorted_keys, set_offsets, ncrit: int, elements, 
     return int(ne.value), int(it.value)
 
 
+def cstone_build_leaves_batched_async(sorted_keys, set_offsets, ncrit: int, elements, element_offsets, counts,
+                                      offsets=None, warm: bool = False, max_iters: int = 64,
+                                      ws: Workspace | None = None, stream=None):
+    """Batched leaf loop without host synchronisation (capturable in a CUDA graph); the outcome is
+    read afterwards with cstone_leaves_result on the same workspace."""
+    lib = load()
+    ws = ws or Workspace(sorted_keys.device)
+    cap = elements.numel()
+    buf = ws.get(_size(lib.cstone_leaves_batched_workspace_size, cap, max_iters))
+    _check(lib.cstone_build_leaves_batched_async(_ptr(sorted_keys), sorted_keys.numel(), _ptr(set_offsets),
+                                                 set_offsets.numel() - 1, ncrit, _ptr(elements), cap,
+                                                 _ptr(element_offsets), 1 if warm else 0, _ptr(counts), _ptr(offsets),
+                                                 max_iters, _ptr(buf), buf.numel(), _stream(stream)),
+           "cstone_build_leaves_batched_async")
+
+
+def cstone_leaves_result(ws: Workspace, elem_cap: int, max_iters: int = 64, stream=None):
+    """(n_elements, iterations) of the last asynchronous batched leaf loop on ``ws``; raises
+    CstoneError (with ``required`` on a capacity overflow) if it failed."""
+    lib = load()
+    ne = ctypes.c_int64(0)
+    it = ctypes.c_int32(0)
+    rc = lib.cstone_leaves_result(_ptr(ws.buf), elem_cap, max_iters, _stream(stream), ctypes.byref(ne),
+                                  ctypes.byref(it))
+    if rc == ERR_CAPACITY:
+        err = CstoneError(rc, "cstone_build_leaves_batched_async", _detail())
+        err.required = int(ne.value)
+        raise err
+    _check(rc, "cstone_build_leaves_batched_async")
+    return int(ne.value), int(it.value)
+
+
 def cstone_link_tree_batched(elements, n_elements: int, element_offsets, n_nodes: int, node_keys, child,
                              level_offsets, leaf_to_node, ws: Workspace | None = None, stream=None):
     lib = load()
@@ -534,3 +576,91 @@ class TimeStepper:
                                     boxes=self.boxes, warm=self.last if warm else None, ws=self.ws)
         self.last = out
         return out
+
+
+class GraphTimeStepper:
+    """Time-step driver whose whole rebuild (keys, segmented sort, warm-started batched leaf loop,
+    linked octrees, node counts) is one CUDA graph, replayed once per step.
+
+    Every buffer is allocated once at a capacity (``elem_cap`` elements over all runs; the node
+    arrays hold at most elem_cap + elem_cap / 7 nodes), the leaf loop takes its warm-start count
+    from the device, and the link and count phases run on capacities with the exact counts read on
+    the device, so no phase needs the host between the launches. After each replay the leaf loop's
+    outcome is read back once (one synchronisation per step); a capacity overflow raises
+    CstoneError. The first rebuild (cold, from the roots) runs without the graph; the warm rebuild
+    is captured on its first use."""
+
+    def __init__(self, x, y, z, set_offsets, curve: int = HILBERT, ncrit: int = 64, pad: float = 0.1,
+                 elem_cap: int | None = None, max_iters: int = 64):
+        dev = x.device
+        self.x, self.y, self.z, self.set_offsets = x, y, z, set_offsets
+        self.curve, self.ncrit, self.max_iters = curve, ncrit, max_iters
+        n, s = x.numel(), set_offsets.numel() - 1
+        self.n, self.n_sets = n, s
+        cube = torch.empty((s, 4), dtype=torch.float64, device=dev)
+        cstone_bbox_batched(x, y, z, set_offsets, cube)
+        self.boxes = padded_boxes(cube, pad)
+        cap = elem_cap or max(4 * s, 16 * (n // (ncrit + 1)) + 2 * s + 4096)
+        self.elem_cap = cap
+        self.node_cap = cap + cap // 7 + s
+        self.ws = {k: Workspace(dev) for k in ("keys", "sort", "leaves", "link", "counts")}
+        self.keys = torch.empty(n, dtype=torch.int64, device=dev)
+        self.sorted_keys = torch.empty_like(self.keys)
+        self.perm = torch.empty(n, dtype=torch.int32, device=dev)
+        self.elements = torch.empty(cap, dtype=torch.int64, device=dev)
+        self.element_offsets = torch.empty(s + 1, dtype=torch.int64, device=dev)
+        self.counts = torch.empty(cap, dtype=torch.int32, device=dev)
+        self.offsets = torch.empty(cap, dtype=torch.int32, device=dev)
+        self.NK = torch.empty(self.node_cap, dtype=torch.int64, device=dev)
+        self.CO = torch.empty(self.node_cap, dtype=torch.int32, device=dev)
+        self.LO = torch.empty((s, LEVELS + 2), dtype=torch.int32, device=dev)
+        self.l2n = torch.empty(cap, dtype=torch.int32, device=dev)
+        self.node_counts = torch.empty(self.node_cap, dtype=torch.int32, device=dev)
+        self.graph = None
+        self.have_arrays = False
+
+    def _launch(self, warm: bool):
+        w = self.ws
+        cstone_keys_batched(self.x, self.y, self.z, self.set_offsets, self.boxes, self.curve, self.keys, w["keys"])
+        cstone_sort_segmented(self.keys, self.sorted_keys, self.perm, self.set_offsets, w["sort"])
+        cstone_build_leaves_batched_async(self.sorted_keys, self.set_offsets, self.ncrit, self.elements,
+                                          self.element_offsets, self.counts, self.offsets, warm, self.max_iters,
+                                          w["leaves"])
+        cstone_link_tree_batched(self.elements, self.elem_cap, self.element_offsets, self.node_cap, self.NK, self.CO,
+                                 self.LO, self.l2n, w["link"])
+        cstone_upsweep_counts_batched(self.counts, self.elem_cap, self.l2n, self.CO, self.LO, self.n_sets,
+                                      self.node_counts, w["counts"])
+
+    def _result(self):
+        ne, iters = cstone_leaves_result(self.ws["leaves"], self.elem_cap, self.max_iters)
+        for k in ("sort", "link", "counts"):  # the phases that record device errors
+            st = self.ws[k].status()
+            if st != OK:
+                raise CstoneError(st, f"time step ({k})", _detail())
+        eo_host = self.element_offsets.cpu().tolist()
+        n_nodes = int(self.LO[-1, -1].item())
+        nl = [eo_host[i + 1] - eo_host[i] - 1 for i in range(self.n_sets)]
+        node_offsets = [0]
+        for v in nl:
+            node_offsets.append(node_offsets[-1] + v + (v - 1) // 7)
+        return {"boxes": self.boxes, "keys": self.keys, "sorted_keys": self.sorted_keys, "perm": self.perm,
+                "elements": self.elements[:ne], "n_elements": ne, "element_offsets": self.element_offsets,
+                "element_offsets_host": eo_host, "leaf_counts": self.counts[:ne], "leaf_offsets": self.offsets[:ne],
+                "iters": iters, "NK": self.NK[:n_nodes], "CO": self.CO[:n_nodes], "LO": self.LO,
+                "leaf_to_node": self.l2n[:ne], "node_counts": self.node_counts[:n_nodes],
+                "node_offsets_host": node_offsets}
+
+    def rebuild(self, warm: bool = True):
+        if not warm or not self.have_arrays:
+            self._launch(False)
+            out = self._result()
+            self.have_arrays = True
+            return out
+        if self.graph is None:
+            self._launch(True)  # sizes every workspace before the capture
+            self._result()
+            self.graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self.graph, capture_error_mode="thread_local"):
+                self._launch(True)
+        self.graph.replay()
+        return self._result()

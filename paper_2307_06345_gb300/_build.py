@@ -4,11 +4,15 @@ Each ``csrc/*.cu`` translation unit is compiled in parallel with
 ``-gencode arch=compute_103a,code=sm_103a -O3 -lineinfo`` and the objects are linked into one
 shared library next to this file. The runtime is linked dynamically, so inside a process that
 already loaded PyTorch the library shares PyTorch's CUDA runtime.
+
+Tile shapes are compile-time knobs; ``tuning.json`` (written by ``autotune.py`` on the target GPU)
+holds the chosen values, which become ``-D`` definitions of every translation unit.
 """
 from __future__ import annotations
 
 import concurrent.futures
 import glob
+import json
 import os
 import shutil
 import subprocess
@@ -19,7 +23,27 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libcstone.so")
 OBJDIR = os.path.join(HERE, "_build")
+TUNING = os.path.join(HERE, "tuning.json")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+# knob name in tuning.json -> preprocessor definition
+KNOBS = {("sort", "threads"): "CSTONE_SORT_THREADS", ("sort", "items"): "CSTONE_SORT_ITEMS",
+         ("sort", "min_blocks"): "CSTONE_SORT_MIN_BLOCKS", ("sort", "window"): "CSTONE_SORT_WINDOW",
+         ("leaves", "items"): "CSTONE_LEAVES_ITEMS"}
+
+
+def tuned_knobs() -> dict:
+    """{definition: value} from tuning.json (empty when the file is absent)."""
+    if not os.path.exists(TUNING):
+        return {}
+    with open(TUNING) as f:
+        t = json.load(f)
+    out = {}
+    for (group, key), name in KNOBS.items():
+        v = t.get("choice", {}).get(group, {}).get(key)
+        if v is not None:
+            out[name] = int(v)
+    return out
 
 
 def nvcc() -> str:
@@ -34,7 +58,8 @@ def _sources():
 
 
 def _deps():
-    return _sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(INCLUDE, "cstone.h")]
+    deps = _sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(INCLUDE, "cstone.h")]
+    return deps + ([TUNING] if os.path.exists(TUNING) else [])
 
 
 def is_stale() -> bool:
@@ -44,16 +69,18 @@ def is_stale() -> bool:
     return any(os.path.getmtime(d) > t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not is_stale():
-        return LIB
-    os.makedirs(OBJDIR, exist_ok=True)
+def _flags(knobs: dict):
+    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden", "-I", INCLUDE,
+                   "-I", CSRC, "--expt-relaxed-constexpr", "-DCSTONE_BUILD"] + [f"-D{k}={v}" for k, v in knobs.items()]
+
+
+def _compile(srcs, objdir: str, knobs: dict, verbose: bool = False):
+    os.makedirs(objdir, exist_ok=True)
     cc = nvcc()
-    flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden", "-I", INCLUDE,
-                    "-I", CSRC, "--expt-relaxed-constexpr", "-DCSTONE_BUILD"]
+    flags = _flags(knobs)
 
     def compile_one(src):
-        obj = os.path.join(OBJDIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")
         cmd = [cc] + flags + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -63,15 +90,41 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return obj
 
     with concurrent.futures.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 2)) as ex:
-        objs = list(ex.map(compile_one, _sources()))
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [cc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + [
+        return list(ex.map(compile_one, srcs))
+
+
+def _link(objs, out: str):
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = [nvcc()] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + [
         "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, out)
+    return out
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    if not force and not is_stale():
+        return LIB
+    objs = _compile(_sources(), OBJDIR, tuned_knobs(), verbose)
+    return _link(objs, LIB)
+
+
+def build_variant(knobs: dict, out: str, objdir: str) -> str:
+    """A copy of the library with the given knob definitions (on top of the tuned ones), for the
+    autotuner. Translation units that no knob of ``knobs`` can affect reuse the main build's objects."""
+    build()
+    merged = dict(tuned_knobs())
+    merged.update(knobs)
+    touched = {"sort.cu"} if any(k.startswith("CSTONE_SORT") for k in knobs) else set()
+    if any(k.startswith("CSTONE_LEAVES") for k in knobs):
+        touched.add("leaves.cu")
+    srcs = [s for s in _sources() if os.path.basename(s) in touched]
+    new_objs = {os.path.basename(o): o for o in _compile(srcs, objdir, merged)}
+    objs = [new_objs.get(os.path.basename(s)[:-3] + ".o", os.path.join(OBJDIR, os.path.basename(s)[:-3] + ".o"))
+            for s in _sources()]
+    return _link(objs, out)
 
 
 if __name__ == "__main__":

@@ -20,6 +20,7 @@ constexpr u64 kKeyEnd = 1ULL << 63;     // 8^L
 int fail(int status, const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);
 int sm_count();
+void note_launch();  // counts a kernel launch of this library (cstone_kernel_launches)
 
 #define CST_CUDA(call)                                          \
     do {                                                        \
@@ -27,7 +28,18 @@ int sm_count();
         if (cst_e_ != cudaSuccess) return cst::cuda_fail(cst_e_, #call); \
     } while (0)
 
-#define CST_LAUNCHED(name) CST_CUDA(cudaGetLastError())
+#define CST_LAUNCHED(name)              \
+    do {                                \
+        cst::note_launch();             \
+        CST_CUDA(cudaGetLastError());   \
+    } while (0)
+
+// A cooperative launch: counted, then checked like any CUDA call.
+#define CST_COOP(call)        \
+    do {                      \
+        cst::note_launch();   \
+        CST_CUDA(call);       \
+    } while (0)
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 

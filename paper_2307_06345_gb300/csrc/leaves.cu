@@ -26,7 +26,11 @@ namespace cst {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kItems = 8;
+// Elements per thread and tile (a tuning knob, set by the build from the autotuner's choice).
+#ifndef CSTONE_LEAVES_ITEMS
+#define CSTONE_LEAVES_ITEMS 8
+#endif
+constexpr int kItems = CSTONE_LEAVES_ITEMS;
 constexpr int kTile = kThreads * kItems;  // elements per tile
 constexpr int kMaxIters = 256;
 constexpr int kSplitChunks = 16;                 // keys per lane loaded at once when counting a split
@@ -100,12 +104,38 @@ __device__ __forceinline__ u32 decide(const u64* __restrict__ K, const u32* __re
     return 1u;
 }
 
+constexpr u32 kDeviceCount = 0xffffffffu;  // ne_start: take the element count from the device
+
+// Outputs of a failed asynchronous build: every set gets its root array {0, 8^L}, so that the
+// phases queued after it stay within their buffers. The failure itself is in the workspace.
+template <bool BATCH>
+__device__ void write_root_arrays(const u64* P, u32 n, SetView sv, u32 gtid, u32 gthreads, u64* out_keys,
+                                  u32* out_counts, u32* out_offsets) {
+    const u32 ns = BATCH ? static_cast<u32>(sv.n_sets) : 1u;
+    for (u32 q = gtid; q < ns; q += gthreads) {
+        const u32 lo = BATCH ? static_cast<u32>(sv.particle_offsets[q]) : 0u;
+        const u32 hi = BATCH ? static_cast<u32>(sv.particle_offsets[q + 1]) : n;
+        out_keys[2 * q] = 0ULL;
+        out_keys[2 * q + 1] = kKeyEnd;
+        out_counts[2 * q] = hi - lo;
+        if (BATCH) {
+            out_counts[2 * q + 1] = 0u;
+            sv.element_offsets[q] = 2 * q;
+            if (q == 0) sv.element_offsets[ns] = 2 * ns;
+        }
+        if (out_offsets) {
+            out_offsets[2 * q] = lo;
+            out_offsets[2 * q + 1] = hi;
+        }
+    }
+}
+
 template <bool BATCH>
 __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const u64* __restrict__ P, u32 n, u32 ncrit,
                                                                LeafBufs b, u32 ecap, int max_iters, int warm,
-                                                               u64* look, u32 max_tiles, LoopState* ls,
-                                                               WsHeader* hdr, SetView sv, u64* out_keys,
-                                                               u32* out_counts, u32* out_offsets) {
+                                                               u32 ne_start, int fallback, u64* look, u32 max_tiles,
+                                                               LoopState* ls, WsHeader* hdr, SetView sv,
+                                                               u64* out_keys, u32* out_counts, u32* out_offsets) {
     __shared__ u32 s_warp[kThreads / 32];
     __shared__ unsigned char s_op[kTile];
     __shared__ unsigned short s_split[kTile];
@@ -118,9 +148,18 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const u64* __rest
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const u32 gtid = blockIdx.x * kThreads + tid, gthreads = gridDim.x * kThreads;
 
-    // ---- initial arrays in buffer 0, with the particle position of every key
+    // ---- initial arrays in buffer 0, with the particle position of every key. A warm start reads
+    // the previous arrays from the output buffers; their element count is ne_start, or the last
+    // element offset on the device when ne_start is kDeviceCount.
+    const int ns = BATCH ? sv.n_sets : 1;
+    u32 ne_init = 2u * static_cast<u32>(ns);
+    if (warm) ne_init = ne_start != kDeviceCount ? ne_start : static_cast<u32>(sv.element_offsets[sv.n_sets]);
+    if (ne_init < 2u * static_cast<u32>(ns) || ne_init > ecap) {  // the same decision in every block
+        if (gtid == 0) raise_error(hdr, CSTONE_ERR_INVALID_ARG, 0x60000u);
+        ne_init = 0;
+    }
+    if (gtid == 0) ls->ne[0] = ne_init;
     if (!warm) {  // every set starts from its root {0, 8^L}
-        const int ns = BATCH ? sv.n_sets : 1;
         for (u32 q = gtid; q < static_cast<u32>(ns); q += gthreads) {
             b.K[0][2 * q] = 0ULL;
             b.K[0][2 * q + 1] = kKeyEnd;
@@ -129,7 +168,7 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const u64* __rest
             if (BATCH) b.set[0][2 * q] = b.set[0][2 * q + 1] = q;
         }
     } else {
-        const u32 ne0 = ls->ne[0];
+        const u32 ne0 = ne_init;
         for (u32 e = gtid; e < ne0; e += gthreads) {
             u32 lo = 0, hi = n;
             if (BATCH) {
@@ -145,7 +184,8 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const u64* __rest
                 lo = static_cast<u32>(sv.particle_offsets[a]);
                 hi = static_cast<u32>(sv.particle_offsets[a + 1]);
             }
-            const u64 k = b.K[0][e];
+            const u64 k = out_keys[e];
+            b.K[0][e] = k;
             b.pos[0][e] = k == kKeyEnd ? hi : lower_bound_in(P, lo, hi, k);
         }
     }
@@ -359,7 +399,10 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const u64* __rest
         }
     }
 
-    if (ld_volatile(&hdr->err)) return;
+    if (ld_volatile(&hdr->err)) {
+        if (fallback) write_root_arrays<BATCH>(P, n, sv, gtid, gthreads, out_keys, out_counts, out_offsets);
+        return;
+    }
     const bool converged = (t <= max_iters) && ld_volatile(&ls->changed[t - 1]) == 0u;
     if (gtid == 0) {
         unsigned long long now;
@@ -369,7 +412,10 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const u64* __rest
         ls->converged = converged ? 1u : 0u;
         ls->final_buf = static_cast<u32>(t & 1);
     }
-    if (!converged) return;
+    if (!converged) {
+        if (fallback) write_root_arrays<BATCH>(P, n, sv, gtid, gthreads, out_keys, out_counts, out_offsets);
+        return;
+    }
     const u32 ne = ld_volatile(&ls->ne[t]);
     const u64* K = b.K[t & 1];
     const u32* pos = b.pos[t & 1];
@@ -418,40 +464,15 @@ int leaves_grid() {
     return cooperative_grid(reinterpret_cast<const void*>(leaves_loop_kernel<BATCH>), kThreads, 0, 8);
 }
 
-// Runs the loop; on success *ne_out is the element count of the converged arrays.
-template <bool BATCH>
-int run_leaves(const u64* P, long long n, u32 ncrit, u64* leaves, long long ecap, long long ne0, long long* ne_out,
-               u32* counts, u32* offsets, int max_iters, int* iters, SetView sv, void* ws, cudaStream_t st,
-               const char* who) {
-    LeavesLayout l = leaves_layout(ws, ecap, max_iters, BATCH);
-    WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
-    CST_CUDA(cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st));
-    CST_CUDA(cudaMemsetAsync(l.ls, 0, sizeof(LoopState), st));
-    CST_CUDA(cudaMemsetAsync(l.look, 0, (size_t)l.max_tiles * max_iters * sizeof(u64), st));
-    int warm = ne0 > 0 ? 1 : 0;
-    const u32 ne_start = warm ? static_cast<u32>(ne0) : static_cast<u32>(2 * (BATCH ? sv.n_sets : 1));
-    CST_CUDA(cudaMemcpyAsync(&l.ls->ne[0], &ne_start, sizeof(u32), cudaMemcpyHostToDevice, st));
-    if (warm)
-        CST_CUDA(cudaMemcpyAsync(l.bufs.K[0], leaves, (size_t)ne0 * sizeof(u64), cudaMemcpyDeviceToDevice, st));
-
-    const u64* P_ = P;
-    u32 n_ = static_cast<u32>(n), ncrit_ = ncrit, ecap_ = static_cast<u32>(ecap), max_tiles = l.max_tiles;
-    int max_iters_ = max_iters;
-    LeafBufs bufs = l.bufs;
-    u64* look = l.look;
-    LoopState* ls = l.ls;
-    u64* out_keys = leaves;
-    u32* out_counts = counts;
-    u32* out_offsets = offsets;
-    void* args[] = {&P_, &n_, &ncrit_, &bufs, &ecap_, &max_iters_, &warm, &look, &max_tiles, &ls, &hdr, &sv,
-                    &out_keys, &out_counts, &out_offsets};
-    CST_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(leaves_loop_kernel<BATCH>), dim3(leaves_grid<BATCH>()),
-                                         dim3(kThreads), args, 0, st));
-
+// Outcome of the loop recorded in a workspace: status, passes, element count (or, on a capacity
+// overflow, the count needed). Synchronises the stream.
+int read_leaves_result(void* ws, cudaStream_t st, long long ecap, int max_iters, long long* ne_out, int* iters,
+                       const char* who) {
+    LoopState* lsp = reinterpret_cast<LoopState*>(static_cast<char*>(ws) + sizeof(WsHeader));
     WsHeader h;
     LoopState s;
-    CST_CUDA(cudaMemcpyAsync(&h, hdr, sizeof(h), cudaMemcpyDeviceToHost, st));
-    CST_CUDA(cudaMemcpyAsync(&s, l.ls, sizeof(s), cudaMemcpyDeviceToHost, st));
+    CST_CUDA(cudaMemcpyAsync(&h, ws, sizeof(h), cudaMemcpyDeviceToHost, st));
+    CST_CUDA(cudaMemcpyAsync(&s, lsp, sizeof(s), cudaMemcpyDeviceToHost, st));
     CST_CUDA(cudaStreamSynchronize(st));
     if (iters) *iters = static_cast<int>(s.iters);
     if (h.err == CSTONE_ERR_CAPACITY) {
@@ -462,6 +483,40 @@ int run_leaves(const u64* P, long long n, u32 ncrit, u64* leaves, long long ecap
     if (!s.converged) return fail(CSTONE_ERR_NOT_CONVERGED, "%s: not converged after %d passes", who, max_iters);
     *ne_out = s.ne[s.iters];
     return CSTONE_OK;
+}
+
+// Runs the loop. ne0: element count of the warm-start arrays held in `leaves` (0 = cold start from
+// the roots, -1 = warm start with the count read on the device). With sync, *ne_out is the element
+// count of the converged arrays on success; without, nothing is read back (the outcome stays in
+// the workspace for read_leaves_result) and a failure leaves every set's root array as output.
+template <bool BATCH>
+int run_leaves(const u64* P, long long n, u32 ncrit, u64* leaves, long long ecap, long long ne0, long long* ne_out,
+               u32* counts, u32* offsets, int max_iters, int* iters, SetView sv, void* ws, cudaStream_t st,
+               const char* who, bool sync = true) {
+    LeavesLayout l = leaves_layout(ws, ecap, max_iters, BATCH);
+    WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
+    CST_CUDA(cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st));
+    CST_CUDA(cudaMemsetAsync(l.ls, 0, sizeof(LoopState), st));
+    CST_CUDA(cudaMemsetAsync(l.look, 0, (size_t)l.max_tiles * max_iters * sizeof(u64), st));
+    int warm = ne0 != 0 ? 1 : 0;
+    u32 ne_start = ne0 < 0 ? kDeviceCount : static_cast<u32>(ne0);
+    int fallback = sync ? 0 : 1;
+
+    const u64* P_ = P;
+    u32 n_ = static_cast<u32>(n), ncrit_ = ncrit, ecap_ = static_cast<u32>(ecap), max_tiles = l.max_tiles;
+    int max_iters_ = max_iters;
+    LeafBufs bufs = l.bufs;
+    u64* look = l.look;
+    LoopState* ls = l.ls;
+    u64* out_keys = leaves;
+    u32* out_counts = counts;
+    u32* out_offsets = offsets;
+    void* args[] = {&P_,       &n_,   &ncrit_,    &bufs, &ecap_, &max_iters_, &warm,     &ne_start,   &fallback,
+                    &look,     &max_tiles, &ls,   &hdr,  &sv,    &out_keys,   &out_counts, &out_offsets};
+    CST_COOP(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(leaves_loop_kernel<BATCH>), dim3(leaves_grid<BATCH>()),
+                                         dim3(kThreads), args, 0, st));
+    if (!sync) return CSTONE_OK;
+    return read_leaves_result(ws, st, ecap, max_iters, ne_out, iters, who);
 }
 
 }  // namespace
@@ -483,6 +538,14 @@ int launch_build_leaves(const u64* P, long long n, u32 ncrit, u64* leaves, long 
     }
     if (rc == CSTONE_OK) *n_leaves = ne - 1;
     return rc;
+}
+
+int launch_build_leaves_batched_async(const u64* P, long long n, const long long* particle_offsets, int n_sets,
+                                      u32 ncrit, u64* leaves, long long ecap, long long* element_offsets, int warm,
+                                      u32* counts, u32* offsets, int max_iters, void* ws, cudaStream_t st) {
+    return run_leaves<true>(P, n, ncrit, leaves, ecap, warm ? -1 : 0, nullptr, counts, offsets, max_iters, nullptr,
+                            SetView{particle_offsets, element_offsets, n_sets}, ws, st,
+                            "cstone_build_leaves_batched_async", false);
 }
 
 int launch_build_leaves_batched(const u64* P, long long n, const long long* particle_offsets, int n_sets, u32 ncrit,
@@ -557,6 +620,37 @@ int cstone_build_leaves_batched(const uint64_t* sorted_keys, int64_t n, const in
                                               reinterpret_cast<cst::u64*>(elements), elem_cap,
                                               reinterpret_cast<long long*>(element_offsets), &ne, counts, offsets,
                                               max_iters, &it, ws, cst::as_stream(stream));
+    *n_elements = ne;
+    if (iters) *iters = it;
+    return rc;
+}
+
+int cstone_build_leaves_batched_async(const uint64_t* sorted_keys, int64_t n, const int64_t* set_offsets,
+                                      int32_t n_sets, uint32_t ncrit, uint64_t* elements, int64_t elem_cap,
+                                      int64_t* element_offsets, int32_t warm, uint32_t* counts, uint32_t* offsets,
+                                      int32_t max_iters, void* ws, size_t ws_bytes, void* stream) {
+    if (n < 0 || n >= CSTONE_MAX_PARTICLES || n_sets < 1 || n_sets > (1 << 20) || !set_offsets || !elements ||
+        !element_offsets || !counts || elem_cap < 2 * (int64_t)n_sets || elem_cap > CSTONE_MAX_LEAVES ||
+        max_iters < 1 || max_iters > 256 || (n > 0 && !sorted_keys))
+        return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_build_leaves_batched_async: bad argument");
+    if (int rc = cst::check_ws(ws, ws_bytes, cst::leaves_batched_ws_bytes(elem_cap, max_iters),
+                               "cstone_build_leaves_batched_async"))
+        return rc;
+    return cst::launch_build_leaves_batched_async(reinterpret_cast<const cst::u64*>(sorted_keys), n,
+                                                  reinterpret_cast<const long long*>(set_offsets), n_sets, ncrit,
+                                                  reinterpret_cast<cst::u64*>(elements), elem_cap,
+                                                  reinterpret_cast<long long*>(element_offsets), warm ? 1 : 0, counts,
+                                                  offsets, max_iters, ws, cst::as_stream(stream));
+}
+
+int cstone_leaves_result(void* ws, int64_t elem_cap, int32_t max_iters, void* stream, int64_t* n_elements,
+                         int32_t* iters) {
+    if (!ws || !n_elements || elem_cap < 1 || max_iters < 1 || max_iters > 256)
+        return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_leaves_result: bad argument");
+    long long ne = 0;
+    int it = 0;
+    const int rc = cst::read_leaves_result(ws, cst::as_stream(stream), elem_cap, max_iters, &ne, &it,
+                                           "cstone_build_leaves_batched_async");
     *n_elements = ne;
     if (iters) *iters = it;
     return rc;

@@ -273,7 +273,11 @@ __global__ void __launch_bounds__(1024) link_b_setup_kernel(LinkSets ls) {
     }
 }
 
-__global__ void __launch_bounds__(kThreads) link_b_tiles_kernel(LinkSets ls, u32 max_tiles) {
+__global__ void __launch_bounds__(kThreads) link_b_tiles_kernel(LinkSets ls, u32 max_tiles, u32 elem_cap,
+                                                                int* __restrict__ leaf_to_node) {
+    // elements between the actual count and the capacity map to no node
+    const u32 ne = static_cast<u32>(ls.elem_offsets[ls.n_sets]);
+    for (u32 e = ne + blockIdx.x * kThreads + threadIdx.x; e < elem_cap; e += gridDim.x * kThreads) leaf_to_node[e] = -1;
     const u32 total = *ls.n_tiles;
     for (u32 t = blockIdx.x * kThreads + threadIdx.x; t < max_tiles; t += gridDim.x * kThreads) {
         if (t >= total) {
@@ -416,8 +420,10 @@ __global__ void __launch_bounds__(kThreads) link_b_scatter_kernel(const u64* __r
     }
 }
 
-__global__ void __launch_bounds__(kThreads) link_b_child_kernel(const u64* __restrict__ NK, u32 n_nodes, int n_sets,
+__global__ void __launch_bounds__(kThreads) link_b_child_kernel(const u64* __restrict__ NK, u32 node_cap, int n_sets,
                                                                 const int* __restrict__ LO, int* __restrict__ CO) {
+    const u32 last = static_cast<u32>(LO[n_sets * (kNumLevels + 1) - 1]);  // nodes of all sets
+    const u32 n_nodes = last < node_cap ? last : node_cap;
     for (u32 x = blockIdx.x * kThreads + threadIdx.x; x < n_nodes; x += gridDim.x * kThreads) {
         int lo_s = 0, hi_s = n_sets;  // set whose node block contains x
         while (hi_s - lo_s > 1) {
@@ -488,7 +494,7 @@ int launch_link_batched(const u64* K, long long n_elements, const long long* ele
     CST_LAUNCHED("link_b_setup_kernel");
     const long long want = (l.max_tiles + kThreads - 1) / kThreads;
     const int tgrid = static_cast<int>(want < (long long)sm_count() * 4 ? want : (long long)sm_count() * 4);
-    link_b_tiles_kernel<<<tgrid, kThreads, 0, st>>>(l.ls, l.max_tiles);
+    link_b_tiles_kernel<<<tgrid, kThreads, 0, st>>>(l.ls, l.max_tiles, static_cast<u32>(n_elements), leaf_to_node);
     CST_LAUNCHED("link_b_tiles_kernel");
     link_b_count_kernel<<<l.max_tiles, kThreads, 0, st>>>(K, l.ls, l.counts);
     CST_LAUNCHED("link_b_count_kernel");

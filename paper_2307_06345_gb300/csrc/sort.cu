@@ -24,7 +24,8 @@ namespace {
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 constexpr int kPasses = 8;
-// Tile shape (compile-time tuning knobs): threads per block, keys per thread, blocks per SM.
+// Tile shape (compile-time tuning knobs, set by the build from the autotuner's choice): threads per
+// block, keys per thread, blocks per SM, and look-back descriptors read per step.
 #ifndef CSTONE_SORT_THREADS
 #define CSTONE_SORT_THREADS 256
 #endif
@@ -40,7 +41,10 @@ constexpr int kItems = CSTONE_SORT_ITEMS;
 static_assert(kThreads >= 256 && kThreads % 32 == 0, "one thread per digit is needed");
 static_assert(kItems % 2 == 0, "ranks are packed two per register");
 constexpr int kTile = kThreads * kItems;  // keys per tile
-constexpr int kWindow = 8;  // look-back descriptors loaded per step
+#ifndef CSTONE_SORT_WINDOW
+#define CSTONE_SORT_WINDOW 4
+#endif
+constexpr int kWindow = CSTONE_SORT_WINDOW;  // look-back descriptors loaded per step
 constexpr u32 kFlagAggregate = 1u << 30;
 constexpr u32 kFlagPrefix = 2u << 30;
 constexpr u32 kValueMask = (1u << 30) - 1u;
@@ -212,9 +216,8 @@ __global__ void seg_scan_kernel(const long long* __restrict__ seg_offsets_in, co
 struct PassSmem {
     u64 keys[kTile];
     u32 vals[kTile];
-    u32 warp_hist[kWarps][kRadix];  // per-warp digit counts, then per-warp exclusive offsets
-    u32 tile_start[kRadix];         // first slot of each digit in the staged tile
-    u32 global_base[kRadix];        // output position of the tile's first key of each digit
+    u32 warp_hist[kWarps][kRadix];  // per-warp digit counts, then each warp's first staging slot
+    u32 delta[kRadix];              // output position minus staging slot, per digit
     u32 scan_tmp[kWarps];
     u32 tile;
 };
@@ -233,19 +236,20 @@ __global__ void __launch_bounds__(kThreads, CSTONE_SORT_MIN_BLOCKS)
     if (tid == 0) sm.tile = atomicAdd(&ctl->tile_counter[pass], 1u);
     __syncthreads();
     const u32 tile = sm.tile;
-    long long base, end;
+    u32 base, count;  // first key of the tile and keys in it (n < 2^30, so 32-bit offsets)
     u32 first_tile;
     const u32* digit_offsets;
     if (SEG) {
         if (tile >= *seg.n_tiles) return;
         base = seg.tile_base[tile];
-        end = base + seg.tile_count[tile];
+        count = seg.tile_count[tile];
         const u32 sg = seg.tile_seg[tile];
         first_tile = seg.seg_first[sg];
         digit_offsets = seg.seg_offsets + ((size_t)sg * kPasses + pass) * kRadix;
     } else {
-        base = (long long)tile * kTile;
-        end = n;
+        base = tile * static_cast<u32>(kTile);
+        const long long remain = n - (long long)base;
+        count = remain < kTile ? static_cast<u32>(remain) : static_cast<u32>(kTile);
         first_tile = 0;
         digit_offsets = ctl->offsets[pass];
     }
@@ -253,19 +257,20 @@ __global__ void __launch_bounds__(kThreads, CSTONE_SORT_MIN_BLOCKS)
     // ---- load (warp-striped: warp w owns keys base + w*32*kItems + it*32 + lane)
     u64 key[kItems];
     u32 val[kItems];
-    const long long wbase = base + (long long)warp * 32 * kItems + lane;
+    const u64* tkeys = kin + base;
+    const u32 woff = static_cast<u32>(warp * 32 * kItems + lane);  // offset of item 0 within the tile
 #pragma unroll
     for (int it = 0; it < kItems; ++it) {
-        long long idx = wbase + it * 32;
-        bool ok = idx < end;
-        key[it] = ok ? __ldcs(kin + idx) : ~0ULL;
+        const u32 o = woff + it * 32;
+        const bool ok = o < count;
+        key[it] = ok ? __ldcs(tkeys + o) : ~0ULL;
         if (FIRST)
-            val[it] = static_cast<u32>(idx);
+            val[it] = base + o;
         else
-            val[it] = ok ? __ldcs(vin + idx) : 0u;
+            val[it] = ok ? __ldcs(vin + base + o) : 0u;
     }
     auto digit_of = [&](int it) -> u32 {
-        return (wbase + it * 32 < end) ? static_cast<u32>((key[it] >> shift) & (kRadix - 1)) : static_cast<u32>(kRadix);
+        return (woff + it * 32 < count) ? static_cast<u32>((key[it] >> shift) & (kRadix - 1)) : static_cast<u32>(kRadix);
     };
 
     // ---- rank within the warp, in memory order (stable); ranks packed two per register.
@@ -306,11 +311,7 @@ __global__ void __launch_bounds__(kThreads, CSTONE_SORT_MIN_BLOCKS)
     u32* my_look = look + (size_t)tile * kRadix + d;
     if (owner) {
 #pragma unroll
-        for (int w = 0; w < kWarps; ++w) {
-            const u32 c = sm.warp_hist[w][d];
-            sm.warp_hist[w][d] = total;
-            total += c;
-        }
+        for (int w = 0; w < kWarps; ++w) total += sm.warp_hist[w][d];
         st_volatile(my_look, (tile == first_tile ? kFlagPrefix : kFlagAggregate) | total);
         // block-wide exclusive scan of the totals over digits -> staging slots
         incl = total;
@@ -324,7 +325,15 @@ __global__ void __launch_bounds__(kThreads, CSTONE_SORT_MIN_BLOCKS)
     if (owner) {
         u32 wpre = 0;
         for (int w = 0; w < warp; ++w) wpre += sm.scan_tmp[w];
-        sm.tile_start[d] = wpre + incl - total;
+        const u32 start = wpre + incl - total;  // first staging slot of digit d
+        // staging slot of warp w's first key of digit d
+        u32 run = start;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            const u32 c = sm.warp_hist[w][d];
+            sm.warp_hist[w][d] = run;
+            run += c;
+        }
 
         // decoupled look-back over preceding tiles for digit d, kWindow descriptors per step
         u32 excl = 0;
@@ -360,7 +369,7 @@ __global__ void __launch_bounds__(kThreads, CSTONE_SORT_MIN_BLOCKS)
             }
             st_volatile(my_look, kFlagPrefix | ((excl + total) & kValueMask));
         }
-        sm.global_base[d] = digit_offsets[d] + excl;
+        sm.delta[d] = digit_offsets[d] + excl - start;  // output position minus staging slot
         look_other[(size_t)tile * kRadix + d] = 0u;  // clear the previous pass's row for the next pass
     }
     __syncthreads();
@@ -371,7 +380,7 @@ __global__ void __launch_bounds__(kThreads, CSTONE_SORT_MIN_BLOCKS)
         const u32 dd = digit_of(it);
         if (dd < kRadix) {
             const u32 r = (rank2[it >> 1] >> ((it & 1) * 16)) & 0xffffu;
-            u32 slot = sm.tile_start[dd] + sm.warp_hist[warp][dd] + r;
+            const u32 slot = sm.warp_hist[warp][dd] + r;
             sm.keys[slot] = key[it];
             sm.vals[slot] = val[it];
         }
@@ -379,12 +388,9 @@ __global__ void __launch_bounds__(kThreads, CSTONE_SORT_MIN_BLOCKS)
     __syncthreads();
 
     // ---- write each digit's run contiguously
-    const long long remain = end - base;
-    const int count = remain < kTile ? static_cast<int>(remain) : kTile;
-    for (int s = tid; s < count; s += kThreads) {
-        u64 k = sm.keys[s];
-        u32 dd = static_cast<u32>((k >> shift) & (kRadix - 1));
-        u32 pos = sm.global_base[dd] + (static_cast<u32>(s) - sm.tile_start[dd]);
+    for (u32 s = tid; s < count; s += kThreads) {
+        const u64 k = sm.keys[s];
+        const u32 pos = sm.delta[static_cast<u32>(k >> shift) & (kRadix - 1)] + s;
         kout[pos] = k;
         vout[pos] = sm.vals[s];
     }

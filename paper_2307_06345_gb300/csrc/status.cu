@@ -1,4 +1,5 @@
 // Status strings, per-thread error detail and small shared host utilities of the C ABI.
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -9,7 +10,10 @@ namespace cst {
 
 namespace {
 thread_local char g_detail[512] = "";
-}
+std::atomic<long long> g_launches{0};
+}  // namespace
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 int fail(int status, const char* fmt, ...) {
     va_list ap;
@@ -76,6 +80,8 @@ int cstone_last_error_detail(char* buf, size_t len) {
 }
 
 int cstone_version(void) { return 100; }
+
+int64_t cstone_kernel_launches(void) { return cst::g_launches.load(std::memory_order_relaxed); }
 
 int cstone_workspace_status(const void* ws, void* stream, int* status) {
     if (!ws || !status) return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_workspace_status: NULL argument");

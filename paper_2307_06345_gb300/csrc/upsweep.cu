@@ -485,7 +485,7 @@ int launch_upsweep_counts(const u32* leaf_counts, long long nl, const int* leaf_
     GridBarrier* bar = l.bar;
     void* args[] = {&leaf_counts, &nl_, &leaf_to_node, &child, &level_offsets, &node_counts, &bar, &hdr};
     const int grid = cooperative_grid(reinterpret_cast<const void*>(upsweep_counts_kernel), kThreads, 0, 4);
-    CST_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(upsweep_counts_kernel), dim3(grid), dim3(kThreads),
+    CST_COOP(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(upsweep_counts_kernel), dim3(grid), dim3(kThreads),
                                          args, 0, st));
     return CSTONE_OK;
 }
@@ -501,7 +501,7 @@ int launch_upsweep_counts_batched(const u32* elem_counts, long long n_elements, 
     GridBarrier* bar = l.bar;
     void* args[] = {&elem_counts, &ne, &leaf_to_node, &child, &level_offsets, &n_sets, &node_counts, &bar, &hdr};
     const int grid = cooperative_grid(reinterpret_cast<const void*>(upsweep_counts_batched_kernel), kThreads, 0, 4);
-    CST_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(upsweep_counts_batched_kernel), dim3(grid),
+    CST_COOP(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(upsweep_counts_batched_kernel), dim3(grid),
                                          dim3(kThreads), args, 0, st));
     return CSTONE_OK;
 }
@@ -532,7 +532,7 @@ int launch_upsweep_multipoles(const double* x, const double* y, const double* z,
         GridBarrier* bar = l.bar;
         void* args[] = {&child, &level_offsets, &nn_, &mp, &box, &mass, &com, &quad, &bar, &hdr};
         const int grid = cooperative_grid(reinterpret_cast<const void*>(multipole_level_kernel), kThreads, 0, 4);
-        CST_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(multipole_level_kernel), dim3(grid),
+        CST_COOP(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(multipole_level_kernel), dim3(grid),
                                              dim3(kThreads), args, 0, st));
     }
     return CSTONE_OK;

@@ -8,7 +8,8 @@ arrays feed the CUDA library and the CPU oracle. Distributions:
   r > r_max, isotropic direction (the 3D analogue of the paper's Gaussian / 1/r test sets).
 * ``clumps``   - 1,000 Gaussian clumps with centres U[0,1)^3 and sigma = 10^U(-4,-2), 80% of the
   particles pick a clump uniformly at random, 20% are a U[0,1)^3 background.
-* ``gaussian`` - one isotropic 3D Gaussian (the density profile of the paper's Table 1).
+* ``gaussian`` - one isotropic 3D Gaussian, sigma 0.1 around (0.5, 0.5, 0.5) (the density profile
+  of the paper's Table 1, whose width the paper does not state).
 * ``lognormal_masses`` - float32 masses, lognormal(0, 1).
 """
 from __future__ import annotations
@@ -119,3 +120,13 @@ def plummer_device(n: int, seed: int, device, a: float = 1.0, r_max: float = 20.
     phi = 2.0 * torch.pi * torch.rand(n, dtype=torch.float64, device=device, generator=g)
     sin_t = torch.sqrt(torch.clamp(1.0 - cos_t * cos_t, min=0.0))
     return r * sin_t * torch.cos(phi), r * sin_t * torch.sin(phi), r * cos_t
+
+
+def gaussian_device(n: int, seed: int, device, sigma: float = 0.1):
+    """One isotropic 3D Gaussian drawn on the device with torch's generator (same recipe as
+    ``gaussian``), for the largest sizes of the Table 1 replay."""
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    return tuple(0.5 + sigma * torch.randn(n, dtype=torch.float64, device=device, generator=g) for _ in range(3))

@@ -40,6 +40,8 @@ def test_status_strings(clib):
         assert s and s.decode()
     assert clib.cstone_status_string(99).decode() == "unknown status"
     assert clib.cstone_version() >= 100
+    clib.cstone_kernel_launches.restype = ctypes.c_int64
+    assert clib.cstone_kernel_launches() >= 0
 
 
 def test_workspace_queries_and_argument_checks(clib):

@@ -6,6 +6,9 @@
 * 2^27 clump particles, Hilbert, Ncrit 16 and 64 (the benchmark workload): sampled keys against
   the oracle, size-independent properties of the sort and the tree, and sampled subtrees whose
   particle sets the oracle rebuilds from the raw coordinates (leaves, counts, multipoles).
+* 2^20 particles of one 3D Gaussian, Morton and Hilbert, Ncrit 64 (the smallest size of the
+  paper's Table 1 replay): every output against the oracle, and about 18 particles per leaf as
+  the paper reports for its Gaussian sets.
 """
 import numpy as np
 import pytest
@@ -50,6 +53,19 @@ def test_uniform_65536_morton_full_parity(lib, oracle):
     err = multipole_errors(M_ref, c_ref, q_ref, out["mass"].cpu().numpy().astype(np.float64),
                            out["com"].cpu().numpy().T.copy(), out["quad"].cpu().numpy().T.astype(np.float64), side)
     assert max(err.values()) <= 1e-6, err
+
+
+@pytest.mark.parametrize("curve", [0, 1])
+def test_gaussian_2p20_full_parity(lib, oracle, curve):
+    from paper_2307_06345_gb300 import workloads as w
+    n = 1 << 20
+    x, y, z = w.gaussian(n, w.BASE_SEED + 7)
+    ref = oracle.full_build(x, y, z, curve, 64)
+    out = lib.build_octree(dev(x), dev(y), dev(z), curve=curve, ncrit=64)
+    torch.cuda.synchronize()
+    _check_all(out, ref)
+    # Table 1 reports 55.8K leaves for 1M Gaussian particles at Ncrit 64 (about 18.8 per leaf)
+    assert 15.0 < n / out["n_leaves"] < 23.0
 
 
 def test_plummer_2p25_hilbert_full_parity(lib, oracle):

@@ -114,6 +114,18 @@ def test_sort_in_place(lib, oracle):
     assert np.array_equal(u64(t), s) and np.array_equal(u32(perm), p)
 
 
+def test_kernel_launch_counter(lib):
+    k = dev(np.arange(1000, dtype=np.uint64)[::-1].copy())
+    kout = torch.empty_like(k)
+    perm = torch.empty(1000, dtype=torch.int32, device="cuda")
+    ws = lib.Workspace()
+    before = lib.cstone_kernel_launches()
+    lib.cstone_sort(k, kout, perm, ws)
+    torch.cuda.synchronize()
+    # histogram, scan and one launch per 8-bit digit pass
+    assert lib.cstone_kernel_launches() - before == 10
+
+
 def test_sort_repeated_calls_reuse_workspace(lib, oracle):
     # the look-back regions are reused across calls of different sizes
     ws = lib.Workspace()

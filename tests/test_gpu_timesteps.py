@@ -11,6 +11,8 @@ from _gpu_util import dev, i32, u32, u64
 
 pytestmark = pytest.mark.gpu
 
+KEY_END = 1 << 63
+
 
 def _equal(a, b, keys):
     for k in keys:
@@ -53,3 +55,109 @@ def test_time_steps_warm_equals_cold_and_oracle(lib, oracle):
             assert np.array_equal(E[eo[r]: eo[r + 1]], ref["K"])
             assert np.array_equal(NK[no[r]: no[r + 1]], ref["NK"])
             assert np.array_equal(counts[no[r]: no[r + 1]], ref["counts"])
+
+
+def test_graph_time_steps_equal_eager_and_oracle(lib, oracle):
+    # the whole rebuild replayed as one CUDA graph per step gives the eager driver's trees
+    from paper_2307_06345_gb300 import workloads as w
+    runs, n, steps = 4, 1 << 16, 5
+    parts = [w.plummer(n, w.BASE_SEED + 40 + r) for r in range(runs)]
+    x = np.concatenate([p[0] for p in parts])
+    y = np.concatenate([p[1] for p in parts])
+    z = np.concatenate([p[2] for p in parts])
+    off = (np.arange(runs + 1) * n).astype(np.int64)
+    X, Y, Z, OFF = dev(x), dev(y), dev(z), dev(off)
+    g = lib.GraphTimeStepper(X, Y, Z, OFF, curve=lib.HILBERT, ncrit=32)
+    e = lib.TimeStepper(X, Y, Z, OFF, curve=lib.HILBERT, ncrit=32)
+    assert torch.equal(g.boxes, e.boxes)
+    boxes = g.boxes.cpu().numpy()
+    side0 = float(boxes[0, 3]) / 1.2
+    for step in range(steps):
+        if step > 0:
+            dx, dy, dz = w.displacement(x.size, w.BASE_SEED + 140 + step, 2e-3 * side0)
+            x, y, z = x + dx, y + dy, z + dz
+            X.copy_(dev(x)), Y.copy_(dev(y)), Z.copy_(dev(z))
+        a = g.rebuild(warm=step > 0)
+        b = e.rebuild(warm=step > 0)
+        torch.cuda.synchronize()
+        _equal(a, b, ["sorted_keys", "perm", "elements", "element_offsets", "leaf_counts", "NK", "CO", "LO",
+                      "leaf_to_node", "node_counts"])
+        assert a["node_offsets_host"] == b["node_offsets_host"]
+        if step == steps - 1:
+            assert g.graph is not None  # warm steps were replayed from the graph
+            eo, no = a["element_offsets_host"], a["node_offsets_host"]
+            E, NK, counts = u64(a["elements"]), u64(a["NK"]), u32(a["node_counts"])
+            for r in range(runs):
+                ra, rb = off[r], off[r + 1]
+                ref = oracle.full_build(x[ra:rb], y[ra:rb], z[ra:rb], oracle.HILBERT, 32, box=boxes[r])
+                assert np.array_equal(E[eo[r]: eo[r + 1]], ref["K"])
+                assert np.array_equal(NK[no[r]: no[r + 1]], ref["NK"])
+                assert np.array_equal(counts[no[r]: no[r + 1]], ref["counts"])
+
+
+@pytest.mark.parametrize("failure", ["capacity", "not_converged"])
+def test_async_leaves_failure_leaves_root_arrays(lib, failure):
+    # a failed asynchronous leaf loop reports its status afterwards and leaves every set's root
+    # array, so that the phases queued after it run within their buffers
+    from paper_2307_06345_gb300 import workloads as w
+    sizes = [5000, 3000, 0, 7000]
+    xs = [w.uniform(k, w.BASE_SEED + 60 + i) for i, k in enumerate(sizes)]
+    x, y, z = (np.concatenate([p[d] for p in xs]) for d in range(3))
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    X, Y, Z, OFF = dev(x), dev(y), dev(z), dev(off)
+    s = len(sizes)
+    boxes = torch.tensor([[0.0, 0.0, 0.0, 1.0]] * s, dtype=torch.float64, device="cuda")
+    ws = lib.Workspace()
+    keys = torch.empty(x.size, dtype=torch.int64, device="cuda")
+    lib.cstone_keys_batched(X, Y, Z, OFF, boxes, lib.MORTON, keys, ws)
+    sk, perm = torch.empty_like(keys), torch.empty(x.size, dtype=torch.int32, device="cuda")
+    lib.cstone_sort_segmented(keys, sk, perm, OFF, ws)
+    cap, iters = (2 * s + 8, 64) if failure == "capacity" else (4096, 2)
+    elements = torch.empty(cap, dtype=torch.int64, device="cuda")
+    eo = torch.empty(s + 1, dtype=torch.int64, device="cuda")
+    counts = torch.empty(cap, dtype=torch.int32, device="cuda")
+    lws = lib.Workspace()
+    lib.cstone_build_leaves_batched_async(sk, OFF, 8, elements, eo, counts, None, False, iters, lws)
+    node_cap = cap + cap // 7 + s
+    NK = torch.empty(node_cap, dtype=torch.int64, device="cuda")
+    CO = torch.empty(node_cap, dtype=torch.int32, device="cuda")
+    LO = torch.empty((s, 23), dtype=torch.int32, device="cuda")
+    l2n = torch.empty(cap, dtype=torch.int32, device="cuda")
+    nc = torch.empty(node_cap, dtype=torch.int32, device="cuda")
+    kws, cws = lib.Workspace(), lib.Workspace()
+    lib.cstone_link_tree_batched(elements, cap, eo, node_cap, NK, CO, LO, l2n, kws)
+    lib.cstone_upsweep_counts_batched(counts, cap, l2n, CO, LO, s, nc, cws)
+    with pytest.raises(lib.CstoneError) as ei:
+        lib.cstone_leaves_result(lws, cap, iters)
+    assert ei.value.status == (lib.ERR_CAPACITY if failure == "capacity" else lib.ERR_NOT_CONVERGED)
+    if failure == "capacity":
+        assert ei.value.required > cap
+    assert kws.status() == 0 and cws.status() == 0
+    assert u64(eo).tolist() == [2 * q for q in range(s + 1)]
+    E = u64(elements[: 2 * s])
+    assert E[0::2].tolist() == [0] * s and E[1::2].tolist() == [KEY_END] * s
+    assert u32(counts[: 2 * s])[0::2].tolist() == sizes
+    assert u32(nc[:s]).tolist() == sizes  # one root node per set, holding the whole set
+
+
+def test_async_leaves_equal_sync(lib, oracle):
+    from paper_2307_06345_gb300 import workloads as w
+    sizes = [20_000, 1, 0, 33_333, 4096]
+    xs = [w.plummer(k, w.BASE_SEED + 70 + i) for i, k in enumerate(sizes)]
+    x, y, z = (np.concatenate([p[d] for p in xs]) for d in range(3))
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    X, Y, Z, OFF = dev(x), dev(y), dev(z), dev(off)
+    ref = lib.build_octrees_batched(X, Y, Z, OFF, curve=lib.HILBERT, ncrit=16)
+    cap = 1 << 16  # room for the intermediate arrays of the loop, not only the result
+    elements = torch.empty(cap, dtype=torch.int64, device="cuda")
+    eo = torch.empty(len(sizes) + 1, dtype=torch.int64, device="cuda")
+    counts = torch.empty(cap, dtype=torch.int32, device="cuda")
+    ws = lib.Workspace()
+    for warm in (False, True):  # cold, then warm from its own (converged) output
+        lib.cstone_build_leaves_batched_async(ref["sorted_keys"], OFF, 16, elements, eo, counts, None, warm, 64, ws)
+        ne, iters = lib.cstone_leaves_result(ws, cap, 64)
+        assert ne == ref["n_elements"]
+        assert torch.equal(elements[:ne], ref["elements"]) and torch.equal(eo, ref["element_offsets"])
+        assert torch.equal(counts[:ne], ref["leaf_counts"])
+        if warm:
+            assert iters == 1
