@@ -582,17 +582,18 @@ class GraphTimeStepper:
     """Time-step driver whose whole rebuild (keys, segmented sort, warm-started batched leaf loop,
     linked octrees, node counts) is one CUDA graph, replayed once per step.
 
-    Every buffer is allocated once at a capacity (``elem_cap`` elements over all runs; the node
-    arrays hold at most elem_cap + elem_cap / 7 nodes), the leaf loop takes its warm-start count
-    from the device, and the link and count phases run on capacities with the exact counts read on
-    the device, so no phase needs the host between the launches. After each replay the leaf loop's
-    outcome is read back once (one synchronisation per step); a capacity overflow raises
-    CstoneError. The first rebuild (cold, from the roots) runs without the graph; the warm rebuild
-    is captured on its first use."""
+    Every buffer is allocated at a capacity (``elem_cap`` elements over all runs; the node arrays
+    hold at most elem_cap + elem_cap / 7 + S nodes), the leaf loop takes its warm-start count from
+    the device, and the link and count phases run on capacities with the exact counts read on the
+    device, so no phase needs the host between the launches. After each replay the outcome is read
+    back (two synchronisations per step). The first rebuild (cold, from the roots) runs without the
+    graph and sets the capacity to twice its element count; the warm rebuild is captured on its
+    first use. A capacity overflow doubles the capacity, drops the graph and rebuilds cold."""
 
     def __init__(self, x, y, z, set_offsets, curve: int = HILBERT, ncrit: int = 64, pad: float = 0.1,
                  elem_cap: int | None = None, max_iters: int = 64):
         dev = x.device
+        self.device = dev
         self.x, self.y, self.z, self.set_offsets = x, y, z, set_offsets
         self.curve, self.ncrit, self.max_iters = curve, ncrit, max_iters
         n, s = x.numel(), set_offsets.numel() - 1
@@ -600,24 +601,32 @@ class GraphTimeStepper:
         cube = torch.empty((s, 4), dtype=torch.float64, device=dev)
         cstone_bbox_batched(x, y, z, set_offsets, cube)
         self.boxes = padded_boxes(cube, pad)
-        cap = elem_cap or max(4 * s, 16 * (n // (ncrit + 1)) + 2 * s + 4096)
-        self.elem_cap = cap
-        self.node_cap = cap + cap // 7 + s
+        self.fixed_cap = elem_cap is not None
         self.ws = {k: Workspace(dev) for k in ("keys", "sort", "leaves", "link", "counts")}
         self.keys = torch.empty(n, dtype=torch.int64, device=dev)
         self.sorted_keys = torch.empty_like(self.keys)
         self.perm = torch.empty(n, dtype=torch.int32, device=dev)
-        self.elements = torch.empty(cap, dtype=torch.int64, device=dev)
         self.element_offsets = torch.empty(s + 1, dtype=torch.int64, device=dev)
-        self.counts = torch.empty(cap, dtype=torch.int32, device=dev)
-        self.offsets = torch.empty(cap, dtype=torch.int32, device=dev)
+        self.LO = torch.empty((s, LEVELS + 2), dtype=torch.int32, device=dev)
+        self._alloc(elem_cap or max(4 * s, 16 * (n // (ncrit + 1)) + 2 * s + 4096))
+        self.have_arrays = False
+
+    def _alloc(self, cap: int, keep: int = 0):
+        """(Re)allocates the capacity-sized buffers; the first ``keep`` elements survive."""
+        dev, s = self.device, self.n_sets
+        old = getattr(self, "elements", None)
+        self.elem_cap = int(cap)
+        self.node_cap = self.elem_cap + self.elem_cap // 7 + s
+        self.elements = torch.empty(self.elem_cap, dtype=torch.int64, device=dev)
+        if keep:
+            self.elements[:keep].copy_(old[:keep])
+        self.counts = torch.empty(self.elem_cap, dtype=torch.int32, device=dev)
+        self.offsets = torch.empty(self.elem_cap, dtype=torch.int32, device=dev)
         self.NK = torch.empty(self.node_cap, dtype=torch.int64, device=dev)
         self.CO = torch.empty(self.node_cap, dtype=torch.int32, device=dev)
-        self.LO = torch.empty((s, LEVELS + 2), dtype=torch.int32, device=dev)
-        self.l2n = torch.empty(cap, dtype=torch.int32, device=dev)
+        self.l2n = torch.empty(self.elem_cap, dtype=torch.int32, device=dev)
         self.node_counts = torch.empty(self.node_cap, dtype=torch.int32, device=dev)
         self.graph = None
-        self.have_arrays = False
 
     def _launch(self, warm: bool):
         w = self.ws
@@ -633,12 +642,16 @@ class GraphTimeStepper:
 
     def _result(self):
         ne, iters = cstone_leaves_result(self.ws["leaves"], self.elem_cap, self.max_iters)
-        for k in ("sort", "link", "counts"):  # the phases that record device errors
-            st = self.ws[k].status()
+        # error words of the phases that record device errors, the element offsets and the node
+        # count, in one read-back
+        names = ("sort", "link", "counts")
+        words = [self.ws[k].buf[:4].view(torch.int32).to(torch.int64) for k in names]
+        small = torch.cat(words + [self.element_offsets, self.LO[-1, -1:].to(torch.int64)]).cpu().tolist()
+        for k, st in zip(names, small[:3]):
             if st != OK:
-                raise CstoneError(st, f"time step ({k})", _detail())
-        eo_host = self.element_offsets.cpu().tolist()
-        n_nodes = int(self.LO[-1, -1].item())
+                raise CstoneError(int(st), f"time step ({k})", "device error word")
+        eo_host = small[3: 4 + self.n_sets]
+        n_nodes = small[-1]
         nl = [eo_host[i + 1] - eo_host[i] - 1 for i in range(self.n_sets)]
         node_offsets = [0]
         for v in nl:
@@ -650,17 +663,44 @@ class GraphTimeStepper:
                 "leaf_to_node": self.l2n[:ne], "node_counts": self.node_counts[:n_nodes],
                 "node_offsets_host": node_offsets}
 
+    def _cold(self):
+        while True:
+            self._launch(False)
+            try:
+                out = self._result()
+                break
+            except CstoneError as e:
+                if e.status != ERR_CAPACITY:
+                    raise
+                self._alloc(max(2 * self.elem_cap, getattr(e, "required", 0) + 1024))
+        ne = out["n_elements"]
+        tight = 2 * ne + 64 * self.n_sets + 4096
+        if not self.fixed_cap and tight < self.elem_cap:
+            self._alloc(tight, keep=ne)  # element offsets live outside the capacity buffers
+            out = dict(out, elements=self.elements[:ne])
+        self.have_arrays = True
+        return out
+
     def rebuild(self, warm: bool = True):
         if not warm or not self.have_arrays:
-            self._launch(False)
-            out = self._result()
-            self.have_arrays = True
-            return out
+            return self._cold()
         if self.graph is None:
             self._launch(True)  # sizes every workspace before the capture
-            self._result()
+            try:
+                self._result()
+            except CstoneError as e:
+                if e.status != ERR_CAPACITY:
+                    raise
+                self._alloc(max(2 * self.elem_cap, getattr(e, "required", 0) + 1024))
+                return self._cold()  # the failed pass left root arrays: start again from the roots
             self.graph = torch.cuda.CUDAGraph()
             with torch.cuda.graph(self.graph, capture_error_mode="thread_local"):
                 self._launch(True)
         self.graph.replay()
-        return self._result()
+        try:
+            return self._result()
+        except CstoneError as e:
+            if e.status != ERR_CAPACITY:
+                raise
+            self._alloc(max(2 * self.elem_cap, getattr(e, "required", 0) + 1024))
+            return self._cold()
