@@ -18,13 +18,20 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "cstone_oracle.c")
 _HDR = os.path.join(_HERE, "cstone_oracle.h")
-_LIB = os.path.join(_HERE, "liboracle.so")
+# one build of the C source per number of levels: 21 (63-bit keys) and 10 (30-bit keys)
+_LIBS = {21: os.path.join(_HERE, "liboracle.so"), 10: os.path.join(_HERE, "liboracle30.so")}
+_LIB = _LIBS[21]
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 L = 21
 KEY_END = 1 << 63
 MORTON, HILBERT = 0, 1
+
+
+def key_end(levels: int = L) -> int:
+    """8^L, one past the last key."""
+    return 1 << (3 * levels)
 
 
 class OracleError(RuntimeError):
@@ -32,24 +39,26 @@ class OracleError(RuntimeError):
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle shared library in-tree (gcc, -O2 -ffp-contract=off)."""
-    stale = (not os.path.exists(_LIB)) or any(
-        os.path.getmtime(s) > os.path.getmtime(_LIB) for s in (_SRC, _HDR))
-    if force or stale:
-        tmp = _LIB + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-               "-o", tmp, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB)
+    """Compile the oracle shared libraries in-tree (gcc, -O2 -ffp-contract=off), one per number of
+    levels."""
+    for levels, path in _LIBS.items():
+        stale = (not os.path.exists(path)) or any(os.path.getmtime(s) > os.path.getmtime(path) for s in (_SRC, _HDR))
+        if force or stale:
+            tmp = path + f".tmp{os.getpid()}"
+            cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                   f"-DORACLE_L={levels}", "-o", tmp, _SRC, "-lm"]
+            subprocess.run(cmd, check=True)
+            os.replace(tmp, path)
     return _LIB
 
 
-def _load():
-    global _lib
+def _load(levels: int = L):
     with _lock:
-        if _lib is None:
+        if levels not in _libs:
+            if levels not in _LIBS:
+                raise ValueError(f"the oracle is built for {sorted(_LIBS)} levels, not {levels}")
             build()
-            lib = ctypes.CDLL(_LIB)
+            lib = ctypes.CDLL(_LIBS[levels])
             P = ctypes.c_void_p
             i64, u32, i32, dbl = ctypes.c_int64, ctypes.c_uint32, ctypes.c_int, ctypes.c_double
             sigs = {
@@ -79,8 +88,8 @@ def _load():
                 fn = getattr(lib, name)
                 fn.restype = res
                 fn.argtypes = args
-            _lib = lib
-    return _lib
+            _libs[levels] = lib
+    return _libs[levels]
 
 
 def _ptr(a: np.ndarray):
@@ -104,18 +113,18 @@ def bounding_cube(x, y, z) -> np.ndarray:
     return box
 
 
-def grid_coord(x: float, lo: float, side: float) -> int:
-    lib = _load()
+def grid_coord(x: float, lo: float, side: float, levels: int = L) -> int:
+    lib = _load(levels)
     return int(lib.oracle_grid_coord(x, lo, lib.oracle_scale(side)))
 
 
-def morton_key(ix: int, iy: int, iz: int) -> int:
-    return int(_load().oracle_morton_key(ix, iy, iz))
+def morton_key(ix: int, iy: int, iz: int, levels: int = L) -> int:
+    return int(_load(levels).oracle_morton_key(ix, iy, iz))
 
 
-def morton_decode(key: int):
+def morton_decode(key: int, levels: int = L):
     a, b, c = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
-    _load().oracle_morton_decode(key, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+    _load(levels).oracle_morton_decode(key, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
     return a.value, b.value, c.value
 
 
@@ -129,11 +138,11 @@ def hilbert_decode(key: int, order: int = L):
     return a.value, b.value, c.value
 
 
-def keys(x, y, z, box, curve: int) -> np.ndarray:
+def keys(x, y, z, box, curve: int, levels: int = L) -> np.ndarray:
     x, y, z = (_c(a, np.float64) for a in (x, y, z))
     box = _c(box, np.float64)
     out = np.empty(x.size, np.uint64)
-    _check(_load().oracle_keys(_ptr(x), _ptr(y), _ptr(z), x.size, _ptr(box), curve, _ptr(out)), "keys")
+    _check(_load(levels).oracle_keys(_ptr(x), _ptr(y), _ptr(z), x.size, _ptr(box), curve, _ptr(out)), "keys")
     return out
 
 
@@ -158,10 +167,10 @@ def histogram(P, K) -> np.ndarray:
     return N
 
 
-def rebalance_decision(K, N, ncrit: int) -> np.ndarray:
+def rebalance_decision(K, N, ncrit: int, levels: int = L) -> np.ndarray:
     K, N = _c(K, np.uint64), _c(N, np.uint32)
     O = np.empty(K.size, np.uint32)
-    _check(_load().oracle_rebalance_decision(_ptr(K), _ptr(N), K.size - 1, ncrit, _ptr(O)), "g1")
+    _check(_load(levels).oracle_rebalance_decision(_ptr(K), _ptr(N), K.size - 1, ncrit, _ptr(O)), "g1")
     return O
 
 
@@ -172,25 +181,25 @@ def exclusive_scan(O) -> np.ndarray:
     return out
 
 
-def rebalance(K, O, Oprime) -> np.ndarray:
+def rebalance(K, O, Oprime, levels: int = L) -> np.ndarray:
     K, O, Op = _c(K, np.uint64), _c(O, np.uint32), _c(Oprime, np.uint64)
     nl = K.size - 1
     out = np.empty(int(Op[nl]) + 1, np.uint64)
-    _check(_load().oracle_rebalance(_ptr(K), _ptr(O), _ptr(Op), nl, _ptr(out)), "g3")
+    _check(_load(levels).oracle_rebalance(_ptr(K), _ptr(O), _ptr(Op), nl, _ptr(out)), "g3")
     return out
 
 
-def leaf_capacity_bound(n: int, ncrit: int) -> int:
+def leaf_capacity_bound(n: int, ncrit: int, levels: int = L) -> int:
     """Upper bound on the leaves of a balanced tree: every split needs more than Ncrit particles in
     the node, so each level holds at most n / (Ncrit + 1) split nodes, each adding 7 leaves."""
-    return 1 + 7 * L * (n // (ncrit + 1) + 1)
+    return 1 + 7 * levels * (n // (ncrit + 1) + 1)
 
 
-def build_leaves(P, ncrit: int, K_init=None, max_iters: int = 64, cap: int | None = None):
+def build_leaves(P, ncrit: int, K_init=None, max_iters: int = 64, cap: int | None = None, levels: int = L):
     """Literal f/g iteration of Sec. 4. Returns (K, N, iterations)."""
     P = _c(P, np.uint64)
     if cap is None:
-        cap = leaf_capacity_bound(P.size, ncrit)
+        cap = leaf_capacity_bound(P.size, ncrit, levels)
     Kout = np.empty(cap + 1, np.uint64)
     Nout = np.empty(cap, np.uint32)
     nl = ctypes.c_int64()
@@ -200,52 +209,52 @@ def build_leaves(P, ncrit: int, K_init=None, max_iters: int = 64, cap: int | Non
     else:
         kin = _c(K_init, np.uint64)
         nl_init = kin.size - 1
-    rc = _load().oracle_build_leaves(_ptr(P), P.size, ncrit, _ptr(kin) if kin is not None else None, nl_init,
+    rc = _load(levels).oracle_build_leaves(_ptr(P), P.size, ncrit, _ptr(kin) if kin is not None else None, nl_init,
                                      _ptr(Kout), cap, ctypes.byref(nl), _ptr(Nout), max_iters, ctypes.byref(it))
     _check(rc, "build_leaves")
     return Kout[: nl.value + 1].copy(), Nout[: nl.value].copy(), it.value
 
 
-def canonical_leaves(P, ncrit: int, cap: int | None = None) -> np.ndarray:
+def canonical_leaves(P, ncrit: int, cap: int | None = None, levels: int = L) -> np.ndarray:
     """The balanced octree by its definition (top-down), for comparison with the iteration."""
     P = _c(P, np.uint64)
     if cap is None:
-        cap = leaf_capacity_bound(P.size, ncrit)
+        cap = leaf_capacity_bound(P.size, ncrit, levels)
     Kout = np.empty(cap + 1, np.uint64)
     nl = ctypes.c_int64()
-    _check(_load().oracle_canonical_leaves(_ptr(P), P.size, ncrit, _ptr(Kout), cap, ctypes.byref(nl)),
+    _check(_load(levels).oracle_canonical_leaves(_ptr(P), P.size, ncrit, _ptr(Kout), cap, ctypes.byref(nl)),
            "canonical_leaves")
     return Kout[: nl.value + 1].copy()
 
 
-def check_cornerstone(K) -> bool:
+def check_cornerstone(K, levels: int = L) -> bool:
     K = _c(K, np.uint64)
-    return _load().oracle_check_cornerstone(_ptr(K), K.size - 1) == 0
+    return _load(levels).oracle_check_cornerstone(_ptr(K), K.size - 1) == 0
 
 
 # ---------------------------------------------------------------- Sec. 5: linked octree
-def link(K):
+def link(K, levels: int = L):
     """Returns dict NK, CO, LO, leaf_to_node, parent."""
     K = _c(K, np.uint64)
     nl = K.size - 1
     n = nl + (nl - 1) // 7
     NK = np.empty(n, np.uint64)
     CO = np.empty(n, np.int32)
-    LO = np.empty(L + 2, np.int32)
+    LO = np.empty(levels + 2, np.int32)
     l2n = np.empty(nl, np.int32)
     parent = np.empty(max((n - 1) // 8, 1), np.int32)
-    _check(_load().oracle_link(_ptr(K), nl, _ptr(NK), _ptr(CO), _ptr(LO), _ptr(l2n), _ptr(parent)), "link")
+    _check(_load(levels).oracle_link(_ptr(K), nl, _ptr(NK), _ptr(CO), _ptr(LO), _ptr(l2n), _ptr(parent)), "link")
     return {"NK": NK, "CO": CO, "LO": LO, "leaf_to_node": l2n, "parent": parent[: (n - 1) // 8]}
 
 
-def node_counts(P, NK) -> np.ndarray:
+def node_counts(P, NK, levels: int = L) -> np.ndarray:
     P, NK = _c(P, np.uint64), _c(NK, np.uint64)
     out = np.empty(NK.size, np.uint32)
-    _check(_load().oracle_node_counts(_ptr(P), P.size, _ptr(NK), NK.size, _ptr(out)), "node_counts")
+    _check(_load(levels).oracle_node_counts(_ptr(P), P.size, _ptr(NK), NK.size, _ptr(out)), "node_counts")
     return out
 
 
-def multipoles(x, y, z, m, P, perm, NK, nodes=None):
+def multipoles(x, y, z, m, P, perm, NK, nodes=None, levels: int = L):
     """FP64 monopole / centre of mass / second moments of the selected nodes (all by default)."""
     x, y, z = (_c(a, np.float64) for a in (x, y, z))
     m = _c(m, np.float32)
@@ -256,20 +265,20 @@ def multipoles(x, y, z, m, P, perm, NK, nodes=None):
     M = np.empty(nodes.size, np.float64)
     com = np.empty((nodes.size, 3), np.float64)
     quad = np.empty((nodes.size, 6), np.float64)
-    _check(_load().oracle_multipoles(_ptr(x), _ptr(y), _ptr(z), _ptr(m), _ptr(P), _ptr(perm), P.size, _ptr(NK),
+    _check(_load(levels).oracle_multipoles(_ptr(x), _ptr(y), _ptr(z), _ptr(m), _ptr(P), _ptr(perm), P.size, _ptr(NK),
                                      _ptr(nodes), nodes.size, _ptr(M), _ptr(com), _ptr(quad)), "multipoles")
     return M, com, quad
 
 
-def full_build(x, y, z, curve: int, ncrit: int, box=None):
+def full_build(x, y, z, curve: int, ncrit: int, box=None, levels: int = L):
     """The whole path in the paper's order; returns a dict of every intermediate result."""
     if box is None:
         box = bounding_cube(x, y, z)
-    k = keys(x, y, z, box, curve)
+    k = keys(x, y, z, box, curve, levels)
     P, perm = sort(k)
-    K, N, iters = build_leaves(P, ncrit)
-    tree = link(K)
-    counts = node_counts(P, tree["NK"])
+    K, N, iters = build_leaves(P, ncrit, levels=levels)
+    tree = link(K, levels)
+    counts = node_counts(P, tree["NK"], levels)
     out = {"box": np.asarray(box, np.float64), "keys": k, "P": P, "perm": perm, "K": K, "N": N, "iters": iters,
            "counts": counts}
     out.update(tree)

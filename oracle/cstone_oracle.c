@@ -14,7 +14,7 @@
 #include <string.h>
 
 #define L ORACLE_L
-#define KEY_END (1ULL << (3 * L)) /* 8^L = 2^63, one past the last key */
+#define KEY_END (1ULL << (3 * L)) /* 8^L (2^63 at L = 21), one past the last key */
 
 /* =====================================================================================
  * Sec. 3: keys. A key of 3L bits is a sequence of L octal digits; digit i selects the octant
@@ -47,8 +47,10 @@ int oracle_bounding_cube(const double* x, const double* y, const double* z, int6
     return ORACLE_OK;
 }
 
+#define GRID_CELLS (1u << L) /* 2^L cells per axis */
+
 /* Scale from coordinates to grid units: 2^L / side, one correctly rounded division. */
-double oracle_scale(double side) { return 2097152.0 / side; }
+double oracle_scale(double side) { return (double)GRID_CELLS / side; }
 
 /* Grid coordinate of one axis (Sec. 3 maps the box onto [0, 2^L)^3): u = (x - lo) * scale with
  * two roundings, then floor, clamped to [0, 2^L - 1]. Points left of the box map to 0, points at
@@ -56,7 +58,7 @@ double oracle_scale(double side) { return 2097152.0 / side; }
 uint32_t oracle_grid_coord(double x, double lo, double scale) {
     double u = (x - lo) * scale;
     if (!(u > 0.0)) return 0u;
-    if (u >= 2097152.0) return 2097151u;
+    if (u >= (double)GRID_CELLS) return GRID_CELLS - 1u;
     return (uint32_t)floor(u);
 }
 

@@ -10,7 +10,8 @@
  * contraction (-ffp-contract=off) so that every floating-point operation is one IEEE
  * round-to-nearest operation.
  *
- * Notation follows the paper: L = 21 octree levels (63-bit keys), K = cornerstone array,
+ * Notation follows the paper: L octree levels (L = 21: 63-bit keys; the same source compiled
+ * with -DORACLE_L=10 gives the 30-bit keys of Sec. 3's other choice), K = cornerstone array,
  * P = sorted particle keys, N = leaf counts, O / O' = rebalance ops and their exclusive
  * scan, NK / CO / LO = node keys, first-child indices and level offsets.
  *
@@ -21,7 +22,9 @@
 
 #include <stdint.h>
 
+#ifndef ORACLE_L
 #define ORACLE_L 21
+#endif
 
 #define ORACLE_OK 0
 #define ORACLE_E_ARG (-1)
