@@ -136,6 +136,13 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# DRAM bytes per key of one sort (upfront histogram + 8 passes), measured with ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum over the sort's launches) on 2^24 keys of the same
+# workload and scaled by the key count (the passes stream, so traffic grows with n):
+# profiles/kernels_clumps_2p24_full.md.
+SORT_DRAM_BYTES_PER_KEY = 177.9
+
+
 def algorithmic_bytes(n: int, n_leaves: int, iter_leaves: int, n_nodes: int):
     """Compulsory DRAM traffic of one step (bytes), by phase."""
     return {
@@ -303,7 +310,8 @@ def run_ours(args, rank, world, local):
             "step_algorithmic_bytes": step_bytes,
             "step_hbm_frac": step_bytes / (ms_per_step * 1e-3) / 1e9 / hbm,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "peak_source": peak_kind, "traffic": None,
+                         "frac": achieved / hbm, "peak_source": peak_kind,
+                         "traffic": SORT_DRAM_BYTES_PER_KEY * n if dom == "sort" else None,
                          "algorithmic_bytes_per_launch": algo[dom]},
             "cpu_baseline": cpu,
             "e2e": e2e,
