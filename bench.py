@@ -44,6 +44,7 @@ def parse():
     p.add_argument("--no-timesteps", action="store_true")
     p.add_argument("--ts-steps", type=int, default=100)
     p.add_argument("--no-table1", action="store_true")
+    p.add_argument("--no-keys30", action="store_true")
     return p.parse_args()
 
 
@@ -283,6 +284,8 @@ def run_ours(args, rank, world, local):
                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}
 
     extra = {}
+    if rank == 0 and not args.no_keys30:
+        extra["keys30_same_workload"] = measure_keys30(X, Y, Z, M, K=max(3, min(K, 10)))
     if rank == 0 and not args.no_batched:
         extra["batched_512_sets"] = measure_batched(dev)
     if rank == 0 and (not args.no_timesteps and args.ts_steps > 0 or not args.no_table1):
@@ -323,6 +326,55 @@ def run_ours(args, rank, world, local):
         dist.barrier()
         dist.destroy_process_group()
     return line
+
+
+def measure_keys30(X, Y, Z, M, K: int = 10):
+    """The same workload and step with 30-bit keys (L = 10, Sec. 3's other key length): bbox, keys,
+    a 4-pass sort of 32-bit words, leaves, link, counts and multipoles; CUDA events per phase."""
+    import numpy as np
+    import torch
+
+    import paper_2307_06345_gb300 as cs
+
+    stream = torch.cuda.current_stream()
+    out = cs.build_octree(X, Y, Z, curve=cs.HILBERT, ncrit=NCRIT, masses=M, levels=10)
+    b = out["buffers"]
+    torch.cuda.synchronize()
+    phases = ["bbox", "keys", "sort", "leaves", "link", "counts", "multipoles"]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(phases) + 1)] for _ in range(K)]
+    nl = 0
+    for k in range(K + 2):
+        e = ev[k - 2] if k >= 2 else ev[0]  # two untimed warm-up steps
+        e[0].record(stream)
+        cs.cstone_bbox(X, Y, Z, b.box, b.ws)
+        e[1].record(stream)
+        cs.cstone_keys(X, Y, Z, b.box, cs.HILBERT, b.keys, levels=10)
+        e[2].record(stream)
+        cs.cstone_sort(b.keys, b.sorted_keys, b.perm, b.ws, levels=10)
+        e[3].record(stream)
+        nl, it = cs.cstone_build_leaves(b.sorted_keys, NCRIT, b.leaves, b.counts, b.offsets, 0, 64, b.ws, levels=10)
+        e[4].record(stream)
+        t = b.tree_buffers(nl)
+        cs.cstone_link_tree(b.leaves, nl, t["NK"], t["CO"], t["LO"], t["leaf_to_node"], t["parent"], b.ws,
+                            levels=10)
+        e[5].record(stream)
+        cs.cstone_upsweep_counts(b.counts, nl, t["leaf_to_node"], t["CO"], t["LO"], t["counts"], b.ws, levels=10)
+        e[6].record(stream)
+        nn = cs.n_nodes(nl)
+        cs.cstone_upsweep_multipoles(X, Y, Z, M, b.perm, b.offsets, nl, t["leaf_to_node"], t["CO"], t["LO"], b.box,
+                                     t["mass"][:nn], t["com"][: 3 * nn], t["quad"][: 6 * nn], b.ws, levels=10)
+        e[7].record(stream)
+    torch.cuda.synchronize()
+    phase_ms = {p: float(np.mean([ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(K)]))
+                for i, p in enumerate(phases)}
+    step_ms = sum(phase_ms.values())
+    n = X.numel()
+    counts = t["counts"][:nn]
+    return {"levels": 10, "key_bits": 30, "n_particles": n, "ncrit": NCRIT, "curve": "hilbert",
+            "ms_per_step": step_ms, "particles_per_s": n / (step_ms * 1e-3), "phase_ms": phase_ms,
+            "n_leaves": nl, "leaf_iterations": it,
+            "max_leaf_count": int(b.counts[:nl].max().item()), "root_count": int(counts[0].item()),
+            "sort_algorithmic_bytes_per_key": 4 + 12 + 3 * 16}
 
 
 def measure_batched(dev, reps: int = 5):

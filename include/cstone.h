@@ -34,7 +34,8 @@
 extern "C" {
 #endif
 
-#define CSTONE_LEVELS 21
+#define CSTONE_LEVELS 21   /* L of the 63-bit keys (entry points cstone_*) */
+#define CSTONE30_LEVELS 10 /* L of the 30-bit keys (entry points cstone30_*) */
 #define CSTONE_MAX_PARTICLES ((int64_t)1 << 30)
 #define CSTONE_MAX_LEAVES ((int64_t)1 << 28)
 
@@ -299,6 +300,40 @@ CSTONE_API int cstone_upsweep_counts_batched(const uint32_t* elem_counts, int64_
                                              const int32_t* leaf_to_node, const int32_t* child,
                                              const int32_t* level_offsets, int32_t n_sets, uint32_t* node_counts,
                                              void* ws, size_t ws_bytes, void* stream);
+
+/* ==========================================================================================
+ * 30-bit keys (L = 10): the other key length of Sec. 3, one 32-bit word per key. Every entry
+ * point below is its cstone_* counterpart with uint32_t keys and 10 levels: a key of this
+ * family is the top 30 bits of the 63-bit key of the same point (the grid of 2^10 cells per
+ * axis nests in the one of 2^21 cells, and both curves nest level by level); end key 8^10 = 2^30;
+ * level_offsets has CSTONE30_LEVELS + 2 = 12 entries; the sort takes 4 passes of 8-bit digits;
+ * a leaf that is a single level-10 cell is not split whatever its count. Arguments, ownership,
+ * errors and synchronisation are those of the 63-bit entry point. The bounding cube
+ * (cstone_bbox) does not depend on the key length.
+ * ========================================================================================== */
+CSTONE_API int cstone30_keys(const double* x, const double* y, const double* z, int64_t n, const double* box,
+                             int curve, uint32_t* keys, void* stream);
+CSTONE_API int cstone30_sort_workspace_size(int64_t n, size_t* bytes);
+CSTONE_API int cstone30_sort(const uint32_t* keys_in, uint32_t* keys_out, uint32_t* perm, int64_t n, void* ws,
+                             size_t ws_bytes, void* stream);
+CSTONE_API int cstone30_leaves_workspace_size(int64_t n, int64_t leaf_cap, int32_t max_iters, size_t* bytes);
+CSTONE_API int cstone30_build_leaves(const uint32_t* sorted_keys, int64_t n, uint32_t ncrit, uint32_t* leaves,
+                                     int64_t leaf_cap, int64_t* n_leaves, uint32_t* counts, uint32_t* offsets,
+                                     int32_t max_iters, int32_t* iters, void* ws, size_t ws_bytes, void* stream);
+CSTONE_API int cstone30_link_workspace_size(int64_t n_leaves, size_t* bytes);
+CSTONE_API int cstone30_link_tree(const uint32_t* leaves, int64_t n_leaves, uint32_t* node_keys, int32_t* child,
+                                  int32_t* level_offsets, int32_t* leaf_to_node, int32_t* parent, void* ws,
+                                  size_t ws_bytes, void* stream);
+CSTONE_API int cstone30_upsweep_workspace_size(int64_t n_leaves, size_t* bytes);
+CSTONE_API int cstone30_upsweep_counts(const uint32_t* leaf_counts, int64_t n_leaves, const int32_t* leaf_to_node,
+                                       const int32_t* child, const int32_t* level_offsets, uint32_t* node_counts,
+                                       void* ws, size_t ws_bytes, void* stream);
+CSTONE_API int cstone30_multipole_workspace_size(int64_t n, int64_t n_leaves, size_t* bytes);
+CSTONE_API int cstone30_upsweep_multipoles(const double* x, const double* y, const double* z, const float* m,
+                                           const uint32_t* perm, int64_t n, const uint32_t* offsets, int64_t n_leaves,
+                                           const int32_t* leaf_to_node, const int32_t* child,
+                                           const int32_t* level_offsets, const double* box, float* mass, double* com,
+                                           float* quad, void* ws, size_t ws_bytes, void* stream);
 
 #ifdef __cplusplus
 }

@@ -30,7 +30,8 @@ __all__ = [
 ]
 
 MORTON, HILBERT = 0, 1
-LEVELS = 21
+LEVELS = 21    # 63-bit keys (entry points cstone_*, int64 key tensors)
+LEVELS30 = 10  # 30-bit keys (entry points cstone30_*, int32 key tensors)
 KEY_END = 1 << 63
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_CAPACITY, ERR_TIMEOUT, ERR_NOT_CONVERGED = range(6)
 
@@ -96,6 +97,10 @@ def load():
                                                                 sz, P]),
             "cstone_leaves_result": (ctypes.c_int, [P, i64, i32, P, pi64, pi32]),
         }
+        for name in ("keys", "sort_workspace_size", "sort", "leaves_workspace_size", "build_leaves",
+                     "link_workspace_size", "link_tree", "upsweep_workspace_size", "upsweep_counts",
+                     "multipole_workspace_size", "upsweep_multipoles"):
+            sigs["cstone30_" + name] = sigs["cstone_" + name]
         for name, (res, args) in sigs.items():
             fn = getattr(lib, name)
             fn.restype = res
@@ -160,6 +165,17 @@ def _need(t: torch.Tensor, dtype, name):
 
 
 # ------------------------------------------------------------------------- C entry points
+def _family(levels: int):
+    """(C function, key dtype) picker for the key length: 21 levels -> cstone_*, int64 keys;
+    10 levels -> cstone30_*, int32 keys (bit patterns of uint32)."""
+    lib = load()
+    if levels == LEVELS:
+        return (lambda name: getattr(lib, "cstone_" + name)), torch.int64
+    if levels == LEVELS30:
+        return (lambda name: getattr(lib, "cstone30_" + name)), torch.int32
+    raise ValueError(f"levels must be {LEVELS} or {LEVELS30}, not {levels}")
+
+
 def cstone_kernel_launches() -> int:
     """Kernels the library has launched in this process so far."""
     return int(load().cstone_kernel_launches())
@@ -177,23 +193,23 @@ def cstone_bbox(x, y, z, box, ws: Workspace, stream=None):
            "cstone_bbox")
 
 
-def cstone_keys(x, y, z, box, curve: int, keys, stream=None):
-    lib = load()
+def cstone_keys(x, y, z, box, curve: int, keys, stream=None, levels: int = LEVELS):
+    fn, kdt = _family(levels)
     for t, nm in ((x, "x"), (y, "y"), (z, "z"), (box, "box")):
         _need(t, torch.float64, nm)
-    _need(keys, torch.int64, "keys")
-    _check(lib.cstone_keys(_ptr(x), _ptr(y), _ptr(z), x.numel(), _ptr(box), curve, _ptr(keys), _stream(stream)),
+    _need(keys, kdt, "keys")
+    _check(fn("keys")(_ptr(x), _ptr(y), _ptr(z), x.numel(), _ptr(box), curve, _ptr(keys), _stream(stream)),
            "cstone_keys")
 
 
-def cstone_sort(keys_in, keys_out, perm, ws: Workspace, stream=None):
-    lib = load()
+def cstone_sort(keys_in, keys_out, perm, ws: Workspace, stream=None, levels: int = LEVELS):
+    fn, kdt = _family(levels)
     n = keys_in.numel()
-    _need(keys_in, torch.int64, "keys_in")
-    _need(keys_out, torch.int64, "keys_out")
+    _need(keys_in, kdt, "keys_in")
+    _need(keys_out, kdt, "keys_out")
     _need(perm, torch.int32, "perm")
-    buf = ws.get(_size(lib.cstone_sort_workspace_size, n))
-    _check(lib.cstone_sort(_ptr(keys_in), _ptr(keys_out), _ptr(perm), n, _ptr(buf), buf.numel(), _stream(stream)),
+    buf = ws.get(_size(fn("sort_workspace_size"), n))
+    _check(fn("sort")(_ptr(keys_in), _ptr(keys_out), _ptr(perm), n, _ptr(buf), buf.numel(), _stream(stream)),
            "cstone_sort")
 
 
@@ -209,24 +225,24 @@ def cstone_sort_static(keys_in, keys_out, perm, stream=None):
 
 
 def cstone_build_leaves(sorted_keys, ncrit: int, leaves, counts, offsets=None, n_leaves: int = 0,
-                        max_iters: int = 64, ws: Workspace | None = None, stream=None):
+                        max_iters: int = 64, ws: Workspace | None = None, stream=None, levels: int = LEVELS):
     """Returns (n_leaves, iterations). ``leaves`` holds the initial array when n_leaves > 0."""
-    lib = load()
+    fn, kdt = _family(levels)
     n = sorted_keys.numel()
     cap = counts.numel()
-    _need(sorted_keys, torch.int64, "sorted_keys")
-    _need(leaves, torch.int64, "leaves")
+    _need(sorted_keys, kdt, "sorted_keys")
+    _need(leaves, kdt, "leaves")
     _need(counts, torch.int32, "counts")
     if leaves.numel() < cap + 1:
         raise ValueError("leaves needs leaf_cap + 1 entries")
     if offsets is not None:
         _need(offsets, torch.int32, "offsets")
     ws = ws or Workspace(sorted_keys.device)
-    buf = ws.get(_size(lib.cstone_leaves_workspace_size, n, cap, max_iters))
+    buf = ws.get(_size(fn("leaves_workspace_size"), n, cap, max_iters))
     nl = ctypes.c_int64(n_leaves)
     it = ctypes.c_int32(0)
-    rc = lib.cstone_build_leaves(_ptr(sorted_keys), n, ncrit, _ptr(leaves), cap, ctypes.byref(nl), _ptr(counts),
-                                 _ptr(offsets), max_iters, ctypes.byref(it), _ptr(buf), buf.numel(), _stream(stream))
+    rc = fn("build_leaves")(_ptr(sorted_keys), n, ncrit, _ptr(leaves), cap, ctypes.byref(nl), _ptr(counts),
+                            _ptr(offsets), max_iters, ctypes.byref(it), _ptr(buf), buf.numel(), _stream(stream))
     if rc == ERR_CAPACITY:
         err = CstoneError(rc, "cstone_build_leaves", _detail())
         err.required = int(nl.value)
@@ -236,35 +252,38 @@ def cstone_build_leaves(sorted_keys, ncrit: int, leaves, counts, offsets=None, n
 
 
 def cstone_link_tree(leaves, n_leaves: int, node_keys, child, level_offsets, leaf_to_node, parent=None,
-                     ws: Workspace | None = None, stream=None):
-    lib = load()
+                     ws: Workspace | None = None, stream=None, levels: int = LEVELS):
+    fn, kdt = _family(levels)
+    _need(leaves, kdt, "leaves")
+    _need(node_keys, kdt, "node_keys")
+    if level_offsets.numel() < levels + 2:
+        raise ValueError(f"level_offsets needs {levels + 2} entries")
     ws = ws or Workspace(leaves.device)
-    buf = ws.get(_size(lib.cstone_link_workspace_size, n_leaves))
-    _check(lib.cstone_link_tree(_ptr(leaves), n_leaves, _ptr(node_keys), _ptr(child), _ptr(level_offsets),
-                                _ptr(leaf_to_node), _ptr(parent), _ptr(buf), buf.numel(), _stream(stream)),
+    buf = ws.get(_size(fn("link_workspace_size"), n_leaves))
+    _check(fn("link_tree")(_ptr(leaves), n_leaves, _ptr(node_keys), _ptr(child), _ptr(level_offsets),
+                           _ptr(leaf_to_node), _ptr(parent), _ptr(buf), buf.numel(), _stream(stream)),
            "cstone_link_tree")
 
 
 def cstone_upsweep_counts(leaf_counts, n_leaves: int, leaf_to_node, child, level_offsets, node_counts,
-                          ws: Workspace | None = None, stream=None):
-    lib = load()
+                          ws: Workspace | None = None, stream=None, levels: int = LEVELS):
+    fn, _ = _family(levels)
     ws = ws or Workspace(leaf_counts.device)
-    buf = ws.get(_size(lib.cstone_upsweep_workspace_size, n_leaves))
-    _check(lib.cstone_upsweep_counts(_ptr(leaf_counts), n_leaves, _ptr(leaf_to_node), _ptr(child),
-                                     _ptr(level_offsets), _ptr(node_counts), _ptr(buf), buf.numel(), _stream(stream)),
+    buf = ws.get(_size(fn("upsweep_workspace_size"), n_leaves))
+    _check(fn("upsweep_counts")(_ptr(leaf_counts), n_leaves, _ptr(leaf_to_node), _ptr(child), _ptr(level_offsets),
+                                _ptr(node_counts), _ptr(buf), buf.numel(), _stream(stream)),
            "cstone_upsweep_counts")
 
 
 def cstone_upsweep_multipoles(x, y, z, m, perm, offsets, n_leaves: int, leaf_to_node, child, level_offsets, box,
-                              mass, com, quad, ws: Workspace | None = None, stream=None):
-    lib = load()
+                              mass, com, quad, ws: Workspace | None = None, stream=None, levels: int = LEVELS):
+    fn, _ = _family(levels)
     _need(m, torch.float32, "m")
     ws = ws or Workspace(x.device)
-    buf = ws.get(_size(lib.cstone_multipole_workspace_size, x.numel(), n_leaves))
-    _check(lib.cstone_upsweep_multipoles(_ptr(x), _ptr(y), _ptr(z), _ptr(m), _ptr(perm), x.numel(), _ptr(offsets),
-                                         n_leaves, _ptr(leaf_to_node), _ptr(child), _ptr(level_offsets), _ptr(box),
-                                         _ptr(mass),
-                                         _ptr(com), _ptr(quad), _ptr(buf), buf.numel(), _stream(stream)),
+    buf = ws.get(_size(fn("multipole_workspace_size"), x.numel(), n_leaves))
+    _check(fn("upsweep_multipoles")(_ptr(x), _ptr(y), _ptr(z), _ptr(m), _ptr(perm), x.numel(), _ptr(offsets),
+                                    n_leaves, _ptr(leaf_to_node), _ptr(child), _ptr(level_offsets), _ptr(box),
+                                    _ptr(mass), _ptr(com), _ptr(quad), _ptr(buf), buf.numel(), _stream(stream)),
            "cstone_upsweep_multipoles")
 
 
@@ -293,16 +312,18 @@ class OctreeBuffers:
     offsets: torch.Tensor = None
     ws: Workspace = None
     tree: dict = field(default_factory=dict)
+    levels: int = LEVELS
 
     @classmethod
-    def allocate(cls, n: int, cap: int, device="cuda"):
+    def allocate(cls, n: int, cap: int, device="cuda", levels: int = LEVELS):
         d = torch.device(device)
-        b = cls(device=d, n=n, cap=cap)
-        b.keys = torch.empty(n, dtype=torch.int64, device=d)
-        b.sorted_keys = torch.empty(n, dtype=torch.int64, device=d)
+        kdt = torch.int64 if levels == LEVELS else torch.int32
+        b = cls(device=d, n=n, cap=cap, levels=levels)
+        b.keys = torch.empty(n, dtype=kdt, device=d)
+        b.sorted_keys = torch.empty(n, dtype=kdt, device=d)
         b.perm = torch.empty(n, dtype=torch.int32, device=d)
         b.box = torch.empty(4, dtype=torch.float64, device=d)
-        b.leaves = torch.empty(cap + 1, dtype=torch.int64, device=d)
+        b.leaves = torch.empty(cap + 1, dtype=kdt, device=d)
         b.counts = torch.empty(cap, dtype=torch.int32, device=d)
         b.offsets = torch.empty(cap + 1, dtype=torch.int32, device=d)
         b.ws = Workspace(d)
@@ -316,9 +337,9 @@ class OctreeBuffers:
             cap_nodes = max(nn, int(1.25 * nn))
             t.clear()
             t["cap_nodes"] = cap_nodes
-            t["NK"] = torch.empty(cap_nodes, dtype=torch.int64, device=d)
+            t["NK"] = torch.empty(cap_nodes, dtype=self.keys.dtype, device=d)
             t["CO"] = torch.empty(cap_nodes, dtype=torch.int32, device=d)
-            t["LO"] = torch.empty(LEVELS + 2, dtype=torch.int32, device=d)
+            t["LO"] = torch.empty(self.levels + 2, dtype=torch.int32, device=d)
             t["leaf_to_node"] = torch.empty(max(self.cap, 1), dtype=torch.int32, device=d)
             t["parent"] = torch.empty(max(cap_nodes // 8, 1), dtype=torch.int32, device=d)
             t["counts"] = torch.empty(cap_nodes, dtype=torch.int32, device=d)
@@ -326,23 +347,24 @@ class OctreeBuffers:
 
 
 def build_octree(x, y, z, curve: int = HILBERT, ncrit: int = 64, box=None, masses=None, buffers=None,
-                 warm_leaves=None, max_iters: int = 64, stream=None, compute_bbox: bool | None = None):
+                 warm_leaves=None, max_iters: int = 64, stream=None, levels: int = LEVELS):
     """Full build: keys -> sort -> cornerstone leaves -> linked octree -> node counts
     (-> multipoles when ``masses`` is given). Coordinates are float64 CUDA tensors.
 
     ``box`` is a float64 tensor {lo_x, lo_y, lo_z, side} (CUDA); when None the bounding cube is
-    computed on the device. ``warm_leaves`` (int64 CUDA, n_l + 1 keys) warm-starts the leaf loop.
+    computed on the device. ``warm_leaves`` (CUDA, n_l + 1 keys) warm-starts the leaf loop.
+    ``levels``: 21 (63-bit keys in int64 tensors) or 10 (30-bit keys in int32 tensors).
     Returns a dict of device tensors sized to the built tree plus 'n_leaves' and 'iters'.
     """
     n = x.numel()
-    if buffers is None or buffers.n != n:
-        buffers = OctreeBuffers.allocate(n, leaf_capacity(n, ncrit), x.device)
+    if buffers is None or buffers.n != n or buffers.levels != levels:
+        buffers = OctreeBuffers.allocate(n, leaf_capacity(n, ncrit), x.device, levels)
     b = buffers
     if box is None:
         cstone_bbox(x, y, z, b.box, b.ws, stream)
         box = b.box
-    cstone_keys(x, y, z, box, curve, b.keys, stream)
-    cstone_sort(b.keys, b.sorted_keys, b.perm, b.ws, stream)
+    cstone_keys(x, y, z, box, curve, b.keys, stream, levels)
+    cstone_sort(b.keys, b.sorted_keys, b.perm, b.ws, stream, levels)
     while True:
         nl0 = 0
         if warm_leaves is not None:
@@ -352,7 +374,7 @@ def build_octree(x, y, z, curve: int = HILBERT, ncrit: int = 64, box=None, masse
             b.leaves[: nl0 + 1].copy_(warm_leaves)
         try:
             nl, iters = cstone_build_leaves(b.sorted_keys, ncrit, b.leaves, b.counts, b.offsets, nl0, max_iters,
-                                            b.ws, stream)
+                                            b.ws, stream, levels)
             break
         except CstoneError as e:
             if e.status != ERR_CAPACITY:
@@ -360,8 +382,8 @@ def build_octree(x, y, z, curve: int = HILBERT, ncrit: int = 64, box=None, masse
             b = _grow(b, max(getattr(e, "required", 0), 2 * b.cap))
     t = b.tree_buffers(nl)
     nn = n_nodes(nl)
-    cstone_link_tree(b.leaves, nl, t["NK"], t["CO"], t["LO"], t["leaf_to_node"], t["parent"], b.ws, stream)
-    cstone_upsweep_counts(b.counts, nl, t["leaf_to_node"], t["CO"], t["LO"], t["counts"], b.ws, stream)
+    cstone_link_tree(b.leaves, nl, t["NK"], t["CO"], t["LO"], t["leaf_to_node"], t["parent"], b.ws, stream, levels)
+    cstone_upsweep_counts(b.counts, nl, t["leaf_to_node"], t["CO"], t["LO"], t["counts"], b.ws, stream, levels)
     out = {
         "buffers": b, "box": box, "keys": b.keys, "sorted_keys": b.sorted_keys, "perm": b.perm,
         "leaves": b.leaves[: nl + 1], "leaf_counts": b.counts[:nl], "leaf_offsets": b.offsets[: nl + 1],
@@ -376,7 +398,7 @@ def build_octree(x, y, z, curve: int = HILBERT, ncrit: int = 64, box=None, masse
             t["quad"] = torch.empty(6 * cap_nodes, dtype=torch.float32, device=b.device)
         mass, com, quad = t["mass"][:nn], t["com"][: 3 * nn], t["quad"][: 6 * nn]
         cstone_upsweep_multipoles(x, y, z, masses, b.perm, b.offsets, nl, t["leaf_to_node"], t["CO"], t["LO"], box,
-                                  mass, com, quad, b.ws, stream)
+                                  mass, com, quad, b.ws, stream, levels)
         out.update({"mass": mass, "com": com.view(3, nn), "quad": quad.view(6, nn)})
     return out
 
@@ -541,7 +563,7 @@ def build_octrees_batched(x, y, z, set_offsets, curve: int = MORTON, ncrit: int 
 
 def _grow(b: OctreeBuffers, want: int) -> OctreeBuffers:
     cap = int(min(1 << 28, max(want, 2 * b.cap)))
-    nb = OctreeBuffers.allocate(b.n, cap, b.device)
+    nb = OctreeBuffers.allocate(b.n, cap, b.device, b.levels)
     nb.keys, nb.sorted_keys, nb.perm, nb.box, nb.ws = b.keys, b.sorted_keys, b.perm, b.box, b.ws
     return nb
 

@@ -57,6 +57,22 @@ def _sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
+# Translation units that do not depend on the key length; every other one is compiled twice, for
+# 63-bit keys (entry points cstone_*) and with CSTONE_KEY32 for 30-bit keys (cstone30_*).
+KEY_INDEPENDENT = {"status.cu"}
+
+
+def _units():
+    """(source, object name, extra definitions) of every object of the library."""
+    out = []
+    for src in _sources():
+        base = os.path.basename(src)[:-3]
+        out.append((src, base + ".o", {}))
+        if os.path.basename(src) not in KEY_INDEPENDENT:
+            out.append((src, base + "30.o", {"CSTONE_KEY32": 1}))
+    return out
+
+
 def _deps():
     deps = _sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(INCLUDE, "cstone.h")]
     return deps + ([TUNING] if os.path.exists(TUNING) else [])
@@ -74,14 +90,14 @@ def _flags(knobs: dict):
                    "-I", CSRC, "--expt-relaxed-constexpr", "-DCSTONE_BUILD"] + [f"-D{k}={v}" for k, v in knobs.items()]
 
 
-def _compile(srcs, objdir: str, knobs: dict, verbose: bool = False):
+def _compile(units, objdir: str, knobs: dict, verbose: bool = False):
     os.makedirs(objdir, exist_ok=True)
     cc = nvcc()
-    flags = _flags(knobs)
 
-    def compile_one(src):
-        obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")
-        cmd = [cc] + flags + ["-c", src, "-o", obj]
+    def compile_one(unit):
+        src, name, extra = unit
+        obj = os.path.join(objdir, name)
+        cmd = [cc] + _flags({**knobs, **extra}) + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
@@ -89,8 +105,8 @@ def _compile(srcs, objdir: str, knobs: dict, verbose: bool = False):
             print(r.stderr)
         return obj
 
-    with concurrent.futures.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 2)) as ex:
-        return list(ex.map(compile_one, srcs))
+    with concurrent.futures.ThreadPoolExecutor(max_workers=min(12, os.cpu_count() or 2)) as ex:
+        return list(ex.map(compile_one, units))
 
 
 def _link(objs, out: str):
@@ -107,23 +123,23 @@ def _link(objs, out: str):
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not is_stale():
         return LIB
-    objs = _compile(_sources(), OBJDIR, tuned_knobs(), verbose)
+    objs = _compile(_units(), OBJDIR, tuned_knobs(), verbose)
     return _link(objs, LIB)
 
 
 def build_variant(knobs: dict, out: str, objdir: str) -> str:
     """A copy of the library with the given knob definitions (on top of the tuned ones), for the
-    autotuner. Translation units that no knob of ``knobs`` can affect reuse the main build's objects."""
+    autotuner. Only the 63-bit-key objects of the translation units the knobs affect are rebuilt; the
+    others are the main build's objects."""
     build()
     merged = dict(tuned_knobs())
     merged.update(knobs)
     touched = {"sort.cu"} if any(k.startswith("CSTONE_SORT") for k in knobs) else set()
     if any(k.startswith("CSTONE_LEAVES") for k in knobs):
         touched.add("leaves.cu")
-    srcs = [s for s in _sources() if os.path.basename(s) in touched]
-    new_objs = {os.path.basename(o): o for o in _compile(srcs, objdir, merged)}
-    objs = [new_objs.get(os.path.basename(s)[:-3] + ".o", os.path.join(OBJDIR, os.path.basename(s)[:-3] + ".o"))
-            for s in _sources()]
+    units = [u for u in _units() if os.path.basename(u[0]) in touched and not u[2]]  # 63-bit keys only
+    new_objs = {os.path.basename(o): o for o in _compile(units, objdir, merged)}
+    objs = [new_objs.get(name, os.path.join(OBJDIR, name)) for _, name, _ in _units()]
     return _link(objs, out)
 
 

@@ -8,13 +8,28 @@
 
 #include "cstone.h"
 
+// Key length of this build. Every translation unit that depends on it is compiled twice: by
+// default for 63-bit keys (L = 21, uint64 words, namespace cst, entry points cstone_*), and with
+// CSTONE_KEY32 for 30-bit keys (L = 10, uint32 words, namespace cst30, entry points cstone30_*),
+// the two key lengths Sec. 3 names. Status handling, workspace carving and device helpers below
+// are shared by both.
+#define CST_STR2(x) #x
+#define CST_STR(x) CST_STR2(x)  // CST_STR(CSTONE_FN(sort)) is the entry point's name as a string
+
+#ifdef CSTONE_KEY32
+#define CST_NS cst30
+#define CSTONE_FN(name) cstone30_##name
+#define CST_KEY_C uint32_t  // key word in the C signatures
+#else
+#define CST_NS cst
+#define CSTONE_FN(name) cstone_##name
+#define CST_KEY_C uint64_t
+#endif
+
 namespace cst {
 
 using u64 = unsigned long long;
 using u32 = unsigned int;
-
-constexpr int kLevels = CSTONE_LEVELS;  // L
-constexpr u64 kKeyEnd = 1ULL << 63;     // 8^L
 
 // ---------------------------------------------------------------- host-side status plumbing
 int fail(int status, const char* fmt, ...);
@@ -124,3 +139,27 @@ __device__ inline void grid_barrier(GridBarrier* bar, WsHeader* hdr) {
 int cooperative_grid(const void* kernel, int threads, size_t smem, int cap_per_sm);
 
 }  // namespace cst
+
+namespace CST_NS {
+using namespace cst;
+
+#ifdef CSTONE_KEY32
+using Key = unsigned int;  // key word
+constexpr int kLevels = CSTONE30_LEVELS;  // L
+#else
+using Key = unsigned long long;
+constexpr int kLevels = CSTONE_LEVELS;
+#endif
+constexpr int kKeyBits = 3 * kLevels;                     // bits of a key
+constexpr int kWordBits = 8 * static_cast<int>(sizeof(Key));
+constexpr Key kKeyEnd = static_cast<Key>(1) << kKeyBits;  // 8^L
+static_assert(kKeyBits < kWordBits, "8^L must fit the key word");
+
+// Index (from 0) of the lowest set bit of a non-zero key, and leading zero bits of a key word.
+__device__ __forceinline__ int key_ffs(Key k) {
+    return sizeof(Key) == 8 ? __ffsll(static_cast<long long>(k)) - 1 : __ffs(static_cast<int>(k)) - 1;
+}
+__device__ __forceinline__ int key_clz(Key k) {
+    return sizeof(Key) == 8 ? __clzll(static_cast<long long>(k)) : __clz(static_cast<int>(k));
+}
+}  // namespace CST_NS

@@ -16,7 +16,7 @@
 
 #include "common.cuh"
 
-namespace cst {
+namespace CST_NS {
 
 // ---------------------------------------------------------------------------------- bounding cube
 namespace {
@@ -220,6 +220,11 @@ __device__ __forceinline__ u64 morton_of(u32 gx, u32 gy, u32 gz) {
     return (spread3(gx) << 2) | (spread3(gy) << 1) | spread3(gz);
 }
 
+// Key of this build's length from a 63-bit key: the cell of a coarser grid is the top 3L bits of
+// the 21-level key (octree prefix of both curves, and floor(cell_21 / 2^(21-L)) = cell_L exactly
+// because the grid scales differ by a power of two).
+__device__ __forceinline__ Key to_key(u64 k63) { return static_cast<Key>(k63 >> (63 - kKeyBits)); }
+
 // Hilbert key from the Morton interleave: the top level through the one-level table, then the
 // remaining 20 levels two at a time.
 __device__ __forceinline__ u64 hilbert_of(u64 m, const unsigned short* t1, const unsigned short* t2) {
@@ -238,7 +243,7 @@ __device__ __forceinline__ u64 hilbert_of(u64 m, const unsigned short* t1, const
 template <int CURVE, bool VEC>
 __global__ void __launch_bounds__(256) keys_kernel(const double* __restrict__ x, const double* __restrict__ y,
                                                    const double* __restrict__ z, long long n,
-                                                   const double* __restrict__ box, u64* __restrict__ keys,
+                                                   const double* __restrict__ box, Key* __restrict__ keys,
                                                    const __grid_constant__ HilbertTable table) {
     __shared__ unsigned short s_t2[kHilbertStates * 64];
     __shared__ unsigned short s_t1[kHilbertStates * 8];
@@ -252,15 +257,15 @@ __global__ void __launch_bounds__(256) keys_kernel(const double* __restrict__ x,
     const FixedGrid gx = s_grid[0], gy = s_grid[1], gz = s_grid[2];
     const bool fast = gx.fast && gy.fast && gz.fast;
 
-    auto encode = [&](double px, double py, double pz) -> u64 {
+    auto encode = [&](double px, double py, double pz) -> Key {
         u64 m;
         if (fast)
             m = morton_of(grid_cell_fixed(px, gx), grid_cell_fixed(py, gy), grid_cell_fixed(pz, gz));
         else
             m = morton_of(grid_cell(px, gx.lo, gx.scale), grid_cell(py, gy.lo, gy.scale),
                           grid_cell(pz, gz.lo, gz.scale));
-        if (CURVE == CSTONE_HILBERT) return hilbert_of(m, s_t1, s_t2);
-        return m;
+        if (CURVE == CSTONE_HILBERT) return to_key(hilbert_of(m, s_t1, s_t2));
+        return to_key(m);
     };
 
     if (!VEC) {
@@ -272,13 +277,13 @@ __global__ void __launch_bounds__(256) keys_kernel(const double* __restrict__ x,
     const double2* x2 = reinterpret_cast<const double2*>(x);
     const double2* y2 = reinterpret_cast<const double2*>(y);
     const double2* z2 = reinterpret_cast<const double2*>(z);
-    ulonglong2* k2 = reinterpret_cast<ulonglong2*>(keys);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < pairs; i += (long long)gridDim.x * blockDim.x) {
         double2 a = __ldcs(x2 + i), b = __ldcs(y2 + i), c = __ldcs(z2 + i);
-        ulonglong2 out;
-        out.x = encode(a.x, b.x, c.x);
-        out.y = encode(a.y, b.y, c.y);
-        __stcs(k2 + i, out);
+        const Key k0 = encode(a.x, b.x, c.x), k1 = encode(a.y, b.y, c.y);
+        if constexpr (sizeof(Key) == 8)
+            __stcs(reinterpret_cast<ulonglong2*>(keys) + i, make_ulonglong2(k0, k1));
+        else
+            __stcs(reinterpret_cast<uint2*>(keys) + i, make_uint2(k0, k1));
     }
     if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
         long long i = n - 1;
@@ -441,7 +446,7 @@ __global__ void __launch_bounds__(256) keys_batched_kernel(const double* __restr
                                                            const double* __restrict__ z,
                                                            const long long* __restrict__ set_offsets, int n_sets,
                                                            long long n, const FixedGrid* __restrict__ grids,
-                                                           u64* __restrict__ keys,
+                                                           Key* __restrict__ keys,
                                                            const __grid_constant__ HilbertTable table) {
     __shared__ unsigned short s_t2[kHilbertStates * 64];
     __shared__ unsigned short s_t1[kHilbertStates * 8];
@@ -462,7 +467,7 @@ __global__ void __launch_bounds__(256) keys_batched_kernel(const double* __restr
             c[d] = f.fast ? grid_cell_fixed(pc[d], f) : grid_cell(pc[d], f.lo, f.scale);
         }
         const u64 m = morton_of(c[0], c[1], c[2]);
-        keys[i] = CURVE == CSTONE_HILBERT ? hilbert_of(m, s_t1, s_t2) : m;
+        keys[i] = to_key(CURVE == CSTONE_HILBERT ? hilbert_of(m, s_t1, s_t2) : m);
     }
 }
 
@@ -482,7 +487,7 @@ int launch_bbox_batched(const double* x, const double* y, const double* z, const
 }
 
 int launch_keys_batched(const double* x, const double* y, const double* z, const long long* set_offsets, int n_sets,
-                        long long n, const double* boxes, int curve, u64* keys, void* ws, cudaStream_t st) {
+                        long long n, const double* boxes, int curve, Key* keys, void* ws, cudaStream_t st) {
     Carver c(ws);
     FixedGrid* grids = c.take<FixedGrid>((size_t)n_sets * 3);
     keys_batched_setup_kernel<<<(3 * n_sets + 127) / 128, 128, 0, st>>>(boxes, n_sets, grids);
@@ -500,7 +505,7 @@ int launch_keys_batched(const double* x, const double* y, const double* z, const
 }
 
 int launch_keys(const double* x, const double* y, const double* z, long long n, const double* box, int curve,
-                u64* keys, cudaStream_t st) {
+                Key* keys, cudaStream_t st) {
     if (n == 0) return CSTONE_OK;
     const HilbertTable& tab = hilbert_table();
     long long pairs = (n + 1) / 2;
@@ -546,10 +551,23 @@ size_t bbox_ws_bytes() {
     return c.size();
 }
 
-}  // namespace cst
+}  // namespace CST_NS
 
 extern "C" {
 
+int CSTONE_FN(keys)(const double* x, const double* y, const double* z, int64_t n, const double* box, int curve,
+                    CST_KEY_C* keys, void* stream) {
+    if (n < 0 || n >= CSTONE_MAX_PARTICLES || !box || (n > 0 && (!x || !y || !z || !keys)))
+        return cst::fail(CSTONE_ERR_INVALID_ARG, CST_STR(CSTONE_FN(keys)) ": bad argument (n=%lld)", (long long)n);
+    if (curve != CSTONE_MORTON && curve != CSTONE_HILBERT)
+        return cst::fail(CSTONE_ERR_INVALID_ARG, CST_STR(CSTONE_FN(keys)) ": unknown curve %d", curve);
+    if (((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y) | reinterpret_cast<uintptr_t>(z)) & 7u) != 0 ||
+        (reinterpret_cast<uintptr_t>(keys) & (sizeof(CST_KEY_C) - 1)) != 0)
+        return cst::fail(CSTONE_ERR_INVALID_ARG, CST_STR(CSTONE_FN(keys)) ": arrays must be aligned to their element size");
+    return CST_NS::launch_keys(x, y, z, n, box, curve, reinterpret_cast<CST_NS::Key*>(keys), cst::as_stream(stream));
+}
+
+#ifndef CSTONE_KEY32  // the bounding cube and the batched entry points exist once, for 63-bit keys
 int cstone_bbox_workspace_size(int64_t n, size_t* bytes) {
     if (!bytes || n < 0) return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_bbox_workspace_size: bad argument");
     *bytes = cst::bbox_ws_bytes();
@@ -562,18 +580,6 @@ int cstone_bbox(const double* x, const double* y, const double* z, int64_t n, do
         return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_bbox: bad argument (n=%lld)", (long long)n);
     if (int rc = cst::check_ws(ws, ws_bytes, cst::bbox_ws_bytes(), "cstone_bbox")) return rc;
     return cst::launch_bbox(x, y, z, n, box, ws, cst::as_stream(stream));
-}
-
-int cstone_keys(const double* x, const double* y, const double* z, int64_t n, const double* box, int curve,
-                uint64_t* keys, void* stream) {
-    if (n < 0 || n >= CSTONE_MAX_PARTICLES || !box || (n > 0 && (!x || !y || !z || !keys)))
-        return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_keys: bad argument (n=%lld)", (long long)n);
-    if (curve != CSTONE_MORTON && curve != CSTONE_HILBERT)
-        return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_keys: unknown curve %d", curve);
-    if (((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y) | reinterpret_cast<uintptr_t>(z) |
-          reinterpret_cast<uintptr_t>(keys)) & 7u) != 0)
-        return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_keys: arrays must be 8-byte aligned");
-    return cst::launch_keys(x, y, z, n, box, curve, reinterpret_cast<cst::u64*>(keys), cst::as_stream(stream));
 }
 
 int cstone_bbox_batched(const double* x, const double* y, const double* z, const int64_t* set_offsets, int32_t n_sets,
@@ -603,5 +609,6 @@ int cstone_keys_batched(const double* x, const double* y, const double* z, int64
     return cst::launch_keys_batched(x, y, z, reinterpret_cast<const long long*>(set_offsets), n_sets, n, boxes, curve,
                                     reinterpret_cast<cst::u64*>(keys), ws, cst::as_stream(stream));
 }
+#endif
 
 }  // extern "C"

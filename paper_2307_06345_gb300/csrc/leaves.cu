@@ -22,7 +22,7 @@
 // no host round trip.
 #include "common.cuh"
 
-namespace cst {
+namespace CST_NS {
 namespace {
 
 constexpr int kThreads = 256;
@@ -55,7 +55,7 @@ struct LoopState {
 struct LeafBufs {
     u32* split_elem;  // [ecap] element index of each queued split
     u32* split_pos;   // [ecap] its first position in the new array
-    u64* K[2];
+    Key* K[2];
     u32* pos[2];   // lower bound of the element's key among its set's sorted keys (global index)
     u32* set[2];   // set of the element (batched builds only)
 };
@@ -70,7 +70,7 @@ __device__ __forceinline__ u64 ld_volatile64(const u64* p) { return *reinterpret
 __device__ __forceinline__ void st_volatile64(u64* p, u64 v) { *reinterpret_cast<volatile u64*>(p) = v; }
 
 // First position in P[lo, hi) whose key is >= key.
-__device__ __forceinline__ u32 lower_bound_in(const u64* __restrict__ P, u32 lo, u32 hi, u64 key) {
+__device__ __forceinline__ u32 lower_bound_in(const Key* __restrict__ P, u32 lo, u32 hi, Key key) {
     while (lo < hi) {
         u32 mid = lo + ((hi - lo) >> 1);
         if (__ldg(P + mid) < key)
@@ -86,19 +86,19 @@ __device__ __forceinline__ u32 lower_bound_in(const u64* __restrict__ P, u32 lo,
 // leaves of one set holding <= ncrit in total are merged away (octant 0 keeps its key, which is
 // the parent's); anything else is kept.
 template <bool BATCH>
-__device__ __forceinline__ u32 decide(const u64* __restrict__ K, const u32* __restrict__ pos,
+__device__ __forceinline__ u32 decide(const Key* __restrict__ K, const u32* __restrict__ pos,
                                       const u32* __restrict__ set, u32 e, u32 ne, u32 ncrit) {
-    const u64 ke = K[e];
+    const Key ke = K[e];
     if (ke == kKeyEnd) return 1u;
-    const u64 delta = K[e + 1] - ke;
+    const Key delta = K[e + 1] - ke;
     const u32 cnt = pos[e + 1] - pos[e];
     if (cnt > ncrit && delta > 1ULL) return 8u;
     if (delta < kKeyEnd) {
-        const u32 j = static_cast<u32>((ke >> (__ffsll(static_cast<long long>(delta)) - 1)) & 7ULL);
+        const u32 j = static_cast<u32>((ke >> key_ffs(delta)) & 7u);
         if (j >= 1u && j <= e && e - j + 8u < ne) {
             const u32 first = e - j;
             if (!BATCH || (set[first] == set[e] && set[first + 8] == set[e]))
-                if (K[first] + 8ULL * delta == K[first + 8] && pos[first + 8] - pos[first] <= ncrit) return 0u;
+                if (K[first] + static_cast<Key>(8) * delta == K[first + 8] && pos[first + 8] - pos[first] <= ncrit) return 0u;
         }
     }
     return 1u;
@@ -109,13 +109,13 @@ constexpr u32 kDeviceCount = 0xffffffffu;  // ne_start: take the element count f
 // Outputs of a failed asynchronous build: every set gets its root array {0, 8^L}, so that the
 // phases queued after it stay within their buffers. The failure itself is in the workspace.
 template <bool BATCH>
-__device__ void write_root_arrays(const u64* P, u32 n, SetView sv, u32 gtid, u32 gthreads, u64* out_keys,
+__device__ void write_root_arrays(const Key* P, u32 n, SetView sv, u32 gtid, u32 gthreads, Key* out_keys,
                                   u32* out_counts, u32* out_offsets) {
     const u32 ns = BATCH ? static_cast<u32>(sv.n_sets) : 1u;
     for (u32 q = gtid; q < ns; q += gthreads) {
         const u32 lo = BATCH ? static_cast<u32>(sv.particle_offsets[q]) : 0u;
         const u32 hi = BATCH ? static_cast<u32>(sv.particle_offsets[q + 1]) : n;
-        out_keys[2 * q] = 0ULL;
+        out_keys[2 * q] = 0;
         out_keys[2 * q + 1] = kKeyEnd;
         out_counts[2 * q] = hi - lo;
         if (BATCH) {
@@ -131,11 +131,11 @@ __device__ void write_root_arrays(const u64* P, u32 n, SetView sv, u32 gtid, u32
 }
 
 template <bool BATCH>
-__global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const u64* __restrict__ P, u32 n, u32 ncrit,
+__global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const Key* __restrict__ P, u32 n, u32 ncrit,
                                                                LeafBufs b, u32 ecap, int max_iters, int warm,
                                                                u32 ne_start, int fallback, u64* look, u32 max_tiles,
                                                                LoopState* ls, WsHeader* hdr, SetView sv,
-                                                               u64* out_keys, u32* out_counts, u32* out_offsets) {
+                                                               Key* out_keys, u32* out_counts, u32* out_offsets) {
     __shared__ u32 s_warp[kThreads / 32];
     __shared__ unsigned char s_op[kTile];
     __shared__ unsigned short s_split[kTile];
@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const u64* __rest
     if (gtid == 0) ls->ne[0] = ne_init;
     if (!warm) {  // every set starts from its root {0, 8^L}
         for (u32 q = gtid; q < static_cast<u32>(ns); q += gthreads) {
-            b.K[0][2 * q] = 0ULL;
+            b.K[0][2 * q] = 0;
             b.K[0][2 * q + 1] = kKeyEnd;
             b.pos[0][2 * q] = BATCH ? static_cast<u32>(sv.particle_offsets[q]) : 0u;
             b.pos[0][2 * q + 1] = BATCH ? static_cast<u32>(sv.particle_offsets[q + 1]) : n;
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const u64* __rest
                 lo = static_cast<u32>(sv.particle_offsets[a]);
                 hi = static_cast<u32>(sv.particle_offsets[a + 1]);
             }
-            const u64 k = out_keys[e];
+            const Key k = out_keys[e];
             b.K[0][e] = k;
             b.pos[0][e] = k == kKeyEnd ? hi : lower_bound_in(P, lo, hi, k);
         }
@@ -199,10 +199,10 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const u64* __rest
             ls->stamp[t] = now;
         }
         if (ld_volatile(&hdr->err)) break;
-        const u64* K = b.K[t & 1];
+        const Key* K = b.K[t & 1];
         const u32* pos = b.pos[t & 1];
         const u32* set = b.set[t & 1];
-        u64* Kn = b.K[(t + 1) & 1];
+        Key* Kn = b.K[(t + 1) & 1];
         u32* posn = b.pos[(t + 1) & 1];
         u32* setn = b.set[(t + 1) & 1];
         const u32 ne = ld_volatile(&ls->ne[t]);
@@ -320,12 +320,12 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const u64* __rest
                         }
                     }
                 } else if (o == 8u) {
-                    const u64 ke = K[e];
-                    const u64 step = (K[e + 1] - ke) >> 3;
+                    const Key ke = K[e];
+                    const Key step = (K[e + 1] - ke) >> 3;
                     if (o_pos + 8 <= ecap) {
 #pragma unroll
                         for (int c = 0; c < 8; ++c) {
-                            Kn[o_pos + c] = ke + static_cast<u64>(c) * step;
+                            Kn[o_pos + c] = ke + static_cast<Key>(c) * step;
                             if (BATCH) setn[o_pos + c] = set[e];
                         }
                         posn[o_pos] = pos[e];
@@ -355,10 +355,10 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const u64* __rest
             for (u32 q = gwarp; q < nsplit; q += nwarps) {
                 const u32 e = b.split_elem[q];
                 const u32 o_pos = b.split_pos[q];
-                const u64 ke = K[e];
-                const u64 delta = K[e + 1] - ke;
+                const Key ke = K[e];
+                const Key delta = K[e + 1] - ke;
                 const u32 lo = pos[e], cnt_all = pos[e + 1] - lo;
-                const int child_shift = __ffsll(static_cast<long long>(delta)) - 1 - 3;
+                const int child_shift = key_ffs(delta) - 3;
                 u32 below = 0;  // lane c in 1..7: particles whose child digit is < c
                 if (cnt_all <= kLinearSplit) {
                     u32 dg[kSplitChunks];
@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const u64* __rest
                         }
                     }
                 } else if (lane >= 1 && lane < 8) {
-                    const u64 key = ke + static_cast<u64>(lane) * (delta >> 3);
+                    const Key key = ke + static_cast<Key>(lane) * (delta >> 3);
                     for (u32 st = 1u << (31 - __clz(cnt_all)); st > 0; st >>= 1) {
                         const u32 probe = below + st;
                         if (probe <= cnt_all && __ldg(P + lo + probe - 1) < key) below = probe;
@@ -417,11 +417,11 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const u64* __rest
         return;
     }
     const u32 ne = ld_volatile(&ls->ne[t]);
-    const u64* K = b.K[t & 1];
+    const Key* K = b.K[t & 1];
     const u32* pos = b.pos[t & 1];
     const u32* set = b.set[t & 1];
     for (u32 e = gtid; e < ne; e += gthreads) {
-        const u64 k = K[e];
+        const Key k = K[e];
         out_keys[e] = k;
         if (BATCH) {
             out_counts[e] = k == kKeyEnd ? 0u : pos[e + 1] - pos[e];
@@ -449,7 +449,7 @@ LeavesLayout leaves_layout(void* ws, long long ecap, int max_iters, bool batch) 
     l.bufs.split_elem = c.take<u32>((size_t)ecap);
     l.bufs.split_pos = c.take<u32>((size_t)ecap);
     for (int k = 0; k < 2; ++k) {
-        l.bufs.K[k] = c.take<u64>((size_t)ecap);
+        l.bufs.K[k] = c.take<Key>((size_t)ecap);
         l.bufs.pos[k] = c.take<u32>((size_t)ecap);
         l.bufs.set[k] = batch ? c.take<u32>((size_t)ecap) : nullptr;
     }
@@ -490,7 +490,7 @@ int read_leaves_result(void* ws, cudaStream_t st, long long ecap, int max_iters,
 // count of the converged arrays on success; without, nothing is read back (the outcome stays in
 // the workspace for read_leaves_result) and a failure leaves every set's root array as output.
 template <bool BATCH>
-int run_leaves(const u64* P, long long n, u32 ncrit, u64* leaves, long long ecap, long long ne0, long long* ne_out,
+int run_leaves(const Key* P, long long n, u32 ncrit, Key* leaves, long long ecap, long long ne0, long long* ne_out,
                u32* counts, u32* offsets, int max_iters, int* iters, SetView sv, void* ws, cudaStream_t st,
                const char* who, bool sync = true) {
     LeavesLayout l = leaves_layout(ws, ecap, max_iters, BATCH);
@@ -502,13 +502,13 @@ int run_leaves(const u64* P, long long n, u32 ncrit, u64* leaves, long long ecap
     u32 ne_start = ne0 < 0 ? kDeviceCount : static_cast<u32>(ne0);
     int fallback = sync ? 0 : 1;
 
-    const u64* P_ = P;
+    const Key* P_ = P;
     u32 n_ = static_cast<u32>(n), ncrit_ = ncrit, ecap_ = static_cast<u32>(ecap), max_tiles = l.max_tiles;
     int max_iters_ = max_iters;
     LeafBufs bufs = l.bufs;
     u64* look = l.look;
     LoopState* ls = l.ls;
-    u64* out_keys = leaves;
+    Key* out_keys = leaves;
     u32* out_counts = counts;
     u32* out_offsets = offsets;
     void* args[] = {&P_,       &n_,   &ncrit_,    &bufs, &ecap_, &max_iters_, &warm,     &ne_start,   &fallback,
@@ -526,12 +526,12 @@ size_t leaves_batched_ws_bytes(long long ecap, int max_iters) {
     return leaves_layout(nullptr, ecap, max_iters, true).bytes;
 }
 
-int launch_build_leaves(const u64* P, long long n, u32 ncrit, u64* leaves, long long cap, long long* n_leaves,
+int launch_build_leaves(const Key* P, long long n, u32 ncrit, Key* leaves, long long cap, long long* n_leaves,
                         u32* counts, u32* offsets, int max_iters, int* iters, void* ws, cudaStream_t st) {
     const long long ne0 = *n_leaves > 0 ? *n_leaves + 1 : 0;
     long long ne = 0;
     const int rc = run_leaves<false>(P, n, ncrit, leaves, cap + 1, ne0, &ne, counts, offsets, max_iters, iters,
-                                     SetView{nullptr, nullptr, 1}, ws, st, "cstone_build_leaves");
+                                     SetView{nullptr, nullptr, 1}, ws, st, CST_STR(CSTONE_FN(build_leaves)));
     if (rc == CSTONE_ERR_CAPACITY) {
         *n_leaves = ne - 1;
         return rc;
@@ -540,16 +540,16 @@ int launch_build_leaves(const u64* P, long long n, u32 ncrit, u64* leaves, long 
     return rc;
 }
 
-int launch_build_leaves_batched_async(const u64* P, long long n, const long long* particle_offsets, int n_sets,
-                                      u32 ncrit, u64* leaves, long long ecap, long long* element_offsets, int warm,
+int launch_build_leaves_batched_async(const Key* P, long long n, const long long* particle_offsets, int n_sets,
+                                      u32 ncrit, Key* leaves, long long ecap, long long* element_offsets, int warm,
                                       u32* counts, u32* offsets, int max_iters, void* ws, cudaStream_t st) {
     return run_leaves<true>(P, n, ncrit, leaves, ecap, warm ? -1 : 0, nullptr, counts, offsets, max_iters, nullptr,
                             SetView{particle_offsets, element_offsets, n_sets}, ws, st,
                             "cstone_build_leaves_batched_async", false);
 }
 
-int launch_build_leaves_batched(const u64* P, long long n, const long long* particle_offsets, int n_sets, u32 ncrit,
-                                u64* leaves, long long ecap, long long* element_offsets, long long* n_elements,
+int launch_build_leaves_batched(const Key* P, long long n, const long long* particle_offsets, int n_sets, u32 ncrit,
+                                Key* leaves, long long ecap, long long* element_offsets, long long* n_elements,
                                 u32* counts, u32* offsets, int max_iters, int* iters, void* ws, cudaStream_t st) {
     long long ne = 0;
     const int rc = run_leaves<true>(P, n, ncrit, leaves, ecap, *n_elements, &ne, counts, offsets, max_iters, iters,
@@ -559,39 +559,41 @@ int launch_build_leaves_batched(const u64* P, long long n, const long long* part
     return rc;
 }
 
-}  // namespace cst
+}  // namespace CST_NS
 
 extern "C" {
 
-int cstone_leaves_workspace_size(int64_t n, int64_t leaf_cap, int32_t max_iters, size_t* bytes) {
+int CSTONE_FN(leaves_workspace_size)(int64_t n, int64_t leaf_cap, int32_t max_iters, size_t* bytes) {
     if (!bytes || n < 0 || n >= CSTONE_MAX_PARTICLES || leaf_cap < 1 || leaf_cap > CSTONE_MAX_LEAVES ||
         max_iters < 1 || max_iters > 256)
-        return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_leaves_workspace_size: bad argument");
-    *bytes = cst::leaves_ws_bytes(leaf_cap, max_iters);
+        return cst::fail(CSTONE_ERR_INVALID_ARG, CST_STR(CSTONE_FN(leaves_workspace_size)) ": bad argument");
+    *bytes = CST_NS::leaves_ws_bytes(leaf_cap, max_iters);
     return CSTONE_OK;
 }
 
-int cstone_build_leaves(const uint64_t* sorted_keys, int64_t n, uint32_t ncrit, uint64_t* leaves, int64_t leaf_cap,
-                        int64_t* n_leaves, uint32_t* counts, uint32_t* offsets, int32_t max_iters, int32_t* iters,
-                        void* ws, size_t ws_bytes, void* stream) {
+int CSTONE_FN(build_leaves)(const CST_KEY_C* sorted_keys, int64_t n, uint32_t ncrit, CST_KEY_C* leaves,
+                            int64_t leaf_cap, int64_t* n_leaves, uint32_t* counts, uint32_t* offsets,
+                            int32_t max_iters, int32_t* iters, void* ws, size_t ws_bytes, void* stream) {
     if (n < 0 || n >= CSTONE_MAX_PARTICLES || leaf_cap < 1 || leaf_cap > CSTONE_MAX_LEAVES || !leaves || !counts ||
         !n_leaves || max_iters < 1 || max_iters > 256 || (n > 0 && !sorted_keys))
-        return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_build_leaves: bad argument");
+        return cst::fail(CSTONE_ERR_INVALID_ARG, CST_STR(CSTONE_FN(build_leaves)) ": bad argument");
     if (*n_leaves < 0 || *n_leaves > leaf_cap)
-        return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_build_leaves: initial n_leaves %lld outside [0, %lld]",
-                         (long long)*n_leaves, (long long)leaf_cap);
-    if (int rc = cst::check_ws(ws, ws_bytes, cst::leaves_ws_bytes(leaf_cap, max_iters), "cstone_build_leaves"))
+        return cst::fail(CSTONE_ERR_INVALID_ARG, CST_STR(CSTONE_FN(build_leaves)) ": initial n_leaves %lld outside "
+                         "[0, %lld]", (long long)*n_leaves, (long long)leaf_cap);
+    if (int rc = cst::check_ws(ws, ws_bytes, CST_NS::leaves_ws_bytes(leaf_cap, max_iters),
+                               CST_STR(CSTONE_FN(build_leaves))))
         return rc;
     long long nl = *n_leaves;
     int it = 0;
-    int rc = cst::launch_build_leaves(reinterpret_cast<const cst::u64*>(sorted_keys), n, ncrit,
-                                      reinterpret_cast<cst::u64*>(leaves), leaf_cap, &nl, counts, offsets, max_iters,
-                                      &it, ws, cst::as_stream(stream));
+    int rc = CST_NS::launch_build_leaves(reinterpret_cast<const CST_NS::Key*>(sorted_keys), n, ncrit,
+                                         reinterpret_cast<CST_NS::Key*>(leaves), leaf_cap, &nl, counts, offsets,
+                                         max_iters, &it, ws, cst::as_stream(stream));
     *n_leaves = nl;
     if (iters) *iters = it;
     return rc;
 }
 
+#ifndef CSTONE_KEY32  // batched builds exist for 63-bit keys only
 int cstone_leaves_batched_workspace_size(int64_t elem_cap, int32_t max_iters, size_t* bytes) {
     if (!bytes || elem_cap < 2 || elem_cap > CSTONE_MAX_LEAVES || max_iters < 1 || max_iters > 256)
         return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_leaves_batched_workspace_size: bad argument");
@@ -655,5 +657,7 @@ int cstone_leaves_result(void* ws, int64_t elem_cap, int32_t max_iters, void* st
     if (iters) *iters = it;
     return rc;
 }
+
+#endif
 
 }  // extern "C"

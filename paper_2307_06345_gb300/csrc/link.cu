@@ -2,7 +2,7 @@
 //
 // Node keys: every leaf i gives a node at level L - log8(K_{i+1} - K_i); every adjacent pair
 // (K_i, K_{i+1}) whose first differing bit is the leading bit of an octal digit (d % 3 == 0 with
-// d the number of equal leading bits of the 63-bit keys, step 2) gives the internal node at level
+// d the number of equal leading bits of the 3L-bit keys, step 2) gives the internal node at level
 // d / 3 that is the lowest common ancestor of the two leaves: the pair straddles the boundary
 // between its child 3 and child 4, so each internal node appears exactly once.
 //
@@ -11,36 +11,36 @@
 // partition of that sequence by level therefore gives the breadth-first layout without sorting
 // 64-bit keys, and the offsets of the partition are the level offsets LO (step 4). This replaces
 // the paper's digit-weight slot mapping of step 2 followed by a radix sort of NK: the final NK
-// is the same. The partition is a counting sort with 22 buckets: per-tile level counts, one scan
+// is the same. The partition is a counting sort with L + 1 buckets: per-tile level counts, one scan
 // over (level, tile), and a scatter that ranks items stably inside each tile.
 //
 // Step 5: the first child of an internal node is found by binary search for its key << 3 within
 // the next level's range of NK; the same pass fills the parent of every sibling group.
 #include "common.cuh"
 
-namespace cst {
+namespace CST_NS {
 namespace {
 
 constexpr int kThreads = 256;
 constexpr int kItems = 8;
 constexpr int kTile = kThreads * kItems;
-constexpr int kNumLevels = kLevels + 1;  // 0..21
+constexpr int kNumLevels = kLevels + 1;  // levels 0..L
 
-__device__ __forceinline__ int leaf_level(u64 delta) {  // delta is a power of 8
-    return kLevels - (__ffsll(static_cast<long long>(delta)) - 1) / 3;
+__device__ __forceinline__ int leaf_level(Key delta) {  // delta is a power of 8
+    return kLevels - key_ffs(delta) / 3;
 }
 
 // Level of the internal node implied by the pair (i, i+1), or -1 when d % 3 != 0.
-__device__ __forceinline__ int pair_level(u64 a, u64 b) {
-    int d = __clzll(static_cast<long long>(a ^ b)) - 1;  // equal leading bits of the 63-bit keys
+__device__ __forceinline__ int pair_level(Key a, Key b) {
+    int d = key_clz(a ^ b) - (kWordBits - kKeyBits);  // equal leading bits of the 3L-bit keys
     return (d >= 0 && d % 3 == 0) ? d / 3 : -1;
 }
 
-__device__ __forceinline__ u64 placeholder(u64 key, int level) {
-    return (1ULL << (3 * level)) | (key >> (3 * (kLevels - level)));
+__device__ __forceinline__ Key placeholder(Key key, int level) {
+    return (static_cast<Key>(1) << (3 * level)) | (key >> (3 * (kLevels - level)));
 }
 
-__global__ void __launch_bounds__(kThreads) link_count_kernel(const u64* __restrict__ K, u32 nl, u32 ntiles,
+__global__ void __launch_bounds__(kThreads) link_count_kernel(const Key* __restrict__ K, u32 nl, u32 ntiles,
                                                               u32* __restrict__ counts) {
     __shared__ u32 s_cnt[kNumLevels];
     if (threadIdx.x < kNumLevels) s_cnt[threadIdx.x] = 0;
@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(kThreads) link_count_kernel(const u64* __restr
     for (int k = 0; k < kItems; ++k) {
         u32 i = i0 + k;
         if (i >= nl) break;
-        u64 a = K[i], b = K[i + 1];
+        Key a = K[i], b = K[i + 1];
         int ll = leaf_level(b - a);
 #pragma unroll
         for (int l = 0; l < kNumLevels; ++l) local[l] += (l == ll);
@@ -110,9 +110,9 @@ __global__ void __launch_bounds__(1024) link_scan_kernel(u32* __restrict__ count
     }
 }
 
-__global__ void __launch_bounds__(kThreads) link_scatter_kernel(const u64* __restrict__ K, u32 nl, u32 ntiles,
+__global__ void __launch_bounds__(kThreads) link_scatter_kernel(const Key* __restrict__ K, u32 nl, u32 ntiles,
                                                                 const u32* __restrict__ offsets, u32 n_nodes,
-                                                                u64* __restrict__ NK, int* __restrict__ leaf_to_node) {
+                                                                Key* __restrict__ NK, int* __restrict__ leaf_to_node) {
     __shared__ u32 s_rank[kNumLevels][kThreads];  // per-thread counts, then per-thread slots
     const int tid = threadIdx.x;
     const u32 tile = blockIdx.x;
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(kThreads) link_scatter_kernel(const u64* __res
     for (int k = 0; k < kItems; ++k) {
         u32 i = i0 + k;
         if (i >= nl) break;
-        u64 a = K[i], b = K[i + 1];
+        Key a = K[i], b = K[i + 1];
         s_rank[leaf_level(b - a)][tid] += 1;
         if (i + 1 < nl) {
             int pl = pair_level(a, b);
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(kThreads) link_scatter_kernel(const u64* __res
     for (int k = 0; k < kItems; ++k) {
         u32 i = i0 + k;
         if (i >= nl) break;
-        u64 a = K[i], b = K[i + 1];
+        Key a = K[i], b = K[i + 1];
         int ll = leaf_level(b - a);
         u32 x = s_rank[ll][tid]++;
         if (x < n_nodes) {
@@ -175,18 +175,18 @@ __global__ void __launch_bounds__(kThreads) link_scatter_kernel(const u64* __res
     }
 }
 
-__global__ void __launch_bounds__(kThreads) link_child_kernel(const u64* __restrict__ NK, u32 n_nodes,
+__global__ void __launch_bounds__(kThreads) link_child_kernel(const Key* __restrict__ NK, u32 n_nodes,
                                                               const int* __restrict__ LO, int* __restrict__ CO,
                                                               int* __restrict__ parent) {
     __shared__ int s_lo[kNumLevels + 1];
     if (threadIdx.x <= kNumLevels) s_lo[threadIdx.x] = LO[threadIdx.x];
     __syncthreads();
     for (u32 x = blockIdx.x * kThreads + threadIdx.x; x < n_nodes; x += gridDim.x * kThreads) {
-        u64 k = NK[x];
-        int level = (63 - __clzll(static_cast<long long>(k))) / 3;
+        Key k = NK[x];
+        int level = (kWordBits - 1 - key_clz(k)) / 3;
         int c = 0;
         if (level < kLevels) {
-            u64 want = k << 3;
+            Key want = k << 3;
             u32 lo = min(static_cast<u32>(s_lo[level + 1]), n_nodes);
             u32 hi = min(static_cast<u32>(s_lo[level + 2]), n_nodes);
             const u32 end = hi;
@@ -305,7 +305,7 @@ __device__ __forceinline__ u32 count_index(const LinkSets& ls, u32 set, int leve
     return tf * kNumLevels + static_cast<u32>(level) * nt + k;
 }
 
-__global__ void __launch_bounds__(kThreads) link_b_count_kernel(const u64* __restrict__ K, LinkSets ls,
+__global__ void __launch_bounds__(kThreads) link_b_count_kernel(const Key* __restrict__ K, LinkSets ls,
                                                                 u32* __restrict__ counts) {
     __shared__ u32 s_cnt[kNumLevels];
     const u32 tile = blockIdx.x;
@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(kThreads) link_b_count_kernel(const u64* __res
     const u32 e0 = ls.tile_elem[tile];
     for (u32 q = threadIdx.x; q < cnt; q += kThreads) {
         const u32 e = e0 + q;
-        const u64 a = K[e], b = K[e + 1];
+        const Key a = K[e], b = K[e + 1];
         atomicAdd(&s_cnt[leaf_level(b - a)], 1u);
         if (b != kKeyEnd) {
             const int pl = pair_level(a, b);
@@ -352,9 +352,9 @@ __global__ void link_b_lo_kernel(const u32* __restrict__ counts, LinkSets ls, in
     }
 }
 
-__global__ void __launch_bounds__(kThreads) link_b_scatter_kernel(const u64* __restrict__ K, LinkSets ls,
+__global__ void __launch_bounds__(kThreads) link_b_scatter_kernel(const Key* __restrict__ K, LinkSets ls,
                                                                   const u32* __restrict__ offsets, u32 n_nodes,
-                                                                  u64* __restrict__ NK, int* __restrict__ leaf_to_node) {
+                                                                  Key* __restrict__ NK, int* __restrict__ leaf_to_node) {
     __shared__ u32 s_rank[kNumLevels][kThreads];
     const int tid = threadIdx.x;
     const u32 tile = blockIdx.x;
@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(kThreads) link_b_scatter_kernel(const u64* __r
     for (int k = 0; k < kItems; ++k) {
         const u32 q = i0 + k;
         if (q >= cnt) break;
-        const u64 a = K[e0 + q], b = K[e0 + q + 1];
+        const Key a = K[e0 + q], b = K[e0 + q + 1];
         s_rank[leaf_level(b - a)][tid] += 1;
         if (b != kKeyEnd) {
             const int pl = pair_level(a, b);
@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(kThreads) link_b_scatter_kernel(const u64* __r
         const u32 q = i0 + k;
         if (q >= cnt) break;
         const u32 e = e0 + q;
-        const u64 a = K[e], b = K[e + 1];
+        const Key a = K[e], b = K[e + 1];
         const int ll = leaf_level(b - a);
         const u32 x = s_rank[ll][tid]++;
         if (x < n_nodes) {
@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(kThreads) link_b_scatter_kernel(const u64* __r
     }
 }
 
-__global__ void __launch_bounds__(kThreads) link_b_child_kernel(const u64* __restrict__ NK, u32 node_cap, int n_sets,
+__global__ void __launch_bounds__(kThreads) link_b_child_kernel(const Key* __restrict__ NK, u32 node_cap, int n_sets,
                                                                 const int* __restrict__ LO, int* __restrict__ CO) {
     const u32 last = static_cast<u32>(LO[n_sets * (kNumLevels + 1) - 1]);  // nodes of all sets
     const u32 n_nodes = last < node_cap ? last : node_cap;
@@ -434,11 +434,11 @@ __global__ void __launch_bounds__(kThreads) link_b_child_kernel(const u64* __res
                 hi_s = mid;
         }
         const int* row = LO + lo_s * (kNumLevels + 1);
-        const u64 k = NK[x];
-        const int level = (63 - __clzll(static_cast<long long>(k))) / 3;
+        const Key k = NK[x];
+        const int level = (kWordBits - 1 - key_clz(k)) / 3;
         int c = 0;
         if (level < kLevels) {
-            const u64 want = k << 3;
+            const Key want = k << 3;
             u32 lo = min(static_cast<u32>(row[level + 1]), n_nodes);
             u32 hi = min(static_cast<u32>(row[level + 2]), n_nodes);
             const u32 end = hi;
@@ -483,7 +483,7 @@ LinkBLayout link_b_layout(void* ws, long long n_elements, int n_sets) {
 
 size_t link_batched_ws_bytes(long long n_elements, int n_sets) { return link_b_layout(nullptr, n_elements, n_sets).bytes; }
 
-int launch_link_batched(const u64* K, long long n_elements, const long long* elem_offsets, int n_sets, u64* NK,
+int launch_link_batched(const Key* K, long long n_elements, const long long* elem_offsets, int n_sets, Key* NK,
                         int* CO, int* LO, int* leaf_to_node, long long n_nodes, void* ws, cudaStream_t st) {
     LinkBLayout l = link_b_layout(ws, n_elements, n_sets);
     l.ls.elem_offsets = elem_offsets;
@@ -519,7 +519,7 @@ namespace {
 
 size_t link_ws_bytes(long long nl) { return link_layout(nullptr, nl).bytes; }
 
-int launch_link(const u64* K, long long nl, u64* NK, int* CO, int* LO, int* leaf_to_node, int* parent, void* ws,
+int launch_link(const Key* K, long long nl, Key* NK, int* CO, int* LO, int* leaf_to_node, int* parent, void* ws,
                 cudaStream_t st) {
     LinkLayout l = link_layout(ws, nl);
     WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
@@ -539,30 +539,33 @@ int launch_link(const u64* K, long long nl, u64* NK, int* CO, int* LO, int* leaf
     return CSTONE_OK;
 }
 
-}  // namespace cst
+}  // namespace CST_NS
 
 extern "C" {
 
-int cstone_link_workspace_size(int64_t n_leaves, size_t* bytes) {
+int CSTONE_FN(link_workspace_size)(int64_t n_leaves, size_t* bytes) {
     if (!bytes || n_leaves < 1 || n_leaves > CSTONE_MAX_LEAVES)
-        return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_link_workspace_size: bad argument");
-    *bytes = cst::link_ws_bytes(n_leaves);
+        return cst::fail(CSTONE_ERR_INVALID_ARG, CST_STR(CSTONE_FN(link_workspace_size)) ": bad argument");
+    *bytes = CST_NS::link_ws_bytes(n_leaves);
     return CSTONE_OK;
 }
 
-int cstone_link_tree(const uint64_t* leaves, int64_t n_leaves, uint64_t* node_keys, int32_t* child,
-                     int32_t* level_offsets, int32_t* leaf_to_node, int32_t* parent, void* ws, size_t ws_bytes,
-                     void* stream) {
+int CSTONE_FN(link_tree)(const CST_KEY_C* leaves, int64_t n_leaves, CST_KEY_C* node_keys, int32_t* child,
+                         int32_t* level_offsets, int32_t* leaf_to_node, int32_t* parent, void* ws, size_t ws_bytes,
+                         void* stream) {
     if (n_leaves < 1 || n_leaves > CSTONE_MAX_LEAVES || (n_leaves - 1) % 7 != 0 || !leaves || !node_keys || !child ||
         !level_offsets || !leaf_to_node)
         return cst::fail(CSTONE_ERR_INVALID_ARG,
-                         "cstone_link_tree: bad argument (n_leaves=%lld must be 1 + 7k, arrays non-NULL)",
+                         CST_STR(CSTONE_FN(link_tree)) ": bad argument (n_leaves=%lld must be 1 + 7k, arrays non-NULL)",
                          (long long)n_leaves);
-    if (int rc = cst::check_ws(ws, ws_bytes, cst::link_ws_bytes(n_leaves), "cstone_link_tree")) return rc;
-    return cst::launch_link(reinterpret_cast<const cst::u64*>(leaves), n_leaves, reinterpret_cast<cst::u64*>(node_keys),
-                            child, level_offsets, leaf_to_node, parent, ws, cst::as_stream(stream));
+    if (int rc = cst::check_ws(ws, ws_bytes, CST_NS::link_ws_bytes(n_leaves), CST_STR(CSTONE_FN(link_tree))))
+        return rc;
+    return CST_NS::launch_link(reinterpret_cast<const CST_NS::Key*>(leaves), n_leaves,
+                               reinterpret_cast<CST_NS::Key*>(node_keys), child, level_offsets, leaf_to_node, parent,
+                               ws, cst::as_stream(stream));
 }
 
+#ifndef CSTONE_KEY32  // batched builds exist for 63-bit keys only
 int cstone_link_batched_workspace_size(int64_t n_elements, int32_t n_sets, size_t* bytes) {
     if (!bytes || n_sets < 1 || n_sets > (1 << 20) || n_elements < 2 * (int64_t)n_sets ||
         n_elements > CSTONE_MAX_LEAVES)
@@ -586,5 +589,7 @@ int cstone_link_tree_batched(const uint64_t* elements, int64_t n_elements, const
                                     reinterpret_cast<cst::u64*>(node_keys), child, level_offsets, leaf_to_node,
                                     n_nodes, ws, cst::as_stream(stream));
 }
+
+#endif
 
 }  // extern "C"

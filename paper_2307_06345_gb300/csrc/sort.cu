@@ -1,8 +1,9 @@
-// Stable LSD radix sort_by_key of 64-bit keys with the identity permutation as values
+// Stable LSD radix sort_by_key of the particle keys with the identity permutation as values
 // (Sec. 4 and the caption of Table 1: the particle keys are sorted with a permutation that
-// records where each particle went).
+// records where each particle went). 63-bit keys in 64-bit words take 8 passes of 8-bit digits,
+// 30-bit keys in 32-bit words take 4.
 //
-// One-sweep design: a single upfront pass histograms all eight 8-bit digits at once, then each
+// One-sweep design: a single upfront pass histograms all 8-bit digits at once, then each
 // digit pass reads a tile of keys (and values), ranks them within the tile with warp-level
 // match, publishes the tile's per-digit counts and resolves its global offsets by decoupled
 // look-back over the preceding tiles (tiles are claimed in order through an atomic counter, so
@@ -18,12 +19,12 @@
 
 #include "common.cuh"
 
-namespace cst {
+namespace CST_NS {
 namespace {
 
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
-constexpr int kPasses = 8;
+constexpr int kPasses = (kKeyBits + kRadixBits - 1) / kRadixBits;  // 8 (63-bit keys) or 4 (30-bit keys)
 // Tile shape (compile-time tuning knobs, set by the build from the autotuner's choice): threads per
 // block, keys per thread, blocks per SM, and look-back descriptors read per step.
 #ifndef CSTONE_SORT_THREADS
@@ -58,12 +59,12 @@ struct SortCtl {
 
 // Histograms of all 8 digits in one read of the keys. Per-block shared histograms, one global
 // atomic per non-empty bin per block.
-__global__ void __launch_bounds__(kThreads) sort_hist_kernel(const u64* __restrict__ keys, long long n, SortCtl* ctl) {
+__global__ void __launch_bounds__(kThreads) sort_hist_kernel(const Key* __restrict__ keys, long long n, SortCtl* ctl) {
     __shared__ u32 sh[kPasses][kRadix];
     for (int i = threadIdx.x; i < kPasses * kRadix; i += kThreads) (&sh[0][0])[i] = 0;
     __syncthreads();
     for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kThreads) {
-        u64 k = __ldg(keys + i);
+        Key k = __ldg(keys + i);
 #pragma unroll
         for (int p = 0; p < kPasses; ++p) atomicAdd(&sh[p][(k >> (p * kRadixBits)) & (kRadix - 1)], 1u);
     }
@@ -171,7 +172,7 @@ __global__ void __launch_bounds__(kThreads) seg_tiles_kernel(const long long* __
 }
 
 // Per-segment digit histograms of all 8 passes, one block per tile.
-__global__ void __launch_bounds__(kThreads) seg_hist_kernel(const u64* __restrict__ keys, SegTiles st, u32* seg_hist) {
+__global__ void __launch_bounds__(kThreads) seg_hist_kernel(const Key* __restrict__ keys, SegTiles st, u32* seg_hist) {
     __shared__ u32 sh[kPasses][kRadix];
     const u32 t = blockIdx.x;
     const u32 count = st.tile_count[t];
@@ -180,7 +181,7 @@ __global__ void __launch_bounds__(kThreads) seg_hist_kernel(const u64* __restric
     __syncthreads();
     const u32 base = st.tile_base[t];
     for (u32 i = threadIdx.x; i < count; i += kThreads) {
-        const u64 k = __ldg(keys + base + i);
+        const Key k = __ldg(keys + base + i);
 #pragma unroll
         for (int p = 0; p < kPasses; ++p) atomicAdd(&sh[p][(k >> (p * kRadixBits)) & (kRadix - 1)], 1u);
     }
@@ -214,7 +215,7 @@ __global__ void seg_scan_kernel(const long long* __restrict__ seg_offsets_in, co
 }
 
 struct PassSmem {
-    u64 keys[kTile];
+    Key keys[kTile];
     u32 vals[kTile];
     u32 warp_hist[kWarps][kRadix];  // per-warp digit counts, then each warp's first staging slot
     u32 delta[kRadix];              // output position minus staging slot, per digit
@@ -224,7 +225,7 @@ struct PassSmem {
 
 template <bool FIRST, bool SEG>
 __global__ void __launch_bounds__(kThreads, CSTONE_SORT_MIN_BLOCKS)
-    sort_pass_kernel(const u64* __restrict__ kin, u64* __restrict__ kout, const u32* __restrict__ vin,
+    sort_pass_kernel(const Key* __restrict__ kin, Key* __restrict__ kout, const u32* __restrict__ vin,
                      u32* __restrict__ vout, long long n, int pass, SortCtl* ctl, u32* look, u32* look_other,
                      WsHeader* hdr, SegTiles seg) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -255,15 +256,15 @@ __global__ void __launch_bounds__(kThreads, CSTONE_SORT_MIN_BLOCKS)
     }
 
     // ---- load (warp-striped: warp w owns keys base + w*32*kItems + it*32 + lane)
-    u64 key[kItems];
+    Key key[kItems];
     u32 val[kItems];
-    const u64* tkeys = kin + base;
+    const Key* tkeys = kin + base;
     const u32 woff = static_cast<u32>(warp * 32 * kItems + lane);  // offset of item 0 within the tile
 #pragma unroll
     for (int it = 0; it < kItems; ++it) {
         const u32 o = woff + it * 32;
         const bool ok = o < count;
-        key[it] = ok ? __ldcs(tkeys + o) : ~0ULL;
+        key[it] = ok ? __ldcs(tkeys + o) : ~static_cast<Key>(0);
         if (FIRST)
             val[it] = base + o;
         else
@@ -389,7 +390,7 @@ __global__ void __launch_bounds__(kThreads, CSTONE_SORT_MIN_BLOCKS)
 
     // ---- write each digit's run contiguously
     for (u32 s = tid; s < count; s += kThreads) {
-        const u64 k = sm.keys[s];
+        const Key k = sm.keys[s];
         const u32 pos = sm.delta[static_cast<u32>(k >> shift) & (kRadix - 1)] + s;
         kout[pos] = k;
         vout[pos] = sm.vals[s];
@@ -399,7 +400,7 @@ __global__ void __launch_bounds__(kThreads, CSTONE_SORT_MIN_BLOCKS)
 struct SortLayout {
     SortCtl* ctl;
     u32* look[2];
-    u64* keys_alt;
+    Key* keys_alt;
     u32* vals_alt;
     size_t bytes;
     long long tiles;
@@ -412,7 +413,7 @@ SortLayout sort_layout(void* ws, long long n) {
     l.ctl = c.take<SortCtl>(1);
     l.look[0] = c.take<u32>((size_t)l.tiles * kRadix);
     l.look[1] = c.take<u32>((size_t)l.tiles * kRadix);
-    l.keys_alt = c.take<u64>((size_t)n);
+    l.keys_alt = c.take<Key>((size_t)n);
     l.vals_alt = c.take<u32>((size_t)n);
     l.bytes = c.size();
     return l;
@@ -422,6 +423,7 @@ SortLayout sort_layout(void* ws, long long n) {
 
 size_t sort_ws_bytes(long long n) { return sort_layout(nullptr, n).bytes; }
 
+#ifndef CSTONE_KEY32  // the allocation-free sort exists for 63-bit keys only
 // ---------------------------------------------------------------- sort without allocation
 // Scratch of cstone_sort_static: the same layout as the caller workspace of cstone_sort, sized for
 // CSTONE_SORT_STATIC_MAX_KEYS keys, held in a file-scope device array that every GPU loading the
@@ -458,19 +460,21 @@ int static_sort_scratch(void** out) {
     return CSTONE_OK;
 }
 }  // namespace
+#endif
 
-// The 8 digit passes. Ping-pong: odd passes (1-based) write the workspace buffers, even passes the
-// output, so the eighth pass lands in keys_out / perm.
+// The digit passes (an even number). Ping-pong: odd passes (1-based) write the workspace buffers,
+// even passes the output, so the last pass lands in keys_out / perm.
 template <bool SEG>
-int run_passes(const u64* keys_in, u64* keys_out, u32* perm, long long n, long long tiles, SortCtl* ctl, u32* const look2[2],
-               u64* keys_alt, u32* vals_alt, WsHeader* hdr, SegTiles seg, cudaStream_t st) {
+int run_passes(const Key* keys_in, Key* keys_out, u32* perm, long long n, long long tiles, SortCtl* ctl, u32* const look2[2],
+               Key* keys_alt, u32* vals_alt, WsHeader* hdr, SegTiles seg, cudaStream_t st) {
     const int smem = static_cast<int>(sizeof(PassSmem));
     CST_CUDA(cudaFuncSetAttribute(sort_pass_kernel<true, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     CST_CUDA(cudaFuncSetAttribute(sort_pass_kernel<false, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    const u64* ksrc = keys_in;
+    const Key* ksrc = keys_in;
     const u32* vsrc = nullptr;
+    static_assert(kPasses % 2 == 0, "the last pass must write the output buffers");
     for (int p = 0; p < kPasses; ++p) {
-        u64* kdst = (p % 2 == 0) ? keys_alt : keys_out;
+        Key* kdst = (p % 2 == 0) ? keys_alt : keys_out;
         u32* vdst = (p % 2 == 0) ? vals_alt : perm;
         u32* look = look2[p & 1];
         u32* other = look2[(p + 1) & 1];
@@ -487,7 +491,7 @@ int run_passes(const u64* keys_in, u64* keys_out, u32* perm, long long n, long l
     return CSTONE_OK;
 }
 
-int launch_sort(const u64* keys_in, u64* keys_out, u32* perm, long long n, void* ws, cudaStream_t st) {
+int launch_sort(const Key* keys_in, Key* keys_out, u32* perm, long long n, void* ws, cudaStream_t st) {
     SortLayout l = sort_layout(ws, n);
     WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
     CST_CUDA(cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st));
@@ -512,7 +516,7 @@ struct SegLayout {
     SortCtl* ctl;
     SegBuild b;
     u32* look[2];
-    u64* keys_alt;
+    Key* keys_alt;
     u32* vals_alt;
     size_t bytes;
     long long max_tiles;
@@ -532,7 +536,7 @@ SegLayout seg_layout(void* ws, long long n, int n_segs) {
     l.b.seg_offsets = c.take<u32>((size_t)n_segs * kPasses * kRadix);
     l.look[0] = c.take<u32>((size_t)l.max_tiles * kRadix);
     l.look[1] = c.take<u32>((size_t)l.max_tiles * kRadix);
-    l.keys_alt = c.take<u64>((size_t)n);
+    l.keys_alt = c.take<Key>((size_t)n);
     l.vals_alt = c.take<u32>((size_t)n);
     l.bytes = c.size();
     return l;
@@ -542,7 +546,7 @@ SegLayout seg_layout(void* ws, long long n, int n_segs) {
 
 size_t sort_segmented_ws_bytes(long long n, int n_segs) { return seg_layout(nullptr, n, n_segs).bytes; }
 
-int launch_sort_segmented(const u64* keys_in, u64* keys_out, u32* perm, long long n, const long long* seg_offsets,
+int launch_sort_segmented(const Key* keys_in, Key* keys_out, u32* perm, long long n, const long long* seg_offsets,
                           int n_segs, void* ws, cudaStream_t st) {
     SegLayout l = seg_layout(ws, n, n_segs);
     WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
@@ -565,26 +569,28 @@ int launch_sort_segmented(const u64* keys_in, u64* keys_out, u32* perm, long lon
     return run_passes<true>(keys_in, keys_out, perm, n, l.max_tiles, l.ctl, l.look, l.keys_alt, l.vals_alt, hdr, view, st);
 }
 
-}  // namespace cst
+}  // namespace CST_NS
 
 extern "C" {
 
-int cstone_sort_workspace_size(int64_t n, size_t* bytes) {
+int CSTONE_FN(sort_workspace_size)(int64_t n, size_t* bytes) {
     if (!bytes || n < 0 || n >= CSTONE_MAX_PARTICLES)
-        return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_sort_workspace_size: bad argument (n=%lld)", (long long)n);
-    *bytes = cst::sort_ws_bytes(n);
+        return cst::fail(CSTONE_ERR_INVALID_ARG, CST_STR(CSTONE_FN(sort_workspace_size)) ": bad argument (n=%lld)",
+                         (long long)n);
+    *bytes = CST_NS::sort_ws_bytes(n);
     return CSTONE_OK;
 }
 
-int cstone_sort(const uint64_t* keys_in, uint64_t* keys_out, uint32_t* perm, int64_t n, void* ws, size_t ws_bytes,
-                void* stream) {
+int CSTONE_FN(sort)(const CST_KEY_C* keys_in, CST_KEY_C* keys_out, uint32_t* perm, int64_t n, void* ws,
+                    size_t ws_bytes, void* stream) {
     if (n < 0 || n >= CSTONE_MAX_PARTICLES || (n > 0 && (!keys_in || !keys_out || !perm)))
-        return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_sort: bad argument (n=%lld)", (long long)n);
-    if (int rc = cst::check_ws(ws, ws_bytes, cst::sort_ws_bytes(n), "cstone_sort")) return rc;
-    return cst::launch_sort(reinterpret_cast<const cst::u64*>(keys_in), reinterpret_cast<cst::u64*>(keys_out), perm,
-                            n, ws, cst::as_stream(stream));
+        return cst::fail(CSTONE_ERR_INVALID_ARG, CST_STR(CSTONE_FN(sort)) ": bad argument (n=%lld)", (long long)n);
+    if (int rc = cst::check_ws(ws, ws_bytes, CST_NS::sort_ws_bytes(n), CST_STR(CSTONE_FN(sort)))) return rc;
+    return CST_NS::launch_sort(reinterpret_cast<const CST_NS::Key*>(keys_in), reinterpret_cast<CST_NS::Key*>(keys_out),
+                               perm, n, ws, cst::as_stream(stream));
 }
 
+#ifndef CSTONE_KEY32
 int cstone_sort_static(const uint64_t* keys_in, uint64_t* keys_out, uint32_t* perm, int64_t n, void* stream) {
     if (n < 0 || (n > 0 && (!keys_in || !keys_out || !perm)))
         return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_sort_static: bad argument (n=%lld)", (long long)n);
@@ -622,5 +628,7 @@ int cstone_sort_segmented(const uint64_t* keys_in, uint64_t* keys_out, uint32_t*
                                       perm, n, reinterpret_cast<const long long*>(seg_offsets), n_segs, ws,
                                       cst::as_stream(stream));
 }
+
+#endif
 
 }  // extern "C"

@@ -18,7 +18,7 @@
 // Q = sum_c [Q_c + M_c (c_c - c)(c_c - c)^T].
 #include "common.cuh"
 
-namespace cst {
+namespace CST_NS {
 namespace {
 
 constexpr int kThreads = 256;
@@ -538,36 +538,37 @@ int launch_upsweep_multipoles(const double* x, const double* y, const double* z,
     return CSTONE_OK;
 }
 
-}  // namespace cst
+}  // namespace CST_NS
 
 extern "C" {
 
-int cstone_upsweep_workspace_size(int64_t n_leaves, size_t* bytes) {
+int CSTONE_FN(upsweep_workspace_size)(int64_t n_leaves, size_t* bytes) {
     if (!bytes || n_leaves < 1 || n_leaves > CSTONE_MAX_LEAVES)
-        return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_upsweep_workspace_size: bad argument");
-    *bytes = cst::upsweep_ws_bytes(n_leaves);
+        return cst::fail(CSTONE_ERR_INVALID_ARG, CST_STR(CSTONE_FN(upsweep_workspace_size)) ": bad argument");
+    *bytes = CST_NS::upsweep_ws_bytes(n_leaves);
     return CSTONE_OK;
 }
 
-int cstone_upsweep_counts(const uint32_t* leaf_counts, int64_t n_leaves, const int32_t* leaf_to_node,
+int CSTONE_FN(upsweep_counts)(const uint32_t* leaf_counts, int64_t n_leaves, const int32_t* leaf_to_node,
                           const int32_t* child, const int32_t* level_offsets, uint32_t* node_counts, void* ws,
                           size_t ws_bytes, void* stream) {
     if (n_leaves < 1 || n_leaves > CSTONE_MAX_LEAVES || (n_leaves - 1) % 7 != 0 || !leaf_counts || !leaf_to_node ||
         !child || !level_offsets || !node_counts)
-        return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_upsweep_counts: bad argument");
-    if (int rc = cst::check_ws(ws, ws_bytes, cst::upsweep_ws_bytes(n_leaves), "cstone_upsweep_counts")) return rc;
-    return cst::launch_upsweep_counts(leaf_counts, n_leaves, leaf_to_node, child, level_offsets, node_counts, ws,
+        return cst::fail(CSTONE_ERR_INVALID_ARG, CST_STR(CSTONE_FN(upsweep_counts)) ": bad argument");
+    if (int rc = cst::check_ws(ws, ws_bytes, CST_NS::upsweep_ws_bytes(n_leaves), CST_STR(CSTONE_FN(upsweep_counts))))
+        return rc;
+    return CST_NS::launch_upsweep_counts(leaf_counts, n_leaves, leaf_to_node, child, level_offsets, node_counts, ws,
                                       cst::as_stream(stream));
 }
 
-int cstone_multipole_workspace_size(int64_t n, int64_t n_leaves, size_t* bytes) {
+int CSTONE_FN(multipole_workspace_size)(int64_t n, int64_t n_leaves, size_t* bytes) {
     if (!bytes || n < 0 || n >= CSTONE_MAX_PARTICLES || n_leaves < 1 || n_leaves > CSTONE_MAX_LEAVES)
-        return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_multipole_workspace_size: bad argument");
-    *bytes = cst::multipole_ws_bytes(n_leaves, n);
+        return cst::fail(CSTONE_ERR_INVALID_ARG, CST_STR(CSTONE_FN(multipole_workspace_size)) ": bad argument");
+    *bytes = CST_NS::multipole_ws_bytes(n_leaves, n);
     return CSTONE_OK;
 }
 
-int cstone_upsweep_multipoles(const double* x, const double* y, const double* z, const float* m,
+int CSTONE_FN(upsweep_multipoles)(const double* x, const double* y, const double* z, const float* m,
                               const uint32_t* perm, int64_t n, const uint32_t* offsets, int64_t n_leaves,
                               const int32_t* leaf_to_node, const int32_t* child, const int32_t* level_offsets,
                               const double* box, float* mass, double* com, float* quad, void* ws, size_t ws_bytes,
@@ -575,13 +576,15 @@ int cstone_upsweep_multipoles(const double* x, const double* y, const double* z,
     if (n < 0 || n >= CSTONE_MAX_PARTICLES || n_leaves < 1 || n_leaves > CSTONE_MAX_LEAVES ||
         (n_leaves - 1) % 7 != 0 || !offsets || !leaf_to_node || !child || !level_offsets || !mass || !com || !quad ||
         !box || (n > 0 && (!x || !y || !z || !m || !perm)))
-        return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_upsweep_multipoles: bad argument");
-    if (int rc = cst::check_ws(ws, ws_bytes, cst::multipole_ws_bytes(n_leaves, n), "cstone_upsweep_multipoles"))
+        return cst::fail(CSTONE_ERR_INVALID_ARG, CST_STR(CSTONE_FN(upsweep_multipoles)) ": bad argument");
+    if (int rc = cst::check_ws(ws, ws_bytes, CST_NS::multipole_ws_bytes(n_leaves, n),
+                               CST_STR(CSTONE_FN(upsweep_multipoles))))
         return rc;
-    return cst::launch_upsweep_multipoles(x, y, z, m, perm, n, offsets, n_leaves, leaf_to_node, child, level_offsets,
+    return CST_NS::launch_upsweep_multipoles(x, y, z, m, perm, n, offsets, n_leaves, leaf_to_node, child, level_offsets,
                                           box, mass, com, quad, ws, cst::as_stream(stream));
 }
 
+#ifndef CSTONE_KEY32  // batched builds exist for 63-bit keys only
 int cstone_upsweep_counts_batched(const uint32_t* elem_counts, int64_t n_elements, const int32_t* leaf_to_node,
                                   const int32_t* child, const int32_t* level_offsets, int32_t n_sets,
                                   uint32_t* node_counts, void* ws, size_t ws_bytes, void* stream) {
@@ -593,5 +596,7 @@ int cstone_upsweep_counts_batched(const uint32_t* elem_counts, int64_t n_element
     return cst::launch_upsweep_counts_batched(elem_counts, n_elements, leaf_to_node, child, level_offsets, n_sets,
                                               node_counts, ws, cst::as_stream(stream));
 }
+
+#endif
 
 }  // extern "C"
