@@ -81,6 +81,14 @@ CSTONE_API int cstone_bbox_workspace_size(int64_t n, size_t* bytes);
 CSTONE_API int cstone_bbox(const double* x, const double* y, const double* z, int64_t n, double* box, void* ws, size_t ws_bytes,
                 void* stream);
 
+/* Per-axis bounds of the points: bounds[6] (device) = {min x, min y, min z, max x, max y, max z};
+ * with n = 0 the minima are +inf and the maxima -inf. A set spread over several processes takes
+ * the minimum and maximum of these over the processes and forms the same bounding cube as
+ * cstone_bbox (lo = minima, side = largest extent, 1 if zero). Workspace as for cstone_bbox.
+ * Asynchronous. */
+CSTONE_API int cstone_bounds(const double* x, const double* y, const double* z, int64_t n, double* bounds, void* ws,
+                             size_t ws_bytes, void* stream);
+
 /* ------------------------------------------------------------------------------------------
  * SFC keys (Sec. 3). Each coordinate is mapped to a grid cell of [0, 2^21) per axis by
  * g = clamp(floor((x - lo) * s), 0, 2^21 - 1) with s = 2^21 / side, the subtraction and the
@@ -301,6 +309,27 @@ CSTONE_API int cstone_upsweep_counts_batched(const uint32_t* elem_counts, int64_
                                              const int32_t* level_offsets, int32_t n_sets, uint32_t* node_counts,
                                              void* ws, size_t ws_bytes, void* stream);
 
+/* ------------------------------------------------------------------------------------------
+ * f and g as separate steps, for a leaf array whose counts are summed over several processes
+ * (the global tree of Sec. 6: every rank counts its own particles, the counts are summed by an
+ * allreduce, and every rank applies the same g to the summed counts).
+ *
+ * cstone_leaf_counts (Eq. histogram): counts[i] = number of sorted_keys in [leaves[i],
+ *   leaves[i+1]) for i < n_leaves. sorted_keys [n] device, ascending; leaves [n_leaves + 1]
+ *   device (a cornerstone array); counts [n_leaves] device output. Asynchronous.
+ * cstone_rebalance (Eqs. g1, g2, g3): one pass of the split / merge rule on the given counts,
+ *   writing the new array to leaves_out [leaf_cap + 1] (must not alias leaves) with
+ *   *n_leaves_out (host) leaves; *changed (host) = 1 if any leaf was split or merged, 0 if the
+ *   array is final. Returns CSTONE_ERR_CAPACITY (with *n_leaves_out = the leaves needed) when
+ *   the new array does not fit. Synchronises `stream`.
+ * ------------------------------------------------------------------------------------------ */
+CSTONE_API int cstone_leaf_counts(const uint64_t* sorted_keys, int64_t n, const uint64_t* leaves, int64_t n_leaves,
+                                  uint32_t* counts, void* stream);
+CSTONE_API int cstone_rebalance_workspace_size(int64_t n_leaves, size_t* bytes);
+CSTONE_API int cstone_rebalance(const uint64_t* leaves, const uint32_t* counts, int64_t n_leaves, uint32_t ncrit,
+                                uint64_t* leaves_out, int64_t leaf_cap, int64_t* n_leaves_out, int32_t* changed,
+                                void* ws, size_t ws_bytes, void* stream);
+
 /* ==========================================================================================
  * 30-bit keys (L = 10): the other key length of Sec. 3, one 32-bit word per key. Every entry
  * point below is its cstone_* counterpart with uint32_t keys and 10 levels: a key of this
@@ -329,6 +358,12 @@ CSTONE_API int cstone30_upsweep_counts(const uint32_t* leaf_counts, int64_t n_le
                                        const int32_t* child, const int32_t* level_offsets, uint32_t* node_counts,
                                        void* ws, size_t ws_bytes, void* stream);
 CSTONE_API int cstone30_multipole_workspace_size(int64_t n, int64_t n_leaves, size_t* bytes);
+CSTONE_API int cstone30_leaf_counts(const uint32_t* sorted_keys, int64_t n, const uint32_t* leaves, int64_t n_leaves,
+                                    uint32_t* counts, void* stream);
+CSTONE_API int cstone30_rebalance_workspace_size(int64_t n_leaves, size_t* bytes);
+CSTONE_API int cstone30_rebalance(const uint32_t* leaves, const uint32_t* counts, int64_t n_leaves, uint32_t ncrit,
+                                  uint32_t* leaves_out, int64_t leaf_cap, int64_t* n_leaves_out, int32_t* changed,
+                                  void* ws, size_t ws_bytes, void* stream);
 CSTONE_API int cstone30_upsweep_multipoles(const double* x, const double* y, const double* z, const float* m,
                                            const uint32_t* perm, int64_t n, const uint32_t* offsets, int64_t n_leaves,
                                            const int32_t* leaf_to_node, const int32_t* child,

@@ -26,7 +26,8 @@ __all__ = [
     "build_octree", "Workspace", "leaf_capacity", "n_nodes", "cstone_sort_static", "cstone_bbox_batched",
     "cstone_keys_batched", "cstone_sort_segmented", "cstone_build_leaves_batched", "cstone_link_tree_batched",
     "cstone_upsweep_counts_batched", "build_octrees_batched", "cstone_build_leaves_batched_async",
-    "cstone_leaves_result", "cstone_kernel_launches", "TimeStepper", "GraphTimeStepper",
+    "cstone_leaves_result", "cstone_kernel_launches", "TimeStepper", "GraphTimeStepper", "cstone_leaf_counts",
+    "cstone_rebalance", "cstone_bounds", "LEVELS", "LEVELS30",
 ]
 
 MORTON, HILBERT = 0, 1
@@ -96,10 +97,15 @@ def load():
             "cstone_build_leaves_batched_async": (ctypes.c_int, [P, i64, P, i32, u32, P, i64, P, i32, P, P, i32, P,
                                                                 sz, P]),
             "cstone_leaves_result": (ctypes.c_int, [P, i64, i32, P, pi64, pi32]),
+            "cstone_leaf_counts": (ctypes.c_int, [P, i64, P, i64, P, P]),
+            "cstone_bounds": (ctypes.c_int, [P, P, P, i64, P, P, sz, P]),
+            "cstone_rebalance_workspace_size": (ctypes.c_int, [i64, psz]),
+            "cstone_rebalance": (ctypes.c_int, [P, P, i64, u32, P, i64, pi64, pi32, P, sz, P]),
         }
         for name in ("keys", "sort_workspace_size", "sort", "leaves_workspace_size", "build_leaves",
                      "link_workspace_size", "link_tree", "upsweep_workspace_size", "upsweep_counts",
-                     "multipole_workspace_size", "upsweep_multipoles"):
+                     "multipole_workspace_size", "upsweep_multipoles", "leaf_counts", "rebalance_workspace_size",
+                     "rebalance"):
             sigs["cstone30_" + name] = sigs["cstone_" + name]
         for name, (res, args) in sigs.items():
             fn = getattr(lib, name)
@@ -191,6 +197,16 @@ def cstone_bbox(x, y, z, box, ws: Workspace, stream=None):
     buf = ws.get(need)
     _check(lib.cstone_bbox(_ptr(x), _ptr(y), _ptr(z), n, _ptr(box), _ptr(buf), buf.numel(), _stream(stream)),
            "cstone_bbox")
+
+
+def cstone_bounds(x, y, z, bounds, ws: Workspace, stream=None):
+    """bounds[6] (float64 CUDA) = per-axis minima then maxima (+inf / -inf when empty)."""
+    lib = load()
+    for t, nm in ((x, "x"), (y, "y"), (z, "z"), (bounds, "bounds")):
+        _need(t, torch.float64, nm)
+    buf = ws.get(_size(lib.cstone_bbox_workspace_size, x.numel()))
+    _check(lib.cstone_bounds(_ptr(x), _ptr(y), _ptr(z), x.numel(), _ptr(bounds), _ptr(buf), buf.numel(),
+                             _stream(stream)), "cstone_bounds")
 
 
 def cstone_keys(x, y, z, box, curve: int, keys, stream=None, levels: int = LEVELS):
@@ -285,6 +301,37 @@ def cstone_upsweep_multipoles(x, y, z, m, perm, offsets, n_leaves: int, leaf_to_
                                     n_leaves, _ptr(leaf_to_node), _ptr(child), _ptr(level_offsets), _ptr(box),
                                     _ptr(mass), _ptr(com), _ptr(quad), _ptr(buf), buf.numel(), _stream(stream)),
            "cstone_upsweep_multipoles")
+
+
+def cstone_leaf_counts(sorted_keys, leaves, n_leaves: int, counts, stream=None, levels: int = LEVELS):
+    """f: counts[i] = particles of sorted_keys in [leaves[i], leaves[i+1])."""
+    fn, kdt = _family(levels)
+    _need(sorted_keys, kdt, "sorted_keys")
+    _need(leaves, kdt, "leaves")
+    _need(counts, torch.int32, "counts")
+    _check(fn("leaf_counts")(_ptr(sorted_keys), sorted_keys.numel(), _ptr(leaves), n_leaves, _ptr(counts),
+                             _stream(stream)), "cstone_leaf_counts")
+
+
+def cstone_rebalance(leaves, counts, n_leaves: int, ncrit: int, leaves_out, ws: Workspace, stream=None,
+                     levels: int = LEVELS):
+    """g1-g3 on the given counts; returns (n_leaves_out, changed). ``leaves_out`` holds
+    leaf_cap + 1 keys."""
+    fn, kdt = _family(levels)
+    _need(leaves, kdt, "leaves")
+    _need(leaves_out, kdt, "leaves_out")
+    _need(counts, torch.int32, "counts")
+    buf = ws.get(_size(fn("rebalance_workspace_size"), n_leaves))
+    nl = ctypes.c_int64(0)
+    ch = ctypes.c_int32(0)
+    rc = fn("rebalance")(_ptr(leaves), _ptr(counts), n_leaves, ncrit, _ptr(leaves_out), leaves_out.numel() - 1,
+                         ctypes.byref(nl), ctypes.byref(ch), _ptr(buf), buf.numel(), _stream(stream))
+    if rc == ERR_CAPACITY:
+        err = CstoneError(rc, "cstone_rebalance", _detail())
+        err.required = int(nl.value)
+        raise err
+    _check(rc, "cstone_rebalance")
+    return int(nl.value), bool(ch.value)
 
 
 # ------------------------------------------------------------------------- whole build

@@ -99,6 +99,15 @@ __global__ void __launch_bounds__(256) bbox_reduce_kernel(const double* __restri
     }
 }
 
+// Per-axis minima and maxima {min x, min y, min z, max x, max y, max z}; with no points the
+// minima are +inf and the maxima -inf, so that a reduction over several sets ignores an empty one.
+__global__ void bounds_finalize_kernel(const BoxAcc* acc, long long n, double* bounds) {
+    if (threadIdx.x >= 3) return;
+    const int d = threadIdx.x;
+    bounds[d] = n > 0 ? from_ordered(acc->lo[d]) : __longlong_as_double(0x7ff0000000000000LL);
+    bounds[3 + d] = n > 0 ? from_ordered(acc->hi[d]) : __longlong_as_double(static_cast<long long>(0xfff0000000000000ULL));
+}
+
 __global__ void bbox_finalize_kernel(const BoxAcc* acc, long long n, double* box) {
     if (threadIdx.x != 0) return;
     if (n == 0) {
@@ -528,8 +537,9 @@ int launch_keys(const double* x, const double* y, const double* z, long long n, 
     return CSTONE_OK;
 }
 
+// bounding cube (bounds == false: box = {lo, side}) or per-axis bounds (bounds == true)
 int launch_bbox(const double* x, const double* y, const double* z, long long n, double* box, void* ws,
-                cudaStream_t st) {
+                cudaStream_t st, bool bounds = false) {
     Carver c(ws);
     BoxAcc* acc = c.take<BoxAcc>(1);
     bbox_init_kernel<<<1, 32, 0, st>>>(acc);
@@ -540,8 +550,13 @@ int launch_bbox(const double* x, const double* y, const double* z, long long n, 
         bbox_reduce_kernel<<<grid, 256, 0, st>>>(x, y, z, n, acc);
         CST_LAUNCHED("bbox_reduce_kernel");
     }
-    bbox_finalize_kernel<<<1, 32, 0, st>>>(acc, n, box);
-    CST_LAUNCHED("bbox_finalize_kernel");
+    if (bounds) {
+        bounds_finalize_kernel<<<1, 32, 0, st>>>(acc, n, box);
+        CST_LAUNCHED("bounds_finalize_kernel");
+    } else {
+        bbox_finalize_kernel<<<1, 32, 0, st>>>(acc, n, box);
+        CST_LAUNCHED("bbox_finalize_kernel");
+    }
     return CSTONE_OK;
 }
 
@@ -580,6 +595,14 @@ int cstone_bbox(const double* x, const double* y, const double* z, int64_t n, do
         return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_bbox: bad argument (n=%lld)", (long long)n);
     if (int rc = cst::check_ws(ws, ws_bytes, cst::bbox_ws_bytes(), "cstone_bbox")) return rc;
     return cst::launch_bbox(x, y, z, n, box, ws, cst::as_stream(stream));
+}
+
+int cstone_bounds(const double* x, const double* y, const double* z, int64_t n, double* bounds, void* ws,
+                  size_t ws_bytes, void* stream) {
+    if (n < 0 || n >= CSTONE_MAX_PARTICLES || !bounds || (n > 0 && (!x || !y || !z)))
+        return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_bounds: bad argument (n=%lld)", (long long)n);
+    if (int rc = cst::check_ws(ws, ws_bytes, cst::bbox_ws_bytes(), "cstone_bounds")) return rc;
+    return cst::launch_bbox(x, y, z, n, bounds, ws, cst::as_stream(stream), true);
 }
 
 int cstone_bbox_batched(const double* x, const double* y, const double* z, const int64_t* set_offsets, int32_t n_sets,

@@ -7,10 +7,10 @@
 // between levels. Level l occupies nodes [LO[l], LO[l+1]); a level whose next level is empty has no
 // internal node and is skipped.
 //
-// Multipoles (three launches: pack, leaf sums, level-by-level combination): FP32 accumulation with
-// compensation. Each sum is a pair (sum, compensation) updated with an exact two-sum step
-// (Neumaier), and the pairs of mass and second moments are carried up the tree in scratch so the
-// compensation survives all 21 levels. Positions are held in 64-bit fixed point, so coordinate
+// Multipoles (four launches: pack, leaf sums, sums of the few leaves too large for one group of
+// lanes, level-by-level combination): FP32 accumulation with compensation. Each sum is a pair
+// (sum, compensation) updated with an exact two-sum step (Neumaier), and the pairs of mass and
+// second moments are carried up the tree in scratch so the compensation survives all L levels. Positions are held in 64-bit fixed point, so coordinate
 // differences are exact and are rounded to FP32 once; the expansion centre (centre of mass) is kept
 // in fixed point and written out in FP64.
 // A leaf takes its first particle as the anchor for the differences, an internal node its first
@@ -204,6 +204,8 @@ struct MpScratch {  // per node: compensated sums and the fixed-point centre car
     ff* quad;           // [6 n], component-major
     long long* cfix;    // [3 n], component-major
     Record* rec;        // [n_particles]
+    u32* big;           // [n_leaves] leaves handed to the block-per-leaf kernel
+    u32* n_big;         // their number
 };
 
 __device__ __forceinline__ void store_node(int v, u32 n_nodes, ff M, const long long c[3], const ff q[6], MpScratch s,
@@ -286,6 +288,7 @@ __global__ void __launch_bounds__(kThreads) multipole_pack_kernel(const double* 
 // about it.
 constexpr int kLeafThreads = 256;
 constexpr int kGroupLanes = 8;  // lanes per leaf
+constexpr u32 kBigLeaf = 512;   // larger leaves are summed by a whole block
 
 __device__ __forceinline__ ff group_sum(ff v) {
 #pragma unroll
@@ -312,8 +315,13 @@ __global__ void __launch_bounds__(kLeafThreads) multipole_leaf_kernel(const u32*
     const FixedFrame f = s_f;
     const u32 gl = threadIdx.x % kGroupLanes;
     const u32 i = (blockIdx.x * kLeafThreads + threadIdx.x) / kGroupLanes;
-    const bool active = i < nl;
-    const u32 a = active ? offsets[i] : 0u, b = active ? offsets[i + 1] : 0u;
+    bool active = i < nl;
+    u32 a = active ? offsets[i] : 0u, b = active ? offsets[i + 1] : 0u;
+    if (b - a > kBigLeaf) {  // a whole block sums this leaf later (multipole_bigleaf_kernel)
+        if (gl == 0) s.big[atomicAdd(s.n_big, 1u)] = i;
+        active = false;
+        a = b = 0u;
+    }
     u32 trips = (b - a + kGroupLanes - 1) / kGroupLanes;
     for (int o = 16; o > 0; o >>= 1) trips = max(trips, __shfl_xor_sync(0xffffffffu, trips, o));
     ff M = ff_zero(), S[3] = {ff_zero(), ff_zero(), ff_zero()}, Q[6];
@@ -364,6 +372,87 @@ __global__ void __launch_bounds__(kLeafThreads) multipole_leaf_kernel(const u32*
 #pragma unroll
     for (int k = 0; k < 6; ++k) Q[k] = group_sum(Q[k]);
     if (active && gl == 0) store_node(leaf_to_node[i], n_nodes, M, c, Q, s, f, mass, com, quad);
+}
+
+// Sum of a compensated pair over the block (every thread gets the total); red holds kThreads / 32
+// pairs of scratch.
+__device__ __forceinline__ ff block_sum(ff v, ff* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ff w;
+        w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+        w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+        v = ff_add(v, w);
+    }
+    __syncthreads();  // red may still be read by the previous call
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    ff t = red[0];
+#pragma unroll
+    for (int w = 1; w < kLeafThreads / 32; ++w) t = ff_add(t, red[w]);
+    return t;
+}
+
+// Leaves of more than kBigLeaf particles (full-depth cells of dense data, which are never split),
+// one block per leaf: the same two passes (first moments about the first particle, then second
+// moments about the centre), each thread taking every kLeafThreads-th particle.
+__global__ void __launch_bounds__(kLeafThreads) multipole_bigleaf_kernel(const u32* __restrict__ offsets,
+                                                                         const u32* __restrict__ perm,
+                                                                         const int* __restrict__ leaf_to_node,
+                                                                         u32 n_nodes, MpScratch s,
+                                                                         const double* __restrict__ box,
+                                                                         float* __restrict__ mass,
+                                                                         double* __restrict__ com,
+                                                                         float* __restrict__ quad) {
+    __shared__ FixedFrame s_f;
+    __shared__ ff s_red[kLeafThreads / 32];
+    if (threadIdx.x == 0) s_f = make_frame(box);
+    __syncthreads();
+    const FixedFrame f = s_f;
+    const u32 nbig = *s.n_big;
+    for (u32 q = blockIdx.x; q < nbig; q += gridDim.x) {
+        const u32 i = s.big[q];
+        const u32 a = offsets[i], b = offsets[i + 1];
+        const Record r0 = s.rec[__ldg(perm + a)];
+        ff M = ff_zero(), S[3] = {ff_zero(), ff_zero(), ff_zero()}, Q[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) Q[k] = ff_zero();
+        for (u32 j = a + threadIdx.x; j < b; j += kLeafThreads) {
+            const Record r = s.rec[__ldg(perm + j)];
+            M = ff_add(M, r.m);
+            S[0] = ff_add(S[0], __fmul_rn(r.m, fixed_diff(r.x, r0.x, f)));
+            S[1] = ff_add(S[1], __fmul_rn(r.m, fixed_diff(r.y, r0.y, f)));
+            S[2] = ff_add(S[2], __fmul_rn(r.m, fixed_diff(r.z, r0.z, f)));
+        }
+        M = block_sum(M, s_red);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) S[d] = block_sum(S[d], s_red);
+        long long c[3];
+        const float Mv = ff_val(M);
+        const long long r0c[3] = {r0.x, r0.y, r0.z};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const float off = Mv != 0.f ? __fdiv_rn(ff_val(S[d]), Mv) : 0.f;
+            c[d] = r0c[d] + __float2ll_rn(__fmul_rn(__fmul_rn(off, 1.0f / f.s1), 1.0f / f.s2));
+        }
+        for (u32 j = a + threadIdx.x; j < b; j += kLeafThreads) {
+            const Record r = s.rec[__ldg(perm + j)];
+            const float e0 = fixed_diff(r.x, c[0], f);
+            const float e1 = fixed_diff(r.y, c[1], f);
+            const float e2 = fixed_diff(r.z, c[2], f);
+            const float me0 = __fmul_rn(r.m, e0), me1 = __fmul_rn(r.m, e1), me2 = __fmul_rn(r.m, e2);
+            Q[0] = ff_add(Q[0], __fmul_rn(me0, e0));
+            Q[1] = ff_add(Q[1], __fmul_rn(me0, e1));
+            Q[2] = ff_add(Q[2], __fmul_rn(me0, e2));
+            Q[3] = ff_add(Q[3], __fmul_rn(me1, e1));
+            Q[4] = ff_add(Q[4], __fmul_rn(me1, e2));
+            Q[5] = ff_add(Q[5], __fmul_rn(me2, e2));
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) Q[k] = block_sum(Q[k], s_red);
+        if (threadIdx.x == 0) store_node(leaf_to_node[i], n_nodes, M, c, Q, s, f, mass, com, quad);
+        __syncthreads();
+    }
 }
 
 // Internal nodes, level by level from the deepest: every internal node of a level combines its 8
@@ -465,6 +554,8 @@ UpLayout up_layout(void* ws, long long nl, long long n_particles, bool multipole
         l.mp.quad = c.take<ff>((size_t)nn * 6);
         l.mp.cfix = c.take<long long>((size_t)nn * 3);
         l.mp.rec = c.take<Record>((size_t)(n_particles > 0 ? n_particles : 1));
+        l.mp.big = c.take<u32>((size_t)nl);
+        l.mp.n_big = c.take<u32>(1);
     }
     l.bytes = c.size();
     return l;
@@ -521,11 +612,15 @@ int launch_upsweep_multipoles(const double* x, const double* y, const double* z,
         multipole_pack_kernel<<<pgrid, kThreads, 0, st>>>(x, y, z, m, static_cast<u32>(n), box, l.mp.rec, hdr);
         CST_LAUNCHED("multipole_pack_kernel");
     }
+    CST_CUDA(cudaMemsetAsync(l.mp.n_big, 0, sizeof(u32), st));
     const long long groups_per_block = kLeafThreads / kGroupLanes;
     unsigned lgrid = static_cast<unsigned>((nl + groups_per_block - 1) / groups_per_block);
     multipole_leaf_kernel<<<lgrid, kLeafThreads, 0, st>>>(offsets, static_cast<u32>(nl), perm, leaf_to_node, nn, l.mp,
                                                           box, mass, com, quad);
     CST_LAUNCHED("multipole_leaf_kernel");
+    multipole_bigleaf_kernel<<<sm_count() * 4, kLeafThreads, 0, st>>>(offsets, perm, leaf_to_node, nn, l.mp, box, mass,
+                                                                     com, quad);
+    CST_LAUNCHED("multipole_bigleaf_kernel");
     if (nl > 1) {
         u32 nn_ = nn;
         MpScratch mp = l.mp;

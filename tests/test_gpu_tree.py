@@ -165,6 +165,17 @@ def test_multipoles_within_tolerance(lib, oracle, kind):
     assert err["mass"] <= TOL and err["com"] <= TOL and err["quad"] <= TOL, err
 
 
+def test_multipoles_of_leaves_larger_than_a_group(lib, oracle):
+    # full-depth leaves of thousands of coincident particles are summed by a whole block
+    rng = np.random.default_rng(5)
+    base = rng.random((30, 3))
+    pts = np.concatenate([np.repeat(base[:6], 3000, axis=0) + 1e-9 * rng.standard_normal((18000, 3)),
+                          rng.random((5000, 3))])
+    m = rng.lognormal(0, 1, len(pts)).astype(np.float32)
+    err = _multipole_case(lib, oracle, pts[:, 0].copy(), pts[:, 1].copy(), pts[:, 2].copy(), m, 1, 16)
+    assert err["mass"] <= TOL and err["com"] <= TOL and err["quad"] <= TOL, err
+
+
 def test_multipoles_duplicates_and_single_particles(lib, oracle):
     rng = np.random.default_rng(4)
     base = rng.random((50, 3))
