@@ -83,6 +83,13 @@ def _load(levels: int = L):
                 "oracle_link": (i32, [P, i64, P, P, P, P, P]),
                 "oracle_node_counts": (i32, [P, i64, P, i64, P]),
                 "oracle_multipoles": (i32, [P, P, P, P, P, P, i64, P, P, i64, P, P, P]),
+                "oracle_focus_tiles": (i32, [ctypes.c_uint64, ctypes.c_uint64, P, P, i32]),
+                "oracle_mac_passes": (i32, [ctypes.c_uint64, i32, ctypes.c_uint64, ctypes.c_uint64, dbl, i32]),
+                "oracle_focus_decision": (i32, [P, P, i64, u32, ctypes.c_uint64, ctypes.c_uint64, dbl, i32, P]),
+                "oracle_build_focus_leaves": (i32, [P, i64, u32, ctypes.c_uint64, ctypes.c_uint64, dbl, i32, P, i64,
+                                                    P, i64, P, P, i32, P]),
+                "oracle_canonical_focus_leaves": (i32, [P, i64, u32, ctypes.c_uint64, ctypes.c_uint64, dbl, i32, P,
+                                                        i64, P]),
             }
             for name, (res, args) in sigs.items():
                 fn = getattr(lib, name)
@@ -268,6 +275,62 @@ def multipoles(x, y, z, m, P, perm, NK, nodes=None, levels: int = L):
     _check(_load(levels).oracle_multipoles(_ptr(x), _ptr(y), _ptr(z), _ptr(m), _ptr(P), _ptr(perm), P.size, _ptr(NK),
                                      _ptr(nodes), nodes.size, _ptr(M), _ptr(com), _ptr(quad)), "multipoles")
     return M, com, quad
+
+
+# ---------------------------------------------------------------- Sec. 7: focused (locally essential) tree
+def focus_tiles(f_start: int, f_end: int, levels: int = L):
+    """The maximal octree nodes tiling the key range [f_start, f_end): list of (start, level)."""
+    cap = 2 * 7 * (levels + 1)
+    ts = np.empty(cap, np.uint64)
+    tl = np.empty(cap, np.int32)
+    nt = _load(levels).oracle_focus_tiles(f_start, f_end, _ptr(ts), _ptr(tl), cap)
+    if nt < 0:
+        raise OracleError(f"focus_tiles failed with code {nt}")
+    return [(int(ts[i]), int(tl[i])) for i in range(nt)]
+
+
+def mac_passes(start: int, level: int, f_start: int, f_end: int, theta: float, curve: int, levels: int = L) -> bool:
+    """Minimum-distance MAC of the node (start, level) against every point of the focus."""
+    return bool(_load(levels).oracle_mac_passes(start, level, f_start, f_end, theta, curve))
+
+
+def focus_decision(K, N, ncrit: int, f_start: int, f_end: int, theta: float, curve: int, levels: int = L):
+    K, N = _c(K, np.uint64), _c(N, np.uint32)
+    O = np.empty(K.size, np.uint32)
+    _check(_load(levels).oracle_focus_decision(_ptr(K), _ptr(N), K.size - 1, ncrit, f_start, f_end, theta, curve,
+                                               _ptr(O)), "focus_decision")
+    return O
+
+
+def build_focus_leaves(P, ncrit: int, f_start: int, f_end: int, theta: float, curve: int, K_init=None,
+                       max_iters: int = 64, cap: int | None = None, levels: int = L):
+    """Literal f / g1^LE / g2 / g3 iteration of Sec. 7 on one process. Returns (K, N, iterations)."""
+    P = _c(P, np.uint64)
+    if cap is None:
+        cap = leaf_capacity_bound(P.size, ncrit, levels)
+    Kout = np.empty(cap + 1, np.uint64)
+    Nout = np.empty(cap, np.uint32)
+    nl = ctypes.c_int64()
+    it = ctypes.c_int()
+    kin, nl_init = (None, 0) if K_init is None else (_c(K_init, np.uint64), len(K_init) - 1)
+    rc = _load(levels).oracle_build_focus_leaves(_ptr(P), P.size, ncrit, f_start, f_end, theta, curve,
+                                                 _ptr(kin) if kin is not None else None, nl_init, _ptr(Kout), cap,
+                                                 ctypes.byref(nl), _ptr(Nout), max_iters, ctypes.byref(it))
+    _check(rc, "build_focus_leaves")
+    return Kout[: nl.value + 1].copy(), Nout[: nl.value].copy(), it.value
+
+
+def canonical_focus_leaves(P, ncrit: int, f_start: int, f_end: int, theta: float, curve: int,
+                           cap: int | None = None, levels: int = L):
+    """The focused tree by its definition (top-down)."""
+    P = _c(P, np.uint64)
+    if cap is None:
+        cap = leaf_capacity_bound(P.size, ncrit, levels)
+    Kout = np.empty(cap + 1, np.uint64)
+    nl = ctypes.c_int64()
+    _check(_load(levels).oracle_canonical_focus_leaves(_ptr(P), P.size, ncrit, f_start, f_end, theta, curve,
+                                                       _ptr(Kout), cap, ctypes.byref(nl)), "canonical_focus_leaves")
+    return Kout[: nl.value + 1].copy()
 
 
 def full_build(x, y, z, curve: int, ncrit: int, box=None, levels: int = L):

@@ -412,6 +412,223 @@ int oracle_check_cornerstone(const uint64_t* K, int64_t nl) {
 }
 
 /* =====================================================================================
+ * Sec. 7: locally essential (focused) octree on one process. The focus F is the contiguous key
+ * range [f_start, f_end). A node is the key range [s, s + 8^(L-l)) at level l; its cube is the
+ * level-l cell holding the first key's grid cell. The minimum-distance MAC of a node holds for
+ * every point of F when r_min > l_node / theta, with r_min the smallest distance between the node
+ * cube and the cubes that tile F, and l_node the node's edge; both in grid units (cells of the
+ * 2^L grid), r_min^2 an exact integer and (l_node / theta)^2 evaluated as two IEEE double roundings.
+ * ===================================================================================== */
+static void node_cell(uint64_t start, int level, int curve, uint32_t c[3]) {
+    uint32_t ix, iy, iz;
+    if (curve == 0)
+        oracle_morton_decode(start, &ix, &iy, &iz);
+    else
+        oracle_hilbert_decode_order(start, L, &ix, &iy, &iz);
+    int sh = L - level;
+    c[0] = (ix >> sh) << sh;
+    c[1] = (iy >> sh) << sh;
+    c[2] = (iz >> sh) << sh;
+}
+
+/* The maximal octree nodes tiling [f_start, f_end), in key order: at each position take the
+ * largest node that starts there and ends inside the range. At most 2 * 7 * L nodes. */
+int oracle_focus_tiles(uint64_t f_start, uint64_t f_end, uint64_t* tile_start, int* tile_level, int cap) {
+    int nt = 0;
+    uint64_t s = f_start;
+    while (s < f_end) {
+        int level = 0;
+        for (; level <= L; ++level) {
+            uint64_t size = 1ULL << (3 * (L - level));
+            if (s % size == 0 && s + size <= f_end) break;
+        }
+        if (nt >= cap) return ORACLE_E_CAPACITY;
+        tile_start[nt] = s;
+        tile_level[nt] = level;
+        ++nt;
+        s += 1ULL << (3 * (L - level));
+    }
+    return nt;
+}
+
+static uint64_t cube_gap2(const uint32_t a[3], uint64_t asz, const uint32_t b[3], uint64_t bsz) {
+    uint64_t r2 = 0;
+    for (int d = 0; d < 3; ++d) {
+        uint64_t a0 = a[d], a1 = a[d] + asz, b0 = b[d], b1 = b[d] + bsz;
+        uint64_t gap = 0;
+        if (b0 > a1) gap = b0 - a1;
+        if (a0 > b1) gap = a0 - b1;
+        r2 += gap * gap;
+    }
+    return r2;
+}
+
+int oracle_mac_passes(uint64_t start, int level, uint64_t f_start, uint64_t f_end, double theta, int curve) {
+    uint64_t ts[2 * 7 * (L + 1)];
+    int tl[2 * 7 * (L + 1)];
+    int nt = oracle_focus_tiles(f_start, f_end, ts, tl, 2 * 7 * (L + 1));
+    if (nt < 0) return nt;
+    uint32_t c[3];
+    node_cell(start, level, curve, c);
+    uint64_t size = 1ULL << (L - level);
+    uint64_t best = UINT64_MAX;
+    for (int t = 0; t < nt; ++t) {
+        uint32_t tc[3];
+        node_cell(ts[t], tl[t], curve, tc);
+        uint64_t r2 = cube_gap2(c, size, tc, 1ULL << (L - tl[t]));
+        if (r2 < best) best = r2;
+    }
+    if (nt == 0) return 1; /* an empty focus accepts every node */
+    double q = (double)size / theta;
+    return (double)best > q * q;
+}
+
+/* The node [start, start + size) shares no key with F (always true for an empty F). */
+static int outside_focus(uint64_t start, uint64_t size, uint64_t f_start, uint64_t f_end) {
+    return f_end <= f_start || start + size <= f_start || start >= f_end;
+}
+
+/* g1^LE: inside (or overlapping) F exactly g1; outside F a leaf splits only when it also fails the
+ * MAC, and 8 sibling leaves merge when their parent holds at most Ncrit particles or lies outside F
+ * and passes the MAC. */
+int oracle_focus_decision(const uint64_t* K, const uint32_t* N, int64_t nl, uint32_t ncrit, uint64_t f_start,
+                          uint64_t f_end, double theta, int curve, uint32_t* O) {
+    if (nl < 1) return ORACLE_E_ARG;
+    for (int64_t i = 0; i < nl; ++i) {
+        uint64_t delta = K[i + 1] - K[i];
+        int level = L;
+        for (uint64_t d = delta; d > 1; d >>= 3) --level;
+        uint32_t op = 1;
+        int splittable = N[i] > ncrit && delta > 1;
+        if (splittable && outside_focus(K[i], delta, f_start, f_end) &&
+            oracle_mac_passes(K[i], level, f_start, f_end, theta, curve))
+            splittable = 0;
+        if (splittable) {
+            op = 8;
+        } else if (delta < KEY_END) {
+            uint64_t j = (K[i] % (8 * delta)) / delta;
+            if (j >= 1 && (int64_t)j <= i && i - (int64_t)j + 8 <= nl) {
+                int64_t first = i - (int64_t)j;
+                if (K[first] + 8 * delta == K[first + 8]) {
+                    uint64_t sum = 0;
+                    for (int64_t s2 = first; s2 < first + 8; ++s2) sum += N[s2];
+                    int parent_out = outside_focus(K[first], 8 * delta, f_start, f_end);
+                    if (sum <= ncrit ||
+                        (parent_out && oracle_mac_passes(K[first], level - 1, f_start, f_end, theta, curve)))
+                        op = 0;
+                }
+            }
+        }
+        O[i] = op;
+    }
+    O[nl] = 0;
+    return ORACLE_OK;
+}
+
+/* The literal iteration of f (counts), g1^LE, g2, g3 until nothing changes (Sec. 7, Eqs.
+ * histogramf, mac, rebalancef on one process, so f^LE_1 is the plain histogram). */
+int oracle_build_focus_leaves(const uint64_t* P, int64_t n, uint32_t ncrit, uint64_t f_start, uint64_t f_end,
+                              double theta, int curve, const uint64_t* Kinit, int64_t nl_init, uint64_t* Kout,
+                              int64_t cap, int64_t* nl_out, uint32_t* Nout, int max_iters, int* iters_out) {
+    if (cap < 1 || n < 0 || !(theta > 0.0)) return ORACLE_E_ARG;
+    int64_t work_cap = cap * 8 + 8;
+    uint64_t* K = (uint64_t*)malloc((size_t)(work_cap + 1) * sizeof(uint64_t));
+    uint64_t* Kn = (uint64_t*)malloc((size_t)(work_cap + 1) * sizeof(uint64_t));
+    uint32_t* N = (uint32_t*)malloc((size_t)(work_cap + 1) * sizeof(uint32_t));
+    uint32_t* O = (uint32_t*)malloc((size_t)(work_cap + 1) * sizeof(uint32_t));
+    uint64_t* Op = (uint64_t*)malloc((size_t)(work_cap + 1) * sizeof(uint64_t));
+    int rc = ORACLE_OK;
+    int64_t nl;
+    if (nl_init <= 0) {
+        nl = 1;
+        K[0] = 0;
+        K[1] = KEY_END;
+    } else {
+        if (nl_init > work_cap || oracle_check_cornerstone(Kinit, nl_init) != ORACLE_OK) {
+            rc = ORACLE_E_ARG;
+            goto done;
+        }
+        nl = nl_init;
+        memcpy(K, Kinit, (size_t)(nl + 1) * sizeof(uint64_t));
+    }
+    int it = 0;
+    for (;;) {
+        if (it >= max_iters) {
+            rc = ORACLE_E_NOT_CONVERGED;
+            break;
+        }
+        ++it;
+        oracle_histogram(P, n, K, nl, N);
+        oracle_focus_decision(K, N, nl, ncrit, f_start, f_end, theta, curve, O);
+        int changed = 0;
+        for (int64_t i = 0; i < nl; ++i) changed |= (O[i] != 1);
+        if (!changed) break;
+        oracle_exclusive_scan(O, nl + 1, Op);
+        int64_t nl_new = (int64_t)Op[nl];
+        if (nl_new > work_cap) {
+            rc = ORACLE_E_CAPACITY;
+            goto done;
+        }
+        oracle_rebalance(K, O, Op, nl, Kn);
+        uint64_t* t = K;
+        K = Kn;
+        Kn = t;
+        nl = nl_new;
+    }
+    *iters_out = it;
+    *nl_out = nl;
+    if (rc == ORACLE_OK) {
+        if (nl > cap) {
+            rc = ORACLE_E_CAPACITY;
+        } else {
+            memcpy(Kout, K, (size_t)(nl + 1) * sizeof(uint64_t));
+            memcpy(Nout, N, (size_t)nl * sizeof(uint32_t));
+        }
+    }
+done:
+    free(K);
+    free(Kn);
+    free(N);
+    free(O);
+    free(Op);
+    return rc;
+}
+
+/* Definition of the focused tree, top-down: a node is split exactly when it is above level L,
+ * holds more than Ncrit particles, and overlaps F or fails the MAC. */
+static int canonical_focus_rec(const uint64_t* P, int64_t n, uint32_t ncrit, uint64_t f_start, uint64_t f_end,
+                               double theta, int curve, uint64_t start, int level, uint64_t* Kout, int64_t cap,
+                               int64_t* nl) {
+    uint64_t size = 1ULL << (3 * (L - level));
+    int64_t cnt = oracle_lower_bound(P, n, start + size) - oracle_lower_bound(P, n, start);
+    int split = cnt > (int64_t)ncrit && level < L;
+    if (split && outside_focus(start, size, f_start, f_end) &&
+        oracle_mac_passes(start, level, f_start, f_end, theta, curve))
+        split = 0;
+    if (split) {
+        for (uint64_t c = 0; c < 8; ++c) {
+            int rc = canonical_focus_rec(P, n, ncrit, f_start, f_end, theta, curve, start + c * (size / 8), level + 1,
+                                         Kout, cap, nl);
+            if (rc) return rc;
+        }
+        return ORACLE_OK;
+    }
+    if (*nl >= cap) return ORACLE_E_CAPACITY;
+    Kout[(*nl)++] = start;
+    return ORACLE_OK;
+}
+
+int oracle_canonical_focus_leaves(const uint64_t* P, int64_t n, uint32_t ncrit, uint64_t f_start, uint64_t f_end,
+                                  double theta, int curve, uint64_t* Kout, int64_t cap, int64_t* nl_out) {
+    int64_t nl = 0;
+    int rc = canonical_focus_rec(P, n, ncrit, f_start, f_end, theta, curve, 0, 0, Kout, cap, &nl);
+    if (rc) return rc;
+    Kout[nl] = KEY_END;
+    *nl_out = nl;
+    return ORACLE_OK;
+}
+
+/* =====================================================================================
  * Sec. 5: fully linked octree in breadth-first order.
  * Node keys use the Warren-Salmon placeholder-bit format: a 1 bit followed by the node's
  * `level` octal digits. The node set of the tree defined by K is every leaf plus every proper

@@ -60,6 +60,17 @@ int oracle_canonical_leaves(const uint64_t* P, int64_t n, uint32_t ncrit, uint64
                             int64_t* nl_out);
 int oracle_check_cornerstone(const uint64_t* K, int64_t nl);
 
+/* ---- Sec. 7: locally essential octree focused on the key range [f_start, f_end) ---- */
+int oracle_focus_tiles(uint64_t f_start, uint64_t f_end, uint64_t* tile_start, int* tile_level, int cap);
+int oracle_mac_passes(uint64_t start, int level, uint64_t f_start, uint64_t f_end, double theta, int curve);
+int oracle_focus_decision(const uint64_t* K, const uint32_t* N, int64_t nl, uint32_t ncrit, uint64_t f_start,
+                          uint64_t f_end, double theta, int curve, uint32_t* O);
+int oracle_build_focus_leaves(const uint64_t* P, int64_t n, uint32_t ncrit, uint64_t f_start, uint64_t f_end,
+                              double theta, int curve, const uint64_t* Kinit, int64_t nl_init, uint64_t* Kout,
+                              int64_t cap, int64_t* nl_out, uint32_t* Nout, int max_iters, int* iters_out);
+int oracle_canonical_focus_leaves(const uint64_t* P, int64_t n, uint32_t ncrit, uint64_t f_start, uint64_t f_end,
+                                  double theta, int curve, uint64_t* Kout, int64_t cap, int64_t* nl_out);
+
 /* ---- Sec. 5: fully linked octree ---- */
 int oracle_link(const uint64_t* K, int64_t nl, uint64_t* NK, int32_t* CO, int32_t* LO, int32_t* leaf_to_node,
                 int32_t* parent);
