@@ -330,6 +330,23 @@ CSTONE_API int cstone_rebalance(const uint64_t* leaves, const uint32_t* counts, 
                                 uint64_t* leaves_out, int64_t leaf_cap, int64_t* n_leaves_out, int32_t* changed,
                                 void* ws, size_t ws_bytes, void* stream);
 
+/* Locally essential octree focused on the key range F = [f_start, f_end) (Sec. 7): one pass of
+ * g1^LE, g2, g3 on the given counts. Inside F, and for a node overlapping F, the rule of
+ * cstone_rebalance. Outside F a leaf is split only when it also fails the minimum-distance
+ * multipole acceptance criterion r_min > l / theta, and 8 sibling leaves are merged when their
+ * parent holds at most ncrit particles or lies outside F and passes the criterion. r_min is the
+ * smallest distance between the node's cube and the cubes of the maximal octree nodes tiling F,
+ * l the node's edge, both in cells of the key grid; the comparison is r_min^2 (an exact integer)
+ * > (l / theta)^2 with l / theta and the square each rounded once in IEEE double. An empty F
+ * accepts every node. curve: the curve of the keys (their cubes are decoded from them).
+ * f_end <= 8^L, theta > 0. Otherwise as cstone_rebalance (same workspace size). Iterating
+ * cstone_leaf_counts and this call until *changed == 0 gives the focused tree; on one process the
+ * counts are the plain histogram of the process's particles. */
+CSTONE_API int cstone_rebalance_focus(const uint64_t* leaves, const uint32_t* counts, int64_t n_leaves, uint32_t ncrit,
+                                      uint64_t f_start, uint64_t f_end, double theta, int curve, uint64_t* leaves_out,
+                                      int64_t leaf_cap, int64_t* n_leaves_out, int32_t* changed, void* ws,
+                                      size_t ws_bytes, void* stream);
+
 /* ==========================================================================================
  * 30-bit keys (L = 10): the other key length of Sec. 3, one 32-bit word per key. Every entry
  * point below is its cstone_* counterpart with uint32_t keys and 10 levels: a key of this
@@ -364,6 +381,10 @@ CSTONE_API int cstone30_rebalance_workspace_size(int64_t n_leaves, size_t* bytes
 CSTONE_API int cstone30_rebalance(const uint32_t* leaves, const uint32_t* counts, int64_t n_leaves, uint32_t ncrit,
                                   uint32_t* leaves_out, int64_t leaf_cap, int64_t* n_leaves_out, int32_t* changed,
                                   void* ws, size_t ws_bytes, void* stream);
+CSTONE_API int cstone30_rebalance_focus(const uint32_t* leaves, const uint32_t* counts, int64_t n_leaves,
+                                        uint32_t ncrit, uint32_t f_start, uint32_t f_end, double theta, int curve,
+                                        uint32_t* leaves_out, int64_t leaf_cap, int64_t* n_leaves_out,
+                                        int32_t* changed, void* ws, size_t ws_bytes, void* stream);
 CSTONE_API int cstone30_upsweep_multipoles(const double* x, const double* y, const double* z, const float* m,
                                            const uint32_t* perm, int64_t n, const uint32_t* offsets, int64_t n_leaves,
                                            const int32_t* leaf_to_node, const int32_t* child,

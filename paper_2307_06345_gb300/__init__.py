@@ -27,7 +27,7 @@ __all__ = [
     "cstone_keys_batched", "cstone_sort_segmented", "cstone_build_leaves_batched", "cstone_link_tree_batched",
     "cstone_upsweep_counts_batched", "build_octrees_batched", "cstone_build_leaves_batched_async",
     "cstone_leaves_result", "cstone_kernel_launches", "TimeStepper", "GraphTimeStepper", "cstone_leaf_counts",
-    "cstone_rebalance", "cstone_bounds", "LEVELS", "LEVELS30",
+    "cstone_rebalance", "cstone_bounds", "cstone_rebalance_focus", "build_focus_leaves", "LEVELS", "LEVELS30",
 ]
 
 MORTON, HILBERT = 0, 1
@@ -99,14 +99,18 @@ def load():
             "cstone_leaves_result": (ctypes.c_int, [P, i64, i32, P, pi64, pi32]),
             "cstone_leaf_counts": (ctypes.c_int, [P, i64, P, i64, P, P]),
             "cstone_bounds": (ctypes.c_int, [P, P, P, i64, P, P, sz, P]),
+            "cstone_rebalance_focus": (ctypes.c_int, [P, P, i64, u32, ctypes.c_uint64, ctypes.c_uint64,
+                                                      ctypes.c_double, ctypes.c_int, P, i64, pi64, pi32, P, sz, P]),
             "cstone_rebalance_workspace_size": (ctypes.c_int, [i64, psz]),
             "cstone_rebalance": (ctypes.c_int, [P, P, i64, u32, P, i64, pi64, pi32, P, sz, P]),
         }
         for name in ("keys", "sort_workspace_size", "sort", "leaves_workspace_size", "build_leaves",
                      "link_workspace_size", "link_tree", "upsweep_workspace_size", "upsweep_counts",
                      "multipole_workspace_size", "upsweep_multipoles", "leaf_counts", "rebalance_workspace_size",
-                     "rebalance"):
+                     "rebalance", "rebalance_focus"):
             sigs["cstone30_" + name] = sigs["cstone_" + name]
+        res, args = sigs["cstone30_rebalance_focus"]
+        sigs["cstone30_rebalance_focus"] = (res, args[:4] + [u32, u32] + args[6:])
         for name, (res, args) in sigs.items():
             fn = getattr(lib, name)
             fn.restype = res
@@ -332,6 +336,53 @@ def cstone_rebalance(leaves, counts, n_leaves: int, ncrit: int, leaves_out, ws: 
         raise err
     _check(rc, "cstone_rebalance")
     return int(nl.value), bool(ch.value)
+
+
+def cstone_rebalance_focus(leaves, counts, n_leaves: int, ncrit: int, f_start: int, f_end: int, theta: float,
+                           curve: int, leaves_out, ws: Workspace, stream=None, levels: int = LEVELS):
+    """g1^LE-g3 of the tree focused on the key range [f_start, f_end) (Sec. 7); returns
+    (n_leaves_out, changed)."""
+    fn, kdt = _family(levels)
+    _need(leaves, kdt, "leaves")
+    _need(leaves_out, kdt, "leaves_out")
+    _need(counts, torch.int32, "counts")
+    buf = ws.get(_size(fn("rebalance_workspace_size"), n_leaves))
+    nl = ctypes.c_int64(0)
+    ch = ctypes.c_int32(0)
+    rc = fn("rebalance_focus")(_ptr(leaves), _ptr(counts), n_leaves, ncrit, f_start, f_end, theta, curve,
+                               _ptr(leaves_out), leaves_out.numel() - 1, ctypes.byref(nl), ctypes.byref(ch),
+                               _ptr(buf), buf.numel(), _stream(stream))
+    if rc == ERR_CAPACITY:
+        err = CstoneError(rc, "cstone_rebalance_focus", _detail())
+        err.required = int(nl.value)
+        raise err
+    _check(rc, "cstone_rebalance_focus")
+    return int(nl.value), bool(ch.value)
+
+
+def build_focus_leaves(sorted_keys, ncrit: int, f_start: int, f_end: int, theta: float, curve: int,
+                       warm_leaves=None, max_iters: int = 64, ws: Workspace | None = None, levels: int = LEVELS):
+    """The locally essential tree of one process focused on the key range [f_start, f_end) (Sec. 7):
+    f (cstone_leaf_counts) and g1^LE-g3 (cstone_rebalance_focus) until nothing changes, from the
+    root or from ``warm_leaves``. Returns (leaves [n_l + 1], counts [n_l], passes)."""
+    dev = sorted_keys.device
+    kdt = sorted_keys.dtype
+    ws = ws or Workspace(dev)
+    if warm_leaves is None:
+        end = 1 << (3 * levels)
+        K = torch.tensor([0, end - (1 << 64) if end >= 1 << 63 else end], dtype=kdt, device=dev)
+    else:
+        K = warm_leaves
+    nl = K.numel() - 1
+    for it in range(1, max_iters + 1):
+        N = torch.empty(nl, dtype=torch.int32, device=dev)
+        cstone_leaf_counts(sorted_keys, K, nl, N, levels=levels)
+        out = torch.empty(8 * nl + 2, dtype=kdt, device=dev)
+        nl2, changed = cstone_rebalance_focus(K, N, nl, ncrit, f_start, f_end, theta, curve, out, ws, levels=levels)
+        if not changed:
+            return K[: nl + 1], N, it
+        K, nl = out[: nl2 + 1], nl2
+    raise CstoneError(ERR_NOT_CONVERGED, "build_focus_leaves", f"not converged after {max_iters} passes")
 
 
 # ------------------------------------------------------------------------- whole build

@@ -155,6 +155,14 @@ constexpr int kWordBits = 8 * static_cast<int>(sizeof(Key));
 constexpr Key kKeyEnd = static_cast<Key>(1) << kKeyBits;  // 8^L
 static_assert(kKeyBits < kWordBits, "8^L must fit the key word");
 
+// Inverse of the Hilbert state machine of the key kernels, one level at a time: entry
+// state * 8 + digit = octant (x << 2 | y << 1 | z of the cell bits at that level) | next state << 3.
+constexpr int kHilbertStates = 48;
+struct HilbertDecodeTable {
+    unsigned short one[kHilbertStates * 8];
+};
+const HilbertDecodeTable& hilbert_decode_table();  // built once on the host (keys.cu)
+
 // Index (from 0) of the lowest set bit of a non-zero key, and leading zero bits of a key word.
 __device__ __forceinline__ int key_ffs(Key k) {
     return sizeof(Key) == 8 ? __ffsll(static_cast<long long>(k)) - 1 : __ffs(static_cast<int>(k)) - 1;

@@ -127,8 +127,6 @@ __global__ void bbox_finalize_kernel(const BoxAcc* acc, long long n, double* box
 }
 
 // ---------------------------------------------------------------------------------- grid + keys
-constexpr int kHilbertStates = 48;
-
 struct HilbertTable {
     unsigned short two[kHilbertStates * 64];  // (state, 2 octants) -> 6 digit bits | next << 6
     unsigned short one[kHilbertStates * 8];   // (state, 1 octant)  -> 3 digit bits | next << 3
@@ -481,6 +479,20 @@ __global__ void __launch_bounds__(256) keys_batched_kernel(const double* __restr
 }
 
 }  // namespace
+
+const HilbertDecodeTable& hilbert_decode_table() {
+    static HilbertDecodeTable dec;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        const HilbertTable& t = hilbert_table();
+        for (int s = 0; s < kHilbertStates; ++s)
+            for (int o = 0; o < 8; ++o) {
+                const int e = t.one[s * 8 + o];
+                dec.one[s * 8 + (e & 7)] = static_cast<unsigned short>(o | ((e >> 3) << 3));
+            }
+    });
+    return dec;
+}
 
 size_t keys_batched_ws_bytes(int n_sets) {
     Carver c(nullptr);

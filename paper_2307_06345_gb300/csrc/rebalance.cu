@@ -9,6 +9,15 @@
 // f: one thread per leaf, two binary searches in the sorted keys. g: three launches: the decision
 // O_i of every leaf with per-tile sums, one block scanning the tile sums, and a per-tile scan that
 // places every kept, merged-into or split leaf (Eqs. rebalancecopy / rebalancesplit).
+//
+// The locally essential tree of Sec. 7 (focused on the key range F = [f_start, f_end)) uses the
+// same g2 and g3 after its own decision g1^LE: inside F (and for nodes overlapping it) the rule
+// of g1; outside F a leaf splits only when it also fails the minimum-distance MAC r_min > l / theta
+// against F, and 8 sibling leaves merge when their parent holds at most N_crit particles or lies
+// outside F and passes the MAC. r_min is the smallest distance between the node's cube and the
+// cubes of the maximal octree nodes that tile F (at most 2 * 7 * L of them, decoded once per
+// block); distances are in cells of the 2^L grid, r_min^2 an exact integer, (l / theta)^2 two IEEE
+// double roundings.
 #include "common.cuh"
 
 namespace CST_NS {
@@ -179,6 +188,137 @@ __global__ void __launch_bounds__(kThreads) rebalance_scatter_kernel(const Key* 
     }
 }
 
+// ------------------------------------------------------------------ focused decision (Sec. 7)
+constexpr int kMaxFocusTiles = 2 * 7 * (kLevels + 1);
+
+struct FocusParams {
+    Key start[kMaxFocusTiles];
+    unsigned char level[kMaxFocusTiles];
+    int n_tiles;
+    Key f_start, f_end;
+    double theta;
+    int curve;
+};
+
+// Grid cell (2^L per axis) of a key: the Morton de-interleave, or the Hilbert state machine run
+// backwards from the top level.
+__device__ __forceinline__ void key_cell(Key key, int curve, const unsigned short* dec, u32 c[3]) {
+    u32 x = 0, y = 0, z = 0, state = 0;
+    for (int l = kLevels - 1; l >= 0; --l) {
+        u32 o = static_cast<u32>((key >> (3 * l)) & 7u);
+        if (curve == CSTONE_HILBERT) {
+            const u32 e = dec[state * 8 + o];
+            o = e & 7u;
+            state = e >> 3;
+        }
+        x = (x << 1) | (o >> 2);
+        y = (y << 1) | ((o >> 1) & 1u);
+        z = (z << 1) | (o & 1u);
+    }
+    c[0] = x;
+    c[1] = y;
+    c[2] = z;
+}
+
+__device__ __forceinline__ bool outside_focus(Key start, Key size, Key f_start, Key f_end) {
+    return f_end <= f_start || start + size <= f_start || start >= f_end;
+}
+
+// MAC of the cube [c, c + edge)^3 against the focus tiles held in shared memory.
+__device__ __forceinline__ bool mac_passes(const u32 c[3], u32 edge, const u32 (*tc)[4], int nt, double theta) {
+    if (nt == 0) return true;  // an empty focus accepts every node
+    u64 best = ~0ULL;
+    for (int t = 0; t < nt && best != 0; ++t) {
+        u64 r2 = 0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const u64 a0 = c[d], a1 = a0 + edge, b0 = tc[t][d], b1 = b0 + tc[t][3];
+            const u64 gap = b0 > a1 ? b0 - a1 : (a0 > b1 ? a0 - b1 : 0);
+            r2 += gap * gap;
+        }
+        best = r2 < best ? r2 : best;
+    }
+    const double q = __ddiv_rn(static_cast<double>(edge), theta);
+    return __ull2double_rn(best) > __dmul_rn(q, q);
+}
+
+__global__ void __launch_bounds__(kThreads) focus_ops_kernel(const Key* __restrict__ K, const u32* __restrict__ N,
+                                                             u32 nl, u32 ncrit, const __grid_constant__ FocusParams fp,
+                                                             const __grid_constant__ HilbertDecodeTable dt,
+                                                             unsigned char* __restrict__ O,
+                                                             u32* __restrict__ tile_sums, RebalanceState* st) {
+    __shared__ u32 s_warp[kThreads / 32];
+    __shared__ u32 s_tile[kMaxFocusTiles][4];  // cube corner and edge of every focus tile
+    __shared__ unsigned short s_dec[kHilbertStates * 8];
+    for (int i = threadIdx.x; i < kHilbertStates * 8; i += kThreads) s_dec[i] = dt.one[i];
+    __syncthreads();
+    for (int t = threadIdx.x; t < fp.n_tiles; t += kThreads) {
+        u32 c[3];
+        key_cell(fp.start[t], fp.curve, s_dec, c);
+        const u32 edge = 1u << (kLevels - fp.level[t]);
+        for (int d = 0; d < 3; ++d) s_tile[t][d] = c[d] & ~(edge - 1u);
+        s_tile[t][3] = edge;
+    }
+    __syncthreads();
+    const u32 base = blockIdx.x * kTile + threadIdx.x * kItems;
+    u32 sum = 0;
+    bool changed = false;
+    for (int k = 0; k < kItems; ++k) {
+        const u32 i = base + k;
+        if (i > nl) break;
+        u32 op = 0;
+        if (i < nl) {
+            const Key ke = K[i];
+            const Key delta = K[i + 1] - ke;
+            const int level = kLevels - key_ffs(delta) / 3;
+            const u32 edge = 1u << (kLevels - level);
+            bool cube_known = false;
+            u32 c[3];
+            auto cube = [&]() {
+                if (!cube_known) {
+                    key_cell(ke, fp.curve, s_dec, c);
+                    for (int d = 0; d < 3; ++d) c[d] &= ~(edge - 1u);
+                    cube_known = true;
+                }
+            };
+            bool split = N[i] > ncrit && delta > 1;
+            if (split && outside_focus(ke, delta, fp.f_start, fp.f_end)) {
+                cube();
+                split = !mac_passes(c, edge, s_tile, fp.n_tiles, fp.theta);
+            }
+            op = 1u;
+            if (split) {
+                op = 8u;
+            } else if (delta < kKeyEnd) {
+                const u32 j = static_cast<u32>((ke >> key_ffs(delta)) & 7u);
+                if (j >= 1u && j <= i && i - j + 8u <= nl) {
+                    const u32 first = i - j;
+                    if (K[first] + static_cast<Key>(8) * delta == K[first + 8]) {
+                        u32 s8 = 0;
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) s8 += N[first + q];
+                        bool merge = s8 <= ncrit;
+                        if (!merge && outside_focus(K[first], static_cast<Key>(8) * delta, fp.f_start, fp.f_end)) {
+                            cube();
+                            u32 pc[3];
+                            for (int d = 0; d < 3; ++d) pc[d] = c[d] & ~(2u * edge - 1u);
+                            merge = mac_passes(pc, 2u * edge, s_tile, fp.n_tiles, fp.theta);
+                        }
+                        if (merge) op = 0u;
+                    }
+                }
+            }
+        }
+        O[i] = static_cast<unsigned char>(op);
+        sum += op;
+        changed |= i < nl && op != 1u;
+    }
+    if (__syncthreads_or(changed) && threadIdx.x == 0) atomicOr(&st->changed, 1u);
+    u32 total;
+    block_exclusive_scan(sum, s_warp, &total);
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
 struct RebalanceLayout {
     RebalanceState* st;
     u32* tile_sums;
@@ -210,13 +350,40 @@ int launch_leaf_counts(const Key* P, long long n, const Key* K, long long nl, u3
     return CSTONE_OK;
 }
 
+// The maximal octree nodes tiling [f_start, f_end), in key order (host).
+int focus_tiles(Key f_start, Key f_end, FocusParams& fp) {
+    fp.n_tiles = 0;
+    Key s = f_start;
+    while (s < f_end) {
+        int level = 0;
+        for (; level <= kLevels; ++level) {
+            const Key size = static_cast<Key>(1) << (3 * (kLevels - level));
+            if (s % size == 0 && s + size <= f_end) break;
+        }
+        if (fp.n_tiles >= kMaxFocusTiles) return fail(CSTONE_ERR_INVALID_ARG, "focus range needs too many tiles");
+        fp.start[fp.n_tiles] = s;
+        fp.level[fp.n_tiles] = static_cast<unsigned char>(level);
+        ++fp.n_tiles;
+        s += static_cast<Key>(1) << (3 * (kLevels - level));
+    }
+    return CSTONE_OK;
+}
+
+// focus == nullptr: the plain g1; else g1^LE of the focus
 int launch_rebalance(const Key* K, const u32* N, long long nl, u32 ncrit, Key* Kout, long long cap, long long* nl_out,
-                     int* changed, void* ws, cudaStream_t st) {
+                     int* changed, void* ws, cudaStream_t st, const FocusParams* focus = nullptr) {
     RebalanceLayout l = rebalance_layout(ws, nl);
     CST_CUDA(cudaMemsetAsync(ws, 0, sizeof(WsHeader), st));
     CST_CUDA(cudaMemsetAsync(l.st, 0, sizeof(RebalanceState), st));
-    rebalance_ops_kernel<<<l.ntiles, kThreads, 0, st>>>(K, N, static_cast<u32>(nl), ncrit, l.O, l.tile_sums, l.st);
-    CST_LAUNCHED("rebalance_ops_kernel");
+    if (focus) {
+        focus_ops_kernel<<<l.ntiles, kThreads, 0, st>>>(K, N, static_cast<u32>(nl), ncrit, *focus,
+                                                        hilbert_decode_table(), l.O, l.tile_sums, l.st);
+        CST_LAUNCHED("focus_ops_kernel");
+    } else {
+        rebalance_ops_kernel<<<l.ntiles, kThreads, 0, st>>>(K, N, static_cast<u32>(nl), ncrit, l.O, l.tile_sums,
+                                                            l.st);
+        CST_LAUNCHED("rebalance_ops_kernel");
+    }
     rebalance_scan_kernel<<<1, 1024, 0, st>>>(l.tile_sums, l.ntiles, l.st);
     CST_LAUNCHED("rebalance_scan_kernel");
     rebalance_scatter_kernel<<<l.ntiles, kThreads, 0, st>>>(K, l.O, static_cast<u32>(nl), l.tile_sums, Kout,
@@ -267,6 +434,33 @@ int CSTONE_FN(rebalance)(const CST_KEY_C* leaves, const uint32_t* counts, int64_
     const int rc = CST_NS::launch_rebalance(reinterpret_cast<const CST_NS::Key*>(leaves), counts, n_leaves, ncrit,
                                             reinterpret_cast<CST_NS::Key*>(leaves_out), leaf_cap, &nl, &ch, ws,
                                             cst::as_stream(stream));
+    *n_leaves_out = nl;
+    *changed = ch;
+    return rc;
+}
+
+int CSTONE_FN(rebalance_focus)(const CST_KEY_C* leaves, const uint32_t* counts, int64_t n_leaves, uint32_t ncrit,
+                               CST_KEY_C f_start, CST_KEY_C f_end, double theta, int curve, CST_KEY_C* leaves_out,
+                               int64_t leaf_cap, int64_t* n_leaves_out, int32_t* changed, void* ws, size_t ws_bytes,
+                               void* stream) {
+    if (n_leaves < 1 || n_leaves > CSTONE_MAX_LEAVES || leaf_cap < 1 || leaf_cap > CSTONE_MAX_LEAVES || !leaves ||
+        !counts || !leaves_out || !n_leaves_out || !changed || leaves == leaves_out || !(theta > 0.0) ||
+        (curve != CSTONE_MORTON && curve != CSTONE_HILBERT) || f_end > CST_NS::kKeyEnd || f_start > f_end)
+        return cst::fail(CSTONE_ERR_INVALID_ARG, CST_STR(CSTONE_FN(rebalance_focus)) ": bad argument");
+    if (int rc = cst::check_ws(ws, ws_bytes, CST_NS::rebalance_ws_bytes(n_leaves),
+                               CST_STR(CSTONE_FN(rebalance_focus))))
+        return rc;
+    CST_NS::FocusParams fp;
+    if (int rc = CST_NS::focus_tiles(f_start, f_end, fp)) return rc;
+    fp.f_start = f_start;
+    fp.f_end = f_end;
+    fp.theta = theta;
+    fp.curve = curve;
+    long long nl = 0;
+    int ch = 0;
+    const int rc = CST_NS::launch_rebalance(reinterpret_cast<const CST_NS::Key*>(leaves), counts, n_leaves, ncrit,
+                                            reinterpret_cast<CST_NS::Key*>(leaves_out), leaf_cap, &nl, &ch, ws,
+                                            cst::as_stream(stream), &fp);
     *n_leaves_out = nl;
     *changed = ch;
     return rc;
