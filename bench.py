@@ -45,6 +45,7 @@ def parse():
     p.add_argument("--ts-steps", type=int, default=100)
     p.add_argument("--no-table1", action="store_true")
     p.add_argument("--no-keys30", action="store_true")
+    p.add_argument("--no-focus", action="store_true")
     return p.parse_args()
 
 
@@ -284,6 +285,8 @@ def run_ours(args, rank, world, local):
                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}
 
     extra = {}
+    if rank == 0 and not args.no_focus:
+        extra["focused_tree"] = measure_focus(b, n_leaves)
     if rank == 0 and not args.no_keys30:
         extra["keys30_same_workload"] = measure_keys30(X, Y, Z, M, K=max(3, min(K, 10)))
     if rank == 0 and not args.no_batched:
@@ -326,6 +329,39 @@ def run_ours(args, rank, world, local):
         dist.barrier()
         dist.destroy_process_group()
     return line
+
+
+def measure_focus(b, n_leaves: int, reps: int = 5):
+    """The locally essential tree of Sec. 7 on the benchmark workload: focus on the key range of the
+    5th of 8 equal-count domains (the domain an 8-rank decomposition gives rank 4), minimum-distance
+    MAC with theta 0.5, warm-started from the balanced tree of all particles; f and g^LE per pass."""
+    import torch
+
+    import paper_2307_06345_gb300 as cs
+    from paper_2307_06345_gb300 import distributed as D
+
+    Kg = b.leaves[: n_leaves + 1].clone()
+    N = torch.empty(n_leaves, dtype=torch.int32, device=Kg.device)
+    cs.cstone_leaf_counts(b.sorted_keys, Kg, n_leaves, N)
+    cuts = D.decompose(N, 8)
+    f = [int(v) for v in Kg[torch.tensor([cuts[4], cuts[5]], device=Kg.device)].cpu().tolist()]
+    f = [v + (1 << 64) if v < 0 else v for v in f]
+    ws = cs.Workspace(Kg.device)
+    out = cs.build_focus_leaves(b.sorted_keys, NCRIT, f[0], f[1], 0.5, cs.HILBERT, warm_leaves=Kg, ws=ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ts = []
+    for _ in range(reps):
+        e0.record()
+        out = cs.build_focus_leaves(b.sorted_keys, NCRIT, f[0], f[1], 0.5, cs.HILBERT, warm_leaves=Kg, ws=ws)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    K, Nf, passes = out
+    inside = int(N[cuts[4]: cuts[5]].sum().item())
+    return {"focus_keys": f, "theta": 0.5, "ncrit": NCRIT, "ms": sorted(ts)[len(ts) // 2], "passes": passes,
+            "n_leaves_focused": K.numel() - 1, "n_leaves_global": n_leaves, "particles_in_focus": inside,
+            "start": "balanced tree of all particles"}
 
 
 def measure_keys30(X, Y, Z, M, K: int = 10):
