@@ -106,13 +106,12 @@ CSTONE_API int cstone_keys(const double* x, const double* y, const double* z, in
 
 /* ------------------------------------------------------------------------------------------
  * Radix sort_by_key of the particle keys with the identity permutation as values (Sec. 4;
- * Table 1 caption). Stable: equal keys keep ascending input index. LSD, one sweep per 8-bit
- * digit with decoupled look-back between tiles.
+ * Table 1 caption). Stable: equal keys keep ascending input index. LSD, 8-bit digits; every pass
+ * counts the digits of every tile, scans the counts and scatters each tile's digit runs.
  *   keys_in   [n] uint64 input keys (may alias keys_out).
  *   keys_out  [n] uint64 sorted keys P.
  *   perm      [n] uint32 output: keys_out[j] = keys_in[perm[j]].
- * Asynchronous; a look-back timeout is recorded in the workspace header
- * (cstone_workspace_status).
+ * Asynchronous; no device wait is involved.
  * ------------------------------------------------------------------------------------------ */
 CSTONE_API int cstone_sort_workspace_size(int64_t n, size_t* bytes);
 CSTONE_API int cstone_sort(const uint64_t* keys_in, uint64_t* keys_out, uint32_t* perm, int64_t n, void* ws, size_t ws_bytes,
@@ -130,8 +129,6 @@ CSTONE_API int cstone_sort(const uint64_t* keys_in, uint64_t* keys_out, uint32_t
  * make that first call before any stream capture. All calls share the one array, so calls that
  * can overlap on the GPU (other streams, other host threads) race and must be serialised by the
  * caller. Each call clears what has to start at zero; otherwise the array keeps the last call's
- * contents. A look-back timeout, which only a GPU that cannot keep the launched tiles resident
- * could cause, is not reported by this variant: the output is then invalid.
  *   keys_in, keys_out, perm, n, stream: as for cstone_sort. Asynchronous.
  * ------------------------------------------------------------------------------------------ */
 #define CSTONE_SORT_STATIC_MAX_KEYS ((int64_t)1 << 20)
@@ -235,9 +232,9 @@ CSTONE_API int cstone_keys_batched(const double* x, const double* y, const doubl
                                    const int64_t* set_offsets, int32_t n_sets, const double* boxes, int curve,
                                    uint64_t* keys, void* ws, size_t ws_bytes, void* stream);
 
-/* Stable sort of every segment's keys (segments given by seg_offsets), one launch per digit pass
- * for all segments: tiles are aligned to segments and the look-back stops at a segment's first
- * tile. perm holds global input indices. keys_in must not alias keys_out. Asynchronous. */
+/* Stable sort of every segment's keys (segments given by seg_offsets), one set of launches per
+ * digit pass for all segments: tiles are aligned to segments and digits are offset per segment.
+ * perm holds global input indices. keys_in must not alias keys_out. Asynchronous. */
 CSTONE_API int cstone_sort_segmented_workspace_size(int64_t n, int32_t n_segs, size_t* bytes);
 CSTONE_API int cstone_sort_segmented(const uint64_t* keys_in, uint64_t* keys_out, uint32_t* perm, int64_t n,
                                      const int64_t* seg_offsets, int32_t n_segs, void* ws, size_t ws_bytes,

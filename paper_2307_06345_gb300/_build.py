@@ -28,8 +28,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 # knob name in tuning.json -> preprocessor definition
 KNOBS = {("sort", "threads"): "CSTONE_SORT_THREADS", ("sort", "items"): "CSTONE_SORT_ITEMS",
-         ("sort", "min_blocks"): "CSTONE_SORT_MIN_BLOCKS", ("sort", "window"): "CSTONE_SORT_WINDOW",
-         ("leaves", "items"): "CSTONE_LEAVES_ITEMS"}
+         ("sort", "min_blocks"): "CSTONE_SORT_MIN_BLOCKS", ("leaves", "items"): "CSTONE_LEAVES_ITEMS"}
 
 
 def tuned_knobs() -> dict:

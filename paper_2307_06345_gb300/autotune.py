@@ -25,9 +25,8 @@ import torch
 
 from . import _build
 
-SORT_CANDIDATES = [{"threads": 256, "items": i, "min_blocks": b, "window": w}
-                   for i, b in ((10, 4), (12, 4), (14, 3), (16, 3)) for w in (4, 8)]
-SORT_CANDIDATES.append({"threads": 256, "items": 12, "min_blocks": 4, "window": 2})
+SORT_CANDIDATES = [{"threads": 256, "items": i, "min_blocks": b}
+                   for i, b in ((8, 5), (10, 4), (12, 4), (14, 3), (16, 3))]
 LEAVES_CANDIDATES = [{"items": i} for i in (4, 8, 12, 16)]
 
 P = ctypes.c_void_p
@@ -204,7 +203,7 @@ def tune(n_single: int = 1 << 27, reps: int = 5, out: str = _build.TUNING, verbo
     inp = Inputs(dev, n_single)
     tmp = tempfile.mkdtemp(prefix="cstone_tune_")
     jobs = [("sort", c, {"CSTONE_SORT_THREADS": c["threads"], "CSTONE_SORT_ITEMS": c["items"],
-                         "CSTONE_SORT_MIN_BLOCKS": c["min_blocks"], "CSTONE_SORT_WINDOW": c["window"]})
+                         "CSTONE_SORT_MIN_BLOCKS": c["min_blocks"]})
             for c in SORT_CANDIDATES]
     jobs += [("leaves", c, {"CSTONE_LEAVES_ITEMS": c["items"]}) for c in LEAVES_CANDIDATES]
     results = {"sort": [], "leaves": []}

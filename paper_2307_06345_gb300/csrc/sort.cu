@@ -3,18 +3,17 @@
 // records where each particle went). 63-bit keys in 64-bit words take 8 passes of 8-bit digits,
 // 30-bit keys in 32-bit words take 4.
 //
-// One-sweep design: a single upfront pass histograms all 8-bit digits at once, then each
-// digit pass reads a tile of keys (and values), ranks them within the tile with warp-level
-// match, publishes the tile's per-digit counts and resolves its global offsets by decoupled
-// look-back over the preceding tiles (tiles are claimed in order through an atomic counter, so
-// every tile a block waits for is already running), stages the tile in shared memory in digit
-// order and writes each digit's run contiguously. The first pass generates the identity values
-// instead of reading them.
-//
-// Look-back words are 32 bits: 2 flag bits (0 = not ready, 1 = tile aggregate, 2 = inclusive
-// prefix) and a 30-bit count, which bounds n below 2^30. Two look-back regions alternate between
-// passes; every tile clears its row of the other region (written by the previous pass) so that the
-// next pass finds it empty, and only the first region needs a memset per sort.
+// Each digit pass reads a tile of keys (and values), ranks them within the tile (the lanes of a warp
+// holding the same digit are found with one ballot per digit bit, which measured much cheaper than
+// a warp match instruction), stages the tile in shared memory in digit order and writes each
+// digit's run contiguously at the tile's output position for that digit; the first pass generates
+// the identity values instead of reading them. A single upfront pass histograms all digits at once
+// (global digit offsets). Ahead of every pass, a count of every tile's digits and a two-level scan
+// of the counts give each tile its output positions, so no tile waits on another (a decoupled
+// look-back between tiles, measured first, spent a third of the sort's time waiting on
+// predecessors). A segmented sort aligns its tiles to the segments, scans the counts of all tiles
+// at once, and takes a tile's position within its segment as the difference to the segment's
+// first tile, added to the segment's digit offsets.
 #include <mutex>
 
 #include "common.cuh"
@@ -42,17 +41,8 @@ constexpr int kItems = CSTONE_SORT_ITEMS;
 static_assert(kThreads >= 256 && kThreads % 32 == 0, "one thread per digit is needed");
 static_assert(kItems % 2 == 0, "ranks are packed two per register");
 constexpr int kTile = kThreads * kItems;  // keys per tile
-#ifndef CSTONE_SORT_WINDOW
-#define CSTONE_SORT_WINDOW 4
-#endif
-constexpr int kWindow = CSTONE_SORT_WINDOW;  // look-back descriptors loaded per step
-constexpr u32 kFlagAggregate = 1u << 30;
-constexpr u32 kFlagPrefix = 2u << 30;
-constexpr u32 kValueMask = (1u << 30) - 1u;
 
 struct SortCtl {
-    u32 tile_counter[kPasses];
-    u32 pad[56];
     u32 hist[kPasses][kRadix];     // digit counts of all keys, per pass
     u32 offsets[kPasses][kRadix];  // exclusive scan of hist
 };
@@ -93,8 +83,7 @@ __global__ void sort_scan_kernel(SortCtl* ctl) {
 }
 
 // Segmented sorts (many independent key sets stored back to back) use tiles aligned to the
-// segments: every tile holds keys of one segment only, digits are offset per segment, and the
-// look-back of a tile stops at its segment's first tile.
+// segments: every tile holds keys of one segment only, and digits are offset per segment.
 struct SegTiles {
     const u32* n_tiles;      // device scalar: tiles in use
     const u32* tile_seg;     // segment of each tile
@@ -214,45 +203,52 @@ __global__ void seg_scan_kernel(const long long* __restrict__ seg_offsets_in, co
     }
 }
 
+// Lanes of the warp whose value v (9 bits: an 8-bit digit or the marker kRadix) equals this
+// lane's: one ballot per bit.
+__device__ __forceinline__ u32 match_digit(u32 v) {
+    u32 peers = 0xffffffffu;
+#pragma unroll
+    for (int b = 0; b <= kRadixBits; ++b) {
+        const bool bit = (v >> b) & 1u;
+        const u32 bal = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? bal : ~bal;
+    }
+    return peers;
+}
+
 struct PassSmem {
     Key keys[kTile];
     u32 vals[kTile];
     u32 warp_hist[kWarps][kRadix];  // per-warp digit counts, then each warp's first staging slot
     u32 delta[kRadix];              // output position minus staging slot, per digit
     u32 scan_tmp[kWarps];
-    u32 tile;
 };
 
+// One digit pass. tile_pos[tile][d]: for a single-set sort the output position of the tile's
+// first key of digit d; for a segmented sort the keys of digit d in all tiles before this one
+// (over every segment), from which the tile's segment start is subtracted.
 template <bool FIRST, bool SEG>
 __global__ void __launch_bounds__(kThreads, CSTONE_SORT_MIN_BLOCKS)
     sort_pass_kernel(const Key* __restrict__ kin, Key* __restrict__ kout, const u32* __restrict__ vin,
-                     u32* __restrict__ vout, long long n, int pass, SortCtl* ctl, u32* look, u32* look_other,
-                     WsHeader* hdr, SegTiles seg) {
+                     u32* __restrict__ vout, long long n, int pass, const u32* __restrict__ tile_pos,
+                     SegTiles seg) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PassSmem& sm = *reinterpret_cast<PassSmem*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int shift = pass * kRadixBits;
 
     for (int i = tid; i < kWarps * kRadix; i += kThreads) (&sm.warp_hist[0][0])[i] = 0;
-    if (tid == 0) sm.tile = atomicAdd(&ctl->tile_counter[pass], 1u);
     __syncthreads();
-    const u32 tile = sm.tile;
+    const u32 tile = blockIdx.x;
     u32 base, count;  // first key of the tile and keys in it (n < 2^30, so 32-bit offsets)
-    u32 first_tile;
-    const u32* digit_offsets;
     if (SEG) {
         if (tile >= *seg.n_tiles) return;
         base = seg.tile_base[tile];
         count = seg.tile_count[tile];
-        const u32 sg = seg.tile_seg[tile];
-        first_tile = seg.seg_first[sg];
-        digit_offsets = seg.seg_offsets + ((size_t)sg * kPasses + pass) * kRadix;
     } else {
         base = tile * static_cast<u32>(kTile);
         const long long remain = n - (long long)base;
         count = remain < kTile ? static_cast<u32>(remain) : static_cast<u32>(kTile);
-        first_tile = 0;
-        digit_offsets = ctl->offsets[pass];
     }
 
     // ---- load (warp-striped: warp w owns keys base + w*32*kItems + it*32 + lane)
@@ -285,7 +281,7 @@ __global__ void __launch_bounds__(kThreads, CSTONE_SORT_MIN_BLOCKS)
     for (int g0 = 0; g0 < kItems; g0 += kGroup) {
         u32 peers[kGroup], before[kGroup];
 #pragma unroll
-        for (int q = 0; q < kGroup; ++q) peers[q] = __match_any_sync(0xffffffffu, digit_of(g0 + q));
+        for (int q = 0; q < kGroup; ++q) peers[q] = match_digit(digit_of(g0 + q));
 #pragma unroll
         for (int q = 0; q < kGroup; ++q) {
             const u32 d = digit_of(g0 + q);
@@ -309,11 +305,9 @@ __global__ void __launch_bounds__(kThreads, CSTONE_SORT_MIN_BLOCKS)
     const bool owner = tid < kRadix;
     const int d = owner ? tid : 0;
     u32 total = 0, incl = 0;
-    u32* my_look = look + (size_t)tile * kRadix + d;
     if (owner) {
 #pragma unroll
         for (int w = 0; w < kWarps; ++w) total += sm.warp_hist[w][d];
-        st_volatile(my_look, (tile == first_tile ? kFlagPrefix : kFlagAggregate) | total);
         // block-wide exclusive scan of the totals over digits -> staging slots
         incl = total;
         for (int s = 1; s < 32; s <<= 1) {
@@ -336,42 +330,15 @@ __global__ void __launch_bounds__(kThreads, CSTONE_SORT_MIN_BLOCKS)
             run += c;
         }
 
-        // decoupled look-back over preceding tiles for digit d, kWindow descriptors per step
-        u32 excl = 0;
-        if (tile > first_tile) {
-            long long j = (long long)tile - 1;
-            long long polls = 0;
-            for (;;) {
-                u32 v[kWindow];
-#pragma unroll
-                for (int w = 0; w < kWindow; ++w)
-                    v[w] = (j - w >= (long long)first_tile) ? ld_volatile(look + (size_t)(j - w) * kRadix + d)
-                                                            : kFlagPrefix;
-                int used = 0;
-                bool done = false;
-#pragma unroll
-                for (int w = 0; w < kWindow; ++w) {
-                    if (done || used < w) continue;
-                    const u32 flag = v[w] & ~kValueMask;
-                    if (flag == 0u) continue;  // not ready: stop consuming here
-                    excl += v[w] & kValueMask;
-                    used = w + 1;
-                    if (flag == kFlagPrefix) done = true;
-                }
-                if (done) break;
-                j -= used;
-                if (used < kWindow) {
-                    __nanosleep(32);
-                    if (++polls > kSpinLimit || ld_volatile(&hdr->err) != 0u) {
-                        raise_error(hdr, CSTONE_ERR_TIMEOUT, 0x50000u + (u32)pass);
-                        break;
-                    }
-                }
-            }
-            st_volatile(my_look, kFlagPrefix | ((excl + total) & kValueMask));
-        }
-        sm.delta[d] = digit_offsets[d] + excl - start;  // output position minus staging slot
-        look_other[(size_t)tile * kRadix + d] = 0u;  // clear the previous pass's row for the next pass
+        // output position of the tile's first key of digit d, minus its staging slot
+        if (SEG) {
+            const u32 sg = seg.tile_seg[tile];
+            const u32 first_tile = seg.seg_first[sg];
+            const u32 seg_digit_offset = seg.seg_offsets[((size_t)sg * kPasses + pass) * kRadix + d];
+            sm.delta[d] = seg_digit_offset + (tile_pos[(size_t)tile * kRadix + d] -
+                                              tile_pos[(size_t)first_tile * kRadix + d]) - start;
+        } else
+            sm.delta[d] = tile_pos[(size_t)tile * kRadix + d] - start;
     }
     __syncthreads();
 
@@ -397,9 +364,117 @@ __global__ void __launch_bounds__(kThreads, CSTONE_SORT_MIN_BLOCKS)
     }
 }
 
+// ---- output offsets of every tile, ahead of a pass (single-set sorts). A tile's output position
+// for digit d is the digit's global offset plus the keys of digit d in all earlier tiles; counting
+// every tile first and scanning the counts replaces the look-back (which measured a third of the
+// sort's time: tiles in flight wait on their predecessors' prefixes).
+constexpr int kChunkTiles = 32;  // tiles per chunk of the two-level scan
+
+// Digit counts of every tile of the pass (the tile partition of sort_pass_kernel; unused tiles of a
+// segmented sort count nothing).
+template <bool SEG>
+__global__ void __launch_bounds__(kThreads) tile_count_kernel(const Key* __restrict__ kin, long long n, int shift,
+                                                              u32* __restrict__ counts, SegTiles seg) {
+    __shared__ u32 wh[kWarps][kRadix];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    for (int i = tid; i < kWarps * kRadix; i += kThreads) (&wh[0][0])[i] = 0;
+    __syncthreads();
+    long long base;
+    u32 count;
+    if (SEG) {
+        const bool used = blockIdx.x < *seg.n_tiles;
+        base = used ? seg.tile_base[blockIdx.x] : 0;
+        count = used ? seg.tile_count[blockIdx.x] : 0u;
+    } else {
+        base = (long long)blockIdx.x * kTile;
+        const long long remain = n - base;
+        count = remain < kTile ? static_cast<u32>(remain) : static_cast<u32>(kTile);
+    }
+    const Key* tkeys = kin + base;
+    const u32 woff = static_cast<u32>(warp * 32 * kItems + (tid & 31));
+    Key kk[kItems];
+#pragma unroll
+    for (int it = 0; it < kItems; ++it) {
+        const u32 o = woff + it * 32;
+        kk[it] = o < count ? __ldcs(tkeys + o) : ~static_cast<Key>(0);
+    }
+#pragma unroll
+    for (int it = 0; it < kItems; ++it) {
+        const u32 o = woff + it * 32;
+        if (o < count) atomicAdd(&wh[warp][static_cast<u32>((kk[it] >> shift) & (kRadix - 1))], 1u);
+    }
+    __syncthreads();
+    for (int dd = tid; dd < kRadix; dd += kThreads) {
+        u32 c = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) c += wh[w][dd];
+        counts[(size_t)blockIdx.x * kRadix + dd] = c;
+    }
+}
+
+// Per chunk of kChunkTiles tiles: the keys of every digit (thread = digit).
+__global__ void __launch_bounds__(kRadix) chunk_sum_kernel(const u32* __restrict__ counts, long long tiles,
+                                                           u32* __restrict__ chunk) {
+    const int d = threadIdx.x;
+    const long long t0 = (long long)blockIdx.x * kChunkTiles;
+    const long long t1 = t0 + kChunkTiles < tiles ? t0 + kChunkTiles : tiles;
+    u32 sum = 0;
+#pragma unroll 8
+    for (long long t = t0; t < t1; ++t) sum += counts[t * kRadix + d];
+    chunk[(size_t)d * gridDim.x + blockIdx.x] = sum;  // digit-major
+}
+
+// Exclusive scan of the chunk sums over the chunks, per digit, from the digit's global offset (0
+// when digit_offsets is NULL): one block per digit over its contiguous row (in place).
+__global__ void __launch_bounds__(1024) chunk_scan_kernel(u32* __restrict__ chunk, long long nchunks,
+                                                          const u32* __restrict__ digit_offsets) {
+    __shared__ u32 s_warp[32];
+    u32* row = chunk + (size_t)blockIdx.x * nchunks;
+    const long long per = (nchunks + 1023) / 1024;
+    const long long c0 = threadIdx.x * per, c1 = c0 + per < nchunks ? c0 + per : nchunks;
+    u32 sum = 0;
+    for (long long c = c0; c < c1; ++c) sum += row[c];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    u32 incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const u32 t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    u32 before = 0;
+    for (int w = 0; w < warp; ++w) before += s_warp[w];
+    u32 run = (digit_offsets ? digit_offsets[blockIdx.x] : 0u) + before + incl - sum;
+    for (long long c = c0; c < c1; ++c) {
+        const u32 v = row[c];
+        row[c] = run;
+        run += v;
+    }
+}
+
+// Output position of every tile's first key of every digit (thread = digit).
+__global__ void __launch_bounds__(kRadix) tile_offsets_kernel(const u32* __restrict__ counts, long long tiles,
+                                                              const u32* __restrict__ chunk,
+                                                              u32* __restrict__ offsets) {
+    const int d = threadIdx.x;
+    const long long t0 = (long long)blockIdx.x * kChunkTiles;
+    const long long t1 = t0 + kChunkTiles < tiles ? t0 + kChunkTiles : tiles;
+    u32 run = chunk[(size_t)d * gridDim.x + blockIdx.x];
+    u32 v[kChunkTiles];
+#pragma unroll
+    for (int k = 0; k < kChunkTiles; ++k) v[k] = t0 + k < t1 ? counts[(t0 + k) * kRadix + d] : 0u;
+#pragma unroll
+    for (int k = 0; k < kChunkTiles; ++k) {
+        if (t0 + k < t1) offsets[(t0 + k) * kRadix + d] = run;
+        run += v[k];
+    }
+}
+
 struct SortLayout {
     SortCtl* ctl;
-    u32* look[2];
+    u32* look[2];  // per-tile digit counts and output offsets
+    u32* chunk;    // per-chunk digit sums, then their scan
     Key* keys_alt;
     u32* vals_alt;
     size_t bytes;
@@ -413,6 +488,7 @@ SortLayout sort_layout(void* ws, long long n) {
     l.ctl = c.take<SortCtl>(1);
     l.look[0] = c.take<u32>((size_t)l.tiles * kRadix);
     l.look[1] = c.take<u32>((size_t)l.tiles * kRadix);
+    l.chunk = c.take<u32>((size_t)((l.tiles + kChunkTiles - 1) / kChunkTiles) * kRadix);
     l.keys_alt = c.take<Key>((size_t)n);
     l.vals_alt = c.take<u32>((size_t)n);
     l.bytes = c.size();
@@ -433,6 +509,7 @@ constexpr size_t round256(size_t b) { return (b + 255) / 256 * 256; }
 constexpr long long kStaticKeys = CSTONE_SORT_STATIC_MAX_KEYS;
 constexpr size_t kStaticTiles = static_cast<size_t>((kStaticKeys + kTile - 1) / kTile);
 constexpr size_t kStaticBytes = sizeof(WsHeader) + round256(sizeof(SortCtl)) + 2 * round256(kStaticTiles * kRadix * 4) +
+                                round256((kStaticTiles + kChunkTiles - 1) / kChunkTiles * kRadix * 4) +
                                 round256(static_cast<size_t>(kStaticKeys) * 8) +
                                 round256(static_cast<size_t>(kStaticKeys) * 4);
 
@@ -463,27 +540,36 @@ int static_sort_scratch(void** out) {
 #endif
 
 // The digit passes (an even number). Ping-pong: odd passes (1-based) write the workspace buffers,
-// even passes the output, so the last pass lands in keys_out / perm.
+// even passes the output, so the last pass lands in keys_out / perm. Ahead of each pass: tile
+// counts (counts), chunk sums and their scan (chunk), and the per-tile positions (tile_pos).
 template <bool SEG>
-int run_passes(const Key* keys_in, Key* keys_out, u32* perm, long long n, long long tiles, SortCtl* ctl, u32* const look2[2],
-               Key* keys_alt, u32* vals_alt, WsHeader* hdr, SegTiles seg, cudaStream_t st) {
+int run_passes(const Key* keys_in, Key* keys_out, u32* perm, long long n, long long tiles, const SortCtl* ctl,
+               u32* counts, u32* chunk, u32* tile_pos, Key* keys_alt, u32* vals_alt, SegTiles seg, cudaStream_t st) {
     const int smem = static_cast<int>(sizeof(PassSmem));
     CST_CUDA(cudaFuncSetAttribute(sort_pass_kernel<true, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     CST_CUDA(cudaFuncSetAttribute(sort_pass_kernel<false, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     const Key* ksrc = keys_in;
     const u32* vsrc = nullptr;
+    const long long nchunks = (tiles + kChunkTiles - 1) / kChunkTiles;
     static_assert(kPasses % 2 == 0, "the last pass must write the output buffers");
     for (int p = 0; p < kPasses; ++p) {
         Key* kdst = (p % 2 == 0) ? keys_alt : keys_out;
         u32* vdst = (p % 2 == 0) ? vals_alt : perm;
-        u32* look = look2[p & 1];
-        u32* other = look2[(p + 1) & 1];
+        tile_count_kernel<SEG><<<(unsigned)tiles, kThreads, 0, st>>>(ksrc, n, p * kRadixBits, counts, seg);
+        CST_LAUNCHED("tile_count_kernel");
+        chunk_sum_kernel<<<(unsigned)nchunks, kRadix, 0, st>>>(counts, tiles, chunk);
+        CST_LAUNCHED("chunk_sum_kernel");
+        // a segmented sort scans all tiles from 0; each tile subtracts its segment's first tile
+        chunk_scan_kernel<<<kRadix, 1024, 0, st>>>(chunk, nchunks, SEG ? nullptr : ctl->offsets[p]);
+        CST_LAUNCHED("chunk_scan_kernel");
+        tile_offsets_kernel<<<(unsigned)nchunks, kRadix, 0, st>>>(counts, tiles, chunk, tile_pos);
+        CST_LAUNCHED("tile_offsets_kernel");
         if (p == 0)
-            sort_pass_kernel<true, SEG><<<(unsigned)tiles, kThreads, smem, st>>>(ksrc, kdst, vsrc, vdst, n, p, ctl, look,
-                                                                                 other, hdr, seg);
+            sort_pass_kernel<true, SEG><<<(unsigned)tiles, kThreads, smem, st>>>(ksrc, kdst, vsrc, vdst, n, p,
+                                                                                 tile_pos, seg);
         else
-            sort_pass_kernel<false, SEG><<<(unsigned)tiles, kThreads, smem, st>>>(ksrc, kdst, vsrc, vdst, n, p, ctl,
-                                                                                  look, other, hdr, seg);
+            sort_pass_kernel<false, SEG><<<(unsigned)tiles, kThreads, smem, st>>>(ksrc, kdst, vsrc, vdst, n, p,
+                                                                                  tile_pos, seg);
         CST_LAUNCHED("sort_pass_kernel");
         ksrc = kdst;
         vsrc = vdst;
@@ -497,7 +583,6 @@ int launch_sort(const Key* keys_in, Key* keys_out, u32* perm, long long n, void*
     CST_CUDA(cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st));
     if (n == 0) return CSTONE_OK;
     CST_CUDA(cudaMemsetAsync(l.ctl, 0, sizeof(SortCtl), st));
-    CST_CUDA(cudaMemsetAsync(l.look[0], 0, (size_t)l.tiles * kRadix * sizeof(u32), st));
 
     long long want = (n + kThreads - 1) / kThreads;
     int hgrid = static_cast<int>(want < (long long)sm_count() * 4 ? want : (long long)sm_count() * 4);
@@ -506,8 +591,8 @@ int launch_sort(const Key* keys_in, Key* keys_out, u32* perm, long long n, void*
     sort_scan_kernel<<<1, 32 * kPasses, 0, st>>>(l.ctl);
     CST_LAUNCHED("sort_scan_kernel");
 
-    return run_passes<false>(keys_in, keys_out, perm, n, l.tiles, l.ctl, l.look, l.keys_alt, l.vals_alt, hdr, SegTiles{},
-                             st);
+    return run_passes<false>(keys_in, keys_out, perm, n, l.tiles, l.ctl, l.look[0], l.chunk, l.look[1], l.keys_alt,
+                             l.vals_alt, SegTiles{}, st);
 }
 
 // ---------------------------------------------------------------- segmented sort
@@ -515,7 +600,8 @@ namespace {
 struct SegLayout {
     SortCtl* ctl;
     SegBuild b;
-    u32* look[2];
+    u32* look[2];  // per-tile digit counts and positions
+    u32* chunk;
     Key* keys_alt;
     u32* vals_alt;
     size_t bytes;
@@ -536,6 +622,7 @@ SegLayout seg_layout(void* ws, long long n, int n_segs) {
     l.b.seg_offsets = c.take<u32>((size_t)n_segs * kPasses * kRadix);
     l.look[0] = c.take<u32>((size_t)l.max_tiles * kRadix);
     l.look[1] = c.take<u32>((size_t)l.max_tiles * kRadix);
+    l.chunk = c.take<u32>((size_t)((l.max_tiles + kChunkTiles - 1) / kChunkTiles) * kRadix);
     l.keys_alt = c.take<Key>((size_t)n);
     l.vals_alt = c.take<u32>((size_t)n);
     l.bytes = c.size();
@@ -554,7 +641,6 @@ int launch_sort_segmented(const Key* keys_in, Key* keys_out, u32* perm, long lon
     if (n == 0) return CSTONE_OK;
     CST_CUDA(cudaMemsetAsync(l.ctl, 0, sizeof(SortCtl), st));
     CST_CUDA(cudaMemsetAsync(l.b.seg_hist, 0, (size_t)n_segs * kPasses * kRadix * sizeof(u32), st));
-    CST_CUDA(cudaMemsetAsync(l.look[0], 0, (size_t)l.max_tiles * kRadix * sizeof(u32), st));
     seg_setup_kernel<<<1, 1024, 0, st>>>(seg_offsets, n_segs, l.b);
     CST_LAUNCHED("seg_setup_kernel");
     const long long want = (l.max_tiles + kThreads - 1) / kThreads;
@@ -566,7 +652,8 @@ int launch_sort_segmented(const Key* keys_in, Key* keys_out, u32* perm, long lon
     CST_LAUNCHED("seg_hist_kernel");
     seg_scan_kernel<<<(unsigned)n_segs, 32 * kPasses, 0, st>>>(seg_offsets, l.b.seg_hist, l.b.seg_offsets);
     CST_LAUNCHED("seg_scan_kernel");
-    return run_passes<true>(keys_in, keys_out, perm, n, l.max_tiles, l.ctl, l.look, l.keys_alt, l.vals_alt, hdr, view, st);
+    return run_passes<true>(keys_in, keys_out, perm, n, l.max_tiles, l.ctl, l.look[0], l.chunk, l.look[1], l.keys_alt,
+                            l.vals_alt, view, st);
 }
 
 }  // namespace CST_NS
