@@ -138,11 +138,12 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-# DRAM bytes per key of one sort (upfront histogram + 8 passes), measured with ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum over the sort's launches) on 2^24 keys of the same
-# workload and scaled by the key count (the passes stream, so traffic grows with n):
+# DRAM bytes per particle of the sort (histogram, per-pass tile counts and scans, 8 passes) and of
+# the multipole upsweep (pack, leaf sums, levels), measured with ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum over the phase's launches) on 2^24 particles of the same workload and
+# scaled by the particle count (both phases stream or gather per particle, so traffic grows with n):
 # profiles/kernels_clumps_2p24_full.md.
-SORT_DRAM_BYTES_PER_KEY = 177.9
+MEASURED_DRAM_BYTES_PER_PARTICLE = {"sort": 243.6, "multipoles": 199.9}
 
 
 def algorithmic_bytes(n: int, n_leaves: int, iter_leaves: int, n_nodes: int):
@@ -317,8 +318,14 @@ def run_ours(args, rank, world, local):
             "step_hbm_frac": step_bytes / (ms_per_step * 1e-3) / 1e9 / hbm,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "peak_source": peak_kind,
-                         "traffic": SORT_DRAM_BYTES_PER_KEY * n if dom == "sort" else None,
+                         "traffic": (MEASURED_DRAM_BYTES_PER_PARTICLE[dom] * n
+                                     if dom in MEASURED_DRAM_BYTES_PER_PARTICLE else None),
                          "algorithmic_bytes_per_launch": algo[dom]},
+            "roofline_phases": {p: {"achieved_gbs": algo[p] / (phase_ms[p] * 1e-3) / 1e9,
+                                    "frac": algo[p] / (phase_ms[p] * 1e-3) / 1e9 / hbm,
+                                    "traffic": (MEASURED_DRAM_BYTES_PER_PARTICLE[p] * n
+                                                if p in MEASURED_DRAM_BYTES_PER_PARTICLE else None)}
+                                for p in phases},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clocks.summary(),
