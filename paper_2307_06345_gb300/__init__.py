@@ -707,8 +707,9 @@ class GraphTimeStepper:
     the device, and the link and count phases run on capacities with the exact counts read on the
     device, so no phase needs the host between the launches. After each replay the outcome is read
     back (two synchronisations per step). The first rebuild (cold, from the roots) runs without the
-    graph and sets the capacity to twice its element count; the warm rebuild is captured on its
-    first use. A capacity overflow doubles the capacity, drops the graph and rebuilds cold."""
+    graph, with the synchronous leaf loop, and sets the capacity to twice its element count; the
+    warm rebuild is captured on its first use. A capacity overflow doubles the capacity, drops the
+    graph and rebuilds cold."""
 
     def __init__(self, x, y, z, set_offsets, curve: int = HILBERT, ncrit: int = 64, pad: float = 0.1,
                  elem_cap: int | None = None, max_iters: int = 64):
@@ -784,15 +785,26 @@ class GraphTimeStepper:
                 "node_offsets_host": node_offsets}
 
     def _cold(self):
+        # From the roots with the synchronous leaf loop: a capacity overflow is reported before the
+        # link and count phases run, and only the leaf loop is repeated at the grown capacity.
+        w = self.ws
+        cstone_keys_batched(self.x, self.y, self.z, self.set_offsets, self.boxes, self.curve, self.keys, w["keys"])
+        cstone_sort_segmented(self.keys, self.sorted_keys, self.perm, self.set_offsets, w["sort"])
         while True:
-            self._launch(False)
             try:
-                out = self._result()
+                cstone_build_leaves_batched(self.sorted_keys, self.set_offsets, self.ncrit, self.elements,
+                                            self.element_offsets, self.counts, self.offsets, 0, self.max_iters,
+                                            w["leaves"])
                 break
             except CstoneError as e:
                 if e.status != ERR_CAPACITY:
                     raise
                 self._alloc(max(2 * self.elem_cap, getattr(e, "required", 0) + 1024))
+        cstone_link_tree_batched(self.elements, self.elem_cap, self.element_offsets, self.node_cap, self.NK, self.CO,
+                                 self.LO, self.l2n, w["link"])
+        cstone_upsweep_counts_batched(self.counts, self.elem_cap, self.l2n, self.CO, self.LO, self.n_sets,
+                                      self.node_counts, w["counts"])
+        out = self._result()
         ne = out["n_elements"]
         tight = 2 * ne + 64 * self.n_sets + 4096
         if not self.fixed_cap and tight < self.elem_cap:

@@ -84,21 +84,23 @@ __device__ __forceinline__ u32 lower_bound_in(const Key* __restrict__ P, u32 lo,
 // Eq. (g1) for element e of ne. The end key 8^L of a set is kept. A leaf splits when N > ncrit
 // (a single key at depth L stays); the octants 1..7 of a parent whose 8 children are consecutive
 // leaves of one set holding <= ncrit in total are merged away (octant 0 keeps its key, which is
-// the parent's); anything else is kept.
+// the parent's); anything else is kept. K, pos and set were written by other blocks in the
+// previous pass, so they are read through L2 (__ldcg), never through a read-only cache.
 template <bool BATCH>
-__device__ __forceinline__ u32 decide(const Key* __restrict__ K, const u32* __restrict__ pos,
-                                      const u32* __restrict__ set, u32 e, u32 ne, u32 ncrit) {
-    const Key ke = K[e];
+__device__ __forceinline__ u32 decide(const Key* K, const u32* pos, const u32* set, u32 e, u32 ne, u32 ncrit) {
+    const Key ke = __ldcg(K + e);
     if (ke == kKeyEnd) return 1u;
-    const Key delta = K[e + 1] - ke;
-    const u32 cnt = pos[e + 1] - pos[e];
+    const Key delta = __ldcg(K + e + 1) - ke;
+    const u32 cnt = __ldcg(pos + e + 1) - __ldcg(pos + e);
     if (cnt > ncrit && delta > 1ULL) return 8u;
     if (delta < kKeyEnd) {
         const u32 j = static_cast<u32>((ke >> key_ffs(delta)) & 7u);
         if (j >= 1u && j <= e && e - j + 8u < ne) {
             const u32 first = e - j;
-            if (!BATCH || (set[first] == set[e] && set[first + 8] == set[e]))
-                if (K[first] + static_cast<Key>(8) * delta == K[first + 8] && pos[first + 8] - pos[first] <= ncrit) return 0u;
+            if (!BATCH || (__ldcg(set + first) == __ldcg(set + e) && __ldcg(set + first + 8) == __ldcg(set + e)))
+                if (__ldcg(K + first) + static_cast<Key>(8) * delta == __ldcg(K + first + 8) &&
+                    __ldcg(pos + first + 8) - __ldcg(pos + first) <= ncrit)
+                    return 0u;
         }
     }
     return 1u;
@@ -358,6 +360,10 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const Key* __rest
                 const Key ke = K[e];
                 const Key delta = K[e + 1] - ke;
                 const u32 lo = pos[e], cnt_all = pos[e + 1] - lo;
+                if (lo > n || cnt_all > n - lo) {  // self-check: a particle range outside P is never read
+                    if (lane == 0) raise_error(hdr, CSTONE_ERR_INVALID_ARG, 0x70000u);
+                    continue;
+                }
                 const int child_shift = key_ffs(delta) - 3;
                 u32 below = 0;  // lane c in 1..7: particles whose child digit is < c
                 if (cnt_all <= kLinearSplit) {

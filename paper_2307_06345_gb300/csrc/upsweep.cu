@@ -35,13 +35,24 @@ __global__ void __launch_bounds__(kThreads) upsweep_counts_kernel(const u32* __r
     __shared__ int s_lo[kNumLevels + 1];
     if (threadIdx.x <= kNumLevels) s_lo[threadIdx.x] = level_offsets[threadIdx.x];
     const u32 gtid = blockIdx.x * kThreads + threadIdx.x, gthreads = gridDim.x * kThreads;
-    for (u32 i = gtid; i < nl; i += gthreads) node_counts[leaf_to_node[i]] = leaf_counts[i];
+    const u32 n_nodes = nl + (nl - 1) / 7;  // an index outside is recorded in the error word and skipped
+    for (u32 i = gtid; i < nl; i += gthreads) {
+        const int v = leaf_to_node[i];
+        if (v >= 0 && static_cast<u32>(v) < n_nodes)
+            node_counts[v] = leaf_counts[i];
+        else
+            raise_error(hdr, CSTONE_ERR_INVALID_ARG, 0x71000u);
+    }
     grid_barrier(bar, hdr);
     for (int l = kLevels - 1; l >= 0; --l) {
         if (s_lo[l + 2] == s_lo[l + 1]) continue;  // no internal node at level l
-        for (u32 x = s_lo[l] + gtid; x < static_cast<u32>(s_lo[l + 1]); x += gthreads) {
+        for (u32 x = s_lo[l] + gtid; x < static_cast<u32>(s_lo[l + 1]) && x < n_nodes; x += gthreads) {
             const int c = child[x];
             if (c == 0) continue;
+            if (c < 0 || static_cast<u32>(c) + 8u > n_nodes) {
+                raise_error(hdr, CSTONE_ERR_INVALID_ARG, 0x73000u);
+                continue;
+            }
             u32 sum = 0;
 #pragma unroll
             for (int k = 0; k < 8; ++k) sum += __ldcg(node_counts + c + k);
@@ -63,12 +74,20 @@ __global__ void __launch_bounds__(kThreads) upsweep_counts_batched_kernel(
     __shared__ u32 s_prefix[kMaxBatchSets + 1];
     __shared__ u32 s_warp[kThreads / 32];
     const u32 gtid = blockIdx.x * kThreads + threadIdx.x, gthreads = gridDim.x * kThreads;
+    constexpr int kRow = kNumLevels + 1;
+    // nodes of all sets (the node arrays hold at least this many); an index outside is recorded
+    // in the error word and skipped
+    const u32 n_nodes = static_cast<u32>(level_offsets[n_sets * kRow - 1]);
     for (u32 e = gtid; e < n_elements; e += gthreads) {
         const int v = leaf_to_node[e];
-        if (v >= 0) node_counts[v] = elem_counts[e];
+        if (v >= 0) {
+            if (static_cast<u32>(v) < n_nodes)
+                node_counts[v] = elem_counts[e];
+            else
+                raise_error(hdr, CSTONE_ERR_INVALID_ARG, 0x71000u);
+        }
     }
     grid_barrier(bar, hdr);
-    constexpr int kRow = kNumLevels + 1;
     for (int l = kLevels - 1; l >= 0; --l) {
         // exclusive prefix over sets of the number of level-l nodes that can have children
         const int per = (n_sets + kThreads - 1) / kThreads;
@@ -111,8 +130,16 @@ __global__ void __launch_bounds__(kThreads) upsweep_counts_batched_kernel(
             }
             while (a + 1 < n_sets && s_prefix[a + 1] <= k) ++a;
             const u32 x = static_cast<u32>(level_offsets[a * kRow + l]) + (k - s_prefix[a]);
+            if (x >= n_nodes) {
+                raise_error(hdr, CSTONE_ERR_INVALID_ARG, 0x72000u);
+                continue;
+            }
             const int cc = child[x];
             if (cc == 0) continue;
+            if (cc < 0 || static_cast<u32>(cc) + 8u > n_nodes) {
+                raise_error(hdr, CSTONE_ERR_INVALID_ARG, 0x73000u);
+                continue;
+            }
             u32 sm = 0;
 #pragma unroll
             for (int q = 0; q < 8; ++q) sm += __ldcg(node_counts + cc + q);
