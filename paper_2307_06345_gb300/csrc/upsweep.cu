@@ -284,38 +284,26 @@ __global__ void __launch_bounds__(kThreads) multipole_pack_kernel(const double* 
         __stcs(dst, make_longlong2(r.x, r.y));
         __stcs(dst + 1, make_longlong2(r.z, static_cast<long long>(__float_as_uint(r.m))));
     };
-    const bool vec = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y) | reinterpret_cast<uintptr_t>(z) |
-                       reinterpret_cast<uintptr_t>(m)) & 15u) == 0;
-    u32 done = 0;
-    if (vec) {  // four particles per thread and step, 16-byte loads
-        const u32 quads = n >> 2;
-        for (u32 q = blockIdx.x * kThreads + threadIdx.x; q < quads; q += gridDim.x * kThreads) {
-            const double2 x0 = __ldcs(reinterpret_cast<const double2*>(x) + 2 * q);
-            const double2 x1 = __ldcs(reinterpret_cast<const double2*>(x) + 2 * q + 1);
-            const double2 y0 = __ldcs(reinterpret_cast<const double2*>(y) + 2 * q);
-            const double2 y1 = __ldcs(reinterpret_cast<const double2*>(y) + 2 * q + 1);
-            const double2 z0 = __ldcs(reinterpret_cast<const double2*>(z) + 2 * q);
-            const double2 z1 = __ldcs(reinterpret_cast<const double2*>(z) + 2 * q + 1);
-            const float4 mm = __ldcs(reinterpret_cast<const float4*>(m) + q);
-            pack(x0.x, y0.x, z0.x, mm.x, 4 * q);
-            pack(x0.y, y0.y, z0.y, mm.y, 4 * q + 1);
-            pack(x1.x, y1.x, z1.x, mm.z, 4 * q + 2);
-            pack(x1.y, y1.y, z1.y, mm.w, 4 * q + 3);
-        }
-        done = quads << 2;
-    }
-    for (u32 p = done + blockIdx.x * kThreads + threadIdx.x; p < n; p += gridDim.x * kThreads)
+    // one particle per thread and step: 8-byte coalesced loads, and a warp's two 16-byte stores
+    // cover 1 KB of records contiguously
+    for (u32 p = blockIdx.x * kThreads + threadIdx.x; p < n; p += gridDim.x * kThreads)
         pack(__ldcs(x + p), __ldcs(y + p), __ldcs(z + p), __ldcs(m + p), p);
 }
 
 // Leaf moments. A leaf is handled by a group of 8 lanes, each lane taking every 8th particle and
-// loading its 32-byte record through perm (the one random access of the upsweep; the second pass
-// over the same records hits L2), with the group's partial sums combined by shuffles: the centre
-// of mass from fixed-point differences to the leaf's first particle, then the second moments
-// about it.
+// loading its 32-byte record through perm (the one random access of the upsweep), with the group's
+// partial sums combined by shuffles: the centre of mass from fixed-point differences to the leaf's
+// first particle, then the second moments about it. A lane issues the perm loads of its first
+// kHeld particles together, then their record loads together, and keeps those records in
+// registers for the second pass, so a leaf of up to 8 * kHeld particles costs two round trips to
+// memory instead of two per particle; records beyond that are read again for the second pass.
 constexpr int kLeafThreads = 256;
 constexpr int kGroupLanes = 8;  // lanes per leaf
 constexpr u32 kBigLeaf = 512;   // larger leaves are summed by a whole block
+#ifndef CSTONE_MP_HELD
+#define CSTONE_MP_HELD 4
+#endif
+constexpr int kHeld = CSTONE_MP_HELD;  // records per lane held between the two passes
 
 __device__ __forceinline__ ff group_sum(ff v) {
 #pragma unroll
@@ -326,6 +314,18 @@ __device__ __forceinline__ ff group_sum(ff v) {
         v = ff_add(v, o);
     }
     return v;
+}
+
+__device__ __forceinline__ Record load_record(const Record* rec, u32 p) {
+    const longlong2* src = reinterpret_cast<const longlong2*>(rec + p);
+    const longlong2 a = __ldg(src), b = __ldg(src + 1);
+    Record r;
+    r.x = a.x;
+    r.y = a.y;
+    r.z = b.x;
+    r.m = __uint_as_float(static_cast<u32>(b.y));
+    r.pad = 0u;
+    return r;
 }
 
 __global__ void __launch_bounds__(kLeafThreads) multipole_leaf_kernel(const u32* __restrict__ offsets, u32 nl,
@@ -351,21 +351,42 @@ __global__ void __launch_bounds__(kLeafThreads) multipole_leaf_kernel(const u32*
     }
     u32 trips = (b - a + kGroupLanes - 1) / kGroupLanes;
     for (int o = 16; o > 0; o >>= 1) trips = max(trips, __shfl_xor_sync(0xffffffffu, trips, o));
+    // the held records: all perm loads first, then all record loads
+    u32 p[kHeld];
+#pragma unroll
+    for (int t = 0; t < kHeld; ++t) {
+        const u32 j = a + t * kGroupLanes + gl;
+        p[t] = j < b ? __ldg(perm + j) : 0u;
+    }
+    Record held[kHeld];
+#pragma unroll
+    for (int t = 0; t < kHeld; ++t) {
+        const u32 j = a + t * kGroupLanes + gl;
+        if (j < b) held[t] = load_record(s.rec, p[t]);
+        else held[t] = Record{};
+    }
+    Record r0;  // the leaf's first particle (lane 0 of the group holds it)
+    r0.x = __shfl_sync(0xffffffffu, held[0].x, 0, kGroupLanes);
+    r0.y = __shfl_sync(0xffffffffu, held[0].y, 0, kGroupLanes);
+    r0.z = __shfl_sync(0xffffffffu, held[0].z, 0, kGroupLanes);
+    r0.m = __shfl_sync(0xffffffffu, held[0].m, 0, kGroupLanes);
+    r0.pad = 0u;
     ff M = ff_zero(), S[3] = {ff_zero(), ff_zero(), ff_zero()}, Q[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) Q[k] = ff_zero();
-    Record r0{};
-    if (b > a) r0 = s.rec[__ldg(perm + a)];
     auto acc = [](ff& sum, float v) { sum = ff_add(sum, v); };
-    for (u32 t = 0; t < trips; ++t) {
+    auto first_moments = [&](const Record& r) {
+        acc(M, r.m);
+        acc(S[0], __fmul_rn(r.m, fixed_diff(r.x, r0.x, f)));
+        acc(S[1], __fmul_rn(r.m, fixed_diff(r.y, r0.y, f)));
+        acc(S[2], __fmul_rn(r.m, fixed_diff(r.z, r0.z, f)));
+    };
+#pragma unroll
+    for (int t = 0; t < kHeld; ++t)
+        if (a + t * kGroupLanes + gl < b) first_moments(held[t]);
+    for (u32 t = kHeld; t < trips; ++t) {
         const u32 j = a + t * kGroupLanes + gl;
-        if (j < b) {
-            const Record r = s.rec[__ldg(perm + j)];
-            acc(M, r.m);
-            acc(S[0], __fmul_rn(r.m, fixed_diff(r.x, r0.x, f)));
-            acc(S[1], __fmul_rn(r.m, fixed_diff(r.y, r0.y, f)));
-            acc(S[2], __fmul_rn(r.m, fixed_diff(r.z, r0.z, f)));
-        }
+        if (j < b) first_moments(load_record(s.rec, __ldg(perm + j)));
     }
     M = group_sum(M);
 #pragma unroll
@@ -380,21 +401,24 @@ __global__ void __launch_bounds__(kLeafThreads) multipole_leaf_kernel(const u32*
             c[d] = r0c[d] + __float2ll_rn(__fmul_rn(__fmul_rn(off, 1.0f / f.s1), 1.0f / f.s2));
         }
     }
-    for (u32 t = 0; t < trips; ++t) {
+    auto second_moments = [&](const Record& r) {
+        const float e0 = fixed_diff(r.x, c[0], f);
+        const float e1 = fixed_diff(r.y, c[1], f);
+        const float e2 = fixed_diff(r.z, c[2], f);
+        const float me0 = __fmul_rn(r.m, e0), me1 = __fmul_rn(r.m, e1), me2 = __fmul_rn(r.m, e2);
+        acc(Q[0], __fmul_rn(me0, e0));
+        acc(Q[1], __fmul_rn(me0, e1));
+        acc(Q[2], __fmul_rn(me0, e2));
+        acc(Q[3], __fmul_rn(me1, e1));
+        acc(Q[4], __fmul_rn(me1, e2));
+        acc(Q[5], __fmul_rn(me2, e2));
+    };
+#pragma unroll
+    for (int t = 0; t < kHeld; ++t)
+        if (a + t * kGroupLanes + gl < b) second_moments(held[t]);
+    for (u32 t = kHeld; t < trips; ++t) {
         const u32 j = a + t * kGroupLanes + gl;
-        if (j < b) {
-            const Record r = s.rec[__ldg(perm + j)];
-            const float e0 = fixed_diff(r.x, c[0], f);
-            const float e1 = fixed_diff(r.y, c[1], f);
-            const float e2 = fixed_diff(r.z, c[2], f);
-            const float me0 = __fmul_rn(r.m, e0), me1 = __fmul_rn(r.m, e1), me2 = __fmul_rn(r.m, e2);
-            acc(Q[0], __fmul_rn(me0, e0));
-            acc(Q[1], __fmul_rn(me0, e1));
-            acc(Q[2], __fmul_rn(me0, e2));
-            acc(Q[3], __fmul_rn(me1, e1));
-            acc(Q[4], __fmul_rn(me1, e2));
-            acc(Q[5], __fmul_rn(me2, e2));
-        }
+        if (j < b) second_moments(load_record(s.rec, __ldg(perm + j)));
     }
 #pragma unroll
     for (int k = 0; k < 6; ++k) Q[k] = group_sum(Q[k]);
@@ -634,7 +658,7 @@ int launch_upsweep_multipoles(const double* x, const double* y, const double* z,
     CST_CUDA(cudaMemsetAsync(l.bar, 0, sizeof(GridBarrier), st));
     const u32 nn = static_cast<u32>(nl + (nl - 1) / 7);
     if (n > 0) {
-        long long want = (n + 4 * kThreads - 1) / (4 * kThreads);
+        long long want = (n + kThreads - 1) / kThreads;
         int pgrid = static_cast<int>(want < (long long)sm_count() * 8 ? want : (long long)sm_count() * 8);
         multipole_pack_kernel<<<pgrid, kThreads, 0, st>>>(x, y, z, m, static_cast<u32>(n), box, l.mp.rec, hdr);
         CST_LAUNCHED("multipole_pack_kernel");
