@@ -28,6 +28,7 @@ __all__ = [
     "cstone_upsweep_counts_batched", "build_octrees_batched", "cstone_build_leaves_batched_async",
     "cstone_leaves_result", "cstone_kernel_launches", "TimeStepper", "GraphTimeStepper", "cstone_leaf_counts",
     "cstone_rebalance", "cstone_bounds", "cstone_rebalance_focus", "build_focus_leaves", "LEVELS", "LEVELS30",
+    "StreamedBuilder",
 ]
 
 MORTON, HILBERT = 0, 1
@@ -664,6 +665,102 @@ def _grow(b: OctreeBuffers, want: int) -> OctreeBuffers:
     nb = OctreeBuffers.allocate(b.n, cap, b.device, b.levels)
     nb.keys, nb.sorted_keys, nb.perm, nb.box, nb.ws = b.keys, b.sorted_keys, b.perm, b.box, b.ws
     return nb
+
+
+# ------------------------------------------------------------------------- host-resident input
+class StreamedBuilder:
+    """Full builds (as ``build_octree``, with multipoles) of a sequence of particle sets held in
+    pinned host memory, with the host<->device transfers overlapped with the builds.
+
+    Three CUDA streams and two slots of device inputs and output buffers: while set k is built on
+    the compute stream, set k+1's coordinates and masses are copied in on a copy-in stream and set
+    k-1's tree is copied out on a copy-out stream (the link carries both directions at once).
+    Events order every reuse of a slot: a copy-in waits until the build that read the slot is done,
+    and a build waits until the copy-out of the slot's previous tree is done. The results are
+    pinned host tensors, valid once ``run`` returns (or, for set k, once its event has completed).
+    """
+
+    OUT = ("leaves", "leaf_counts", "NK", "CO", "LO", "node_counts", "mass", "com", "quad")
+
+    def __init__(self, n: int, device="cuda", curve: int = HILBERT, ncrit: int = 64, levels: int = LEVELS):
+        self.n, self.curve, self.ncrit, self.levels = n, curve, ncrit, levels
+        self.device = torch.device(device)
+        self.s_comp = torch.cuda.Stream(self.device)
+        self.s_in = torch.cuda.Stream(self.device)
+        self.s_out = torch.cuda.Stream(self.device)
+        f64, f32 = torch.float64, torch.float32
+        self.inputs = [tuple(torch.empty(n, dtype=dt, device=self.device) for dt in (f64, f64, f64, f32))
+                       for _ in range(2)]
+        self.buffers = [None, None]
+        self.host = [{}, {}]
+        self.ev_in = [torch.cuda.Event() for _ in range(2)]     # slot's inputs copied in
+        self.ev_used = [torch.cuda.Event() for _ in range(2)]   # slot's build finished
+        self.ev_out = [torch.cuda.Event() for _ in range(2)]    # slot's tree copied out
+
+    def _copy_in(self, slot: int, src):
+        with torch.cuda.stream(self.s_in):
+            self.s_in.wait_event(self.ev_used[slot])
+            for dst, h in zip(self.inputs[slot], src):
+                dst.copy_(h, non_blocking=True)
+            self.ev_in[slot].record(self.s_in)
+
+    def _copy_out(self, slot: int, out: dict):
+        host = self.host[slot]
+        res = {}
+        with torch.cuda.stream(self.s_out):
+            self.s_out.wait_event(self.ev_used[slot])
+            for k in self.OUT:
+                t = out[k].reshape(-1)
+                h = host.get(k)
+                if h is None or h.numel() < t.numel():
+                    h = host[k] = torch.empty(max(t.numel(), 1), dtype=t.dtype, pin_memory=True)
+                h[: t.numel()].copy_(t, non_blocking=True)
+                res[k] = h[: t.numel()]
+            self.ev_out[slot].record(self.s_out)
+        res["n_leaves"] = out["n_leaves"]
+        res["iters"] = out["iters"]
+        return res
+
+    def run(self, sets, on_result=None, events=None):
+        """Builds every (x, y, z, m) of ``sets`` (pinned host tensors: float64 coordinates, float32
+        masses, n particles each). Returns the number of bytes copied in and out; ``on_result(k,
+        result)`` receives set k's host result dict once its copy-out has completed (a result's
+        tensors are reused two sets later). ``events`` = (start, stop) CUDA events, recorded before
+        the first copy-in and after the last copy-out."""
+        sets = list(sets)
+        for src in sets:
+            if len(src) != 4 or any(t.numel() != self.n or t.is_cuda for t in src):
+                raise ValueError("every set is (x, y, z, m) host tensors of n particles")
+        h2d = d2h = 0
+        pending = []
+        if events is not None:
+            events[0].record(self.s_in)
+        if sets:
+            self._copy_in(0, sets[0])
+        for k in range(len(sets)):
+            slot = k % 2
+            if k + 1 < len(sets):
+                self._copy_in((k + 1) % 2, sets[k + 1])  # queued before this build's host syncs
+            with torch.cuda.stream(self.s_comp):
+                self.s_comp.wait_event(self.ev_in[slot])
+                self.s_comp.wait_event(self.ev_out[slot])  # the slot's previous tree has left
+                x, y, z, m = self.inputs[slot]
+                out = build_octree(x, y, z, curve=self.curve, ncrit=self.ncrit, masses=m,
+                                   buffers=self.buffers[slot], stream=self.s_comp, levels=self.levels)
+                self.buffers[slot] = out["buffers"]
+                self.ev_used[slot].record(self.s_comp)
+            res = self._copy_out(slot, out)
+            if events is not None and k + 1 == len(sets):
+                events[1].record(self.s_out)
+            h2d += sum(t.numel() * t.element_size() for t in sets[k])
+            d2h += sum(res[k2].numel() * res[k2].element_size() for k2 in self.OUT)
+            pending.append((k, slot, res))
+            while pending and (len(pending) > 1 or k + 1 == len(sets)):
+                kk, sl, r = pending.pop(0)
+                self.ev_out[sl].synchronize()
+                if on_result is not None:
+                    on_result(kk, r)
+        return h2d, d2h
 
 
 # ------------------------------------------------------------------------- time steps
