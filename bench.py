@@ -139,23 +139,23 @@ class ClockSampler:
 
 
 # DRAM bytes per particle of the sort (histogram, per-pass tile counts and scans, 8 passes) and of
-# the multipole upsweep (pack, leaf sums, levels), measured with ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum over the phase's launches) on 2^24 particles of the same workload and
-# scaled by the particle count (both phases stream or gather per particle, so traffic grows with n):
-# profiles/kernels_clumps_2p24_full.md.
-MEASURED_DRAM_BYTES_PER_PARTICLE = {"sort": 243.4, "multipoles": 192.7}
+# the multipole upsweep (leaf sums and levels; the records come from the key pass), measured with
+# ncu (dram__bytes_read.sum + dram__bytes_write.sum over the phase's launches) on 2^24 particles of
+# the same workload and scaled by the particle count (both phases stream or gather per particle,
+# so traffic grows with n): profiles/kernels_clumps_2p24_full.md.
+MEASURED_DRAM_BYTES_PER_PARTICLE = {"sort": 243.4, "multipoles": 135.6}
 
 
 def algorithmic_bytes(n: int, n_leaves: int, iter_leaves: int, n_nodes: int):
     """Compulsory DRAM traffic of one step (bytes), by phase."""
     return {
         "bbox": 24 * n,
-        "keys": 32 * n,
+        "keys": 68 * n,                         # read x, y, z, m; write the key and the 32-byte record
         "sort": (8 + 20 + 24 * 7) * n,          # digit histograms + 8 passes (first has no value read)
         "leaves": 24 * iter_leaves + 8 * n,     # K + pos read/written per pass; P read by searches once
         "link": 40 * n_nodes,
         "counts": 8 * n_nodes,
-        "multipoles": 32 * n + 48 * n_nodes,    # xyz fp64 + m fp32 + perm; per-node outputs + scratch
+        "multipoles": 36 * n + 48 * n_nodes,    # record gather + perm; per-node outputs + scratch
     }
 
 
@@ -198,7 +198,7 @@ def run_ours(args, rank, world, local):
         e[0].record(stream)
         cs.cstone_bbox(X, Y, Z, b.box, b.ws)
         e[1].record(stream)
-        cs.cstone_keys(X, Y, Z, b.box, cs.HILBERT, b.keys)
+        cs.cstone_keys_records(X, Y, Z, M, b.box, cs.HILBERT, b.keys, b.records, b.rws)
         e[2].record(stream)
         cs.cstone_sort(b.keys, b.sorted_keys, b.perm, b.ws)
         e[3].record(stream)
@@ -209,8 +209,8 @@ def run_ours(args, rank, world, local):
         e[5].record(stream)
         cs.cstone_upsweep_counts(b.counts, nl, t["leaf_to_node"], t["CO"], t["LO"], t["counts"], b.ws)
         e[6].record(stream)
-        cs.cstone_upsweep_multipoles(X, Y, Z, M, b.perm, b.offsets, nl, t["leaf_to_node"], t["CO"], t["LO"], b.box,
-                                     t["mass"], t["com"], t["quad"], b.ws)
+        cs.cstone_upsweep_multipoles_records(b.records, b.perm, n, b.offsets, nl, t["leaf_to_node"], t["CO"],
+                                             t["LO"], b.box, t["mass"], t["com"], t["quad"], b.ws)
         e[7].record(stream)
         return nl
 
@@ -374,7 +374,7 @@ def measure_keys30(X, Y, Z, M, K: int = 10):
         e[0].record(stream)
         cs.cstone_bbox(X, Y, Z, b.box, b.ws)
         e[1].record(stream)
-        cs.cstone_keys(X, Y, Z, b.box, cs.HILBERT, b.keys, levels=10)
+        cs.cstone_keys_records(X, Y, Z, M, b.box, cs.HILBERT, b.keys, b.records, b.rws, levels=10)
         e[2].record(stream)
         cs.cstone_sort(b.keys, b.sorted_keys, b.perm, b.ws, levels=10)
         e[3].record(stream)
@@ -387,8 +387,9 @@ def measure_keys30(X, Y, Z, M, K: int = 10):
         cs.cstone_upsweep_counts(b.counts, nl, t["leaf_to_node"], t["CO"], t["LO"], t["counts"], b.ws, levels=10)
         e[6].record(stream)
         nn = cs.n_nodes(nl)
-        cs.cstone_upsweep_multipoles(X, Y, Z, M, b.perm, b.offsets, nl, t["leaf_to_node"], t["CO"], t["LO"], b.box,
-                                     t["mass"][:nn], t["com"][: 3 * nn], t["quad"][: 6 * nn], b.ws, levels=10)
+        cs.cstone_upsweep_multipoles_records(b.records, b.perm, X.numel(), b.offsets, nl, t["leaf_to_node"], t["CO"],
+                                             t["LO"], b.box, t["mass"][:nn], t["com"][: 3 * nn], t["quad"][: 6 * nn],
+                                             b.ws, levels=10)
         e[7].record(stream)
     torch.cuda.synchronize()
     phase_ms = {p: float(np.mean([ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(K)]))

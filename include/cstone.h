@@ -215,6 +215,34 @@ CSTONE_API int cstone_upsweep_multipoles(const double* x, const double* y, const
                                          const int32_t* level_offsets, const double* box, float* mass, double* com,
                                          float* quad, void* ws, size_t ws_bytes, void* stream);
 
+/* Keys and multipole records in one read of the coordinates. The paper has no counterpart: it is
+ * the keys step (Sec. 3) fused with the first step of the multipole upsweep above, so that x, y, z
+ * are read once for both. keys are those of cstone_keys for the same box and curve; records
+ * receives one 32-byte record per particle (64-bit fixed-point position in the frame fixed by box,
+ * and the mass; the layout is private to the library), which cstone_upsweep_multipoles_records
+ * reads in place of x, y, z, m.
+ *   m        [n] float32 masses (4-byte aligned).
+ *   records  cstone_records_size(n) bytes of device memory, 16-byte aligned, owned by the caller.
+ *   ws       cstone_keys_records_workspace_size bytes (256-byte aligned); its error word reports
+ *            CSTONE_ERR_INVALID_ARG for a coordinate outside the fixed-point range of box (the
+ *            condition of cstone_upsweep_multipoles); read it with cstone_workspace_status.
+ * Asynchronous. */
+CSTONE_API int cstone_records_size(int64_t n, size_t* bytes);
+CSTONE_API int cstone_keys_records_workspace_size(size_t* bytes);
+CSTONE_API int cstone_keys_records(const double* x, const double* y, const double* z, const float* m, int64_t n,
+                                   const double* box, int curve, uint64_t* keys, void* records, void* ws,
+                                   size_t ws_bytes, void* stream);
+
+/* The multipole upsweep from records written by cstone_keys_records with the same box (the pack
+ * step skipped); results are bit for bit those of cstone_upsweep_multipoles on the same particles.
+ * ws: cstone_multipole_workspace_size(0, n_leaves, &bytes) bytes (no record area). Other arguments
+ * as for cstone_upsweep_multipoles. Asynchronous. */
+CSTONE_API int cstone_upsweep_multipoles_records(const void* records, const uint32_t* perm, int64_t n,
+                                                 const uint32_t* offsets, int64_t n_leaves,
+                                                 const int32_t* leaf_to_node, const int32_t* child,
+                                                 const int32_t* level_offsets, const double* box, float* mass,
+                                                 double* com, float* quad, void* ws, size_t ws_bytes, void* stream);
+
 /* ==========================================================================================
  * Batched builds: S independent particle sets stored back to back (set s owns particles
  * [set_offsets[s], set_offsets[s+1])), built with one launch per phase for all sets. The
@@ -387,6 +415,14 @@ CSTONE_API int cstone30_upsweep_multipoles(const double* x, const double* y, con
                                            const int32_t* leaf_to_node, const int32_t* child,
                                            const int32_t* level_offsets, const double* box, float* mass, double* com,
                                            float* quad, void* ws, size_t ws_bytes, void* stream);
+CSTONE_API int cstone30_keys_records(const double* x, const double* y, const double* z, const float* m, int64_t n,
+                                     const double* box, int curve, uint32_t* keys, void* records, void* ws,
+                                     size_t ws_bytes, void* stream);
+CSTONE_API int cstone30_upsweep_multipoles_records(const void* records, const uint32_t* perm, int64_t n,
+                                                   const uint32_t* offsets, int64_t n_leaves,
+                                                   const int32_t* leaf_to_node, const int32_t* child,
+                                                   const int32_t* level_offsets, const double* box, float* mass,
+                                                   double* com, float* quad, void* ws, size_t ws_bytes, void* stream);
 
 #ifdef __cplusplus
 }

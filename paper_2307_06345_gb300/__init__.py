@@ -28,7 +28,7 @@ __all__ = [
     "cstone_upsweep_counts_batched", "build_octrees_batched", "cstone_build_leaves_batched_async",
     "cstone_leaves_result", "cstone_kernel_launches", "TimeStepper", "GraphTimeStepper", "cstone_leaf_counts",
     "cstone_rebalance", "cstone_bounds", "cstone_rebalance_focus", "build_focus_leaves", "LEVELS", "LEVELS30",
-    "StreamedBuilder",
+    "StreamedBuilder", "records_size", "cstone_keys_records", "cstone_upsweep_multipoles_records",
 ]
 
 MORTON, HILBERT = 0, 1
@@ -104,11 +104,15 @@ def load():
                                                       ctypes.c_double, ctypes.c_int, P, i64, pi64, pi32, P, sz, P]),
             "cstone_rebalance_workspace_size": (ctypes.c_int, [i64, psz]),
             "cstone_rebalance": (ctypes.c_int, [P, P, i64, u32, P, i64, pi64, pi32, P, sz, P]),
+            "cstone_records_size": (ctypes.c_int, [i64, psz]),
+            "cstone_keys_records_workspace_size": (ctypes.c_int, [psz]),
+            "cstone_keys_records": (ctypes.c_int, [P, P, P, P, i64, P, ctypes.c_int, P, P, P, sz, P]),
+            "cstone_upsweep_multipoles_records": (ctypes.c_int, [P, P, i64, P, i64, P, P, P, P, P, P, P, P, sz, P]),
         }
         for name in ("keys", "sort_workspace_size", "sort", "leaves_workspace_size", "build_leaves",
                      "link_workspace_size", "link_tree", "upsweep_workspace_size", "upsweep_counts",
                      "multipole_workspace_size", "upsweep_multipoles", "leaf_counts", "rebalance_workspace_size",
-                     "rebalance", "rebalance_focus"):
+                     "rebalance", "rebalance_focus", "keys_records", "upsweep_multipoles_records"):
             sigs["cstone30_" + name] = sigs["cstone_" + name]
         res, args = sigs["cstone30_rebalance_focus"]
         sigs["cstone30_rebalance_focus"] = (res, args[:4] + [u32, u32] + args[6:])
@@ -308,6 +312,37 @@ def cstone_upsweep_multipoles(x, y, z, m, perm, offsets, n_leaves: int, leaf_to_
            "cstone_upsweep_multipoles")
 
 
+def records_size(n: int) -> int:
+    """Bytes of the multipole records of n particles (cstone_keys_records)."""
+    return _size(load().cstone_records_size, n)
+
+
+def cstone_keys_records(x, y, z, m, box, curve: int, keys, records, ws: Workspace, stream=None,
+                        levels: int = LEVELS):
+    """Keys (as cstone_keys) and the multipole records of the particles in one pass; ``records`` is
+    a uint8 CUDA tensor of records_size(n) bytes. Coordinate range errors go to ws's error word."""
+    fn, kdt = _family(levels)
+    _need(keys, kdt, "keys")
+    _need(m, torch.float32, "m")
+    if records.dtype != torch.uint8 or records.numel() < records_size(x.numel()):
+        raise ValueError("records must be a uint8 CUDA tensor of records_size(n) bytes")
+    buf = ws.get(_size(load().cstone_keys_records_workspace_size))
+    _check(fn("keys_records")(_ptr(x), _ptr(y), _ptr(z), _ptr(m), x.numel(), _ptr(box), curve, _ptr(keys),
+                              _ptr(records), _ptr(buf), buf.numel(), _stream(stream)), "cstone_keys_records")
+
+
+def cstone_upsweep_multipoles_records(records, perm, n: int, offsets, n_leaves: int, leaf_to_node, child,
+                                      level_offsets, box, mass, com, quad, ws: Workspace | None = None, stream=None,
+                                      levels: int = LEVELS):
+    fn, _ = _family(levels)
+    ws = ws or Workspace(perm.device)
+    buf = ws.get(_size(fn("multipole_workspace_size"), 0, n_leaves))
+    _check(fn("upsweep_multipoles_records")(_ptr(records), _ptr(perm), n, _ptr(offsets), n_leaves,
+                                            _ptr(leaf_to_node), _ptr(child), _ptr(level_offsets), _ptr(box),
+                                            _ptr(mass), _ptr(com), _ptr(quad), _ptr(buf), buf.numel(),
+                                            _stream(stream)), "cstone_upsweep_multipoles_records")
+
+
 def cstone_leaf_counts(sorted_keys, leaves, n_leaves: int, counts, stream=None, levels: int = LEVELS):
     """f: counts[i] = particles of sorted_keys in [leaves[i], leaves[i+1])."""
     fn, kdt = _family(levels)
@@ -412,6 +447,8 @@ class OctreeBuffers:
     ws: Workspace = None
     tree: dict = field(default_factory=dict)
     levels: int = LEVELS
+    records: torch.Tensor = None  # multipole records (cstone_keys_records), allocated on first use
+    rws: Workspace = None         # error word of the record-writing key pass
 
     @classmethod
     def allocate(cls, n: int, cap: int, device="cuda", levels: int = LEVELS):
@@ -453,6 +490,9 @@ def build_octree(x, y, z, curve: int = HILBERT, ncrit: int = 64, box=None, masse
     ``box`` is a float64 tensor {lo_x, lo_y, lo_z, side} (CUDA); when None the bounding cube is
     computed on the device. ``warm_leaves`` (CUDA, n_l + 1 keys) warm-starts the leaf loop.
     ``levels``: 21 (63-bit keys in int64 tensors) or 10 (30-bit keys in int32 tensors).
+    With masses, the keys and the multipole records are written in one pass
+    (cstone_keys_records); a coordinate outside the box's fixed-point range is recorded in the
+    error word of ``buffers.rws``.
     Returns a dict of device tensors sized to the built tree plus 'n_leaves' and 'iters'.
     """
     n = x.numel()
@@ -462,7 +502,14 @@ def build_octree(x, y, z, curve: int = HILBERT, ncrit: int = 64, box=None, masse
     if box is None:
         cstone_bbox(x, y, z, b.box, b.ws, stream)
         box = b.box
-    cstone_keys(x, y, z, box, curve, b.keys, stream, levels)
+    if masses is not None:  # keys and multipole records from one read of the coordinates
+        _need(masses, torch.float32, "masses")
+        if b.records is None or b.records.numel() < records_size(n):
+            b.records = torch.empty(records_size(n), dtype=torch.uint8, device=b.device)
+            b.rws = Workspace(b.device)
+        cstone_keys_records(x, y, z, masses, box, curve, b.keys, b.records, b.rws, stream, levels)
+    else:
+        cstone_keys(x, y, z, box, curve, b.keys, stream, levels)
     cstone_sort(b.keys, b.sorted_keys, b.perm, b.ws, stream, levels)
     while True:
         nl0 = 0
@@ -496,8 +543,8 @@ def build_octree(x, y, z, curve: int = HILBERT, ncrit: int = 64, box=None, masse
             t["com"] = torch.empty(3 * cap_nodes, dtype=torch.float64, device=b.device)
             t["quad"] = torch.empty(6 * cap_nodes, dtype=torch.float32, device=b.device)
         mass, com, quad = t["mass"][:nn], t["com"][: 3 * nn], t["quad"][: 6 * nn]
-        cstone_upsweep_multipoles(x, y, z, masses, b.perm, b.offsets, nl, t["leaf_to_node"], t["CO"], t["LO"], box,
-                                  mass, com, quad, b.ws, stream, levels)
+        cstone_upsweep_multipoles_records(b.records, b.perm, n, b.offsets, nl, t["leaf_to_node"], t["CO"], t["LO"],
+                                          box, mass, com, quad, b.ws, stream, levels)
         out.update({"mass": mass, "com": com.view(3, nn), "quad": quad.view(6, nn)})
     return out
 
@@ -664,6 +711,7 @@ def _grow(b: OctreeBuffers, want: int) -> OctreeBuffers:
     cap = int(min(1 << 28, max(want, 2 * b.cap)))
     nb = OctreeBuffers.allocate(b.n, cap, b.device, b.levels)
     nb.keys, nb.sorted_keys, nb.perm, nb.box, nb.ws = b.keys, b.sorted_keys, b.perm, b.box, b.ws
+    nb.records, nb.rws = b.records, b.rws
     return nb
 
 
@@ -803,10 +851,10 @@ class GraphTimeStepper:
     hold at most elem_cap + elem_cap / 7 + S nodes), the leaf loop takes its warm-start count from
     the device, and the link and count phases run on capacities with the exact counts read on the
     device, so no phase needs the host between the launches. After each replay the outcome is read
-    back (two synchronisations per step). The first rebuild (cold, from the roots) runs without the
-    graph, with the synchronous leaf loop, and sets the capacity to twice its element count; the
-    warm rebuild is captured on its first use. A capacity overflow doubles the capacity, drops the
-    graph and rebuilds cold."""
+    back (two synchronisations per step). The capacity is never below the batched builder's
+    first estimate (``elem_cap`` raises it, never lowers it). The first rebuild (cold, from the
+    roots) runs without the graph, with the synchronous leaf loop; the warm rebuild is captured on
+    its first use. A capacity overflow doubles the capacity, drops the graph and rebuilds cold."""
 
     def __init__(self, x, y, z, set_offsets, curve: int = HILBERT, ncrit: int = 64, pad: float = 0.1,
                  elem_cap: int | None = None, max_iters: int = 64):
@@ -826,7 +874,10 @@ class GraphTimeStepper:
         self.perm = torch.empty(n, dtype=torch.int32, device=dev)
         self.element_offsets = torch.empty(s + 1, dtype=torch.int64, device=dev)
         self.LO = torch.empty((s, LEVELS + 2), dtype=torch.int32, device=dev)
-        self._alloc(elem_cap or max(4 * s, 16 * (n // (ncrit + 1)) + 2 * s + 4096))
+        # never below the estimate the batched builder starts from, so that a cold build does not
+        # overflow its capacity in practice
+        self.min_cap = max(4 * s, 16 * (n // (ncrit + 1)) + 2 * s + 4096)
+        self._alloc(max(elem_cap or 0, self.min_cap))
         self.have_arrays = False
 
     def _alloc(self, cap: int, keep: int = 0):
@@ -885,6 +936,8 @@ class GraphTimeStepper:
         # From the roots with the synchronous leaf loop: a capacity overflow is reported before the
         # link and count phases run, and only the leaf loop is repeated at the grown capacity.
         w = self.ws
+        if self.elem_cap < self.min_cap:
+            self._alloc(self.min_cap)
         cstone_keys_batched(self.x, self.y, self.z, self.set_offsets, self.boxes, self.curve, self.keys, w["keys"])
         cstone_sort_segmented(self.keys, self.sorted_keys, self.perm, self.set_offsets, w["sort"])
         while True:
@@ -903,7 +956,7 @@ class GraphTimeStepper:
                                       self.node_counts, w["counts"])
         out = self._result()
         ne = out["n_elements"]
-        tight = 2 * ne + 64 * self.n_sets + 4096
+        tight = max(2 * ne + 64 * self.n_sets + 4096, self.min_cap)
         if not self.fixed_cap and tight < self.elem_cap:
             self._alloc(tight, keep=ne)  # element offsets live outside the capacity buffers
             out = dict(out, elements=self.elements[:ne])

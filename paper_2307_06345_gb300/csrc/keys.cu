@@ -15,6 +15,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "records.cuh"
 
 namespace CST_NS {
 
@@ -247,19 +248,27 @@ __device__ __forceinline__ u64 hilbert_of(u64 m, const unsigned short* t1, const
     return key;
 }
 
-template <int CURVE, bool VEC>
+// REC: also write each particle's multipole record (fixed-point position and mass, records.cuh)
+// from the same read of the coordinates, one particle per thread so that a warp's record stores
+// cover contiguous memory.
+template <int CURVE, bool VEC, bool REC>
 __global__ void __launch_bounds__(256) keys_kernel(const double* __restrict__ x, const double* __restrict__ y,
                                                    const double* __restrict__ z, long long n,
                                                    const double* __restrict__ box, Key* __restrict__ keys,
-                                                   const __grid_constant__ HilbertTable table) {
+                                                   const __grid_constant__ HilbertTable table,
+                                                   const float* __restrict__ m, Record* __restrict__ rec,
+                                                   WsHeader* hdr) {
+    static_assert(!(VEC && REC), "the record-writing kernel takes one particle per thread");
     __shared__ unsigned short s_t2[kHilbertStates * 64];
     __shared__ unsigned short s_t1[kHilbertStates * 8];
     __shared__ FixedGrid s_grid[3];
+    __shared__ FixedFrame s_frame;
     if (CURVE == CSTONE_HILBERT) {
         for (int i = threadIdx.x; i < kHilbertStates * 64; i += blockDim.x) s_t2[i] = table.two[i];
         for (int i = threadIdx.x; i < kHilbertStates * 8; i += blockDim.x) s_t1[i] = table.one[i];
     }
     if (threadIdx.x < 3) s_grid[threadIdx.x] = make_fixed_grid(box[threadIdx.x], box[3]);
+    if (REC && threadIdx.x == 32) s_frame = make_frame(box);
     __syncthreads();
     const FixedGrid gx = s_grid[0], gy = s_grid[1], gz = s_grid[2];
     const bool fast = gx.fast && gy.fast && gz.fast;
@@ -275,6 +284,16 @@ __global__ void __launch_bounds__(256) keys_kernel(const double* __restrict__ x,
         return to_key(m);
     };
 
+    if (REC) {
+        const FixedFrame fr = s_frame;
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+            const double px = __ldcs(x + i), py = __ldcs(y + i), pz = __ldcs(z + i);
+            keys[i] = encode(px, py, pz);
+            if (!store_record(rec, static_cast<u32>(i), px, py, pz, __ldcs(m + i), fr))
+                raise_error(hdr, CSTONE_ERR_INVALID_ARG, static_cast<u32>(i));
+        }
+        return;
+    }
     if (!VEC) {
         for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
             keys[i] = encode(__ldcs(x + i), __ldcs(y + i), __ldcs(z + i));
@@ -534,17 +553,37 @@ int launch_keys(const double* x, const double* y, const double* z, long long n, 
     int grid = static_cast<int>(want < (long long)sm_count() * 8 ? (want > 0 ? want : 1) : (long long)sm_count() * 8);
     bool vec = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y) | reinterpret_cast<uintptr_t>(z) |
                  reinterpret_cast<uintptr_t>(keys)) & 15u) == 0;
+    const float* no_m = nullptr;
+    Record* no_rec = nullptr;
+    WsHeader* no_hdr = nullptr;
     if (curve == CSTONE_HILBERT) {
         if (vec)
-            keys_kernel<CSTONE_HILBERT, true><<<grid, 256, 0, st>>>(x, y, z, n, box, keys, tab);
+            keys_kernel<CSTONE_HILBERT, true, false><<<grid, 256, 0, st>>>(x, y, z, n, box, keys, tab, no_m, no_rec, no_hdr);
         else
-            keys_kernel<CSTONE_HILBERT, false><<<grid, 256, 0, st>>>(x, y, z, n, box, keys, tab);
+            keys_kernel<CSTONE_HILBERT, false, false><<<grid, 256, 0, st>>>(x, y, z, n, box, keys, tab, no_m, no_rec, no_hdr);
     } else {
         if (vec)
-            keys_kernel<CSTONE_MORTON, true><<<grid, 256, 0, st>>>(x, y, z, n, box, keys, tab);
+            keys_kernel<CSTONE_MORTON, true, false><<<grid, 256, 0, st>>>(x, y, z, n, box, keys, tab, no_m, no_rec, no_hdr);
         else
-            keys_kernel<CSTONE_MORTON, false><<<grid, 256, 0, st>>>(x, y, z, n, box, keys, tab);
+            keys_kernel<CSTONE_MORTON, false, false><<<grid, 256, 0, st>>>(x, y, z, n, box, keys, tab, no_m, no_rec, no_hdr);
     }
+    CST_LAUNCHED("keys_kernel");
+    return CSTONE_OK;
+}
+
+// Keys and multipole records in one pass; ws holds only the header (error word).
+int launch_keys_records(const double* x, const double* y, const double* z, const float* m, long long n,
+                        const double* box, int curve, Key* keys, Record* rec, void* ws, cudaStream_t st) {
+    WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
+    CST_CUDA(cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st));
+    if (n == 0) return CSTONE_OK;
+    const HilbertTable& tab = hilbert_table();
+    long long want = (n + 255) / 256;
+    int grid = static_cast<int>(want < (long long)sm_count() * 8 ? (want > 0 ? want : 1) : (long long)sm_count() * 8);
+    if (curve == CSTONE_HILBERT)
+        keys_kernel<CSTONE_HILBERT, false, true><<<grid, 256, 0, st>>>(x, y, z, n, box, keys, tab, m, rec, hdr);
+    else
+        keys_kernel<CSTONE_MORTON, false, true><<<grid, 256, 0, st>>>(x, y, z, n, box, keys, tab, m, rec, hdr);
     CST_LAUNCHED("keys_kernel");
     return CSTONE_OK;
 }
@@ -594,7 +633,38 @@ int CSTONE_FN(keys)(const double* x, const double* y, const double* z, int64_t n
     return CST_NS::launch_keys(x, y, z, n, box, curve, reinterpret_cast<CST_NS::Key*>(keys), cst::as_stream(stream));
 }
 
+int CSTONE_FN(keys_records)(const double* x, const double* y, const double* z, const float* m, int64_t n,
+                            const double* box, int curve, CST_KEY_C* keys, void* records, void* ws, size_t ws_bytes,
+                            void* stream) {
+    if (n < 0 || n >= CSTONE_MAX_PARTICLES || !box || (n > 0 && (!x || !y || !z || !m || !keys || !records)))
+        return cst::fail(CSTONE_ERR_INVALID_ARG, CST_STR(CSTONE_FN(keys_records)) ": bad argument (n=%lld)",
+                         (long long)n);
+    if (curve != CSTONE_MORTON && curve != CSTONE_HILBERT)
+        return cst::fail(CSTONE_ERR_INVALID_ARG, CST_STR(CSTONE_FN(keys_records)) ": unknown curve %d", curve);
+    if (((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y) | reinterpret_cast<uintptr_t>(z)) & 7u) != 0 ||
+        (reinterpret_cast<uintptr_t>(m) & 3u) != 0 || (reinterpret_cast<uintptr_t>(records) & 15u) != 0 ||
+        (reinterpret_cast<uintptr_t>(keys) & (sizeof(CST_KEY_C) - 1)) != 0)
+        return cst::fail(CSTONE_ERR_INVALID_ARG,
+                         CST_STR(CSTONE_FN(keys_records)) ": arrays must be aligned (records to 16 bytes)");
+    if (int rc = cst::check_ws(ws, ws_bytes, sizeof(cst::WsHeader), CST_STR(CSTONE_FN(keys_records)))) return rc;
+    return CST_NS::launch_keys_records(x, y, z, m, n, box, curve, reinterpret_cast<CST_NS::Key*>(keys),
+                                       static_cast<cst::Record*>(records), ws, cst::as_stream(stream));
+}
+
 #ifndef CSTONE_KEY32  // the bounding cube and the batched entry points exist once, for 63-bit keys
+int cstone_records_size(int64_t n, size_t* bytes) {
+    if (!bytes || n < 0 || n >= CSTONE_MAX_PARTICLES)
+        return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_records_size: bad argument");
+    *bytes = static_cast<size_t>(n > 0 ? n : 1) * sizeof(cst::Record);
+    return CSTONE_OK;
+}
+
+int cstone_keys_records_workspace_size(size_t* bytes) {
+    if (!bytes) return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_keys_records_workspace_size: bad argument");
+    *bytes = sizeof(cst::WsHeader);
+    return CSTONE_OK;
+}
+
 int cstone_bbox_workspace_size(int64_t n, size_t* bytes) {
     if (!bytes || n < 0) return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_bbox_workspace_size: bad argument");
     *bytes = cst::bbox_ws_bytes();

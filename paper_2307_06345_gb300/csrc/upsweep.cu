@@ -17,6 +17,7 @@
 // non-empty child's centre; second moments of an internal node use the parallel-axis shift
 // Q = sum_c [Q_c + M_c (c_c - c)(c_c - c)^T].
 #include "common.cuh"
+#include "records.cuh"
 
 namespace CST_NS {
 namespace {
@@ -173,59 +174,6 @@ __device__ __forceinline__ ff ff_add(ff a, ff b) {
 
 __device__ __forceinline__ float ff_val(ff a) { return __fadd_rn(a.hi, a.lo); }
 
-// Coordinates in 64-bit fixed point: X = trunc(x * 2^F) with F chosen from the box so that
-// |X| < 2^61 for |x| < 2^E >= max(|lo|, |lo + 2 side|). Differences of fixed-point values are
-// exact; one conversion rounds them to FP32 and a power-of-two scale (split in two factors so
-// that each is a normal float) restores physical units.
-struct FixedFrame {
-    int F;
-    float s1, s2;  // 2^-F = s1 * s2
-    int e_lim;     // biased exponent bound: |x| < 2^(e_lim - 1023)
-};
-
-__device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }
-
-__device__ FixedFrame make_frame(const double* box) {
-    FixedFrame f;
-    const double lo0 = fmin(fmin(box[0], box[1]), box[2]);
-    const double lo1 = fmax(fmax(box[0], box[1]), box[2]);
-    const double hi = __dadd_rn(lo1, __dmul_rn(2.0, box[3]));
-    const double big = fmax(fabs(lo0), fmax(fabs(lo1), fabs(hi)));
-    const int e = static_cast<int>((static_cast<u64>(__double_as_longlong(big)) >> 52) & 0x7ffu);
-    const int E = e - 1023 + 1;  // 2^E > big
-    f.F = 61 - E;
-    f.e_lim = E + 1023;
-    const int h = f.F / 2;
-    f.s1 = pow2f(-h);
-    f.s2 = pow2f(-(f.F - h));
-    return f;
-}
-
-__device__ __forceinline__ long long fixed_of(double x, int F) {
-    const u64 b = static_cast<u64>(__double_as_longlong(x));
-    const int e = static_cast<int>((b >> 52) & 0x7ffu);
-    u64 mant = b & ((1ULL << 52) - 1);
-    if (e != 0) mant |= (1ULL << 52);
-    const int sh = (e == 0 ? 1 : e) - 1075 + F;
-    const u64 mag = sh >= 0 ? (mant << sh) : (sh > -64 ? (mant >> (-sh)) : 0ULL);
-    return (b >> 63) ? -static_cast<long long>(mag) : static_cast<long long>(mag);
-}
-
-__device__ __forceinline__ float fixed_diff(long long a, long long b, const FixedFrame& f) {
-    return __fmul_rn(__fmul_rn(__ll2float_rn(a - b), f.s1), f.s2);
-}
-
-__device__ __forceinline__ double fixed_to_double(long long a, const FixedFrame& f) {
-    // exact power-of-two scaling of the (rounded) conversion
-    return __dmul_rn(__dmul_rn(__ll2double_rn(a), (double)f.s1), (double)f.s2);
-}
-
-struct __align__(16) Record {  // one particle, original order
-    long long x, y, z;
-    float m;
-    u32 pad;
-};
-
 struct MpScratch {  // per node: compensated sums and the fixed-point centre carried up the tree
     ff* mass;           // [n]
     ff* quad;           // [6 n], component-major
@@ -266,23 +214,7 @@ __global__ void __launch_bounds__(kThreads) multipole_pack_kernel(const double* 
     __syncthreads();
     const FixedFrame f = s_f;
     auto pack = [&](double px, double py, double pz, float pm, u32 p) {
-        const int ex = static_cast<int>((static_cast<u64>(__double_as_longlong(px)) >> 52) & 0x7ffu);
-        const int ey = static_cast<int>((static_cast<u64>(__double_as_longlong(py)) >> 52) & 0x7ffu);
-        const int ez = static_cast<int>((static_cast<u64>(__double_as_longlong(pz)) >> 52) & 0x7ffu);
-        Record r;
-        if (max(ex, max(ey, ez)) >= f.e_lim) {
-            raise_error(hdr, CSTONE_ERR_INVALID_ARG, p);
-            r.x = r.y = r.z = 0;
-        } else {
-            r.x = fixed_of(px, f.F);
-            r.y = fixed_of(py, f.F);
-            r.z = fixed_of(pz, f.F);
-        }
-        r.m = pm;
-        r.pad = 0u;
-        longlong2* dst = reinterpret_cast<longlong2*>(rec + p);
-        __stcs(dst, make_longlong2(r.x, r.y));
-        __stcs(dst + 1, make_longlong2(r.z, static_cast<long long>(__float_as_uint(r.m))));
+        if (!store_record(rec, p, px, py, pz, pm, f)) raise_error(hdr, CSTONE_ERR_INVALID_ARG, p);
     };
     // one particle per thread and step: 8-byte coalesced loads, and a warp's two 16-byte stores
     // cover 1 KB of records contiguously
@@ -648,16 +580,19 @@ int launch_upsweep_counts_batched(const u32* elem_counts, long long n_elements, 
     return CSTONE_OK;
 }
 
+// records == NULL: pack them from x, y, z, m into the workspace first; otherwise they were written
+// by the record-writing key kernel (and the workspace has no record area).
 int launch_upsweep_multipoles(const double* x, const double* y, const double* z, const float* m, const u32* perm,
                               long long n, const u32* offsets, long long nl, const int* leaf_to_node, const int* child,
                               const int* level_offsets, const double* box, float* mass, double* com, float* quad,
-                              void* ws, cudaStream_t st) {
-    UpLayout l = up_layout(ws, nl, n, true);
+                              void* ws, cudaStream_t st, const Record* records = nullptr) {
+    UpLayout l = up_layout(ws, nl, records ? 0 : n, true);
+    if (records) l.mp.rec = const_cast<Record*>(records);
     WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
     CST_CUDA(cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st));
     CST_CUDA(cudaMemsetAsync(l.bar, 0, sizeof(GridBarrier), st));
     const u32 nn = static_cast<u32>(nl + (nl - 1) / 7);
-    if (n > 0) {
+    if (n > 0 && !records) {
         long long want = (n + kThreads - 1) / kThreads;
         int pgrid = static_cast<int>(want < (long long)sm_count() * 8 ? want : (long long)sm_count() * 8);
         multipole_pack_kernel<<<pgrid, kThreads, 0, st>>>(x, y, z, m, static_cast<u32>(n), box, l.mp.rec, hdr);
@@ -712,6 +647,23 @@ int CSTONE_FN(multipole_workspace_size)(int64_t n, int64_t n_leaves, size_t* byt
         return cst::fail(CSTONE_ERR_INVALID_ARG, CST_STR(CSTONE_FN(multipole_workspace_size)) ": bad argument");
     *bytes = CST_NS::multipole_ws_bytes(n_leaves, n);
     return CSTONE_OK;
+}
+
+int CSTONE_FN(upsweep_multipoles_records)(const void* records, const uint32_t* perm, int64_t n,
+                                          const uint32_t* offsets, int64_t n_leaves, const int32_t* leaf_to_node,
+                                          const int32_t* child, const int32_t* level_offsets, const double* box,
+                                          float* mass, double* com, float* quad, void* ws, size_t ws_bytes,
+                                          void* stream) {
+    if (n < 0 || n >= CSTONE_MAX_PARTICLES || n_leaves < 1 || n_leaves > CSTONE_MAX_LEAVES ||
+        (n_leaves - 1) % 7 != 0 || !offsets || !leaf_to_node || !child || !level_offsets || !mass || !com || !quad ||
+        !box || (n > 0 && (!records || !perm)) || (reinterpret_cast<uintptr_t>(records) & 15u) != 0)
+        return cst::fail(CSTONE_ERR_INVALID_ARG, CST_STR(CSTONE_FN(upsweep_multipoles_records)) ": bad argument");
+    if (int rc = cst::check_ws(ws, ws_bytes, CST_NS::multipole_ws_bytes(n_leaves, 0),
+                               CST_STR(CSTONE_FN(upsweep_multipoles_records))))
+        return rc;
+    return CST_NS::launch_upsweep_multipoles(nullptr, nullptr, nullptr, nullptr, perm, n, offsets, n_leaves,
+                                             leaf_to_node, child, level_offsets, box, mass, com, quad, ws,
+                                             cst::as_stream(stream), static_cast<const cst::Record*>(records));
 }
 
 int CSTONE_FN(upsweep_multipoles)(const double* x, const double* y, const double* z, const float* m,

@@ -163,18 +163,19 @@ def test_async_leaves_equal_sync(lib, oracle):
             assert iters == 1
 
 
-def test_graph_time_stepper_grows_its_capacity(lib):
-    # a capacity far too small for the first build is grown until the build fits; later steps
-    # replay the graph at the grown capacity
+def test_graph_time_stepper_capacity_floor(lib):
+    # a requested capacity below the batched builder's estimate is raised to it, so the cold build
+    # fits; later steps replay the graph at that capacity
     from paper_2307_06345_gb300 import workloads as w
     runs, n = 3, 20_000
     parts = [w.uniform(n, w.BASE_SEED + 80 + r) for r in range(runs)]
     X, Y, Z = (dev(np.concatenate([p[d] for p in parts])) for d in range(3))
     OFF = dev((np.arange(runs + 1) * n).astype(np.int64))
     g = lib.GraphTimeStepper(X, Y, Z, OFF, curve=lib.MORTON, ncrit=16, elem_cap=2 * runs + 8)
+    assert g.elem_cap == g.min_cap > 2 * runs + 8
     e = lib.TimeStepper(X, Y, Z, OFF, curve=lib.MORTON, ncrit=16)
     for warm in (False, True, True):
         a, b = g.rebuild(warm=warm), e.rebuild(warm=warm)
         torch.cuda.synchronize()
         _equal(a, b, ["elements", "element_offsets", "leaf_counts", "NK", "CO", "LO", "node_counts"])
-    assert g.elem_cap > 2 * runs + 8 and g.graph is not None
+    assert g.elem_cap == g.min_cap and g.graph is not None
