@@ -248,52 +248,45 @@ __device__ __forceinline__ u64 hilbert_of(u64 m, const unsigned short* t1, const
     return key;
 }
 
-// REC: also write each particle's multipole record (fixed-point position and mass, records.cuh)
-// from the same read of the coordinates, one particle per thread so that a warp's record stores
-// cover contiguous memory.
-template <int CURVE, bool VEC, bool REC>
+// Hilbert tables and the three fixed-point grids of the box in shared memory (both key kernels).
+struct KeySmem {
+    unsigned short t2[kHilbertStates * 64];
+    unsigned short t1[kHilbertStates * 8];
+    FixedGrid grid[3];
+};
+
+template <int CURVE>
+__device__ __forceinline__ void load_key_smem(KeySmem& sm, const HilbertTable& table, const double* box) {
+    if (CURVE == CSTONE_HILBERT) {
+        for (int i = threadIdx.x; i < kHilbertStates * 64; i += blockDim.x) sm.t2[i] = table.two[i];
+        for (int i = threadIdx.x; i < kHilbertStates * 8; i += blockDim.x) sm.t1[i] = table.one[i];
+    }
+    if (threadIdx.x < 3) sm.grid[threadIdx.x] = make_fixed_grid(box[threadIdx.x], box[3]);
+}
+
+template <int CURVE>
+__device__ __forceinline__ Key encode_key(const KeySmem& sm, bool fast, double px, double py, double pz) {
+    u64 m;
+    if (fast)
+        m = morton_of(grid_cell_fixed(px, sm.grid[0]), grid_cell_fixed(py, sm.grid[1]), grid_cell_fixed(pz, sm.grid[2]));
+    else
+        m = morton_of(grid_cell(px, sm.grid[0].lo, sm.grid[0].scale), grid_cell(py, sm.grid[1].lo, sm.grid[1].scale),
+                      grid_cell(pz, sm.grid[2].lo, sm.grid[2].scale));
+    if (CURVE == CSTONE_HILBERT) return to_key(hilbert_of(m, sm.t1, sm.t2));
+    return to_key(m);
+}
+
+template <int CURVE, bool VEC>
 __global__ void __launch_bounds__(256) keys_kernel(const double* __restrict__ x, const double* __restrict__ y,
                                                    const double* __restrict__ z, long long n,
                                                    const double* __restrict__ box, Key* __restrict__ keys,
-                                                   const __grid_constant__ HilbertTable table,
-                                                   const float* __restrict__ m, Record* __restrict__ rec,
-                                                   WsHeader* hdr) {
-    static_assert(!(VEC && REC), "the record-writing kernel takes one particle per thread");
-    __shared__ unsigned short s_t2[kHilbertStates * 64];
-    __shared__ unsigned short s_t1[kHilbertStates * 8];
-    __shared__ FixedGrid s_grid[3];
-    __shared__ FixedFrame s_frame;
-    if (CURVE == CSTONE_HILBERT) {
-        for (int i = threadIdx.x; i < kHilbertStates * 64; i += blockDim.x) s_t2[i] = table.two[i];
-        for (int i = threadIdx.x; i < kHilbertStates * 8; i += blockDim.x) s_t1[i] = table.one[i];
-    }
-    if (threadIdx.x < 3) s_grid[threadIdx.x] = make_fixed_grid(box[threadIdx.x], box[3]);
-    if (REC && threadIdx.x == 32) s_frame = make_frame(box);
+                                                   const __grid_constant__ HilbertTable table) {
+    __shared__ KeySmem sm;
+    load_key_smem<CURVE>(sm, table, box);
     __syncthreads();
-    const FixedGrid gx = s_grid[0], gy = s_grid[1], gz = s_grid[2];
-    const bool fast = gx.fast && gy.fast && gz.fast;
+    const bool fast = sm.grid[0].fast && sm.grid[1].fast && sm.grid[2].fast;
+    auto encode = [&](double px, double py, double pz) -> Key { return encode_key<CURVE>(sm, fast, px, py, pz); };
 
-    auto encode = [&](double px, double py, double pz) -> Key {
-        u64 m;
-        if (fast)
-            m = morton_of(grid_cell_fixed(px, gx), grid_cell_fixed(py, gy), grid_cell_fixed(pz, gz));
-        else
-            m = morton_of(grid_cell(px, gx.lo, gx.scale), grid_cell(py, gy.lo, gy.scale),
-                          grid_cell(pz, gz.lo, gz.scale));
-        if (CURVE == CSTONE_HILBERT) return to_key(hilbert_of(m, s_t1, s_t2));
-        return to_key(m);
-    };
-
-    if (REC) {
-        const FixedFrame fr = s_frame;
-        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-            const double px = __ldcs(x + i), py = __ldcs(y + i), pz = __ldcs(z + i);
-            keys[i] = encode(px, py, pz);
-            if (!store_record(rec, static_cast<u32>(i), px, py, pz, __ldcs(m + i), fr))
-                raise_error(hdr, CSTONE_ERR_INVALID_ARG, static_cast<u32>(i));
-        }
-        return;
-    }
     if (!VEC) {
         for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
             keys[i] = encode(__ldcs(x + i), __ldcs(y + i), __ldcs(z + i));
@@ -314,6 +307,55 @@ __global__ void __launch_bounds__(256) keys_kernel(const double* __restrict__ x,
     if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
         long long i = n - 1;
         keys[i] = encode(x[i], y[i], z[i]);
+    }
+}
+
+// Keys and each particle's multipole record (fixed-point position and mass, records.cuh) from
+// the same read of the coordinates. A warp takes 64 consecutive particles, lane l the particles
+// l and l + 32: both halves keep the warp's loads and stores contiguous (a warp's two 16-byte
+// record stores cover 1 KB), and the two encodings interleave.
+#ifndef CSTONE_KEYS_REC_MIN_BLOCKS
+#define CSTONE_KEYS_REC_MIN_BLOCKS 3
+#endif
+template <int CURVE>
+__global__ void __launch_bounds__(256, CSTONE_KEYS_REC_MIN_BLOCKS)
+    keys_records_kernel(const double* __restrict__ x, const double* __restrict__ y, const double* __restrict__ z,
+                        const float* __restrict__ m, long long n, const double* __restrict__ box,
+                        Key* __restrict__ keys, Record* __restrict__ rec, WsHeader* hdr,
+                        const __grid_constant__ HilbertTable table) {
+    __shared__ KeySmem sm;
+    __shared__ FixedFrame s_frame;
+    load_key_smem<CURVE>(sm, table, box);
+    if (threadIdx.x == 32) s_frame = make_frame(box);
+    __syncthreads();
+    const bool fast = sm.grid[0].fast && sm.grid[1].fast && sm.grid[2].fast;
+    const FixedFrame fr = s_frame;
+    const long long lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long base = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 64; base < n;
+         base += warps * 64) {
+        const long long i0 = base + lane, i1 = base + 32 + lane;
+        if (i0 >= n) break;
+        const bool ok1 = i1 < n;
+        const double ax = __ldcs(x + i0), ay = __ldcs(y + i0), az = __ldcs(z + i0);
+        const float am = __ldcs(m + i0);
+        double bx = 0.0, by = 0.0, bz = 0.0;
+        float bm = 0.f;
+        if (ok1) {
+            bx = __ldcs(x + i1);
+            by = __ldcs(y + i1);
+            bz = __ldcs(z + i1);
+            bm = __ldcs(m + i1);
+        }
+        const Key k0 = encode_key<CURVE>(sm, fast, ax, ay, az), k1 = encode_key<CURVE>(sm, fast, bx, by, bz);
+        keys[i0] = k0;
+        if (!store_record(rec, static_cast<u32>(i0), ax, ay, az, am, fr))
+            raise_error(hdr, CSTONE_ERR_INVALID_ARG, static_cast<u32>(i0));
+        if (ok1) {
+            keys[i1] = k1;
+            if (!store_record(rec, static_cast<u32>(i1), bx, by, bz, bm, fr))
+                raise_error(hdr, CSTONE_ERR_INVALID_ARG, static_cast<u32>(i1));
+        }
     }
 }
 
@@ -553,19 +595,16 @@ int launch_keys(const double* x, const double* y, const double* z, long long n, 
     int grid = static_cast<int>(want < (long long)sm_count() * 8 ? (want > 0 ? want : 1) : (long long)sm_count() * 8);
     bool vec = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y) | reinterpret_cast<uintptr_t>(z) |
                  reinterpret_cast<uintptr_t>(keys)) & 15u) == 0;
-    const float* no_m = nullptr;
-    Record* no_rec = nullptr;
-    WsHeader* no_hdr = nullptr;
     if (curve == CSTONE_HILBERT) {
         if (vec)
-            keys_kernel<CSTONE_HILBERT, true, false><<<grid, 256, 0, st>>>(x, y, z, n, box, keys, tab, no_m, no_rec, no_hdr);
+            keys_kernel<CSTONE_HILBERT, true><<<grid, 256, 0, st>>>(x, y, z, n, box, keys, tab);
         else
-            keys_kernel<CSTONE_HILBERT, false, false><<<grid, 256, 0, st>>>(x, y, z, n, box, keys, tab, no_m, no_rec, no_hdr);
+            keys_kernel<CSTONE_HILBERT, false><<<grid, 256, 0, st>>>(x, y, z, n, box, keys, tab);
     } else {
         if (vec)
-            keys_kernel<CSTONE_MORTON, true, false><<<grid, 256, 0, st>>>(x, y, z, n, box, keys, tab, no_m, no_rec, no_hdr);
+            keys_kernel<CSTONE_MORTON, true><<<grid, 256, 0, st>>>(x, y, z, n, box, keys, tab);
         else
-            keys_kernel<CSTONE_MORTON, false, false><<<grid, 256, 0, st>>>(x, y, z, n, box, keys, tab, no_m, no_rec, no_hdr);
+            keys_kernel<CSTONE_MORTON, false><<<grid, 256, 0, st>>>(x, y, z, n, box, keys, tab);
     }
     CST_LAUNCHED("keys_kernel");
     return CSTONE_OK;
@@ -578,13 +617,13 @@ int launch_keys_records(const double* x, const double* y, const double* z, const
     CST_CUDA(cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st));
     if (n == 0) return CSTONE_OK;
     const HilbertTable& tab = hilbert_table();
-    long long want = (n + 255) / 256;
+    long long want = (n + 511) / 512;  // 64 particles per warp and step
     int grid = static_cast<int>(want < (long long)sm_count() * 8 ? (want > 0 ? want : 1) : (long long)sm_count() * 8);
     if (curve == CSTONE_HILBERT)
-        keys_kernel<CSTONE_HILBERT, false, true><<<grid, 256, 0, st>>>(x, y, z, n, box, keys, tab, m, rec, hdr);
+        keys_records_kernel<CSTONE_HILBERT><<<grid, 256, 0, st>>>(x, y, z, m, n, box, keys, rec, hdr, tab);
     else
-        keys_kernel<CSTONE_MORTON, false, true><<<grid, 256, 0, st>>>(x, y, z, n, box, keys, tab, m, rec, hdr);
-    CST_LAUNCHED("keys_kernel");
+        keys_records_kernel<CSTONE_MORTON><<<grid, 256, 0, st>>>(x, y, z, m, n, box, keys, rec, hdr, tab);
+    CST_LAUNCHED("keys_records_kernel");
     return CSTONE_OK;
 }
 
