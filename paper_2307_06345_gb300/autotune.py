@@ -27,7 +27,8 @@ from . import _build
 
 SORT_CANDIDATES = [{"threads": 256, "items": i, "min_blocks": b}
                    for i, b in ((8, 5), (10, 4), (12, 4), (14, 3), (16, 3))]
-LEAVES_CANDIDATES = [{"items": i} for i in (4, 8, 12, 16)]
+# the leaf loop stages a tile of elements in shared memory: more than 8 per thread exceeds 48 KB
+LEAVES_CANDIDATES = [{"items": i} for i in (4, 6, 8)]
 
 P = ctypes.c_void_p
 i64, i32, u32, sz = ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32, ctypes.c_size_t

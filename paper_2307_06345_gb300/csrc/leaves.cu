@@ -32,6 +32,7 @@ constexpr int kThreads = 256;
 #endif
 constexpr int kItems = CSTONE_LEAVES_ITEMS;
 constexpr int kTile = kThreads * kItems;  // elements per tile
+static_assert(kItems <= 8, "the staged tile (keys, positions, sets, ops, offsets) must fit 48 KB of shared memory");
 constexpr int kMaxIters = 256;
 constexpr int kSplitChunks = 16;                 // keys per lane loaded at once when counting a split
 constexpr u32 kLinearSplit = 32 * kSplitChunks;  // split ranges up to this size are counted, not searched
@@ -84,23 +85,23 @@ __device__ __forceinline__ u32 lower_bound_in(const Key* __restrict__ P, u32 lo,
 // Eq. (g1) for element e of ne. The end key 8^L of a set is kept. A leaf splits when N > ncrit
 // (a single key at depth L stays); the octants 1..7 of a parent whose 8 children are consecutive
 // leaves of one set holding <= ncrit in total are merged away (octant 0 keeps its key, which is
-// the parent's); anything else is kept. K, pos and set were written by other blocks in the
-// previous pass, so they are read through L2 (__ldcg), never through a read-only cache.
+// the parent's); anything else is kept. K, pos and set are the tile's staged window in shared
+// memory: element e sits at index e - h0.
 template <bool BATCH>
-__device__ __forceinline__ u32 decide(const Key* K, const u32* pos, const u32* set, u32 e, u32 ne, u32 ncrit) {
-    const Key ke = __ldcg(K + e);
+__device__ __forceinline__ u32 decide(const Key* K, const u32* pos, const u32* set, u32 e, u32 ne, u32 ncrit,
+                                      long long h0) {
+    const long long i = (long long)e - h0;
+    const Key ke = K[i];
     if (ke == kKeyEnd) return 1u;
-    const Key delta = __ldcg(K + e + 1) - ke;
-    const u32 cnt = __ldcg(pos + e + 1) - __ldcg(pos + e);
+    const Key delta = K[i + 1] - ke;
+    const u32 cnt = pos[i + 1] - pos[i];
     if (cnt > ncrit && delta > 1ULL) return 8u;
     if (delta < kKeyEnd) {
         const u32 j = static_cast<u32>((ke >> key_ffs(delta)) & 7u);
         if (j >= 1u && j <= e && e - j + 8u < ne) {
-            const u32 first = e - j;
-            if (!BATCH || (__ldcg(set + first) == __ldcg(set + e) && __ldcg(set + first + 8) == __ldcg(set + e)))
-                if (__ldcg(K + first) + static_cast<Key>(8) * delta == __ldcg(K + first + 8) &&
-                    __ldcg(pos + first + 8) - __ldcg(pos + first) <= ncrit)
-                    return 0u;
+            const long long f = i - j;
+            if (!BATCH || (set[f] == set[i] && set[f + 8] == set[i]))
+                if (K[f] + static_cast<Key>(8) * delta == K[f + 8] && pos[f + 8] - pos[f] <= ncrit) return 0u;
         }
     }
     return 1u;
@@ -147,6 +148,12 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const Key* __rest
     __shared__ u32 s_tile;
     __shared__ u64 s_prefix;
     __shared__ int s_any;
+    // the tile's elements with a halo of kHalo on each side (the merge test reads up to 7 back
+    // and 8 ahead, the split and count tests one ahead), staged once per tile
+    constexpr int kHalo = 8;
+    __shared__ Key s_K[kTile + 2 * kHalo];
+    __shared__ u32 s_pos[kTile + 2 * kHalo];
+    __shared__ u32 s_set[BATCH ? kTile + 2 * kHalo : 1];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const u32 gtid = blockIdx.x * kThreads + tid, gthreads = gridDim.x * kThreads;
 
@@ -222,13 +229,25 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const Key* __rest
             __syncthreads();
             if (tile >= ntiles) break;
 
-            // g1, striped: item j of the tile is element tile * kTile + j, handled by thread j % kThreads
+            // stage the tile's window (written by other blocks in the previous pass: read through
+            // L2, never through a read-only cache), then g1, striped: item j of the tile is element
+            // tile * kTile + j, handled by thread j % kThreads
             const u32 t0 = tile * kTile;
+            const long long h0 = (long long)t0 - kHalo;
+            for (int i = tid; i < kTile + 2 * kHalo; i += kThreads) {
+                const long long e = h0 + i;
+                if (e >= 0 && e < ne) {
+                    s_K[i] = __ldcg(K + e);
+                    s_pos[i] = __ldcg(pos + e);
+                    if (BATCH) s_set[i] = __ldcg(set + e);
+                }
+            }
+            __syncthreads();
 #pragma unroll
             for (int k = 0; k < kItems; ++k) {
                 const u32 j = k * kThreads + tid;
                 const u32 e = t0 + j;
-                const u32 o = (e < ne) ? decide<BATCH>(K, pos, set, e, ne, ncrit) : 0u;
+                const u32 o = (e < ne) ? decide<BATCH>(s_K, s_pos, s_set, e, ne, ncrit, h0) : 0u;
                 if (e < ne && o != 1u) any_change = 1;
                 s_op[j] = static_cast<unsigned char>(o);
             }
@@ -309,9 +328,9 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const Key* __rest
                 const u32 o = s_op[j];
                 if (o == 1u) {
                     if (o_pos < ecap) {
-                        Kn[o_pos] = K[e];
-                        posn[o_pos] = pos[e];
-                        if (BATCH) setn[o_pos] = set[e];
+                        Kn[o_pos] = s_K[j + kHalo];
+                        posn[o_pos] = s_pos[j + kHalo];
+                        if (BATCH) setn[o_pos] = s_set[j + kHalo];
                     }
                     if (e == ne - 1) {  // the last element is an end key: the new element count
                         const u64 ne_next = o_pos + 1;
@@ -322,15 +341,15 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const Key* __rest
                         }
                     }
                 } else if (o == 8u) {
-                    const Key ke = K[e];
-                    const Key step = (K[e + 1] - ke) >> 3;
+                    const Key ke = s_K[j + kHalo];
+                    const Key step = (s_K[j + kHalo + 1] - ke) >> 3;
                     if (o_pos + 8 <= ecap) {
 #pragma unroll
                         for (int c = 0; c < 8; ++c) {
                             Kn[o_pos + c] = ke + static_cast<Key>(c) * step;
-                            if (BATCH) setn[o_pos + c] = set[e];
+                            if (BATCH) setn[o_pos + c] = s_set[j + kHalo];
                         }
-                        posn[o_pos] = pos[e];
+                        posn[o_pos] = s_pos[j + kHalo];
                     }
                     s_split[atomicAdd(&s_nsplit, 1u)] = static_cast<unsigned short>(j);
                 }
