@@ -138,12 +138,12 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-# DRAM bytes per particle of the sort (histogram, per-pass tile counts and scans, 8 passes) and of
-# the multipole upsweep (leaf sums and levels; the records come from the key pass), measured with
-# ncu (dram__bytes_read.sum + dram__bytes_write.sum over the phase's launches) on 2^24 particles of
-# the same workload and scaled by the particle count (both phases stream or gather per particle,
-# so traffic grows with n): profiles/kernels_clumps_2p24_full.md.
-MEASURED_DRAM_BYTES_PER_PARTICLE = {"sort": 243.4, "multipoles": 135.6}
+# DRAM bytes per particle of the sort (histogram, per-pass tile counts and scans, 8 passes), of the
+# key pass with multipole records, and of the multipole upsweep (leaf sums and levels), measured
+# with ncu (dram__bytes_read.sum + dram__bytes_write.sum over the phase's launches) on 2^24
+# particles of the same workload and scaled by the particle count (these phases stream or gather
+# per particle, so traffic grows with n): profiles/kernels_clumps_2p24_full.md.
+MEASURED_DRAM_BYTES_PER_PARTICLE = {"sort": 243.2, "keys": 64.5, "multipoles": 135.7}
 
 
 def algorithmic_bytes(n: int, n_leaves: int, iter_leaves: int, n_nodes: int):
