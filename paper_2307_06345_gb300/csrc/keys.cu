@@ -180,7 +180,9 @@ __device__ __forceinline__ long long to_fixed(double x, int F) {
     return (b >> 63) ? -static_cast<long long>(mag) : static_cast<long long>(mag);
 }
 
-__device__ FixedGrid make_fixed_grid(double lo, double side) {
+// F_frame != 0: take that fixed-point exponent (a frame shared with other arrays) instead of the
+// axis' own; the fast path is then enabled only where its error bound holds for it.
+__device__ FixedGrid make_fixed_grid(double lo, double side, int F_frame = 0) {
     FixedGrid f;
     f.lo = lo;
     f.scale = __ddiv_rn(2097152.0, side);
@@ -189,7 +191,7 @@ __device__ FixedGrid make_fixed_grid(double lo, double side) {
     f.hi_ord = order_bits(hi);
     // 2^E > max(|lo|, |hi|)
     const int e_max = max(exponent_of(lo), exponent_of(hi)) - 1023 + 1;
-    f.F = 61 - e_max;
+    f.F = F_frame != 0 && F_frame <= 61 - e_max ? F_frame : 61 - e_max;
     const int es = exponent_of(f.scale) - 1023 - 52;  // scale = mantissa * 2^es
     const int G = 11 - es;
     f.R = f.F + G - 64;
@@ -201,11 +203,14 @@ __device__ FixedGrid make_fixed_grid(double lo, double side) {
     return f;
 }
 
-__device__ __forceinline__ u32 grid_cell_fixed(double x, const FixedGrid& f) {
+// X: trunc(x * 2^F) when already known (the record-writing pass shares it with the record), or
+// computed here (only for x inside the box, where it cannot overflow).
+template <bool HAVE_X = false>
+__device__ __forceinline__ u32 grid_cell_fixed(double x, const FixedGrid& f, long long X = 0) {
     const u64 o = order_bits(x);
     if (o <= f.lo_ord) return 0u;
     if (o >= f.hi_ord) return 2097151u;
-    const u64 d = static_cast<u64>(to_fixed(x, f.F) - f.lo_fixed);
+    const u64 d = static_cast<u64>((HAVE_X ? X : to_fixed(x, f.F)) - f.lo_fixed);
     const u64 u = __umul64hi(d, f.scale_fixed);
     const u32 frac20 = static_cast<u32>(u >> (f.R - 20)) & 0xfffffu;
     if (frac20 == 0u || frac20 == 0xfffffu) return grid_cell(x, f.lo, f.scale);
@@ -256,19 +261,23 @@ struct KeySmem {
 };
 
 template <int CURVE>
-__device__ __forceinline__ void load_key_smem(KeySmem& sm, const HilbertTable& table, const double* box) {
+__device__ __forceinline__ void load_key_smem(KeySmem& sm, const HilbertTable& table, const double* box,
+                                              bool record_frame = false) {
     if (CURVE == CSTONE_HILBERT) {
         for (int i = threadIdx.x; i < kHilbertStates * 64; i += blockDim.x) sm.t2[i] = table.two[i];
         for (int i = threadIdx.x; i < kHilbertStates * 8; i += blockDim.x) sm.t1[i] = table.one[i];
     }
-    if (threadIdx.x < 3) sm.grid[threadIdx.x] = make_fixed_grid(box[threadIdx.x], box[3]);
+    if (threadIdx.x < 3)
+        sm.grid[threadIdx.x] = make_fixed_grid(box[threadIdx.x], box[3], record_frame ? make_frame(box).F : 0);
 }
 
-template <int CURVE>
-__device__ __forceinline__ Key encode_key(const KeySmem& sm, bool fast, double px, double py, double pz) {
+template <int CURVE, bool HAVE_X = false>
+__device__ __forceinline__ Key encode_key(const KeySmem& sm, bool fast, double px, double py, double pz,
+                                          long long X = 0, long long Y = 0, long long Z = 0) {
     u64 m;
     if (fast)
-        m = morton_of(grid_cell_fixed(px, sm.grid[0]), grid_cell_fixed(py, sm.grid[1]), grid_cell_fixed(pz, sm.grid[2]));
+        m = morton_of(grid_cell_fixed<HAVE_X>(px, sm.grid[0], X), grid_cell_fixed<HAVE_X>(py, sm.grid[1], Y),
+                      grid_cell_fixed<HAVE_X>(pz, sm.grid[2], Z));
     else
         m = morton_of(grid_cell(px, sm.grid[0].lo, sm.grid[0].scale), grid_cell(py, sm.grid[1].lo, sm.grid[1].scale),
                       grid_cell(pz, sm.grid[2].lo, sm.grid[2].scale));
@@ -325,13 +334,31 @@ __global__ void __launch_bounds__(256, CSTONE_KEYS_REC_MIN_BLOCKS)
                         const __grid_constant__ HilbertTable table) {
     __shared__ KeySmem sm;
     __shared__ FixedFrame s_frame;
-    load_key_smem<CURVE>(sm, table, box);
+    load_key_smem<CURVE>(sm, table, box, true);  // the grids take the records' fixed-point frame
     if (threadIdx.x == 32) s_frame = make_frame(box);
     __syncthreads();
-    const bool fast = sm.grid[0].fast && sm.grid[1].fast && sm.grid[2].fast;
+    // the fixed-point coordinate serves the record and, where the fast path is on, the grid cell
+    const bool fast = sm.grid[0].fast && sm.grid[1].fast && sm.grid[2].fast && sm.grid[0].F == s_frame.F &&
+                      sm.grid[1].F == s_frame.F && sm.grid[2].F == s_frame.F;
     const FixedFrame fr = s_frame;
     const long long lane = threadIdx.x & 31;
     const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    auto fixed = [&](double v, bool& in) -> long long {
+        const bool ok = static_cast<int>((static_cast<u64>(__double_as_longlong(v)) >> 52) & 0x7ffu) < fr.e_lim;
+        in = in && ok;
+        return ok ? fixed_of(v, fr.F) : 0;
+    };
+    auto one = [&](long long i, double px, double py, double pz, float pm) -> Key {
+        bool in = true;
+        const long long X = fixed(px, in), Y = fixed(py, in), Z = fixed(pz, in);
+        const Key k = fast ? encode_key<CURVE, true>(sm, true, px, py, pz, X, Y, Z)
+                           : encode_key<CURVE>(sm, false, px, py, pz);
+        longlong2* dst = reinterpret_cast<longlong2*>(rec + i);
+        __stcs(dst, make_longlong2(in ? X : 0, in ? Y : 0));
+        __stcs(dst + 1, make_longlong2(in ? Z : 0, static_cast<long long>(__float_as_uint(pm))));
+        if (!in) raise_error(hdr, CSTONE_ERR_INVALID_ARG, static_cast<u32>(i));
+        return k;
+    };
     for (long long base = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 64; base < n;
          base += warps * 64) {
         const long long i0 = base + lane, i1 = base + 32 + lane;
@@ -347,15 +374,8 @@ __global__ void __launch_bounds__(256, CSTONE_KEYS_REC_MIN_BLOCKS)
             bz = __ldcs(z + i1);
             bm = __ldcs(m + i1);
         }
-        const Key k0 = encode_key<CURVE>(sm, fast, ax, ay, az), k1 = encode_key<CURVE>(sm, fast, bx, by, bz);
-        keys[i0] = k0;
-        if (!store_record(rec, static_cast<u32>(i0), ax, ay, az, am, fr))
-            raise_error(hdr, CSTONE_ERR_INVALID_ARG, static_cast<u32>(i0));
-        if (ok1) {
-            keys[i1] = k1;
-            if (!store_record(rec, static_cast<u32>(i1), bx, by, bz, bm, fr))
-                raise_error(hdr, CSTONE_ERR_INVALID_ARG, static_cast<u32>(i1));
-        }
+        keys[i0] = one(i0, ax, ay, az, am);
+        if (ok1) keys[i1] = one(i1, bx, by, bz, bm);
     }
 }
 
