@@ -253,36 +253,72 @@ __device__ __forceinline__ u64 hilbert_of(u64 m, const unsigned short* t1, const
     return key;
 }
 
-// Hilbert tables and the three fixed-point grids of the box in shared memory (both key kernels).
+// The three fixed-point grids of the box and the one-level Hilbert table in shared memory (both
+// key kernels); Hilbert keys also use a three-level table in dynamic shared memory, indexed by the
+// state and 3 bits of each coordinate's cell (3 levels, x bits above y bits above z bits), so a key
+// takes 7 lookups and no Morton interleave. Each block builds it from the one-level table.
 struct KeySmem {
-    unsigned short t2[kHilbertStates * 64];
     unsigned short t1[kHilbertStates * 8];
     FixedGrid grid[3];
 };
+constexpr int kHilbert3Entries = kHilbertStates * 512;
+constexpr size_t kHilbert3Bytes = kHilbert3Entries * sizeof(unsigned short);  // 48 KB
 
 template <int CURVE>
-__device__ __forceinline__ void load_key_smem(KeySmem& sm, const HilbertTable& table, const double* box,
-                                              bool record_frame = false) {
-    if (CURVE == CSTONE_HILBERT) {
-        for (int i = threadIdx.x; i < kHilbertStates * 64; i += blockDim.x) sm.t2[i] = table.two[i];
+__device__ __forceinline__ void load_key_smem(KeySmem& sm, unsigned short* t3, const HilbertTable& table,
+                                              const double* box, bool record_frame = false) {
+    if (CURVE == CSTONE_HILBERT)
         for (int i = threadIdx.x; i < kHilbertStates * 8; i += blockDim.x) sm.t1[i] = table.one[i];
-    }
     if (threadIdx.x < 3)
         sm.grid[threadIdx.x] = make_fixed_grid(box[threadIdx.x], box[3], record_frame ? make_frame(box).F : 0);
+    if (CURVE == CSTONE_HILBERT) {
+        __syncthreads();
+        // entry (state, x3 y3 z3): three one-level steps, the octant of each level taken from the
+        // top remaining bit of x3, y3, z3 (x most significant, as in the Morton interleave)
+        for (int e = threadIdx.x; e < kHilbert3Entries; e += blockDim.x) {
+            const int idx = e & 511;
+            u32 state = static_cast<u32>(e >> 9), digits = 0;
+#pragma unroll
+            for (int lv = 2; lv >= 0; --lv) {
+                const u32 o = (((idx >> (6 + lv)) & 1u) << 2) | (((idx >> (3 + lv)) & 1u) << 1) | ((idx >> lv) & 1u);
+                const u32 v = sm.t1[state * 8u + o];
+                digits = (digits << 3) | (v & 7u);
+                state = v >> 3;
+            }
+            t3[e] = static_cast<unsigned short>(digits | (state << 9));
+        }
+    }
+}
+
+// 63-bit Hilbert key of a cell from the three-level table: 7 steps of 3 levels.
+__device__ __forceinline__ u64 hilbert_of_cell(u32 gx, u32 gy, u32 gz, const unsigned short* t3) {
+    u64 key = 0;
+    u32 state = 0;
+#pragma unroll
+    for (int sh = 18; sh >= 0; sh -= 3) {
+        const u32 idx = (((gx >> sh) & 7u) << 6) | (((gy >> sh) & 7u) << 3) | ((gz >> sh) & 7u);
+        const u32 v = t3[state * 512u + idx];
+        key = (key << 9) | (v & 511u);
+        state = v >> 9;
+    }
+    return key;
 }
 
 template <int CURVE, bool HAVE_X = false>
-__device__ __forceinline__ Key encode_key(const KeySmem& sm, bool fast, double px, double py, double pz,
-                                          long long X = 0, long long Y = 0, long long Z = 0) {
-    u64 m;
-    if (fast)
-        m = morton_of(grid_cell_fixed<HAVE_X>(px, sm.grid[0], X), grid_cell_fixed<HAVE_X>(py, sm.grid[1], Y),
-                      grid_cell_fixed<HAVE_X>(pz, sm.grid[2], Z));
-    else
-        m = morton_of(grid_cell(px, sm.grid[0].lo, sm.grid[0].scale), grid_cell(py, sm.grid[1].lo, sm.grid[1].scale),
-                      grid_cell(pz, sm.grid[2].lo, sm.grid[2].scale));
-    if (CURVE == CSTONE_HILBERT) return to_key(hilbert_of(m, sm.t1, sm.t2));
-    return to_key(m);
+__device__ __forceinline__ Key encode_key(const KeySmem& sm, const unsigned short* t3, bool fast, double px,
+                                          double py, double pz, long long X = 0, long long Y = 0, long long Z = 0) {
+    u32 gx, gy, gz;
+    if (fast) {
+        gx = grid_cell_fixed<HAVE_X>(px, sm.grid[0], X);
+        gy = grid_cell_fixed<HAVE_X>(py, sm.grid[1], Y);
+        gz = grid_cell_fixed<HAVE_X>(pz, sm.grid[2], Z);
+    } else {
+        gx = grid_cell(px, sm.grid[0].lo, sm.grid[0].scale);
+        gy = grid_cell(py, sm.grid[1].lo, sm.grid[1].scale);
+        gz = grid_cell(pz, sm.grid[2].lo, sm.grid[2].scale);
+    }
+    if (CURVE == CSTONE_HILBERT) return to_key(hilbert_of_cell(gx, gy, gz, t3));
+    return to_key(morton_of(gx, gy, gz));
 }
 
 template <int CURVE, bool VEC>
@@ -291,10 +327,11 @@ __global__ void __launch_bounds__(256) keys_kernel(const double* __restrict__ x,
                                                    const double* __restrict__ box, Key* __restrict__ keys,
                                                    const __grid_constant__ HilbertTable table) {
     __shared__ KeySmem sm;
-    load_key_smem<CURVE>(sm, table, box);
+    extern __shared__ unsigned short t3[];  // kHilbert3Bytes for Hilbert keys
+    load_key_smem<CURVE>(sm, t3, table, box);
     __syncthreads();
     const bool fast = sm.grid[0].fast && sm.grid[1].fast && sm.grid[2].fast;
-    auto encode = [&](double px, double py, double pz) -> Key { return encode_key<CURVE>(sm, fast, px, py, pz); };
+    auto encode = [&](double px, double py, double pz) -> Key { return encode_key<CURVE>(sm, t3, fast, px, py, pz); };
 
     if (!VEC) {
         for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -334,7 +371,8 @@ __global__ void __launch_bounds__(256, CSTONE_KEYS_REC_MIN_BLOCKS)
                         const __grid_constant__ HilbertTable table) {
     __shared__ KeySmem sm;
     __shared__ FixedFrame s_frame;
-    load_key_smem<CURVE>(sm, table, box, true);  // the grids take the records' fixed-point frame
+    extern __shared__ unsigned short t3[];  // kHilbert3Bytes for Hilbert keys
+    load_key_smem<CURVE>(sm, t3, table, box, true);  // the grids take the records' fixed-point frame
     if (threadIdx.x == 32) s_frame = make_frame(box);
     __syncthreads();
     // the fixed-point coordinate serves the record and, where the fast path is on, the grid cell
@@ -351,8 +389,8 @@ __global__ void __launch_bounds__(256, CSTONE_KEYS_REC_MIN_BLOCKS)
     auto one = [&](long long i, double px, double py, double pz, float pm) -> Key {
         bool in = true;
         const long long X = fixed(px, in), Y = fixed(py, in), Z = fixed(pz, in);
-        const Key k = fast ? encode_key<CURVE, true>(sm, true, px, py, pz, X, Y, Z)
-                           : encode_key<CURVE>(sm, false, px, py, pz);
+        const Key k = fast ? encode_key<CURVE, true>(sm, t3, true, px, py, pz, X, Y, Z)
+                           : encode_key<CURVE>(sm, t3, false, px, py, pz);
         longlong2* dst = reinterpret_cast<longlong2*>(rec + i);
         __stcs(dst, make_longlong2(in ? X : 0, in ? Y : 0));
         __stcs(dst + 1, make_longlong2(in ? Z : 0, static_cast<long long>(__float_as_uint(pm))));
@@ -615,11 +653,15 @@ int launch_keys(const double* x, const double* y, const double* z, long long n, 
     int grid = static_cast<int>(want < (long long)sm_count() * 8 ? (want > 0 ? want : 1) : (long long)sm_count() * 8);
     bool vec = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y) | reinterpret_cast<uintptr_t>(z) |
                  reinterpret_cast<uintptr_t>(keys)) & 15u) == 0;
-    if (curve == CSTONE_HILBERT) {
+    if (curve == CSTONE_HILBERT) {  // the three-level table takes 48 KB of dynamic shared memory
+        CST_CUDA(cudaFuncSetAttribute(keys_kernel<CSTONE_HILBERT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      static_cast<int>(kHilbert3Bytes)));
+        CST_CUDA(cudaFuncSetAttribute(keys_kernel<CSTONE_HILBERT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      static_cast<int>(kHilbert3Bytes)));
         if (vec)
-            keys_kernel<CSTONE_HILBERT, true><<<grid, 256, 0, st>>>(x, y, z, n, box, keys, tab);
+            keys_kernel<CSTONE_HILBERT, true><<<grid, 256, kHilbert3Bytes, st>>>(x, y, z, n, box, keys, tab);
         else
-            keys_kernel<CSTONE_HILBERT, false><<<grid, 256, 0, st>>>(x, y, z, n, box, keys, tab);
+            keys_kernel<CSTONE_HILBERT, false><<<grid, 256, kHilbert3Bytes, st>>>(x, y, z, n, box, keys, tab);
     } else {
         if (vec)
             keys_kernel<CSTONE_MORTON, true><<<grid, 256, 0, st>>>(x, y, z, n, box, keys, tab);
@@ -640,7 +682,10 @@ int launch_keys_records(const double* x, const double* y, const double* z, const
     long long want = (n + 511) / 512;  // 64 particles per warp and step
     int grid = static_cast<int>(want < (long long)sm_count() * 8 ? (want > 0 ? want : 1) : (long long)sm_count() * 8);
     if (curve == CSTONE_HILBERT)
-        keys_records_kernel<CSTONE_HILBERT><<<grid, 256, 0, st>>>(x, y, z, m, n, box, keys, rec, hdr, tab);
+        CST_CUDA(cudaFuncSetAttribute(keys_records_kernel<CSTONE_HILBERT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      static_cast<int>(kHilbert3Bytes)));
+    if (curve == CSTONE_HILBERT)
+        keys_records_kernel<CSTONE_HILBERT><<<grid, 256, kHilbert3Bytes, st>>>(x, y, z, m, n, box, keys, rec, hdr, tab);
     else
         keys_records_kernel<CSTONE_MORTON><<<grid, 256, 0, st>>>(x, y, z, m, n, box, keys, rec, hdr, tab);
     CST_LAUNCHED("keys_records_kernel");
