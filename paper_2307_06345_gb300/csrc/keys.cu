@@ -129,8 +129,7 @@ __global__ void bbox_finalize_kernel(const BoxAcc* acc, long long n, double* box
 
 // ---------------------------------------------------------------------------------- grid + keys
 struct HilbertTable {
-    unsigned short two[kHilbertStates * 64];  // (state, 2 octants) -> 6 digit bits | next << 6
-    unsigned short one[kHilbertStates * 8];   // (state, 1 octant)  -> 3 digit bits | next << 3
+    unsigned short one[kHilbertStates * 8];  // (state, 1 octant) -> 3 digit bits | next << 3
 };
 
 // Cell index of one coordinate: floor((x - lo) * scale) clamped to [0, 2^21 - 1], with the
@@ -238,21 +237,6 @@ __device__ __forceinline__ u64 morton_of(u32 gx, u32 gy, u32 gz) {
 // because the grid scales differ by a power of two).
 __device__ __forceinline__ Key to_key(u64 k63) { return static_cast<Key>(k63 >> (63 - kKeyBits)); }
 
-// Hilbert key from the Morton interleave: the top level through the one-level table, then the
-// remaining 20 levels two at a time.
-__device__ __forceinline__ u64 hilbert_of(u64 m, const unsigned short* t1, const unsigned short* t2) {
-    u32 e = t1[(m >> 60) & 7u];  // initial state 0
-    u64 key = e & 7u;
-    u32 state = e >> 3;
-#pragma unroll
-    for (int sh = 54; sh >= 0; sh -= 6) {
-        u32 e2 = t2[state * 64u + static_cast<u32>((m >> sh) & 63u)];
-        key = (key << 6) | (e2 & 63u);
-        state = e2 >> 6;
-    }
-    return key;
-}
-
 // The three fixed-point grids of the box and the one-level Hilbert table in shared memory (both
 // key kernels); Hilbert keys also use a three-level table in dynamic shared memory, indexed by the
 // state and 3 bits of each coordinate's cell (3 levels, x bits above y bits above z bits), so a key
@@ -266,10 +250,10 @@ constexpr size_t kHilbert3Bytes = kHilbert3Entries * sizeof(unsigned short);  //
 
 template <int CURVE>
 __device__ __forceinline__ void load_key_smem(KeySmem& sm, unsigned short* t3, const HilbertTable& table,
-                                              const double* box, bool record_frame = false) {
+                                              const double* box, bool record_frame = false, bool grids = true) {
     if (CURVE == CSTONE_HILBERT)
         for (int i = threadIdx.x; i < kHilbertStates * 8; i += blockDim.x) sm.t1[i] = table.one[i];
-    if (threadIdx.x < 3)
+    if (grids && threadIdx.x < 3)
         sm.grid[threadIdx.x] = make_fixed_grid(box[threadIdx.x], box[3], record_frame ? make_frame(box).F : 0);
     if (CURVE == CSTONE_HILBERT) {
         __syncthreads();
@@ -479,12 +463,6 @@ const HilbertTable& hilbert_table() {
         for (int s = 0; s < kHilbertStates; ++s) {
             for (int o = 0; o < 8; ++o)
                 table.one[s * 8 + o] = static_cast<unsigned short>(digit1[s][o] | (next1[s][o] << 3));
-            for (int hi = 0; hi < 8; ++hi)
-                for (int lo = 0; lo < 8; ++lo) {
-                    int mid = next1[s][hi];
-                    int digits = (digit1[s][hi] << 3) | digit1[mid][lo];
-                    table.two[s * 64 + hi * 8 + lo] = static_cast<unsigned short>(digits | (next1[mid][lo] << 6));
-                }
         }
     });
     return table;
@@ -574,12 +552,9 @@ __global__ void __launch_bounds__(256) keys_batched_kernel(const double* __restr
                                                            long long n, const FixedGrid* __restrict__ grids,
                                                            Key* __restrict__ keys,
                                                            const __grid_constant__ HilbertTable table) {
-    __shared__ unsigned short s_t2[kHilbertStates * 64];
-    __shared__ unsigned short s_t1[kHilbertStates * 8];
-    if (CURVE == CSTONE_HILBERT) {
-        for (int i = threadIdx.x; i < kHilbertStates * 64; i += blockDim.x) s_t2[i] = table.two[i];
-        for (int i = threadIdx.x; i < kHilbertStates * 8; i += blockDim.x) s_t1[i] = table.one[i];
-    }
+    __shared__ KeySmem sm;  // only its one-level table is used here (the grids are per set)
+    extern __shared__ unsigned short t3[];  // kHilbert3Bytes for Hilbert keys
+    if (CURVE == CSTONE_HILBERT) load_key_smem<CURVE>(sm, t3, table, nullptr, false, false);
     __syncthreads();
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const int sidx = set_of(set_offsets, n_sets, i);
@@ -592,8 +567,7 @@ __global__ void __launch_bounds__(256) keys_batched_kernel(const double* __restr
             const FixedGrid f = g[d];
             c[d] = f.fast ? grid_cell_fixed(pc[d], f) : grid_cell(pc[d], f.lo, f.scale);
         }
-        const u64 m = morton_of(c[0], c[1], c[2]);
-        keys[i] = to_key(CURVE == CSTONE_HILBERT ? hilbert_of(m, s_t1, s_t2) : m);
+        keys[i] = to_key(CURVE == CSTONE_HILBERT ? hilbert_of_cell(c[0], c[1], c[2], t3) : morton_of(c[0], c[1], c[2]));
     }
 }
 
@@ -636,8 +610,12 @@ int launch_keys_batched(const double* x, const double* y, const double* z, const
     const HilbertTable& tab = hilbert_table();
     const long long want = (n + 255) / 256;
     const int grid = static_cast<int>(want < (long long)sm_count() * 8 ? want : (long long)sm_count() * 8);
-    if (curve == CSTONE_HILBERT)
-        keys_batched_kernel<CSTONE_HILBERT><<<grid, 256, 0, st>>>(x, y, z, set_offsets, n_sets, n, grids, keys, tab);
+    if (curve == CSTONE_HILBERT) {  // the three-level table takes 48 KB of dynamic shared memory
+        CST_CUDA(cudaFuncSetAttribute(keys_batched_kernel<CSTONE_HILBERT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      static_cast<int>(kHilbert3Bytes)));
+        keys_batched_kernel<CSTONE_HILBERT><<<grid, 256, kHilbert3Bytes, st>>>(x, y, z, set_offsets, n_sets, n, grids,
+                                                                               keys, tab);
+    }
     else
         keys_batched_kernel<CSTONE_MORTON><<<grid, 256, 0, st>>>(x, y, z, set_offsets, n_sets, n, grids, keys, tab);
     CST_LAUNCHED("keys_batched_kernel");
