@@ -368,7 +368,8 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const Key* __rest
         // particle offsets of the 7 inner children of every split leaf, one warp of the whole grid per
         // split (early passes have few leaves but long particle ranges): the child of a particle is
         // one octal digit of its key, so a short range is counted with ballots over coalesced
-        // loads; a long range is binary-searched, one child boundary per lane
+        // loads; a long range is narrowed by 32 probes at once and then binary-searched, one child
+        // boundary per lane
         grid_barrier(&ls->bar, hdr);
         {
             const u32 nsplit = ld_volatile(&ls->nsplit[t]);
@@ -384,31 +385,61 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const Key* __rest
                     continue;
                 }
                 const int child_shift = key_ffs(delta) - 3;
+                const bool room = static_cast<u64>(o_pos) + 8 <= ecap;
                 u32 below = 0;  // lane c in 1..7: particles whose child digit is < c
                 if (cnt_all <= kLinearSplit) {
+                    // the child digits of the range do not decrease: the offset of child c is the first
+                    // position whose digit is >= c. Lane c first writes the range end (no particle of
+                    // digit >= c), then the lane at each digit change writes the children it opens.
                     u32 dg[kSplitChunks];
 #pragma unroll
                     for (int c = 0; c < kSplitChunks; ++c) {  // every load issued before any use
                         const u32 jj = c * 32 + lane;
                         dg[c] = jj < cnt_all ? static_cast<u32>((__ldg(P + lo + jj) >> child_shift) & 7ULL) : 8u;
                     }
+                    if (lane >= 1 && lane < 8 && room) posn[o_pos + lane] = lo + cnt_all;
+                    __syncwarp();
+                    u32 prev_last = 0;  // digit of the element before this chunk (0 before the first)
 #pragma unroll
                     for (int c = 0; c < kSplitChunks; ++c) {
                         if (c * 32 >= static_cast<int>(cnt_all)) break;
+                        const u32 up = __shfl_up_sync(0xffffffffu, dg[c], 1);
+                        const u32 before_me = lane == 0 ? prev_last : up;
+                        const u32 mine = dg[c] < 7u ? dg[c] : 7u;
+                        if (room)
+                            for (u32 d = before_me + 1; d <= mine; ++d) posn[o_pos + d] = lo + c * 32 + lane;
+                        prev_last = __shfl_sync(0xffffffffu, dg[c], 31);
+                    }
+                    continue;  // the boundaries are written
+                } else {
+                    // one round of 32 probes spread over the range: the child digits of the probes do
+                    // not decrease, so for child c the first n_c probes (digit < c) bound its offset to
+                    // (probe n_c - 1, probe n_c], about cnt_all / 33 particles; lane c then
+                    // binary-searches that interval
+                    const u32 qk = static_cast<u32>((static_cast<u64>(lane + 1) * cnt_all) / 33u);
+                    const u32 gk = static_cast<u32>((__ldg(P + lo + qk) >> child_shift) & 7ULL);
+                    u32 a = 0, hi = cnt_all;  // lane c in 1..7: its offset lies in [a, hi]
 #pragma unroll
-                        for (u32 d = 1; d < 8; ++d) {
-                            const u32 bal = __ballot_sync(0xffffffffu, dg[c] < d);
-                            if (lane == d) below += __popc(bal);
+                    for (u32 d = 1; d < 8; ++d) {
+                        const u32 nc = __popc(__ballot_sync(0xffffffffu, gk < d));
+                        const u32 q_lo = __shfl_sync(0xffffffffu, qk, nc > 0 ? nc - 1 : 0);
+                        const u32 q_hi = __shfl_sync(0xffffffffu, qk, nc < 32 ? nc : 31);
+                        if (lane == d) {
+                            a = nc > 0 ? q_lo + 1 : 0;
+                            hi = nc < 32 ? q_hi : cnt_all;
                         }
                     }
-                } else if (lane >= 1 && lane < 8) {
-                    const Key key = ke + static_cast<Key>(lane) * (delta >> 3);
-                    for (u32 st = 1u << (31 - __clz(cnt_all)); st > 0; st >>= 1) {
-                        const u32 probe = below + st;
-                        if (probe <= cnt_all && __ldg(P + lo + probe - 1) < key) below = probe;
+                    if (lane >= 1 && lane < 8) {
+                        const Key key = ke + static_cast<Key>(lane) * (delta >> 3);
+                        below = a;  // the particle before offset a (a probe of digit < c) is below key
+                        if (hi > a)
+                            for (u32 st = 1u << (31 - __clz(hi - a)); st > 0; st >>= 1) {
+                                const u32 probe = below + st;
+                                if (probe <= hi && __ldg(P + lo + probe - 1) < key) below = probe;
+                            }
                     }
                 }
-                if (lane >= 1 && lane < 8 && static_cast<u64>(o_pos) + 8 <= ecap) posn[o_pos + lane] = lo + below;
+                if (lane >= 1 && lane < 8 && room) posn[o_pos + lane] = lo + below;
             }
         }
         if (tid == 0) s_any = 0;
