@@ -87,3 +87,25 @@ def test_keys_records_argument_checks(lib):
         lib.cstone_keys_records(X, X, X, torch.zeros(n, dtype=torch.float32, device="cuda"),
                                 torch.tensor([0.0, 0, 0, 1], dtype=torch.float64, device="cuda"), 1, keys,
                                 torch.empty(16, dtype=torch.uint8, device="cuda"), lib.Workspace())
+
+
+@pytest.mark.parametrize("n", [0, 1, 31, 63, 64, 65, 129, 1000, 4097])
+def test_keys_records_sizes(lib, oracle, n):
+    # the record pass takes 64 particles per warp (lanes l and l + 32): sizes around that window
+    from paper_2307_06345_gb300 import workloads as w
+    rng = np.random.default_rng(n + 3)
+    x, y, z = rng.random(n), rng.random(n), rng.random(n)
+    m = w.lognormal_masses(n, n + 4)
+    box = np.array([0.0, 0.0, 0.0, 1.0])
+    X, Y, Z, M, B = dev(x), dev(y), dev(z), dev(m), dev(box)
+    for curve in (0, 1):
+        keys = torch.empty(n, dtype=torch.int64, device="cuda")
+        records = torch.empty(lib.records_size(n), dtype=torch.uint8, device="cuda")
+        rws = lib.Workspace()
+        lib.cstone_keys_records(X, Y, Z, M, B, curve, keys, records, rws)
+        torch.cuda.synchronize()
+        assert rws.status() == 0
+        assert np.array_equal(keys.cpu().numpy().view(np.uint64), oracle.keys(x, y, z, box, curve))
+        if n:  # the records hold the masses in order (last 8 bytes of each 32-byte record)
+            rec = records[: 32 * n].cpu().numpy().view(np.uint32).reshape(n, 8)
+            assert np.array_equal(rec[:, 6].view(np.float32), m) and not rec[:, 7].any()

@@ -48,3 +48,16 @@ def test_streamed_rejects_wrong_sets(lib):
         sb.run([(x, x, x, torch.zeros(999, dtype=torch.float32))])
     with pytest.raises(ValueError):
         sb.run([(torch.zeros(1000, dtype=torch.float64, device="cuda"),) * 3 + (torch.zeros(1000),)])
+
+
+@pytest.mark.parametrize("count", [1, 2])
+def test_streamed_short_sequences(lib, count):
+    n = 10_000
+    sets = _sets(n, count)
+    sb = lib.StreamedBuilder(n, "cuda", curve=1, ncrit=16)
+    got = {}
+    sb.run(sets, on_result=lambda k, r: got.setdefault(k, r["NK"].clone()))
+    assert sorted(got) == list(range(count))
+    for k, (x, y, z, m) in enumerate(sets):
+        ref = lib.build_octree(x.cuda(), y.cuda(), z.cuda(), curve=1, ncrit=16, masses=m.cuda())
+        assert torch.equal(got[k], ref["NK"].cpu())
