@@ -2,16 +2,19 @@
 //
 // Keys are streaming work: 24 bytes of coordinates in, 8 bytes of key out per particle. The
 // kernel reads the three coordinate arrays with 16-byte vector loads (two particles per thread
-// per step), computes the grid cell in IEEE double precision with explicitly rounded operations
-// (no FMA contraction, so the cell matches any IEEE host bit for bit) and encodes it.
+// per step), computes the grid cell with the result of IEEE double precision with explicitly
+// rounded operations (an integer fixed-point evaluation where its error bound proves the same
+// cell; no FMA contraction, so the cell matches any IEEE host bit for bit) and encodes it. With
+// masses, a second kernel also writes each particle's multipole record from the same read.
 //
 // Hilbert encoding uses a finite-state machine equivalent to J. Skilling's transpose formulation
 // of the Hilbert curve: walking the bit levels from the top, Skilling's per-level inversions and
 // exchanges act on all lower bits as a signed permutation of the axes, and the final Gray-code
 // flip of a level is the parity of the Gray-coded third axis above it. Tracking (permutation,
-// flips, parity) as a state gives 48 reachable states. The host builds a two-level table
-// (state, 6 input bits) -> (6 output bits, next state) once and passes it to the kernel as a
-// by-value parameter, so no device memory or symbol upload is involved.
+// flips, parity) as a state gives 48 reachable states. The host builds the one-level table
+// (state, octant) -> (digit, next state) once and passes it to the kernels as a by-value
+// parameter (no device memory or symbol upload); each block composes it into a three-level table
+// in shared memory, so a 21-level key takes 7 lookups.
 #include <mutex>
 
 #include "common.cuh"
