@@ -8,11 +8,12 @@
 // internal node and is skipped.
 //
 // Multipoles (four launches: pack, leaf sums, sums of the few leaves too large for one group of
-// lanes, level-by-level combination): FP32 accumulation with compensation. Each sum is a pair
-// (sum, compensation) updated with an exact two-sum step (Neumaier), and the pairs of mass and
-// second moments are carried up the tree in scratch so the compensation survives all L levels. Positions are held in 64-bit fixed point, so coordinate
-// differences are exact and are rounded to FP32 once; the expansion centre (centre of mass) is kept
-// in fixed point and written out in FP64.
+// lanes, level-by-level combination; the pack is skipped when the key pass wrote the records):
+// FP32 accumulation with compensation. Each sum is a pair (sum, compensation) updated with an exact
+// two-sum step (Neumaier), and the pairs of mass and second moments are carried up the tree in
+// scratch so the compensation survives all L levels. Positions are held in 64-bit fixed point
+// (records.cuh), so coordinate differences are exact and are rounded to FP32 once; the expansion
+// centre (centre of mass) is kept in fixed point and written out in FP64.
 // A leaf takes its first particle as the anchor for the differences, an internal node its first
 // non-empty child's centre; second moments of an internal node use the parallel-axis shift
 // Q = sum_c [Q_c + M_c (c_c - c)(c_c - c)^T].
