@@ -94,12 +94,26 @@ __global__ void __launch_bounds__(256) bbox_reduce_kernel(const double* __restri
             hi[d] = b > hi[d] ? b : hi[d];
         }
     }
-    if ((threadIdx.x & 31) == 0) {
+    // the block's warps through shared memory, then one update of the global bounds per block
+    // (all blocks update the same six words)
+    __shared__ u64 s_lo[8][3], s_hi[8][3];
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0)
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            atomicMin(&acc->lo[d], lo[d]);
-            atomicMax(&acc->hi[d], hi[d]);
+            s_lo[warp][d] = lo[d];
+            s_hi[warp][d] = hi[d];
         }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        const int d = threadIdx.x;
+        u64 l = s_lo[0][d], h = s_hi[0][d];
+        for (int w = 1; w < static_cast<int>(blockDim.x >> 5); ++w) {
+            l = s_lo[w][d] < l ? s_lo[w][d] : l;
+            h = s_hi[w][d] > h ? s_hi[w][d] : h;
+        }
+        atomicMin(&acc->lo[d], l);
+        atomicMax(&acc->hi[d], h);
     }
 }
 
