@@ -143,7 +143,7 @@ class ClockSampler:
 # with ncu (dram__bytes_read.sum + dram__bytes_write.sum over the phase's launches) on 2^24
 # particles of the same workload and scaled by the particle count (these phases stream or gather
 # per particle, so traffic grows with n): profiles/kernels_clumps_2p24_full.md.
-MEASURED_DRAM_BYTES_PER_PARTICLE = {"sort": 243.1, "keys": 64.5, "multipoles": 135.7}
+MEASURED_DRAM_BYTES_PER_PARTICLE = {"sort": 243.2, "keys": 64.5, "multipoles": 135.7}
 
 
 def algorithmic_bytes(n: int, n_leaves: int, iter_leaves: int, n_nodes: int):
