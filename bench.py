@@ -256,7 +256,7 @@ def run_ours(args, rank, world, local):
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
-        ke = max(2, min(K, 6))
+        ke = max(2, min(K, 10))
         s2, t2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         h2d, d2h = sb.run([(hx, hy, hz, hm)] * ke, events=(s2, t2))
         torch.cuda.synchronize()
