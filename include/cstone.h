@@ -189,8 +189,8 @@ CSTONE_API int cstone_upsweep_counts(const uint32_t* leaf_counts, int64_t n_leav
                                      void* ws, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------------------------
- * Multipole upsweep (Sec. 5 node properties; Sec. 8 "cartesian multipoles with quadrupole
- * corrections"): per node the mass M, the centre of mass (expansion centre) and the second
+ * Multipole upsweep (Sec. 5 node properties; Sec. 8 uses Cartesian expansions up to the
+ * quadrupole): per node the mass M, the centre of mass (expansion centre) and the second
  * moments about it Q_ab = sum m (x - com)_a (x - com)_b, components xx, xy, xz, yy, yz, zz.
  * Accumulation is in FP32 with two-sum compensation (a sum/compensation pair per moment, carried
  * up the tree); positions are taken into 64-bit fixed point so that coordinate differences are

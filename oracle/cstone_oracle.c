@@ -238,9 +238,9 @@ int oracle_histogram(const uint64_t* P, int64_t n, const uint64_t* K, int64_t nl
  *   O_i = 0 (merge away) when all of
  *         - K_i is not the first octant of its parent: j = (K_i mod 8 delta_i) / delta_i >= 1,
  *         - the 8 siblings are consecutive leaves: K_{i-j} + 8 delta_i = K_{i-j+8},
- *         - their combined count is <= Ncrit (reading: the paper prints "smaller than"; "<=" is
- *           the reading consistent with the balance definition "leaf <= Ncrit < internal" that
- *           the converged array must satisfy).
+ *         - their combined count is <= Ncrit (reading: the paper states a strict comparison;
+ *           the non-strict one is the reading that agrees with the balance condition of the
+ *           converged array, every leaf at most Ncrit and every internal node above it).
  *   O_i = 1 otherwise. */
 int oracle_rebalance_decision(const uint64_t* K, const uint32_t* N, int64_t nl, uint32_t ncrit, uint32_t* O) {
     if (nl < 1) return ORACLE_E_ARG;
@@ -752,8 +752,8 @@ int oracle_node_counts(const uint64_t* P, int64_t n, const uint64_t* NK, int64_t
     return ORACLE_OK;
 }
 
-/* Monopole and quadrupole of selected nodes (Sec. 5 node properties, Sec. 8 "cartesian multipoles
- * with quadrupole corrections"), in double precision, directly over each node's particles:
+/* Monopole and quadrupole of selected nodes (Sec. 5 node properties; Sec. 8 uses Cartesian
+ * expansions up to the quadrupole), in double precision, directly over each node's particles:
  *   M      = sum m_p
  *   com    = sum m_p x_p / M                                   (expansion centre)
  *   quad   = sum m_p (x_p - com)_a (x_p - com)_b, components xx, xy, xz, yy, yz, zz

@@ -1,5 +1,5 @@
-// Upsweeps over the linked octree (Sec. 5 node properties; Sec. 7 computes node properties "by an
-// upward pass" where leaves depend on their particles and internal nodes on their children).
+// Upsweeps over the linked octree (Sec. 5 node properties; Sec. 7 computes them bottom-up: a leaf
+// from its particles, an internal node from its eight children).
 //
 // Both upsweeps walk the levels of the breadth-first tree from the deepest up in one cooperative
 // launch: the leaves' values are written first, then every internal node of a level combines its 8
