@@ -138,12 +138,12 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-# DRAM bytes per particle of the sort (histogram, per-pass tile counts and scans, 8 passes), of the
+# DRAM bytes per particle of the sort (per-pass tile counts and scans, 8 passes), of the
 # key pass with multipole records, and of the multipole upsweep (leaf sums and levels), measured
 # with ncu (dram__bytes_read.sum + dram__bytes_write.sum over the phase's launches) on 2^24
 # particles of the same workload and scaled by the particle count (these phases stream or gather
 # per particle, so traffic grows with n): profiles/kernels_clumps_2p24_full.md.
-MEASURED_DRAM_BYTES_PER_PARTICLE = {"sort": 243.2, "keys": 64.5, "multipoles": 135.7}
+MEASURED_DRAM_BYTES_PER_PARTICLE = {"keys": 64.5, "multipoles": 135.7}
 
 
 def algorithmic_bytes(n: int, n_leaves: int, iter_leaves: int, n_nodes: int):
@@ -151,7 +151,7 @@ def algorithmic_bytes(n: int, n_leaves: int, iter_leaves: int, n_nodes: int):
     return {
         "bbox": 24 * n,
         "keys": 68 * n,                         # read x, y, z, m; write the key and the 32-byte record
-        "sort": (8 + 20 + 24 * 7) * n,          # digit histograms + 8 passes (first has no value read)
+        "sort": (20 + 24 * 7) * n,              # 8 passes (the first has no value read)
         "leaves": 24 * iter_leaves + 8 * n,     # K + pos read/written per pass; P read by searches once
         "link": 40 * n_nodes,
         "counts": 8 * n_nodes,
@@ -237,7 +237,7 @@ def run_ours(args, rank, world, local):
     ms_per_step = elapsed_ms / K
     value = world * n / (ms_per_step * 1e-3)
 
-    # roofline of the dominant kernel group: the radix sort (upfront histogram + 8 one-sweep passes)
+    # roofline of the dominant kernel group: the radix sort (8 digit passes)
     hbm, peak_kind = peaks()
     algo = algorithmic_bytes(n, n_leaves, int(n_leaves * 1.3), n_nodes)
     dom = max(phase_ms, key=phase_ms.get)
@@ -256,6 +256,17 @@ def run_ours(args, rank, world, local):
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
+        # the host link alone (one copy each way of the x coordinates), to read the figure against
+        link = {}
+        dx = torch.empty(hx.shape, dtype=hx.dtype, device=dev)
+        for name, dst, src in (("h2d_gbs", dx, hx), ("d2h_gbs", hx, dx)):
+            l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            l0.record()
+            dst.copy_(src, non_blocking=True)
+            l1.record()
+            torch.cuda.synchronize()
+            link[name] = hx.numel() * hx.element_size() / (l0.elapsed_time(l1) * 1e-3) / 1e9
+        del dx
         ke = max(2, min(K, 10))
         s2, t2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         h2d, d2h = sb.run([(hx, hy, hz, hm)] * ke, events=(s2, t2))
@@ -265,7 +276,8 @@ def run_ours(args, rank, world, local):
                "d2h_bytes_per_step": d2h // ke, "ms_per_step": e2e_ms, "steps": ke,
                "method": "StreamedBuilder: per step H2D of x, y, z, m from pinned memory, full build with "
                          "multipoles, D2H of leaves, counts, NK, CO, LO, node counts, mass, com, quad; copies "
-                         "overlapped with the neighbouring steps' builds"}
+                         "overlapped with the neighbouring steps' builds",
+               "host_link": link}
         del sb
 
     extra = {}
@@ -401,7 +413,7 @@ def measure_keys30(X, Y, Z, M, K: int = 10):
             "ms_per_step": step_ms, "particles_per_s": n / (step_ms * 1e-3), "phase_ms": phase_ms,
             "n_leaves": nl, "leaf_iterations": it,
             "max_leaf_count": int(b.counts[:nl].max().item()), "root_count": int(counts[0].item()),
-            "sort_algorithmic_bytes_per_key": 4 + 12 + 3 * 16}
+            "sort_algorithmic_bytes_per_key": 12 + 3 * 16}
 
 
 def measure_batched(dev, reps: int = 5):

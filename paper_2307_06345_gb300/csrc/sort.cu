@@ -7,11 +7,11 @@
 // holding the same digit are found with one ballot per digit bit, which measured much cheaper than
 // a warp match instruction), stages the tile in shared memory in digit order and writes each
 // digit's run contiguously at the tile's output position for that digit; the first pass generates
-// the identity values instead of reading them. A single upfront pass histograms all digits at once
-// (global digit offsets). Ahead of every pass, a count of every tile's digits and a two-level scan
-// of the counts give each tile its output positions, so no tile waits on another (a decoupled
-// look-back between tiles, measured first, spent a third of the sort's time waiting on
-// predecessors). A segmented sort aligns its tiles to the segments, scans the counts of all tiles
+// the identity values instead of reading them. Ahead of every pass, a count of every tile's digits
+// and a two-level scan of the counts give each tile its output positions, so no tile waits on
+// another (a decoupled look-back between tiles, measured first, spent a third of the sort's time
+// waiting on predecessors); the same counts give the digits' totals, whose scan over the digits
+// places each digit's run, so no separate histogram pass reads the keys. A segmented sort aligns its tiles to the segments, scans the counts of all tiles
 // at once, and takes a tile's position within its segment as the difference to the segment's
 // first tile, added to the segment's digit offsets.
 #include <mutex>
@@ -41,46 +41,6 @@ constexpr int kItems = CSTONE_SORT_ITEMS;
 static_assert(kThreads >= 256 && kThreads % 32 == 0, "one thread per digit is needed");
 static_assert(kItems % 2 == 0, "ranks are packed two per register");
 constexpr int kTile = kThreads * kItems;  // keys per tile
-
-struct SortCtl {
-    u32 hist[kPasses][kRadix];     // digit counts of all keys, per pass
-    u32 offsets[kPasses][kRadix];  // exclusive scan of hist
-};
-
-// Histograms of all 8 digits in one read of the keys. Per-block shared histograms, one global
-// atomic per non-empty bin per block.
-__global__ void __launch_bounds__(kThreads) sort_hist_kernel(const Key* __restrict__ keys, long long n, SortCtl* ctl) {
-    __shared__ u32 sh[kPasses][kRadix];
-    for (int i = threadIdx.x; i < kPasses * kRadix; i += kThreads) (&sh[0][0])[i] = 0;
-    __syncthreads();
-    for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kThreads) {
-        Key k = __ldg(keys + i);
-#pragma unroll
-        for (int p = 0; p < kPasses; ++p) atomicAdd(&sh[p][(k >> (p * kRadixBits)) & (kRadix - 1)], 1u);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < kPasses * kRadix; i += kThreads) {
-        u32 v = (&sh[0][0])[i];
-        if (v) atomicAdd(&ctl->hist[0][0] + i, v);
-    }
-}
-
-// Exclusive scan of each pass's histogram: one warp per pass.
-__global__ void sort_scan_kernel(SortCtl* ctl) {
-    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (warp >= kPasses) return;
-    u32 carry = 0;
-    for (int base = 0; base < kRadix; base += 32) {
-        u32 v = ctl->hist[warp][base + lane];
-        u32 incl = v;
-        for (int s = 1; s < 32; s <<= 1) {
-            u32 t = __shfl_up_sync(0xffffffffu, incl, s);
-            if (lane >= s) incl += t;
-        }
-        ctl->offsets[warp][base + lane] = carry + incl - v;
-        carry += __shfl_sync(0xffffffffu, incl, 31);
-    }
-}
 
 // Segmented sorts (many independent key sets stored back to back) use tiles aligned to the
 // segments: every tile holds keys of one segment only, and digits are offset per segment.
@@ -424,10 +384,11 @@ __global__ void __launch_bounds__(kRadix) chunk_sum_kernel(const u32* __restrict
     chunk[(size_t)d * gridDim.x + blockIdx.x] = sum;  // digit-major
 }
 
-// Exclusive scan of the chunk sums over the chunks, per digit, from the digit's global offset (0
-// when digit_offsets is NULL): one block per digit over its contiguous row (in place).
+// Exclusive scan of the chunk sums over the chunks, per digit: one block per digit over its
+// contiguous row (in place). The row's total (the keys of digit d in the whole pass) goes to
+// totals[d] unless totals is NULL.
 __global__ void __launch_bounds__(1024) chunk_scan_kernel(u32* __restrict__ chunk, long long nchunks,
-                                                          const u32* __restrict__ digit_offsets) {
+                                                          u32* __restrict__ totals) {
     __shared__ u32 s_warp[32];
     u32* row = chunk + (size_t)blockIdx.x * nchunks;
     const long long per = (nchunks + 1023) / 1024;
@@ -445,7 +406,8 @@ __global__ void __launch_bounds__(1024) chunk_scan_kernel(u32* __restrict__ chun
     __syncthreads();
     u32 before = 0;
     for (int w = 0; w < warp; ++w) before += s_warp[w];
-    u32 run = (digit_offsets ? digit_offsets[blockIdx.x] : 0u) + before + incl - sum;
+    if (totals && threadIdx.x == 1023) totals[blockIdx.x] = before + incl;
+    u32 run = before + incl - sum;
     for (long long c = c0; c < c1; ++c) {
         const u32 v = row[c];
         row[c] = run;
@@ -453,14 +415,34 @@ __global__ void __launch_bounds__(1024) chunk_scan_kernel(u32* __restrict__ chun
     }
 }
 
-// Output position of every tile's first key of every digit (thread = digit).
+// Output position of every tile's first key of every digit (thread = digit): the digit's first
+// position in the pass (the keys of all smaller digits: an exclusive scan of totals over the digits,
+// done by every block; 0 when totals is NULL) plus the digit's keys in all earlier tiles.
 __global__ void __launch_bounds__(kRadix) tile_offsets_kernel(const u32* __restrict__ counts, long long tiles,
                                                               const u32* __restrict__ chunk,
+                                                              const u32* __restrict__ totals,
                                                               u32* __restrict__ offsets) {
-    const int d = threadIdx.x;
+    static_assert(kRadix % 32 == 0 && kRadix <= 1024, "one thread per digit");
+    __shared__ u32 s_warp[kRadix / 32];
+    const int d = threadIdx.x, lane = d & 31, warp = d >> 5;
+    u32 digit_first = 0;
+    if (totals) {
+        const u32 v = totals[d];
+        u32 incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const u32 t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) s_warp[warp] = incl;
+        __syncthreads();
+        u32 before = 0;
+        for (int w = 0; w < warp; ++w) before += s_warp[w];
+        digit_first = before + incl - v;
+    }
     const long long t0 = (long long)blockIdx.x * kChunkTiles;
     const long long t1 = t0 + kChunkTiles < tiles ? t0 + kChunkTiles : tiles;
-    u32 run = chunk[(size_t)d * gridDim.x + blockIdx.x];
+    u32 run = digit_first + chunk[(size_t)d * gridDim.x + blockIdx.x];
     u32 v[kChunkTiles];
 #pragma unroll
     for (int k = 0; k < kChunkTiles; ++k) v[k] = t0 + k < t1 ? counts[(t0 + k) * kRadix + d] : 0u;
@@ -472,7 +454,7 @@ __global__ void __launch_bounds__(kRadix) tile_offsets_kernel(const u32* __restr
 }
 
 struct SortLayout {
-    SortCtl* ctl;
+    u32* totals;   // keys of each digit in the current pass
     u32* look[2];  // per-tile digit counts and output offsets
     u32* chunk;    // per-chunk digit sums, then their scan
     Key* keys_alt;
@@ -485,7 +467,7 @@ SortLayout sort_layout(void* ws, long long n) {
     SortLayout l;
     Carver c(ws);
     l.tiles = (n + kTile - 1) / kTile;
-    l.ctl = c.take<SortCtl>(1);
+    l.totals = c.take<u32>(kRadix);
     l.look[0] = c.take<u32>((size_t)l.tiles * kRadix);
     l.look[1] = c.take<u32>((size_t)l.tiles * kRadix);
     l.chunk = c.take<u32>((size_t)((l.tiles + kChunkTiles - 1) / kChunkTiles) * kRadix);
@@ -508,7 +490,7 @@ namespace {
 constexpr size_t round256(size_t b) { return (b + 255) / 256 * 256; }
 constexpr long long kStaticKeys = CSTONE_SORT_STATIC_MAX_KEYS;
 constexpr size_t kStaticTiles = static_cast<size_t>((kStaticKeys + kTile - 1) / kTile);
-constexpr size_t kStaticBytes = sizeof(WsHeader) + round256(sizeof(SortCtl)) + 2 * round256(kStaticTiles * kRadix * 4) +
+constexpr size_t kStaticBytes = sizeof(WsHeader) + round256(kRadix * 4) + 2 * round256(kStaticTiles * kRadix * 4) +
                                 round256((kStaticTiles + kChunkTiles - 1) / kChunkTiles * kRadix * 4) +
                                 round256(static_cast<size_t>(kStaticKeys) * 8) +
                                 round256(static_cast<size_t>(kStaticKeys) * 4);
@@ -543,7 +525,7 @@ int static_sort_scratch(void** out) {
 // even passes the output, so the last pass lands in keys_out / perm. Ahead of each pass: tile
 // counts (counts), chunk sums and their scan (chunk), and the per-tile positions (tile_pos).
 template <bool SEG>
-int run_passes(const Key* keys_in, Key* keys_out, u32* perm, long long n, long long tiles, const SortCtl* ctl,
+int run_passes(const Key* keys_in, Key* keys_out, u32* perm, long long n, long long tiles, u32* totals,
                u32* counts, u32* chunk, u32* tile_pos, Key* keys_alt, u32* vals_alt, SegTiles seg, cudaStream_t st) {
     const int smem = static_cast<int>(sizeof(PassSmem));
     CST_CUDA(cudaFuncSetAttribute(sort_pass_kernel<true, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -559,10 +541,12 @@ int run_passes(const Key* keys_in, Key* keys_out, u32* perm, long long n, long l
         CST_LAUNCHED("tile_count_kernel");
         chunk_sum_kernel<<<(unsigned)nchunks, kRadix, 0, st>>>(counts, tiles, chunk);
         CST_LAUNCHED("chunk_sum_kernel");
-        // a segmented sort scans all tiles from 0; each tile subtracts its segment's first tile
-        chunk_scan_kernel<<<kRadix, 1024, 0, st>>>(chunk, nchunks, SEG ? nullptr : ctl->offsets[p]);
+        // a segmented sort scans all tiles from 0 and places the digits per segment; each tile
+        // subtracts its segment's first tile
+        chunk_scan_kernel<<<kRadix, 1024, 0, st>>>(chunk, nchunks, SEG ? nullptr : totals);
         CST_LAUNCHED("chunk_scan_kernel");
-        tile_offsets_kernel<<<(unsigned)nchunks, kRadix, 0, st>>>(counts, tiles, chunk, tile_pos);
+        tile_offsets_kernel<<<(unsigned)nchunks, kRadix, 0, st>>>(counts, tiles, chunk, SEG ? nullptr : totals,
+                                                                  tile_pos);
         CST_LAUNCHED("tile_offsets_kernel");
         if (p == 0)
             sort_pass_kernel<true, SEG><<<(unsigned)tiles, kThreads, smem, st>>>(ksrc, kdst, vsrc, vdst, n, p,
@@ -582,23 +566,13 @@ int launch_sort(const Key* keys_in, Key* keys_out, u32* perm, long long n, void*
     WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
     CST_CUDA(cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st));
     if (n == 0) return CSTONE_OK;
-    CST_CUDA(cudaMemsetAsync(l.ctl, 0, sizeof(SortCtl), st));
-
-    long long want = (n + kThreads - 1) / kThreads;
-    int hgrid = static_cast<int>(want < (long long)sm_count() * 4 ? want : (long long)sm_count() * 4);
-    sort_hist_kernel<<<hgrid, kThreads, 0, st>>>(keys_in, n, l.ctl);
-    CST_LAUNCHED("sort_hist_kernel");
-    sort_scan_kernel<<<1, 32 * kPasses, 0, st>>>(l.ctl);
-    CST_LAUNCHED("sort_scan_kernel");
-
-    return run_passes<false>(keys_in, keys_out, perm, n, l.tiles, l.ctl, l.look[0], l.chunk, l.look[1], l.keys_alt,
+    return run_passes<false>(keys_in, keys_out, perm, n, l.tiles, l.totals, l.look[0], l.chunk, l.look[1], l.keys_alt,
                              l.vals_alt, SegTiles{}, st);
 }
 
 // ---------------------------------------------------------------- segmented sort
 namespace {
 struct SegLayout {
-    SortCtl* ctl;
     SegBuild b;
     u32* look[2];  // per-tile digit counts and positions
     u32* chunk;
@@ -612,7 +586,6 @@ SegLayout seg_layout(void* ws, long long n, int n_segs) {
     SegLayout l;
     Carver c(ws);
     l.max_tiles = (n + kTile - 1) / kTile + n_segs;
-    l.ctl = c.take<SortCtl>(1);
     l.b.n_tiles = c.take<u32>(1);
     l.b.tile_seg = c.take<u32>((size_t)l.max_tiles);
     l.b.tile_base = c.take<u32>((size_t)l.max_tiles);
@@ -639,7 +612,6 @@ int launch_sort_segmented(const Key* keys_in, Key* keys_out, u32* perm, long lon
     WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
     CST_CUDA(cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st));
     if (n == 0) return CSTONE_OK;
-    CST_CUDA(cudaMemsetAsync(l.ctl, 0, sizeof(SortCtl), st));
     CST_CUDA(cudaMemsetAsync(l.b.seg_hist, 0, (size_t)n_segs * kPasses * kRadix * sizeof(u32), st));
     seg_setup_kernel<<<1, 1024, 0, st>>>(seg_offsets, n_segs, l.b);
     CST_LAUNCHED("seg_setup_kernel");
@@ -652,7 +624,7 @@ int launch_sort_segmented(const Key* keys_in, Key* keys_out, u32* perm, long lon
     CST_LAUNCHED("seg_hist_kernel");
     seg_scan_kernel<<<(unsigned)n_segs, 32 * kPasses, 0, st>>>(seg_offsets, l.b.seg_hist, l.b.seg_offsets);
     CST_LAUNCHED("seg_scan_kernel");
-    return run_passes<true>(keys_in, keys_out, perm, n, l.max_tiles, l.ctl, l.look[0], l.chunk, l.look[1], l.keys_alt,
+    return run_passes<true>(keys_in, keys_out, perm, n, l.max_tiles, nullptr, l.look[0], l.chunk, l.look[1], l.keys_alt,
                             l.vals_alt, view, st);
 }
 
