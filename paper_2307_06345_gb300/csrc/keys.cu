@@ -25,37 +25,43 @@ namespace CST_NS {
 // ---------------------------------------------------------------------------------- bounding cube
 namespace {
 
-__device__ __forceinline__ u64 ordered_bits(double v) {
-    u64 b = static_cast<u64>(__double_as_longlong(v));
-    return (b >> 63) ? ~b : (b | (1ULL << 63));
+// A double as a signed 64-bit integer of the same order: the magnitude bits of a negative value
+// are flipped, so that a more negative double is a smaller integer (the sign bit is kept, which
+// makes the map its own inverse). Minima and maxima then take integer min / max: on this part the
+// FP64 min / max and the unsigned 64-bit compare-and-select both cost more than the HBM stream.
+__device__ __forceinline__ long long ordered_bits(double v) {
+    const long long b = __double_as_longlong(v);
+    return b ^ static_cast<long long>(static_cast<u64>(b >> 63) >> 1);
 }
 
-__device__ __forceinline__ double from_ordered(u64 o) {
-    u64 b = (o >> 63) ? (o & ~(1ULL << 63)) : ~o;
-    return __longlong_as_double(static_cast<long long>(b));
+__device__ __forceinline__ double from_ordered(long long o) {
+    return __longlong_as_double(o ^ static_cast<long long>(static_cast<u64>(o >> 63) >> 1));
 }
+
+constexpr long long kOrderedMax = 0x7fffffffffffffffLL;
+constexpr long long kOrderedMin = -kOrderedMax - 1;
 
 struct BoxAcc {
-    u64 lo[3];  // ordered bits of the per-axis minimum
-    u64 hi[3];  // ordered bits of the per-axis maximum
+    long long lo[3];  // ordered bits of the per-axis minimum
+    long long hi[3];  // ordered bits of the per-axis maximum
 };
 
 __global__ void bbox_init_kernel(BoxAcc* acc) {
     int t = threadIdx.x;
     if (t < 3) {
-        acc->lo[t] = ~0ULL;
-        acc->hi[t] = 0ULL;
+        acc->lo[t] = kOrderedMax;
+        acc->hi[t] = kOrderedMin;
     }
 }
 
 __global__ void __launch_bounds__(256) bbox_reduce_kernel(const double* __restrict__ x, const double* __restrict__ y,
                                                           const double* __restrict__ z, long long n, BoxAcc* acc) {
-    u64 lo[3] = {~0ULL, ~0ULL, ~0ULL}, hi[3] = {0ULL, 0ULL, 0ULL};
+    long long lo[3] = {kOrderedMax, kOrderedMax, kOrderedMax}, hi[3] = {kOrderedMin, kOrderedMin, kOrderedMin};
     const double* c[3] = {x, y, z};
     auto take = [&](int d, double v) {
-        const u64 o = ordered_bits(v);
-        lo[d] = o < lo[d] ? o : lo[d];
-        hi[d] = o > hi[d] ? o : hi[d];
+        const long long o = ordered_bits(v);
+        lo[d] = min(lo[d], o);
+        hi[d] = max(hi[d], o);
     };
     const bool vec = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y) | reinterpret_cast<uintptr_t>(z)) &
                       15u) == 0;
@@ -88,15 +94,13 @@ __global__ void __launch_bounds__(256) bbox_reduce_kernel(const double* __restri
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         for (int s = 16; s > 0; s >>= 1) {
-            u64 a = __shfl_xor_sync(0xffffffffu, lo[d], s);
-            u64 b = __shfl_xor_sync(0xffffffffu, hi[d], s);
-            lo[d] = a < lo[d] ? a : lo[d];
-            hi[d] = b > hi[d] ? b : hi[d];
+            lo[d] = min(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], s));
+            hi[d] = max(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], s));
         }
     }
     // the block's warps through shared memory, then one update of the global bounds per block
     // (all blocks update the same six words)
-    __shared__ u64 s_lo[8][3], s_hi[8][3];
+    __shared__ long long s_lo[8][3], s_hi[8][3];
     const int warp = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0)
 #pragma unroll
@@ -107,10 +111,10 @@ __global__ void __launch_bounds__(256) bbox_reduce_kernel(const double* __restri
     __syncthreads();
     if (threadIdx.x < 3) {
         const int d = threadIdx.x;
-        u64 l = s_lo[0][d], h = s_hi[0][d];
+        long long l = s_lo[0][d], h = s_hi[0][d];
         for (int w = 1; w < static_cast<int>(blockDim.x >> 5); ++w) {
-            l = s_lo[w][d] < l ? s_lo[w][d] : l;
-            h = s_hi[w][d] > h ? s_hi[w][d] : h;
+            l = min(l, s_lo[w][d]);
+            h = max(h, s_hi[w][d]);
         }
         atomicMin(&acc->lo[d], l);
         atomicMax(&acc->hi[d], h);
@@ -505,25 +509,23 @@ __global__ void __launch_bounds__(256) bbox_batched_kernel(const double* __restr
                                                            const double* __restrict__ z,
                                                            const long long* __restrict__ set_offsets,
                                                            double* __restrict__ boxes) {
-    __shared__ u64 s_lo[8][3], s_hi[8][3];
+    __shared__ long long s_lo[8][3], s_hi[8][3];
     const long long a = set_offsets[blockIdx.x], b = set_offsets[blockIdx.x + 1];
-    u64 lo[3] = {~0ULL, ~0ULL, ~0ULL}, hi[3] = {0ULL, 0ULL, 0ULL};
+    long long lo[3] = {kOrderedMax, kOrderedMax, kOrderedMax}, hi[3] = {kOrderedMin, kOrderedMin, kOrderedMin};
     const double* c[3] = {x, y, z};
     for (long long i = a + threadIdx.x; i < b; i += blockDim.x) {
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            const u64 o = ordered_bits(__ldg(c[d] + i));
-            lo[d] = o < lo[d] ? o : lo[d];
-            hi[d] = o > hi[d] ? o : hi[d];
+            const long long o = ordered_bits(__ldg(c[d] + i));
+            lo[d] = min(lo[d], o);
+            hi[d] = max(hi[d], o);
         }
     }
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         for (int sft = 16; sft > 0; sft >>= 1) {
-            const u64 u = __shfl_xor_sync(0xffffffffu, lo[d], sft);
-            const u64 v = __shfl_xor_sync(0xffffffffu, hi[d], sft);
-            lo[d] = u < lo[d] ? u : lo[d];
-            hi[d] = v > hi[d] ? v : hi[d];
+            lo[d] = min(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], sft));
+            hi[d] = max(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], sft));
         }
     }
     const int warp = threadIdx.x >> 5;
@@ -542,10 +544,10 @@ __global__ void __launch_bounds__(256) bbox_batched_kernel(const double* __restr
     }
     double side = 0.0;
     for (int d = 0; d < 3; ++d) {
-        u64 l = s_lo[0][d], h = s_hi[0][d];
+        long long l = s_lo[0][d], h = s_hi[0][d];
         for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
-            l = s_lo[w][d] < l ? s_lo[w][d] : l;
-            h = s_hi[w][d] > h ? s_hi[w][d] : h;
+            l = min(l, s_lo[w][d]);
+            h = max(h, s_hi[w][d]);
         }
         const double lod = from_ordered(l), hid = from_ordered(h);
         box[d] = lod;
@@ -695,8 +697,8 @@ int launch_bbox(const double* x, const double* y, const double* z, long long n, 
     bbox_init_kernel<<<1, 32, 0, st>>>(acc);
     CST_LAUNCHED("bbox_init_kernel");
     if (n > 0) {
-        long long want = (n + 1023) / 1024;
-        int grid = static_cast<int>(want < (long long)sm_count() * 8 ? want : (long long)sm_count() * 8);
+        long long want = (n + 1023) / 1024;  // 16 blocks per SM measured best (two waves of 8)
+        int grid = static_cast<int>(want < (long long)sm_count() * 16 ? want : (long long)sm_count() * 16);
         bbox_reduce_kernel<<<grid, 256, 0, st>>>(x, y, z, n, acc);
         CST_LAUNCHED("bbox_reduce_kernel");
     }

@@ -28,16 +28,44 @@ constexpr int kThreads = 256;
 // ---------------------------------------------------------------------------- counts
 constexpr int kNumLevels = kLevels + 1;
 
+// The internal nodes in breadth-first order of their children. Every node but the root is a child,
+// and siblings are stored together in parent order, so the children of internal node x start at
+// child[x] = 8 g + 1 for the g-th internal node in that order, and the internal nodes of level l are
+// g in [(LO[l + 1] - 1) / 8, (LO[l + 2] - 1) / 8). internal[g] = x lets a level's threads take only
+// its internal nodes instead of all its nodes (most of which are leaves). A child index off that
+// pattern is recorded in the error word and skipped.
+__device__ __forceinline__ void list_internal(const int* __restrict__ child, u32 n_nodes, u32 n_int, int* internal,
+                                              u32 gtid, u32 gthreads, WsHeader* hdr) {
+    for (u32 x = gtid; x < n_nodes; x += gthreads) {
+        const int c = child[x];
+        if (c == 0) continue;
+        const u32 g = static_cast<u32>(c - 1) >> 3;
+        if (c < 1 || ((static_cast<u32>(c) - 1u) & 7u) != 0u || g >= n_int) {
+            raise_error(hdr, CSTONE_ERR_INVALID_ARG, 0x74000u);
+            continue;
+        }
+        internal[g] = static_cast<int>(x);
+    }
+}
+
+// Range [g0, g1) of the internal nodes of level l (empty for a malformed level table).
+__device__ __forceinline__ void internal_range(const int* s_lo, int l, u32 n_int, u32& g0, u32& g1) {
+    g0 = static_cast<u32>(s_lo[l + 1] - 1) >> 3;
+    g1 = min(static_cast<u32>(s_lo[l + 2] - 1) >> 3, n_int);
+}
+
 __global__ void __launch_bounds__(kThreads) upsweep_counts_kernel(const u32* __restrict__ leaf_counts, u32 nl,
                                                                   const int* __restrict__ leaf_to_node,
                                                                   const int* __restrict__ child,
                                                                   const int* __restrict__ level_offsets,
-                                                                  u32* __restrict__ node_counts, GridBarrier* bar,
-                                                                  WsHeader* hdr) {
+                                                                  u32* __restrict__ node_counts, int* internal,
+                                                                  GridBarrier* bar, WsHeader* hdr) {
     __shared__ int s_lo[kNumLevels + 1];
     if (threadIdx.x <= kNumLevels) s_lo[threadIdx.x] = level_offsets[threadIdx.x];
+    __syncthreads();
     const u32 gtid = blockIdx.x * kThreads + threadIdx.x, gthreads = gridDim.x * kThreads;
-    const u32 n_nodes = nl + (nl - 1) / 7;  // an index outside is recorded in the error word and skipped
+    const u32 n_int = (nl - 1) / 7;
+    const u32 n_nodes = nl + n_int;  // an index outside is recorded in the error word and skipped
     for (u32 i = gtid; i < nl; i += gthreads) {
         const int v = leaf_to_node[i];
         if (v >= 0 && static_cast<u32>(v) < n_nodes)
@@ -45,19 +73,22 @@ __global__ void __launch_bounds__(kThreads) upsweep_counts_kernel(const u32* __r
         else
             raise_error(hdr, CSTONE_ERR_INVALID_ARG, 0x71000u);
     }
+    list_internal(child, n_nodes, n_int, internal, gtid, gthreads, hdr);
     grid_barrier(bar, hdr);
     for (int l = kLevels - 1; l >= 0; --l) {
         if (s_lo[l + 2] == s_lo[l + 1]) continue;  // no internal node at level l
-        for (u32 x = s_lo[l] + gtid; x < static_cast<u32>(s_lo[l + 1]) && x < n_nodes; x += gthreads) {
-            const int c = child[x];
-            if (c == 0) continue;
-            if (c < 0 || static_cast<u32>(c) + 8u > n_nodes) {
-                raise_error(hdr, CSTONE_ERR_INVALID_ARG, 0x73000u);
-                continue;
-            }
+        u32 g0, g1;
+        internal_range(s_lo, l, n_int, g0, g1);
+        for (u32 g = g0 + gtid; g < g1; g += gthreads) {
+            const u32 c = 8u * g + 1u;  // c + 7 <= 8 n_int = n_nodes - 1
+            const int x = internal[g];
             u32 sum = 0;
 #pragma unroll
             for (int k = 0; k < 8; ++k) sum += __ldcg(node_counts + c + k);
+            if (x < 0 || static_cast<u32>(x) >= n_nodes || static_cast<u32>(child[x]) != c) {
+                raise_error(hdr, CSTONE_ERR_INVALID_ARG, 0x73000u);
+                continue;
+            }
             node_counts[x] = sum;
         }
         grid_barrier(bar, hdr);
@@ -182,6 +213,7 @@ struct MpScratch {  // per node: compensated sums and the fixed-point centre car
     Record* rec;        // [n_particles]
     u32* big;           // [n_leaves] leaves handed to the block-per-leaf kernel
     u32* n_big;         // their number
+    int* internal;      // [n_internal] internal nodes in breadth-first order of their children
 };
 
 __device__ __forceinline__ void store_node(int v, u32 n_nodes, ff M, const long long c[3], const ff q[6], MpScratch s,
@@ -454,11 +486,16 @@ __global__ void __launch_bounds__(kThreads) multipole_level_kernel(const int* __
     __syncthreads();
     const FixedFrame f = s_f;
     const u32 gtid = blockIdx.x * kThreads + threadIdx.x, gthreads = gridDim.x * kThreads;
+    const u32 n_int = (n_nodes - 1) / 8;
+    list_internal(child, n_nodes, n_int, s.internal, gtid, gthreads, hdr);
+    grid_barrier(bar, hdr);
     for (int l = kLevels - 1; l >= 0; --l) {
         if (s_lo[l + 2] == s_lo[l + 1]) continue;  // no internal node at level l
-        for (u32 x = s_lo[l] + gtid; x < static_cast<u32>(s_lo[l + 1]); x += gthreads) {
-            const int c0 = child[x];
-            if (c0 == 0) continue;
+        u32 g0, g1;
+        internal_range(s_lo, l, n_int, g0, g1);
+        for (u32 g = g0 + gtid; g < g1; g += gthreads) {
+            const int c0 = static_cast<int>(8u * g + 1u);  // c0 + 7 <= 8 n_int = n_nodes - 1
+            const int x = s.internal[g];
             ff Mc[8];
             long long cc[8][3];
             int anchor = -1;
@@ -515,7 +552,11 @@ __global__ void __launch_bounds__(kThreads) multipole_level_kernel(const int* __
                     }
                 }
             }
-            store_node(static_cast<int>(x), n_nodes, Mp, cp, Qp, s, f, mass, com, quad);
+            if (x < 0 || static_cast<u32>(x) >= n_nodes || child[x] != c0) {
+                raise_error(hdr, CSTONE_ERR_INVALID_ARG, 0x75000u);
+                continue;
+            }
+            store_node(x, n_nodes, Mp, cp, Qp, s, f, mass, com, quad);
         }
         grid_barrier(bar, hdr);
     }
@@ -523,6 +564,7 @@ __global__ void __launch_bounds__(kThreads) multipole_level_kernel(const int* __
 
 struct UpLayout {
     GridBarrier* bar;
+    int* internal;  // [n_internal]
     MpScratch mp;
     size_t bytes;
 };
@@ -532,7 +574,9 @@ UpLayout up_layout(void* ws, long long nl, long long n_particles, bool multipole
     Carver c(ws);
     const long long nn = nl + (nl - 1) / 7;
     l.bar = c.take<GridBarrier>(1);
+    l.internal = c.take<int>((size_t)((nl - 1) / 7));
     l.mp = MpScratch{};
+    l.mp.internal = l.internal;
     if (multipoles) {
         l.mp.mass = c.take<ff>((size_t)nn);
         l.mp.quad = c.take<ff>((size_t)nn * 6);
@@ -558,7 +602,8 @@ int launch_upsweep_counts(const u32* leaf_counts, long long nl, const int* leaf_
     CST_CUDA(cudaMemsetAsync(l.bar, 0, sizeof(GridBarrier), st));
     u32 nl_ = static_cast<u32>(nl);
     GridBarrier* bar = l.bar;
-    void* args[] = {&leaf_counts, &nl_, &leaf_to_node, &child, &level_offsets, &node_counts, &bar, &hdr};
+    int* internal = l.internal;
+    void* args[] = {&leaf_counts, &nl_, &leaf_to_node, &child, &level_offsets, &node_counts, &internal, &bar, &hdr};
     const int grid = cooperative_grid(reinterpret_cast<const void*>(upsweep_counts_kernel), kThreads, 0, 4);
     CST_COOP(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(upsweep_counts_kernel), dim3(grid), dim3(kThreads),
                                          args, 0, st));

@@ -87,6 +87,15 @@ def test_link_matches_breadth_first_walk(oracle, seed):
         assert t["CO"][v] == 0
     for g_idx, p in enumerate(t["parent"]):
         assert t["CO"][p] == 1 + 8 * g_idx
+    # the internal nodes of level l are the g-th in that order for g in [(LO[l+1]-1)/8, (LO[l+2]-1)/8)
+    # (the upsweeps take each level's internal nodes this way)
+    internal = [i for i in range(n) if t["CO"][i] != 0]
+    assert sorted(internal) == sorted(int(p) for p in t["parent"])
+    for lev in range(L):
+        lo, hi = t["LO"][lev + 1], t["LO"][lev + 2]
+        assert (lo - 1) % 8 == 0 and (hi - 1) % 8 == 0
+        want = [i for i in internal if t["LO"][lev] <= i < t["LO"][lev + 1]]
+        assert sorted(int(p) for p in t["parent"][(lo - 1) // 8:(hi - 1) // 8]) == want
 
 
 def brute_node_counts(P, NK):
