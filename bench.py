@@ -143,7 +143,7 @@ class ClockSampler:
 # measured with ncu (dram__bytes_read.sum + dram__bytes_write.sum over the phase's launches) on
 # 2^24 particles of the same workload and scaled by the particle count (these phases stream or
 # gather per particle, so traffic grows with n): profiles/dram_clumps_2p24.md.
-MEASURED_DRAM_BYTES_PER_PARTICLE = {"bbox": 24.2, "keys": 64.2, "sort": 232.2, "multipoles": 135.2}
+MEASURED_DRAM_BYTES_PER_PARTICLE = {"bbox": 24.2, "keys": 64.2, "sort": 232.2, "multipoles": 135.4}
 
 
 def algorithmic_bytes(n: int, n_leaves: int, iter_leaves: int, n_nodes: int):

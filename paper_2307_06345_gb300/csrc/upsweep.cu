@@ -293,7 +293,7 @@ __device__ __forceinline__ Record load_record(const Record* rec, u32 p) {
     return r;
 }
 
-__global__ void __launch_bounds__(kLeafThreads) multipole_leaf_kernel(const u32* __restrict__ offsets, u32 nl,
+__global__ void __launch_bounds__(kLeafThreads, 4) multipole_leaf_kernel(const u32* __restrict__ offsets, u32 nl,
                                                                       const u32* __restrict__ perm,
                                                                       const int* __restrict__ leaf_to_node,
                                                                       u32 n_nodes, MpScratch s,
@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(kLeafThreads) multipole_leaf_kernel(const u32*
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             const float off = __fdiv_rn(ff_val(S[d]), Mv);
-            c[d] = r0c[d] + __float2ll_rn(__fmul_rn(__fmul_rn(off, 1.0f / f.s1), 1.0f / f.s2));
+            c[d] = r0c[d] + float_to_int64(__fmul_rn(__fmul_rn(off, 1.0f / f.s1), 1.0f / f.s2));
         }
     }
     auto second_moments = [&](const Record& r) {
@@ -449,7 +449,7 @@ __global__ void __launch_bounds__(kLeafThreads) multipole_bigleaf_kernel(const u
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             const float off = Mv != 0.f ? __fdiv_rn(ff_val(S[d]), Mv) : 0.f;
-            c[d] = r0c[d] + __float2ll_rn(__fmul_rn(__fmul_rn(off, 1.0f / f.s1), 1.0f / f.s2));
+            c[d] = r0c[d] + float_to_int64(__fmul_rn(__fmul_rn(off, 1.0f / f.s1), 1.0f / f.s2));
         }
         for (u32 j = a + threadIdx.x; j < b; j += kLeafThreads) {
             const Record r = s.rec[__ldg(perm + j)];
@@ -532,7 +532,7 @@ __global__ void __launch_bounds__(kThreads) multipole_level_kernel(const int* __
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
                     const float off = __fdiv_rn(ff_val(Sp[d]), Mv);
-                    cp[d] = ca[d] + __float2ll_rn(__fmul_rn(__fmul_rn(off, 1.0f / f.s1), 1.0f / f.s2));
+                    cp[d] = ca[d] + float_to_int64(__fmul_rn(__fmul_rn(off, 1.0f / f.s1), 1.0f / f.s2));
                 }
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
