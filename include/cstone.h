@@ -181,7 +181,9 @@ CSTONE_API int cstone_link_tree(const uint64_t* leaves, int64_t n_leaves, uint64
  * holds its N_i, an internal node the sum of its 8 children. Inputs are the outputs of
  * cstone_build_leaves (counts) and cstone_link_tree (leaf_to_node, child, level_offsets).
  *   node_counts [n] uint32 output.
- * One cooperative launch walking the levels from the deepest; asynchronous.
+ * One cooperative launch walking the levels from the deepest; asynchronous. The workspace holds
+ * the grid barrier and a list of the internal nodes (4 bytes each). A child array off the linked
+ * layout (child[x] = 8 g + 1 for the g-th internal node) is reported in the error word.
  * ------------------------------------------------------------------------------------------ */
 CSTONE_API int cstone_upsweep_workspace_size(int64_t n_leaves, size_t* bytes);
 CSTONE_API int cstone_upsweep_counts(const uint32_t* leaf_counts, int64_t n_leaves, const int32_t* leaf_to_node,
@@ -194,8 +196,10 @@ CSTONE_API int cstone_upsweep_counts(const uint32_t* leaf_counts, int64_t n_leav
  * moments about it Q_ab = sum m (x - com)_a (x - com)_b, components xx, xy, xz, yy, yz, zz.
  * Accumulation is in FP32 with two-sum compensation (a sum/compensation pair per moment, carried
  * up the tree); positions are taken into 64-bit fixed point so that coordinate differences are
- * exact before their single rounding to FP32, and the centre is written in FP64. An empty node has
- * M = 0, com = 0, Q = 0. The workspace holds a 32-byte record per particle and the per-node sums.
+ * exact before their conversion to FP32 (correctly rounded below 2^31 fixed-point units, within one
+ * unit in the last place above), and the centre is written in FP64. An empty node has M = 0,
+ * com = 0, Q = 0. The workspace holds a 32-byte record per particle, the per-node sums and the list
+ * of internal nodes.
  *   x, y, z, m   [n] float64 coordinates and float32 masses in input order.
  *   perm         [n] uint32 sort permutation (cstone_sort).
  *   offsets      [n_leaves + 1] uint32 leaf particle offsets (cstone_build_leaves).
