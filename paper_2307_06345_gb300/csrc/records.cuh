@@ -10,8 +10,8 @@ namespace cst {
 
 // Coordinates in 64-bit fixed point: X = trunc(x * 2^F) with F chosen from the box so that
 // |X| < 2^61 for |x| < 2^E >= max(|lo|, |lo + 2 side|). Differences of fixed-point values are
-// exact; one conversion rounds them to FP32 and a power-of-two scale (split in two factors so
-// that each is a normal float) restores physical units.
+// exact; one conversion takes them to FP32 (int64_to_float below) and a power-of-two scale (split
+// in two factors so that each is a normal float) restores physical units.
 struct FixedFrame {
     int F;
     float s1, s2;  // 2^-F = s1 * s2
