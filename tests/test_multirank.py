@@ -47,3 +47,21 @@ def test_two_gloo_ranks_time_by_slowest_and_reference_on_rank0_only():
     got = dict((r, (v, ref)) for r, v, ref in (q.get(timeout=10) for _ in range(2)))
     assert got[0][0] == got[1][0] == 15.0
     assert got[1][1] is None  # non-zero ranks exit the reference arm without work
+
+
+def test_reference_arm_prints_one_json_line_on_cpu():
+    # the reference arm times the oracle on the host: it runs here, without a GPU
+    import json
+    import subprocess
+    import sys
+
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "particles/s" and d["value"] > 0
+    assert d["higher_is_better"] is True and d["steps"] == 1 and d["n_gpus"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
