@@ -25,7 +25,7 @@ constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 constexpr int kPasses = (kKeyBits + kRadixBits - 1) / kRadixBits;  // 8 (63-bit keys) or 4 (30-bit keys)
 // Tile shape (compile-time tuning knobs, set by the build from the autotuner's choice): threads per
-// block, keys per thread, blocks per SM, and look-back descriptors read per step.
+// block, keys per thread and blocks per SM.
 #ifndef CSTONE_SORT_THREADS
 #define CSTONE_SORT_THREADS 256
 #endif

@@ -47,7 +47,7 @@ def test_status_strings(clib):
 def test_workspace_queries_and_argument_checks(clib):
     sz = ctypes.c_size_t()
     assert clib.cstone_sort_workspace_size(1 << 20, ctypes.byref(sz)) == 0
-    # the sort needs the alternate key/value buffers (12 bytes per key) plus look-back words
+    # the sort needs the alternate key/value buffers (12 bytes per key) plus the per-tile digit counts and offsets
     assert sz.value >= 12 * (1 << 20)
     assert clib.cstone_sort_workspace_size(-1, ctypes.byref(sz)) == 1
     assert clib.cstone_sort_workspace_size(1 << 30, ctypes.byref(sz)) == 1

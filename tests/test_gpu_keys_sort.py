@@ -128,7 +128,7 @@ def test_kernel_launch_counter(lib):
 
 
 def test_sort_repeated_calls_reuse_workspace(lib, oracle):
-    # the look-back regions are reused across calls of different sizes
+    # the per-tile count and offset regions are reused across calls of different sizes
     ws = lib.Workspace()
     rng = np.random.default_rng(10)
     for n in (300_000, 4097, 1 << 18, 17):
