@@ -256,20 +256,21 @@ def run_ours(args, rank, world, local):
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
-        # the host link alone (best of three copies each way of the x coordinates), to read the
-        # figure against
+        # the host link alone (three copies each way of the x coordinates: the best and the worst
+        # rate), to read the figure against
         link = {}
         dx = torch.empty(hx.shape, dtype=hx.dtype, device=dev)
         for name, dst, src in (("h2d_gbs", dx, hx), ("d2h_gbs", hx, dx)):
-            best = float("inf")
+            copy_ms = []
             for _ in range(3):
                 l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 l0.record()
                 dst.copy_(src, non_blocking=True)
                 l1.record()
                 torch.cuda.synchronize()
-                best = min(best, l0.elapsed_time(l1))
-            link[name] = hx.numel() * hx.element_size() / (best * 1e-3) / 1e9
+                copy_ms.append(l0.elapsed_time(l1))
+            link[name] = hx.numel() * hx.element_size() / (min(copy_ms) * 1e-3) / 1e9
+            link[name + "_worst"] = hx.numel() * hx.element_size() / (max(copy_ms) * 1e-3) / 1e9
         del dx
         ke = max(2, min(K, 10))
         s2, t2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
