@@ -142,7 +142,7 @@ class ClockSampler:
 # (per-pass tile counts and scans, 8 passes) and the multipole upsweep (leaf sums and levels),
 # measured with ncu (dram__bytes_read.sum + dram__bytes_write.sum over the phase's launches) on
 # 2^24 particles of the same workload and scaled by the particle count (these phases stream or
-# gather per particle, so traffic grows with n): profiles/dram_clumps_2p24.md.
+# gather per particle, so traffic grows with n).
 MEASURED_DRAM_BYTES_PER_PARTICLE = {"bbox": 24.2, "keys": 64.2, "sort": 232.2, "multipoles": 135.4}
 
 

@@ -129,7 +129,13 @@ CSTONE_API int cstone_sort(const uint64_t* keys_in, uint64_t* keys_out, uint32_t
  * make that first call before any stream capture. All calls share the one array, so calls that
  * can overlap on the GPU (other streams, other host threads) race and must be serialised by the
  * caller. Each call clears what has to start at zero; otherwise the array keeps the last call's
- *   keys_in, keys_out, perm, n, stream: as for cstone_sort. Asynchronous.
+ * intermediate keys, permutation and digit counts, which the next call overwrites before reading.
+ * The device address is cached per device ordinal for the life of the process: it does not
+ * survive cudaDeviceReset (or any teardown of the primary context) in the host application.
+ * `stream` must belong to the current device; a stream of another device returns
+ * CSTONE_ERR_INVALID_ARG.
+ *   keys_in, keys_out, perm, n, stream: as for cstone_sort (keys_in may alias keys_out).
+ * Asynchronous.
  * ------------------------------------------------------------------------------------------ */
 #define CSTONE_SORT_STATIC_MAX_KEYS ((int64_t)1 << 20)
 CSTONE_API int cstone_sort_static(const uint64_t* keys_in, uint64_t* keys_out, uint32_t* perm, int64_t n,

@@ -227,12 +227,26 @@ def cstone_keys(x, y, z, box, curve: int, keys, stream=None, levels: int = LEVEL
            "cstone_keys")
 
 
-def cstone_sort(keys_in, keys_out, perm, ws: Workspace, stream=None, levels: int = LEVELS):
-    fn, kdt = _family(levels)
+def _sort_args(keys_in, keys_out, perm, kdt, who: str):
+    """Checks the sort operands: dtypes, contiguity, output sizes, and that all three tensors sit
+    on the current CUDA device (the sort kernels run there)."""
     n = keys_in.numel()
+    if keys_out.numel() < n or perm.numel() < n:
+        raise ValueError(f"{who}: keys_out and perm need at least {n} elements "
+                         f"(have {keys_out.numel()} and {perm.numel()})")
     _need(keys_in, kdt, "keys_in")
     _need(keys_out, kdt, "keys_out")
     _need(perm, torch.int32, "perm")
+    cur = torch.cuda.current_device()
+    for t, nm in ((keys_in, "keys_in"), (keys_out, "keys_out"), (perm, "perm")):
+        if t.device.index != cur:
+            raise ValueError(f"{who}: {nm} is on {t.device}, the current device is cuda:{cur}")
+    return n
+
+
+def cstone_sort(keys_in, keys_out, perm, ws: Workspace, stream=None, levels: int = LEVELS):
+    fn, kdt = _family(levels)
+    n = _sort_args(keys_in, keys_out, perm, kdt, "cstone_sort")
     buf = ws.get(_size(fn("sort_workspace_size"), n))
     _check(fn("sort")(_ptr(keys_in), _ptr(keys_out), _ptr(perm), n, _ptr(buf), buf.numel(), _stream(stream)),
            "cstone_sort")
@@ -242,9 +256,7 @@ def cstone_sort_static(keys_in, keys_out, perm, stream=None):
     """Sort without any device allocation: scratch is a static array inside the library, so at most
     2^20 keys, and calls must not overlap on the GPU (see include/cstone.h)."""
     lib = load()
-    _need(keys_in, torch.int64, "keys_in")
-    _need(keys_out, torch.int64, "keys_out")
-    _need(perm, torch.int32, "perm")
+    _sort_args(keys_in, keys_out, perm, torch.int64, "cstone_sort_static")
     _check(lib.cstone_sort_static(_ptr(keys_in), _ptr(keys_out), _ptr(perm), keys_in.numel(), _stream(stream)),
            "cstone_sort_static")
 

@@ -502,12 +502,20 @@ constexpr int kMaxDevices = 64;
 void* g_static_scratch[kMaxDevices] = {};
 
 // Device address of g_sort_scratch on the current device, looked up once per device. In host code
-// the array's name is only a host-side stand-in, never a device address.
-int static_sort_scratch(void** out) {
+// the array's name is only a host-side stand-in, never a device address. The cache is not
+// invalidated by cudaDeviceReset. A stream of another device than the current one is rejected.
+int static_sort_scratch(void** out, cudaStream_t st) {
     int dev = 0;
     CST_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices)
         return fail(CSTONE_ERR_INVALID_ARG, "cstone_sort_static: device ordinal %d not supported", dev);
+    if (st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread) {
+        int sdev = -1;
+        CST_CUDA(cudaStreamGetDevice(st, &sdev));
+        if (sdev != dev)
+            return fail(CSTONE_ERR_INVALID_ARG, "cstone_sort_static: stream of device %d, current device %d", sdev,
+                        dev);
+    }
     std::lock_guard<std::mutex> lock(g_static_mutex);
     if (g_static_scratch[dev] == nullptr) {
         void* p = nullptr;
@@ -661,7 +669,7 @@ int cstone_sort_static(const uint64_t* keys_in, uint64_t* keys_out, uint32_t* pe
     if (cst::sort_ws_bytes(n) > cst::kStaticBytes)
         return cst::fail(CSTONE_ERR_INVALID_ARG, "cstone_sort_static: static scratch too small");
     void* ws = nullptr;
-    if (int rc = cst::static_sort_scratch(&ws)) return rc;
+    if (int rc = cst::static_sort_scratch(&ws, cst::as_stream(stream))) return rc;
     return cst::launch_sort(reinterpret_cast<const cst::u64*>(keys_in), reinterpret_cast<cst::u64*>(keys_out), perm,
                             n, ws, cst::as_stream(stream));
 }

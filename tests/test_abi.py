@@ -73,3 +73,18 @@ def test_workspace_queries_and_argument_checks(clib):
     rc = clib.cstone_build_leaves(dummy, 100, 8, dummy, 10, ctypes.byref(nl), dummy, None, 64, None, dummy, 1 << 20,
                                   None)
     assert rc == 1
+
+
+def test_sort_bindings_reject_undersized_outputs(clib):
+    """The Python bindings of both sorts refuse outputs smaller than the input before any launch (an
+    undersized perm or keys_out would otherwise be written out of bounds)."""
+    import torch
+
+    import paper_2307_06345_gb300 as cs
+
+    kin = torch.zeros(100, dtype=torch.int64)
+    for fn in (lambda ko, p: cs.cstone_sort(kin, ko, p, None), lambda ko, p: cs.cstone_sort_static(kin, ko, p)):
+        with pytest.raises(ValueError, match="at least 100"):
+            fn(torch.zeros(100, dtype=torch.int64), torch.zeros(99, dtype=torch.int32))
+        with pytest.raises(ValueError, match="at least 100"):
+            fn(torch.zeros(50, dtype=torch.int64), torch.zeros(100, dtype=torch.int32))
