@@ -45,7 +45,7 @@ def build(force: bool = False) -> str:
         stale = (not os.path.exists(path)) or any(os.path.getmtime(s) > os.path.getmtime(path) for s in (_SRC, _HDR))
         if force or stale:
             tmp = path + f".tmp{os.getpid()}"
-            cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+            cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
                    f"-DORACLE_L={levels}", "-o", tmp, _SRC, "-lm"]
             subprocess.run(cmd, check=True)
             os.replace(tmp, path)
@@ -62,6 +62,8 @@ def _load(levels: int = L):
             P = ctypes.c_void_p
             i64, u32, i32, dbl = ctypes.c_int64, ctypes.c_uint32, ctypes.c_int, ctypes.c_double
             sigs = {
+                "oracle_set_threads": (None, [i32]),
+                "oracle_get_threads": (i32, []),
                 "oracle_bounding_cube": (i32, [P, P, P, i64, P]),
                 "oracle_grid_coord": (u32, [dbl, dbl, dbl]),
                 "oracle_scale": (dbl, [dbl]),
@@ -81,6 +83,8 @@ def _load(levels: int = L):
                 "oracle_canonical_leaves": (i32, [P, i64, u32, P, i64, P]),
                 "oracle_check_cornerstone": (i32, [P, i64]),
                 "oracle_link": (i32, [P, i64, P, P, P, P, P]),
+                "oracle_cube_from_bounds": (i32, [P, P]),
+                "oracle_decompose": (i32, [P, i64, i32, P]),
                 "oracle_node_counts": (i32, [P, i64, P, i64, P]),
                 "oracle_multipoles": (i32, [P, P, P, P, P, P, i64, P, P, i64, P, P, P]),
                 "oracle_focus_tiles": (i32, [ctypes.c_uint64, ctypes.c_uint64, P, P, i32]),
@@ -97,6 +101,18 @@ def _load(levels: int = L):
                 fn.argtypes = args
             _libs[levels] = lib
     return _libs[levels]
+
+
+def set_threads(threads: int = 0) -> int:
+    """Threads of the oracle's parallel loops in both builds (0 = all cores, 1 = sequential);
+    returns the number in effect. Results do not depend on it."""
+    for levels in _LIBS:
+        _load(levels).oracle_set_threads(int(threads))
+    return int(_load().oracle_get_threads())
+
+
+def get_threads() -> int:
+    return int(_load().oracle_get_threads())
 
 
 def _ptr(a: np.ndarray):
@@ -237,6 +253,23 @@ def canonical_leaves(P, ncrit: int, cap: int | None = None, levels: int = L) -> 
 def check_cornerstone(K, levels: int = L) -> bool:
     K = _c(K, np.uint64)
     return _load(levels).oracle_check_cornerstone(_ptr(K), K.size - 1) == 0
+
+
+# ---------------------------------------------------------------- Sec. 6: distributed tree
+def cube_from_bounds(bounds) -> np.ndarray:
+    """Cube {lo_x, lo_y, lo_z, side} from per-axis bounds reduced over processes."""
+    b = _c(bounds, np.float64)
+    box = np.zeros(4, np.float64)
+    _check(_load().oracle_cube_from_bounds(_ptr(b), _ptr(box)), "cube_from_bounds")
+    return box
+
+
+def decompose(N, n_ranks: int) -> np.ndarray:
+    """The n_ranks + 1 leaf cuts of the SFC domain decomposition of the leaf counts N."""
+    N = _c(N, np.uint32)
+    cuts = np.empty(n_ranks + 1, np.int64)
+    _check(_load().oracle_decompose(_ptr(N), N.size, n_ranks, _ptr(cuts)), "decompose")
+    return cuts
 
 
 # ---------------------------------------------------------------- Sec. 5: linked octree

@@ -6,15 +6,80 @@
  *
  * Compile with -O2 -ffp-contract=off: each floating-point expression below is then evaluated as
  * the written sequence of IEEE-754 double round-to-nearest operations.
+ *
+ * Loops whose iterations are independent (one particle, leaf or node each; every iteration
+ * writes only its own outputs and reads nothing another iteration writes) carry an OpenMP
+ * `parallel for`. Each iteration computes exactly what the sequential loop computes, in the same
+ * operation order, so results do not depend on the thread count (oracle_set_threads; 1 = the
+ * plain sequential program). The sorts qsort contiguous chunks in parallel and merge them; the
+ * order they produce is total (distinct (key, index) pairs, distinct node keys), so it is unique.
  */
 #include "cstone_oracle.h"
 
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define L ORACLE_L
 #define KEY_END (1ULL << (3 * L)) /* 8^L (2^63 at L = 21), one past the last key */
+
+/* Threads of the parallel loops (the machine's cores by default; 1 = sequential). */
+void oracle_set_threads(int threads) {
+#ifdef _OPENMP
+    omp_set_num_threads(threads > 0 ? threads : omp_get_num_procs());
+#else
+    (void)threads;
+#endif
+}
+
+int oracle_get_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* Sorts n elements of `size` bytes into ascending order under `cmp`, where elements that compare
+ * equal are identical, so the result is unique: contiguous chunks are qsorted, one per thread,
+ * then merged pairwise. `tmp` holds n elements. */
+static void sort_total(void* base, void* tmp, int64_t n, size_t size, int (*cmp)(const void*, const void*)) {
+    int chunks = oracle_get_threads();
+    if (chunks < 1 || n < 4096) chunks = 1;
+    int64_t per = (n + chunks - 1) / chunks;
+    char* a = (char*)base;
+    char* b = (char*)tmp;
+#pragma omp parallel for schedule(static, 1)
+    for (int c = 0; c < chunks; ++c) {
+        int64_t lo = c * per, hi = lo + per < n ? lo + per : n;
+        if (hi > lo) qsort(a + lo * size, (size_t)(hi - lo), size, cmp);
+    }
+    for (int64_t width = per; width < n; width *= 2) {
+        int64_t pairs = (n + 2 * width - 1) / (2 * width);
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t q = 0; q < pairs; ++q) {
+            int64_t lo = q * 2 * width;
+            int64_t mid = lo + width < n ? lo + width : n;
+            int64_t hi = lo + 2 * width < n ? lo + 2 * width : n;
+            int64_t i = lo, j = mid, k = lo;
+            while (i < mid && j < hi) {
+                if (cmp(a + i * size, a + j * size) < 0)
+                    memcpy(b + (k++) * size, a + (i++) * size, size);
+                else
+                    memcpy(b + (k++) * size, a + (j++) * size, size);
+            }
+            if (i < mid) memcpy(b + k * size, a + i * size, (size_t)(mid - i) * size), k += mid - i;
+            if (j < hi) memcpy(b + k * size, a + j * size, (size_t)(hi - j) * size);
+        }
+        char* t = a;
+        a = b;
+        b = t;
+    }
+    if (a != (char*)base) memcpy(base, a, (size_t)n * size);
+}
 
 /* =====================================================================================
  * Sec. 3: keys. A key of 3L bits is a sequence of L octal digits; digit i selects the octant
@@ -44,6 +109,49 @@ int oracle_bounding_cube(const double* x, const double* y, const double* z, int6
         if (ext > side) side = ext;
     }
     box[3] = (side > 0.0) ? side : 1.0;
+    return ORACLE_OK;
+}
+
+/* Sec. 6: the cube of a point set spread over several processes, from the per-axis bounds
+ * {min x, min y, min z, max x, max y, max z} reduced over the processes (the minima of the minima,
+ * the maxima of the maxima). Same arithmetic as oracle_bounding_cube: lo = minima, side = the
+ * largest extent, 1 when that extent is 0 or when there is no point (a minimum of +inf). */
+int oracle_cube_from_bounds(const double bounds[6], double box[4]) {
+    if (isinf(bounds[0]) && bounds[0] > 0.0) {
+        box[0] = box[1] = box[2] = 0.0;
+        box[3] = 1.0;
+        return ORACLE_OK;
+    }
+    double side = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        box[d] = bounds[d];
+        double ext = bounds[3 + d] - bounds[d];
+        if (ext > side) side = ext;
+    }
+    box[3] = (side > 0.0) ? side : 1.0;
+    return ORACLE_OK;
+}
+
+/* Sec. 6: the domain decomposition groups the leaves into n_ranks bins of consecutive leaves with
+ * about N_tot / n_ranks particles each. Reading of "about": the bin of rank r starts at cut r, the
+ * first leaf whose preceding leaves hold at least r N_tot / n_ranks particles (compared exactly as
+ * integers: prefix * n_ranks >= N_tot * r), n_l when no leaf qualifies; cuts[0] = 0 and
+ * cuts[n_ranks] = n_l. Written as the plain scan of the prefix for every cut. */
+int oracle_decompose(const uint32_t* N, int64_t nl, int n_ranks, int64_t* cuts) {
+    if (nl < 0 || n_ranks < 1) return ORACLE_E_ARG;
+    uint64_t total = 0;
+    for (int64_t i = 0; i < nl; ++i) total += N[i];
+    cuts[0] = 0;
+    for (int r = 1; r < n_ranks; ++r) {
+        uint64_t prefix = 0;
+        int64_t i = 0;
+        while (i < nl && !(prefix * (uint64_t)n_ranks >= total * (uint64_t)r)) {
+            prefix += N[i];
+            ++i;
+        }
+        cuts[r] = i;
+    }
+    cuts[n_ranks] = nl;
     return ORACLE_OK;
 }
 
@@ -160,14 +268,19 @@ int oracle_keys(const double* x, const double* y, const double* z, int64_t n, co
                 uint64_t* keys) {
     if (n < 0 || (curve != 0 && curve != 1) || !(box[3] > 0.0)) return ORACLE_E_ARG;
     double scale = oracle_scale(box[3]);
+    int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
     for (int64_t i = 0; i < n; ++i) {
-        if (isnan(x[i]) || isnan(y[i]) || isnan(z[i])) return ORACLE_E_ARG;
+        if (isnan(x[i]) || isnan(y[i]) || isnan(z[i])) {
+            bad = 1;
+            continue;
+        }
         uint32_t gx = oracle_grid_coord(x[i], box[0], scale);
         uint32_t gy = oracle_grid_coord(y[i], box[1], scale);
         uint32_t gz = oracle_grid_coord(z[i], box[2], scale);
         keys[i] = curve == 0 ? oracle_morton_key(gx, gy, gz) : oracle_hilbert_key(gx, gy, gz);
     }
-    return ORACLE_OK;
+    return bad ? ORACLE_E_ARG : ORACLE_OK;
 }
 
 /* =====================================================================================
@@ -192,17 +305,25 @@ int oracle_sort(const uint64_t* keys, int64_t n, uint64_t* sorted, uint32_t* per
     if (n < 0 || n > 0xFFFFFFFFLL) return ORACLE_E_ARG;
     if (n == 0) return ORACLE_OK;
     key_index* a = (key_index*)malloc((size_t)n * sizeof(key_index));
-    if (!a) return ORACLE_E_ARG;
+    key_index* tmp = (key_index*)malloc((size_t)n * sizeof(key_index));
+    if (!a || !tmp) {
+        free(a);
+        free(tmp);
+        return ORACLE_E_ARG;
+    }
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
         a[i].key = keys[i];
         a[i].idx = (uint32_t)i;
     }
-    qsort(a, (size_t)n, sizeof(key_index), cmp_key_index);
+    sort_total(a, tmp, n, sizeof(key_index), cmp_key_index);
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
         sorted[i] = a[i].key;
         perm[i] = a[i].idx;
     }
     free(a);
+    free(tmp);
     return ORACLE_OK;
 }
 
@@ -227,6 +348,7 @@ int64_t oracle_lower_bound(const uint64_t* P, int64_t n, uint64_t key) {
  * binary-search positions of the bin delimiters. */
 int oracle_histogram(const uint64_t* P, int64_t n, const uint64_t* K, int64_t nl, uint32_t* N) {
     if (nl < 1) return ORACLE_E_ARG;
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < nl; ++i)
         N[i] = (uint32_t)(oracle_lower_bound(P, n, K[i + 1]) - oracle_lower_bound(P, n, K[i]));
     return ORACLE_OK;
@@ -244,6 +366,7 @@ int oracle_histogram(const uint64_t* P, int64_t n, const uint64_t* K, int64_t nl
  *   O_i = 1 otherwise. */
 int oracle_rebalance_decision(const uint64_t* K, const uint32_t* N, int64_t nl, uint32_t ncrit, uint32_t* O) {
     if (nl < 1) return ORACLE_E_ARG;
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < nl; ++i) {
         uint64_t delta = K[i + 1] - K[i];
         uint32_t op = 1;
@@ -279,6 +402,7 @@ int oracle_exclusive_scan(const uint32_t* O, int64_t len, uint64_t* Oprime) {
 /* Eq. (g3) with Eqs. (rebalancecopy) and (rebalancesplit); the new array ends with 8^L at
  * index O'_nl, the new number of leaves. */
 int oracle_rebalance(const uint64_t* K, const uint32_t* O, const uint64_t* Oprime, int64_t nl, uint64_t* Kout) {
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < nl; ++i) {
         uint64_t delta = K[i + 1] - K[i];
         if (O[i] == 1) {
@@ -332,6 +456,7 @@ int oracle_build_leaves(const uint64_t* P, int64_t n, uint32_t ncrit, const uint
         oracle_histogram(P, n, K, nl, N);
         oracle_rebalance_decision(K, N, nl, ncrit, O);
         int changed = 0;
+#pragma omp parallel for schedule(static) reduction(| : changed)
         for (int64_t i = 0; i < nl; ++i) changed |= (O[i] != 1);
         if (!changed) break;
         oracle_exclusive_scan(O, nl + 1, Op);
@@ -494,6 +619,7 @@ static int outside_focus(uint64_t start, uint64_t size, uint64_t f_start, uint64
 int oracle_focus_decision(const uint64_t* K, const uint32_t* N, int64_t nl, uint32_t ncrit, uint64_t f_start,
                           uint64_t f_end, double theta, int curve, uint32_t* O) {
     if (nl < 1) return ORACLE_E_ARG;
+#pragma omp parallel for schedule(dynamic, 1024)
     for (int64_t i = 0; i < nl; ++i) {
         uint64_t delta = K[i + 1] - K[i];
         int level = L;
@@ -561,6 +687,7 @@ int oracle_build_focus_leaves(const uint64_t* P, int64_t n, uint32_t ncrit, uint
         oracle_histogram(P, n, K, nl, N);
         oracle_focus_decision(K, N, nl, ncrit, f_start, f_end, theta, curve, O);
         int changed = 0;
+#pragma omp parallel for schedule(static) reduction(| : changed)
         for (int64_t i = 0; i < nl; ++i) changed |= (O[i] != 1);
         if (!changed) break;
         oracle_exclusive_scan(O, nl + 1, Op);
@@ -659,6 +786,9 @@ static int cmp_u64(const void* a, const void* b) {
     return (p > q) - (p < q);
 }
 
+/* Ascending order of n 64-bit words (equal words end up adjacent; the caller removes repeats). */
+static void sort_total_u64(uint64_t* a, uint64_t* tmp, int64_t n) { sort_total(a, tmp, n, sizeof(uint64_t), cmp_u64); }
+
 static int64_t find_u64(const uint64_t* a, int64_t n, uint64_t v) {
     int64_t lo = 0, hi = n;
     while (lo < hi) {
@@ -688,7 +818,9 @@ int oracle_link(const uint64_t* K, int64_t nl, uint64_t* NK, int32_t* CO, int32_
         int lev = leaf_level(K[i + 1] - K[i]);
         for (int a = 0; a <= lev; ++a) all[cnt++] = placeholder(K[i], a);
     }
-    qsort(all, (size_t)cnt, sizeof(uint64_t), cmp_u64);
+    uint64_t* tmp = (uint64_t*)malloc((size_t)(cnt > 0 ? cnt : 1) * sizeof(uint64_t));
+    sort_total_u64(all, tmp, cnt);
+    free(tmp);
     int64_t n = 0;
     for (int64_t i = 0; i < cnt; ++i)
         if (n == 0 || all[i] != all[n - 1]) all[n++] = all[i];
@@ -713,24 +845,33 @@ int oracle_link(const uint64_t* K, int64_t nl, uint64_t* NK, int32_t* CO, int32_
     }
     LO[L + 1] = (int32_t)n;
 
+    int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
     for (int64_t i = 0; i < n; ++i) {
         int lev = placeholder_level(NK[i]);
         int64_t c = (lev < L) ? find_u64(NK, n, NK[i] << 3) : -1;
         CO[i] = (c < 0) ? 0 : (int32_t)c;
         if (c >= 0) {
-            if ((c - 1) % 8 != 0) return ORACLE_E_INVARIANT;
+            if ((c - 1) % 8 != 0) {
+                bad = 1;
+                continue;
+            }
             for (int j = 0; j < 8; ++j)
-                if (c + j >= n || NK[c + j] != ((NK[i] << 3) | (uint64_t)j)) return ORACLE_E_INVARIANT;
+                if (c + j >= n || NK[c + j] != ((NK[i] << 3) | (uint64_t)j)) bad = 1;
             if (parent) parent[(c - 1) / 8] = (int32_t)i;
         }
     }
+#pragma omp parallel for schedule(static) reduction(| : bad)
     for (int64_t i = 0; i < nl; ++i) {
         int lev = leaf_level(K[i + 1] - K[i]);
         int64_t v = find_u64(NK, n, placeholder(K[i], lev));
-        if (v < 0) return ORACLE_E_INVARIANT;
+        if (v < 0) {
+            bad = 1;
+            continue;
+        }
         leaf_to_node[i] = (int32_t)v;
     }
-    return ORACLE_OK;
+    return bad ? ORACLE_E_INVARIANT : ORACLE_OK;
 }
 
 /* Key range [start, end) covered by a placeholder node key. */
@@ -744,6 +885,7 @@ static void node_range(uint64_t nk, uint64_t* start, uint64_t* end) {
 /* Node particle counts (Sec. 5, node properties): the number of sorted keys inside each node's
  * key range, by definition. */
 int oracle_node_counts(const uint64_t* P, int64_t n, const uint64_t* NK, int64_t nnodes, uint32_t* counts) {
+#pragma omp parallel for schedule(static)
     for (int64_t v = 0; v < nnodes; ++v) {
         uint64_t s, e;
         node_range(NK[v], &s, &e);
@@ -763,6 +905,7 @@ int oracle_node_counts(const uint64_t* P, int64_t n, const uint64_t* NK, int64_t
 int oracle_multipoles(const double* x, const double* y, const double* z, const float* m, const uint64_t* P,
                       const uint32_t* perm, int64_t n, const uint64_t* NK, const int64_t* nodes, int64_t nsel,
                       double* M, double* com, double* quad) {
+#pragma omp parallel for schedule(dynamic, 256)
     for (int64_t k = 0; k < nsel; ++k) {
         uint64_t s, e;
         node_range(NK[nodes[k]], &s, &e);

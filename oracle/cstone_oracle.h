@@ -5,10 +5,12 @@
  * only the test-suite, the smoke check and the CPU-baseline leg of the benchmark use it.
  * It shares no code, header, table or constant with the CUDA library.
  *
- * Every routine is the plain definition (or the paper's algorithm step by step), single
- * threaded, in double precision where floating point is involved, compiled without FMA
- * contraction (-ffp-contract=off) so that every floating-point operation is one IEEE
- * round-to-nearest operation.
+ * Every routine is the plain definition (or the paper's algorithm step by step), in double
+ * precision where floating point is involved, compiled without FMA contraction
+ * (-ffp-contract=off) so that every floating-point operation is one IEEE round-to-nearest
+ * operation. Loops over independent particles, leaves or nodes may run on several threads
+ * (OpenMP); each iteration does the same operations in the same order, so the results are those
+ * of the sequential program.
  *
  * Notation follows the paper: L octree levels (L = 21: 63-bit keys; the same source compiled
  * with -DORACLE_L=10 gives the 30-bit keys of Sec. 3's other choice), K = cornerstone array,
@@ -31,6 +33,11 @@
 #define ORACLE_E_CAPACITY (-2)
 #define ORACLE_E_NOT_CONVERGED (-3)
 #define ORACLE_E_INVARIANT (-4)
+
+/* Threads of the oracle's parallel loops (<= 0: all cores; 1: the sequential program). Results do
+ * not depend on it. */
+void oracle_set_threads(int threads);
+int oracle_get_threads(void);
 
 /* ---- Sec. 3: grid coordinates and space-filling-curve keys ---- */
 int oracle_bounding_cube(const double* x, const double* y, const double* z, int64_t n, double box[4]);
@@ -70,6 +77,10 @@ int oracle_build_focus_leaves(const uint64_t* P, int64_t n, uint32_t ncrit, uint
                               int64_t cap, int64_t* nl_out, uint32_t* Nout, int max_iters, int* iters_out);
 int oracle_canonical_focus_leaves(const uint64_t* P, int64_t n, uint32_t ncrit, uint64_t f_start, uint64_t f_end,
                                   double theta, int curve, uint64_t* Kout, int64_t cap, int64_t* nl_out);
+
+/* ---- Sec. 6: distributed octree and domain decomposition ---- */
+int oracle_cube_from_bounds(const double bounds[6], double box[4]);
+int oracle_decompose(const uint32_t* N, int64_t nl, int n_ranks, int64_t* cuts);
 
 /* ---- Sec. 5: fully linked octree ---- */
 int oracle_link(const uint64_t* K, int64_t nl, uint64_t* NK, int32_t* CO, int32_t* LO, int32_t* leaf_to_node,

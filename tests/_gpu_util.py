@@ -32,9 +32,13 @@ def i32(t) -> np.ndarray:
 
 
 def node_level(nk) -> np.ndarray:
+    """Level of each placeholder node key (1 << 3 level) | prefix: the number of levels l >= 1 with
+    key >= 1 << 3l (exact integer comparisons)."""
     nk = np.asarray(nk, np.uint64)
-    bits = np.array([int(v).bit_length() - 1 for v in nk])
-    return bits // 3
+    lev = np.zeros(nk.shape, np.int64)
+    for lv in range(1, L + 1):
+        lev += nk >= np.uint64(1 << (3 * lv))
+    return lev
 
 
 def multipole_errors(M_ref, com_ref, q_ref, M, com, q, node_side):

@@ -3,9 +3,9 @@
 * 65,536 uniform particles, Morton, Ncrit 64, unit cube: every output against the oracle.
 * 2^25 Plummer particles, Hilbert, Ncrit 64, bounding cube: every integer output against the
   oracle (the oracle finishes this size in well under a minute).
-* 2^27 clump particles, Hilbert, Ncrit 16 and 64 (the benchmark workload): sampled keys against
-  the oracle, size-independent properties of the sort and the tree, and sampled subtrees whose
-  particle sets the oracle rebuilds from the raw coordinates (leaves, counts, multipoles).
+* 2^27 clump particles, Hilbert, Ncrit 16 and 64 (the benchmark workload, built as bench.py builds
+  it, with multipoles): every output against the oracle element by element, and the multipoles of
+  every node within the 1e-6 tolerance of the FP64 oracle.
 * 2^20 particles of one 3D Gaussian, Morton and Hilbert, Ncrit 64 (the smallest size of the
   paper's Table 1 replay): every output against the oracle, and about 18 particles per leaf as
   the paper reports for its Gaussian sets.
@@ -78,119 +78,49 @@ def test_plummer_2p25_hilbert_full_parity(lib, oracle):
     _check_all(out, ref)
 
 
-# ------------------------------------------------------------------ 2^27 clumps, sampled
-def _node_particles(oracle, x, y, z, box, nk, curve):
-    """Indices of the particles inside node nk, found from the raw coordinates: a spatial prefilter
-    of the node's cube (slightly enlarged) followed by the oracle's exact keys."""
-    lev = (int(nk).bit_length() - 1) // 3
-    prefix = int(nk) ^ (1 << (3 * lev))
-    start = prefix << (3 * (L - lev))
-    end = start + (1 << (3 * (L - lev)))
-    g = oracle.hilbert_decode(start) if curve == oracle.HILBERT else oracle.morton_decode(start)
-    cell = [c >> (L - lev) for c in g]
-    h = box[3] / 2.0 ** lev
-    eps = h * 1e-6 + box[3] * 2.0 ** -20
-    sel = np.ones(x.size, bool)
-    for d, c in enumerate((x, y, z)):
-        a = box[d] + cell[d] * h
-        sel &= (c >= a - eps) & (c < a + h + eps)
-    idx = np.nonzero(sel)[0]
-    k = oracle.keys(x[idx], y[idx], z[idx], box, curve)
-    keep = (k >= np.uint64(start)) & (k < np.uint64(end))
-    return idx[keep], k[keep]
-
-
+# ------------------------------------------------------------------ 2^27 clumps, full arrays
 @pytest.fixture(scope="module")
-def clumps_2p27():
+def clumps_2p27(oracle):
+    """The benchmark workload and the oracle's keys and sort of it (shared by both Ncrit values);
+    the oracle runs its independent loops on every core of the host (same results as one)."""
     from paper_2307_06345_gb300 import workloads as w
     n = 1 << 27
     x, y, z = w.clumps(n, w.BASE_SEED + 2)
     m = w.lognormal_masses(n, w.BASE_SEED + 3)
-    return x, y, z, m
+    oracle.set_threads(0)
+    box = oracle.bounding_cube(x, y, z)
+    keys = oracle.keys(x, y, z, box, oracle.HILBERT)
+    P, perm = oracle.sort(keys)
+    return {"x": x, "y": y, "z": z, "m": m, "box": box, "keys": keys, "P": P, "perm": perm}
 
 
 @pytest.mark.parametrize("ncrit", [64, 16])
-def test_clumps_2p27_sampled(lib, oracle, clumps_2p27, ncrit):
-    x, y, z, m = clumps_2p27
-    n = x.size
-    X, Y, Z, M = dev(x), dev(y), dev(z), dev(m)
-    out = lib.build_octree(X, Y, Z, curve=lib.HILBERT, ncrit=ncrit, masses=M)
+def test_clumps_2p27_full_parity(lib, oracle, clumps_2p27, ncrit):
+    """Every output of the benchmark build (bounding cube, keys, sorted keys, permutation, leaves,
+    leaf counts, pass count, NK, CO, LO, leaf-to-node map, node counts) equals the oracle's element
+    by element; the multipoles of every node are within 1e-6 of the oracle's FP64 moments."""
+    r = clumps_2p27
+    x, y, z, m = r["x"], r["y"], r["z"], r["m"]
+    out = lib.build_octree(dev(x), dev(y), dev(z), curve=lib.HILBERT, ncrit=ncrit, masses=dev(m))
     torch.cuda.synchronize()
-    box = out["box"].cpu().numpy()
-    # the bounding cube by definition (min / max are exact, so numpy's reductions agree)
-    lo = np.array([x.min(), y.min(), z.min()])
-    side = max(x.max() - lo[0], y.max() - lo[1], z.max() - lo[2])
-    assert np.array_equal(box, np.array([lo[0], lo[1], lo[2], side]))
-
-    rng = np.random.default_rng(ncrit)
-    # keys: a sample against the oracle
-    idx = rng.integers(0, n, 200_000)
-    assert np.array_equal(u64(out["keys"])[idx], oracle.keys(x[idx], y[idx], z[idx], box, oracle.HILBERT))
-
-    # sort: ordered, a permutation, consistent with the keys, stable
-    keys = out["keys"]
-    P = out["sorted_keys"]
-    perm = out["perm"].long()
-    assert bool((P[1:] >= P[:-1]).all())
-    assert torch.equal(keys[perm], P)
-    seen = torch.zeros(n, dtype=torch.int32, device="cuda")
-    seen.index_add_(0, perm, torch.ones(n, dtype=torch.int32, device="cuda"))
-    assert bool((seen == 1).all())
-    ties = P[1:] == P[:-1]
-    assert bool((perm[1:][ties] > perm[:-1][ties]).all())
-
-    # leaves: Eq. (cstone) invariants, counts are the histogram of P, balance of the leaves
-    K = u64(out["leaves"])
-    nl = out["n_leaves"]
-    assert K[0] == 0 and int(K[-1]) == KEY_END
-    d = np.diff(K)
-    one = np.uint64(1)
-    assert np.all(d > 0)
-    assert np.all((d & (d - one)) == 0)                           # powers of two ...
-    assert np.all((d & np.uint64(0x9249249249249249)) != 0)      # ... of eight
-    assert np.all((K[:-1] & (d - one)) == 0)                      # aligned: octree node keys
-    Pn = u64(P)
-    N = u32(out["leaf_counts"])
-    bounds = np.searchsorted(Pn, u64(out["leaves"]), side="left")
-    assert np.array_equal(N.astype(np.int64), np.diff(bounds))
-    assert np.all((N <= ncrit) | (d.astype(np.float64) == 1.0))
-
-    # tree: size, counts of internal nodes exceed Ncrit, children are consecutive key groups
-    nn = nl + (nl - 1) // 7
-    NK, CO, counts = u64(out["NK"]), i32(out["CO"]), u32(out["node_counts"])
-    assert NK.size == nn and counts[0] == n
-    internal = CO > 0
-    assert np.all(counts[internal] > ncrit)
-    ch = CO[internal]
-    for j in range(8):
-        assert np.array_equal(NK[ch + j], (NK[internal] << np.uint64(3)) | np.uint64(j))
-
-    # sampled subtrees rebuilt by the oracle from the raw coordinates
-    lev = node_level(NK[: min(nn, 2_000_000)])
-    cand = np.nonzero(internal[: lev.size] & (lev >= 4) & (counts[: lev.size] < 200_000))[0]
-    picks = rng.choice(cand, size=min(6, cand.size), replace=False)
-    M_all = out["mass"].cpu().numpy()
-    com_all = out["com"].cpu().numpy()
-    q_all = out["quad"].cpu().numpy()
-    for v in picks:
-        pidx, pkeys = _node_particles(oracle, x, y, z, box, NK[v], oracle.HILBERT)
-        assert pidx.size == counts[v]
-        Ps, pp = oracle.sort(pkeys)
-        Ksub = oracle.canonical_leaves(Ps, ncrit)
-        lv = (int(NK[v]).bit_length() - 1) // 3
-        start = (int(NK[v]) ^ (1 << (3 * lv))) << (3 * (L - lv))
-        end = start + (1 << (3 * (L - lv)))
-        Kg = u64(out["leaves"])
-        inside = Kg[(Kg >= np.uint64(start)) & (Kg < np.uint64(end))]
-        ref_inside = Ksub[(Ksub >= np.uint64(start)) & (Ksub < np.uint64(end))]
-        assert np.array_equal(inside, ref_inside)
-        # multipoles of the node and of its children from the oracle
-        sub = oracle.link(Ksub)
-        rows = [v] + list(range(CO[v], CO[v] + 8))
-        M_ref, c_ref, q_ref = oracle.multipoles(x[pidx], y[pidx], z[pidx], m[pidx], Ps, pp,
-                                                np.array([NK[r] for r in rows], np.uint64))
-        side_r = box[3] * 2.0 ** (-node_level(NK[rows]).astype(np.float64))
-        err = multipole_errors(M_ref, c_ref, q_ref, M_all[rows].astype(np.float64), com_all[:, rows].T.copy(),
-                               q_all[:, rows].T.astype(np.float64), side_r)
-        assert max(err.values()) <= 1e-6, err
-        del sub
+    assert np.array_equal(out["box"].cpu().numpy(), r["box"])
+    assert np.array_equal(u64(out["keys"]), r["keys"])
+    assert np.array_equal(u64(out["sorted_keys"]), r["P"])
+    assert np.array_equal(u32(out["perm"]), r["perm"])
+    K, N, iters = oracle.build_leaves(r["P"], ncrit)
+    assert np.array_equal(u64(out["leaves"]), K)
+    assert np.array_equal(u32(out["leaf_counts"]), N)
+    assert out["iters"] == iters
+    tree = oracle.link(K)
+    for name in ("CO", "LO", "leaf_to_node"):
+        assert np.array_equal(i32(out[name]), tree[name]), name
+    NK = u64(out["NK"])
+    assert np.array_equal(NK, tree["NK"])
+    assert np.array_equal(u32(out["node_counts"]), oracle.node_counts(r["P"], tree["NK"]))
+    M_ref, c_ref, q_ref = oracle.multipoles(x, y, z, m, r["P"], r["perm"], tree["NK"])
+    side = r["box"][3] * 2.0 ** (-node_level(tree["NK"]).astype(np.float64))
+    err = multipole_errors(M_ref, c_ref, q_ref, out["mass"].cpu().numpy().astype(np.float64),
+                           out["com"].cpu().numpy().T.copy(), out["quad"].cpu().numpy().T.astype(np.float64), side)
+    print(f"\nclumps 2^27 Ncrit {ncrit}: {out['n_leaves']} leaves, {NK.size} nodes, {iters} passes; "
+          f"max multipole errors over non-empty nodes: {err}")
+    assert max(err.values()) <= 1e-6, err
