@@ -15,8 +15,15 @@
 // (records.cuh), so coordinate differences are exact and are rounded to FP32 once; the expansion
 // centre (centre of mass) is kept in fixed point and written out in FP64.
 // A leaf takes its first particle as the anchor for the differences, an internal node its first
-// non-empty child's centre; second moments of an internal node use the parallel-axis shift
-// Q = sum_c [Q_c + M_c (c_c - c)(c_c - c)^T].
+// non-empty child's centre. The stored centre c' is the centre of mass rounded (the FP32 quotient
+// of the first moments, on the fixed-point grid), and every second moment is taken about c'. Each
+// node also carries its residual first moment r = sum m (x - c') (zero for the exact centre; the
+// rounding of c' makes it about -M (c' - c)), so that an internal node combines its children with
+// the exact parallel-axis shift about its own c':
+//   Q = sum_k [Q_k + M_k e_k e_k^T + r_k e_k^T + e_k r_k^T],  r = sum_k [r_k + M_k e_k],
+// with e_k = c'_k - c' (exact in fixed point). Dropping the r_k terms would leave an error of
+// order |c'_k - c_k| |e_k| M_k, which is not small against Q when the first moments were taken
+// about an anchor far from a tight concentration of the node's mass.
 #include "common.cuh"
 #include "records.cuh"
 
@@ -209,6 +216,7 @@ __device__ __forceinline__ float ff_val(ff a) { return __fadd_rn(a.hi, a.lo); }
 struct MpScratch {  // per node: compensated sums and the fixed-point centre carried up the tree
     ff* mass;           // [n]
     ff* quad;           // [6 n], component-major
+    ff* res;            // [3 n], component-major: residual first moment about the stored centre
     long long* cfix;    // [3 n], component-major
     Record* rec;        // [n_particles]
     u32* big;           // [n_leaves] leaves handed to the block-per-leaf kernel
@@ -216,10 +224,12 @@ struct MpScratch {  // per node: compensated sums and the fixed-point centre car
     int* internal;      // [n_internal] internal nodes in breadth-first order of their children
 };
 
-__device__ __forceinline__ void store_node(int v, u32 n_nodes, ff M, const long long c[3], const ff q[6], MpScratch s,
-                                           const FixedFrame& f, float* __restrict__ mass, double* __restrict__ com,
-                                           float* __restrict__ quad) {
+__device__ __forceinline__ void store_node(int v, u32 n_nodes, ff M, const long long c[3], const ff q[6],
+                                           const ff r[3], MpScratch s, const FixedFrame& f, float* __restrict__ mass,
+                                           double* __restrict__ com, float* __restrict__ quad) {
     s.mass[v] = M;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) s.res[(size_t)d * n_nodes + v] = r[d];
     mass[v] = ff_val(M);
     const bool empty = M.hi == 0.f && M.lo == 0.f;
 #pragma unroll
@@ -366,11 +376,15 @@ __global__ void __launch_bounds__(kLeafThreads, 4) multipole_leaf_kernel(const u
             c[d] = r0c[d] + float_to_int64(__fmul_rn(__fmul_rn(off, 1.0f / f.s1), 1.0f / f.s2));
         }
     }
+    ff R[3] = {ff_zero(), ff_zero(), ff_zero()};  // residual first moment about c
     auto second_moments = [&](const Record& r) {
         const float e0 = fixed_diff(r.x, c[0], f);
         const float e1 = fixed_diff(r.y, c[1], f);
         const float e2 = fixed_diff(r.z, c[2], f);
         const float me0 = __fmul_rn(r.m, e0), me1 = __fmul_rn(r.m, e1), me2 = __fmul_rn(r.m, e2);
+        acc(R[0], me0);
+        acc(R[1], me1);
+        acc(R[2], me2);
         acc(Q[0], __fmul_rn(me0, e0));
         acc(Q[1], __fmul_rn(me0, e1));
         acc(Q[2], __fmul_rn(me0, e2));
@@ -387,7 +401,9 @@ __global__ void __launch_bounds__(kLeafThreads, 4) multipole_leaf_kernel(const u
     }
 #pragma unroll
     for (int k = 0; k < 6; ++k) Q[k] = group_sum(Q[k]);
-    if (active && gl == 0) store_node(leaf_to_node[i], n_nodes, M, c, Q, s, f, mass, com, quad);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) R[d] = group_sum(R[d]);
+    if (active && gl == 0) store_node(leaf_to_node[i], n_nodes, M, c, Q, R, s, f, mass, com, quad);
 }
 
 // Sum of a compensated pair over the block (every thread gets the total); red holds kThreads / 32
@@ -451,12 +467,16 @@ __global__ void __launch_bounds__(kLeafThreads) multipole_bigleaf_kernel(const u
             const float off = Mv != 0.f ? __fdiv_rn(ff_val(S[d]), Mv) : 0.f;
             c[d] = r0c[d] + float_to_int64(__fmul_rn(__fmul_rn(off, 1.0f / f.s1), 1.0f / f.s2));
         }
+        ff R[3] = {ff_zero(), ff_zero(), ff_zero()};  // residual first moment about c
         for (u32 j = a + threadIdx.x; j < b; j += kLeafThreads) {
             const Record r = s.rec[__ldg(perm + j)];
             const float e0 = fixed_diff(r.x, c[0], f);
             const float e1 = fixed_diff(r.y, c[1], f);
             const float e2 = fixed_diff(r.z, c[2], f);
             const float me0 = __fmul_rn(r.m, e0), me1 = __fmul_rn(r.m, e1), me2 = __fmul_rn(r.m, e2);
+            R[0] = ff_add(R[0], me0);
+            R[1] = ff_add(R[1], me1);
+            R[2] = ff_add(R[2], me2);
             Q[0] = ff_add(Q[0], __fmul_rn(me0, e0));
             Q[1] = ff_add(Q[1], __fmul_rn(me0, e1));
             Q[2] = ff_add(Q[2], __fmul_rn(me0, e2));
@@ -466,7 +486,9 @@ __global__ void __launch_bounds__(kLeafThreads) multipole_bigleaf_kernel(const u
         }
 #pragma unroll
         for (int k = 0; k < 6; ++k) Q[k] = block_sum(Q[k], s_red);
-        if (threadIdx.x == 0) store_node(leaf_to_node[i], n_nodes, M, c, Q, s, f, mass, com, quad);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) R[d] = block_sum(R[d], s_red);
+        if (threadIdx.x == 0) store_node(leaf_to_node[i], n_nodes, M, c, Q, R, s, f, mass, com, quad);
         __syncthreads();
     }
 }
@@ -507,7 +529,7 @@ __global__ void __launch_bounds__(kThreads) multipole_level_kernel(const int* __
 #pragma unroll
                 for (int d = 0; d < 3; ++d) cc[k][d] = __ldcg(s.cfix + (size_t)d * n_nodes + c0 + k);
             }
-            ff Mp = ff_zero(), Sp[3] = {ff_zero(), ff_zero(), ff_zero()}, Qp[6];
+            ff Mp = ff_zero(), Sp[3] = {ff_zero(), ff_zero(), ff_zero()}, Qp[6], Rp[3] = {ff_zero(), ff_zero(), ff_zero()};
 #pragma unroll
             for (int k = 0; k < 6; ++k) Qp[k] = ff_zero();
             long long cp[3] = {0, 0, 0};
@@ -543,12 +565,32 @@ __global__ void __launch_bounds__(kThreads) multipole_level_kernel(const int* __
                     const float me0 = __fmul_rn(mk, e[0]), me1 = __fmul_rn(mk, e[1]), me2 = __fmul_rn(mk, e[2]);
                     const float shift[6] = {__fmul_rn(me0, e[0]), __fmul_rn(me0, e[1]), __fmul_rn(me0, e[2]),
                                             __fmul_rn(me1, e[1]), __fmul_rn(me1, e[2]), __fmul_rn(me2, e[2])};
+                    // the child's residual first moment about its own centre: cross terms r e^T + e r^T
+                    ff rk[3];
+                    float rv[3];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        const float2 rr = __ldcg(reinterpret_cast<const float2*>(s.res + (size_t)d * n_nodes) + c0 + k);
+                        rk[d] = ff{rr.x, rr.y};
+                        rv[d] = ff_val(rk[d]);
+                    }
+                    const float cross[6] = {
+                        __fmul_rn(2.0f, __fmul_rn(rv[0], e[0])), __fadd_rn(__fmul_rn(rv[0], e[1]), __fmul_rn(rv[1], e[0])),
+                        __fadd_rn(__fmul_rn(rv[0], e[2]), __fmul_rn(rv[2], e[0])), __fmul_rn(2.0f, __fmul_rn(rv[1], e[1])),
+                        __fadd_rn(__fmul_rn(rv[1], e[2]), __fmul_rn(rv[2], e[1])), __fmul_rn(2.0f, __fmul_rn(rv[2], e[2]))};
 #pragma unroll
                     for (int q = 0; q < 6; ++q) {
                         const float2 qq =
                             __ldcg(reinterpret_cast<const float2*>(s.quad + (size_t)q * n_nodes) + c0 + k);
                         Qp[q] = ff_add(Qp[q], ff{qq.x, qq.y});
                         Qp[q] = ff_add(Qp[q], shift[q]);
+                        Qp[q] = ff_add(Qp[q], cross[q]);
+                    }
+                    const float me[3] = {me0, me1, me2};
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        Rp[d] = ff_add(Rp[d], rk[d]);
+                        Rp[d] = ff_add(Rp[d], me[d]);
                     }
                 }
             }
@@ -556,7 +598,7 @@ __global__ void __launch_bounds__(kThreads) multipole_level_kernel(const int* __
                 raise_error(hdr, CSTONE_ERR_INVALID_ARG, 0x75000u);
                 continue;
             }
-            store_node(x, n_nodes, Mp, cp, Qp, s, f, mass, com, quad);
+            store_node(x, n_nodes, Mp, cp, Qp, Rp, s, f, mass, com, quad);
         }
         grid_barrier(bar, hdr);
     }
@@ -580,6 +622,7 @@ UpLayout up_layout(void* ws, long long nl, long long n_particles, bool multipole
     if (multipoles) {
         l.mp.mass = c.take<ff>((size_t)nn);
         l.mp.quad = c.take<ff>((size_t)nn * 6);
+        l.mp.res = c.take<ff>((size_t)nn * 3);
         l.mp.cfix = c.take<long long>((size_t)nn * 3);
         l.mp.rec = c.take<Record>((size_t)(n_particles > 0 ? n_particles : 1));
         l.mp.big = c.take<u32>((size_t)nl);
