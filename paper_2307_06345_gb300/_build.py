@@ -58,7 +58,7 @@ def _sources():
 
 # Translation units that do not depend on the key length; every other one is compiled twice, for
 # 63-bit keys (entry points cstone_*) and with CSTONE_KEY32 for 30-bit keys (cstone30_*).
-KEY_INDEPENDENT = {"status.cu"}
+KEY_INDEPENDENT = {"status.cu", "decompose.cu"}
 
 
 def _units():

@@ -15,12 +15,10 @@ parameter so that the protocol can be exercised by processes without a GPU.
 """
 from __future__ import annotations
 
-import math
-
 import torch
 
-from . import (HILBERT, LEVELS, Workspace, cstone_bounds, cstone_keys, cstone_leaf_counts, cstone_rebalance,
-               cstone_sort)
+from . import (HILBERT, LEVELS, Workspace, cstone_bounds, cstone_cube_from_bounds, cstone_decompose, cstone_keys,
+               cstone_leaf_counts, cstone_rebalance, cstone_sort)
 
 
 class DeviceOps:
@@ -36,6 +34,18 @@ class DeviceOps:
         out = torch.empty(6, dtype=torch.float64, device=self.device)
         cstone_bounds(x, y, z, out, self.ws)
         return out
+
+    def cube(self, bounds):
+        """Bounding cube {lo, side} of per-axis bounds reduced over the ranks."""
+        box = torch.empty(4, dtype=torch.float64, device=self.device)
+        cstone_cube_from_bounds(bounds.contiguous(), box)
+        return box
+
+    def decompose(self, N, world: int):
+        """The world + 1 leaf cuts of the decomposition of the global counts N (int64 tensor)."""
+        cuts = torch.empty(world + 1, dtype=torch.int64, device=self.device)
+        cstone_decompose(N, N.numel(), world, cuts, self.ws)
+        return cuts
 
     def keys(self, x, y, z, box, curve):
         k = torch.empty(x.numel(), dtype=self.key_dtype, device=self.device)
@@ -76,18 +86,16 @@ def _allreduce(t, op, group):
 
 
 def global_box(ops, x, y, z, group=None):
-    """Bounding cube of the union of all ranks' particles: {lo_x, lo_y, lo_z, side} (float64)."""
+    """Bounding cube of the union of all ranks' particles: {lo_x, lo_y, lo_z, side} (float64). The
+    per-axis minima and maxima are reduced over the ranks; the cube is formed from them by
+    ``ops.cube`` (cstone_cube_from_bounds on the device)."""
     import torch.distributed as dist
 
     b = ops.bounds(x, y, z)
     lo, hi = b[:3].clone(), b[3:].clone()
     _allreduce(lo, dist.ReduceOp.MIN, group)
     _allreduce(hi, dist.ReduceOp.MAX, group)
-    lo_h, hi_h = lo.cpu().tolist(), hi.cpu().tolist()
-    if any(math.isinf(v) for v in lo_h):  # no particle anywhere
-        return torch.tensor([0.0, 0.0, 0.0, 1.0], dtype=torch.float64, device=b.device)
-    side = max(h - l for l, h in zip(lo_h, hi_h))  # one IEEE subtraction per axis, as on one process
-    return torch.tensor(lo_h + [side if side > 0.0 else 1.0], dtype=torch.float64, device=b.device)
+    return ops.cube(torch.cat([lo, hi]))
 
 
 def global_leaves(ops, P, ncrit: int, group=None, max_iters: int = 64):
@@ -108,21 +116,11 @@ def global_leaves(ops, P, ncrit: int, group=None, max_iters: int = 64):
     raise RuntimeError(f"global leaf array not converged after {max_iters} passes")
 
 
-def decompose(N_global, world: int):
-    """Leaf ranges per rank along the curve: rank r owns leaves [first[r], first[r + 1]), cut where
-    the running global count passes r / world of the total. Returns the list of world + 1 cuts."""
-    counts = [int(v) for v in N_global.cpu().tolist()]
-    total = sum(counts)
-    cuts, run, r = [0], 0, 1
-    for i, c in enumerate(counts):
-        while r < world and run >= total * r / world:
-            cuts.append(i)
-            r += 1
-        run += c
-    while len(cuts) < world:
-        cuts.append(len(counts))
-    cuts.append(len(counts))
-    return cuts
+def decompose(ops, N_global, world: int):
+    """Leaf ranges per rank along the curve (Sec. 6): rank r owns leaves [cuts[r], cuts[r + 1]), cut
+    at the first leaf whose preceding leaves hold r / world of the total (``ops.decompose``,
+    cstone_decompose on the device). Returns the world + 1 cuts as an int64 tensor."""
+    return ops.decompose(N_global, world)
 
 
 def exchange(ops, x, y, z, P, perm, K, cuts, group=None, extra=()):
@@ -132,8 +130,8 @@ def exchange(ops, x, y, z, P, perm, K, cuts, group=None, extra=()):
     *extra) in key order of the senders."""
     import torch.distributed as dist
 
-    world = len(cuts) - 1
-    bounds = K[torch.tensor(cuts, device=K.device)].contiguous()  # range starts + the end key
+    world = cuts.numel() - 1
+    bounds = K[cuts.to(K.device)].contiguous()  # range starts + the end key
     send = ops.leaf_counts(P, bounds, world).to(torch.int64)
     cols = [c.index_select(0, perm.to(torch.int64)) for c in (x, y, z) + tuple(extra)]
     if group is False or not (dist.is_available() and dist.is_initialized()) or dist.get_world_size(group) == 1:

@@ -1,5 +1,5 @@
 """Host protocol of the global tree of a particle set spread over several processes (Sec. 6):
-two gloo ranks on the CPU. The per-rank steps (bounds, keys, sort, f, g) are the oracle's, so the
+two and three gloo ranks on the CPU. The per-rank steps (bounds, keys, sort, f, g) are the oracle's, so the
 test exercises the protocol (allreduce of the counts after every f, identical g on every rank, the
 decomposition and the particle exchange) without a GPU; the kernels behind the same steps are
 checked against the oracle by the GPU tests. The result must equal the oracle's single-process
@@ -27,6 +27,12 @@ class OracleOps:
             return torch.tensor([np.inf] * 3 + [-np.inf] * 3, dtype=torch.float64)
         c = [t.numpy() for t in (x, y, z)]
         return torch.tensor([a.min() for a in c] + [a.max() for a in c], dtype=torch.float64)
+
+    def cube(self, bounds):
+        return torch.from_numpy(self.o.cube_from_bounds(bounds.numpy()))
+
+    def decompose(self, N, world):
+        return torch.from_numpy(self.o.decompose(N.numpy().view(np.uint32), world))
 
     def keys(self, x, y, z, box, curve):
         k = self.o.keys(x.numpy(), y.numpy(), z.numpy(), box.numpy(), curve)
@@ -82,17 +88,17 @@ def _worker(rank, world, port, q, ncrit):
         ids = torch.from_numpy(np.nonzero(mine)[0].astype(np.float64))  # global particle ids ride along
         ops = OracleOps(oracle)
         t = D.build_global_tree(X, Y, Z, curve=1, ncrit=ncrit, group=None, ops=ops)
-        cuts = D.decompose(t["N_global"], world)
+        cuts = D.decompose(ops, t["N_global"], world)
         rx, ry, rz, rid = D.exchange(ops, X, Y, Z, t["P"], t["perm"], t["K"], cuts, extra=(ids,))
         q.put((rank, t["box"].numpy(), t["K"].numpy().view(np.uint64), t["N_global"].numpy().view(np.uint32),
-               t["passes"], cuts, rx.numpy(), ry.numpy(), rz.numpy(), rid.numpy().astype(np.int64)))
+               t["passes"], cuts.tolist(), rx.numpy(), ry.numpy(), rz.numpy(), rid.numpy().astype(np.int64)))
     finally:
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("ncrit", [16, 64])
-def test_two_ranks_build_the_single_process_tree(oracle, ncrit):
-    world, port = 2, _free_port()
+@pytest.mark.parametrize("world,ncrit", [(2, 16), (2, 64), (3, 16)])
+def test_ranks_build_the_single_process_tree(oracle, world, ncrit):
+    port = _free_port()
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     procs = [ctx.Process(target=_worker, args=(r, world, port, q, ncrit)) for r in range(world)]
@@ -129,15 +135,13 @@ def test_two_ranks_build_the_single_process_tree(oracle, ncrit):
     assert np.array_equal(np.sort(np.concatenate(got_ids)), np.arange(x.size))
 
 
-def test_decompose_balances_and_covers():
+def test_decompose_goes_through_the_ops(oracle):
+    """The protocol's decomposition is the ops' (the device call on a GPU rank); with the oracle's
+    ops it gives the oracle's cuts, which the oracle's own tests pin to the definition."""
     from paper_2307_06345_gb300 import distributed as D
     N = torch.tensor([5, 0, 7, 3, 3, 9, 1, 0, 4, 8], dtype=torch.int32)
+    ops = OracleOps(oracle)
     for world in (1, 2, 3, 4, 10, 16):
-        cuts = D.decompose(N, world)
-        assert len(cuts) == world + 1 and cuts[0] == 0 and cuts[-1] == N.numel()
-        assert all(a <= b for a, b in zip(cuts, cuts[1:]))
-        total = int(N.sum())
-        for r in range(world):  # a rank starts at the first leaf whose preceding count reaches r/world
-            before = int(N[: cuts[r]].sum())
-            assert before >= total * r / world - 1e-9 or cuts[r] == 0
-    assert D.decompose(torch.zeros(4, dtype=torch.int32), 3) == [0, 0, 0, 4]
+        cuts = D.decompose(ops, N, world)
+        assert cuts.tolist() == oracle.decompose(N.numpy().view(np.uint32), world).tolist()
+    assert D.decompose(ops, torch.zeros(4, dtype=torch.int32), 3).tolist() == [0, 0, 0, 4]

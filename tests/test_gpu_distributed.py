@@ -92,6 +92,56 @@ def test_emulated_ranks_build_the_union_tree(lib, oracle, levels, curve, ncrit):
     t = D.build_global_tree(dev(x), dev(y), dev(z), curve=curve, ncrit=ncrit, levels=levels)
     got1 = u64(t["K"]) if levels == 21 else u32(t["K"]).astype(np.uint64)
     assert np.array_equal(got1, ref["K"]) and t["passes"] == ref["iters"]
-    cuts = D.decompose(t["N_global"], 4)
+    cuts = D.decompose(ops, t["N_global"], 4)
     rx, ry, rz = D.exchange(ops, dev(x), dev(y), dev(z), t["P"], t["perm"], t["K"], cuts)
     assert np.array_equal(rx.cpu().numpy(), x[ref["perm"]])  # one rank: the particles in key order
+
+
+@pytest.mark.parametrize("world", [1, 2, 3, 8, 97])
+def test_decompose_kernel_matches_oracle(lib, oracle, world):
+    """cstone_decompose through the C ABI against the oracle's cuts (Sec. 6), on leaf counts of the
+    clump workload's balanced tree and on counts with long runs of empty leaves."""
+    import ctypes
+    from paper_2307_06345_gb300 import workloads as w
+    x, y, z = w.clumps(400_000, w.BASE_SEED + 90, n_clumps=30)
+    ref = oracle.full_build(x, y, z, oracle.HILBERT, 16)
+    rng = np.random.default_rng(world)
+    sparse = rng.integers(0, 50, 200_003).astype(np.uint32)
+    sparse[rng.random(sparse.size) < 0.9] = 0
+    clib = lib.load()
+    for N in (ref["N"], sparse, np.zeros(5000, np.uint32), np.zeros(0, np.uint32)):
+        cuts = torch.full((world + 1,), -7, dtype=torch.int64, device="cuda")
+        Nd = dev(N) if N.size else torch.zeros(1, dtype=torch.int32, device="cuda")
+        sz = ctypes.c_size_t()
+        assert clib.cstone_decompose_workspace_size(N.size, world, ctypes.byref(sz)) == lib.OK
+        ws = torch.empty(sz.value, dtype=torch.uint8, device="cuda")
+        rc = clib.cstone_decompose(ctypes.c_void_p(Nd.data_ptr()), N.size, world, ctypes.c_void_p(cuts.data_ptr()),
+                                   ctypes.c_void_p(ws.data_ptr()), sz.value,
+                                   ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert rc == lib.OK
+        torch.cuda.synchronize()
+        assert cuts.cpu().tolist() == oracle.decompose(N, world).tolist()
+
+
+def test_cube_from_bounds_kernel_matches_oracle(lib, oracle):
+    """cstone_cube_from_bounds on bounds reduced over three parts equals the oracle's cube of the
+    same bounds and the bounding cube of the union; no points give the unit cube at the origin."""
+    from paper_2307_06345_gb300 import workloads as w
+    parts = [w.plummer(20_000 + 5000 * k, w.BASE_SEED + 91 + k) for k in range(3)]
+    ws = lib.Workspace()
+    lo, hi = [], []
+    for p in parts:
+        b = torch.empty(6, dtype=torch.float64, device="cuda")
+        lib.cstone_bounds(dev(p[0]), dev(p[1]), dev(p[2]), b, ws)
+        lo.append(b[:3])
+        hi.append(b[3:])
+    bounds = torch.cat([torch.stack(lo).min(0).values, torch.stack(hi).max(0).values])
+    box = torch.empty(4, dtype=torch.float64, device="cuda")
+    lib.cstone_cube_from_bounds(bounds, box)
+    torch.cuda.synchronize()
+    union = [np.concatenate([p[d] for p in parts]) for d in range(3)]
+    assert np.array_equal(box.cpu().numpy(), oracle.cube_from_bounds(bounds.cpu().numpy()))
+    assert np.array_equal(box.cpu().numpy(), oracle.bounding_cube(*union))
+    empty = torch.tensor([np.inf] * 3 + [-np.inf] * 3, dtype=torch.float64, device="cuda")
+    lib.cstone_cube_from_bounds(empty, box)
+    assert box.cpu().tolist() == [0.0, 0.0, 0.0, 1.0]
