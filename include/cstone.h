@@ -345,6 +345,67 @@ CSTONE_API int cstone_upsweep_counts_batched(const uint32_t* elem_counts, int64_
                                              void* ws, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------------------------
+ * The whole batched build in one call (Sec. 4: the f / g loop of every set from its root, or
+ * warm-started from the previous arrays; Sec. 5: the linked octree of every set and its node
+ * counts): bounding cubes (when no boxes are given), keys, segmented sort, leaf loop, linked trees
+ * and node counts, one launch per phase for all sets. Nothing is read back to the host and nothing
+ * is allocated, so the call can be captured in a CUDA graph: the phases after the leaf loop run on
+ * the capacities elem_cap and node_cap, the element count of the result is element_offsets[S] and
+ * the node count level_offsets[S-1][22] (both on the device), and the outcome stays in the
+ * workspace until cstone_build_batched_result reads it. On a failure of the leaf loop (capacity,
+ * max_iters, a timeout) every set's output is its root array, so the later phases stay in bounds;
+ * the caller then retries with a larger elem_cap (cold, since the warm arrays were overwritten).
+ * Per-set results equal those of the single-set calls on each set alone. At most 4096 sets.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct {
+    const double* x;             /* [n] float64 device, all sets back to back */
+    const double* y;
+    const double* z;
+    int64_t n;
+    const int64_t* set_offsets;  /* [S + 1] int64 device: set s owns particles [off[s], off[s+1]) */
+    int32_t n_sets;              /* S, 1 .. 4096 */
+    const double* boxes;         /* [S][4] float64 device {lo, side} per set, or NULL: bounding cubes */
+} cstone_batch_input;
+
+typedef struct {
+    int32_t curve;      /* CSTONE_MORTON or CSTONE_HILBERT */
+    uint32_t ncrit;     /* N_crit */
+    int32_t max_iters;  /* bound on f / g passes, 1 .. 256 */
+    int32_t warm;       /* 0: every set from its root; else elements / element_offsets hold the previous
+                           arrays, their element count being element_offsets[S] (on the device) */
+} cstone_batch_params;
+
+typedef struct {                /* all device arrays, owned by the caller */
+    double* boxes_out;          /* [S][4]: the bounding cubes when input boxes is NULL (else unused) */
+    uint64_t* keys;             /* [n] keys in input order */
+    uint64_t* sorted_keys;      /* [n] sorted within each set (must not alias keys) */
+    uint32_t* perm;             /* [n] global input index of each sorted key */
+    uint64_t* elements;         /* [elem_cap] every set's leaves followed by its end key 8^L */
+    int64_t elem_cap;           /* at least 2 S */
+    int64_t* element_offsets;   /* [S + 1] set s owns elements [eo[s], eo[s+1]) */
+    uint32_t* leaf_counts;      /* [elem_cap] (0 at end keys) */
+    uint32_t* leaf_offsets;     /* [elem_cap] first sorted particle (global) of each element, or NULL */
+    uint64_t* node_keys;        /* [node_cap] NK of every set, one breadth-first block per set */
+    int32_t* child;             /* [node_cap] CO, global node indices, 0 for a leaf */
+    int32_t* level_offsets;     /* [S][23] LO, global node indices */
+    int32_t* leaf_to_node;      /* [elem_cap] global node index of each leaf, -1 at end keys and beyond */
+    uint32_t* node_counts;      /* [node_cap] */
+    int64_t node_cap;           /* at least elem_cap + elem_cap / 7 + S */
+} cstone_batch_buffers;
+
+CSTONE_API int cstone_build_batched_workspace_size(int64_t n, int32_t n_sets, int64_t elem_cap, int32_t max_iters,
+                                                   size_t* bytes);
+CSTONE_API int cstone_build_batched(const cstone_batch_input* in, const cstone_batch_params* params,
+                                    const cstone_batch_buffers* out, void* ws, size_t ws_bytes, void* stream);
+/* Outcome of the last cstone_build_batched on `ws` (n, n_sets, elem_cap and max_iters as given to
+ * it; level_offsets its output): returns its status, with *n_elements (host) = elements of the
+ * result (on CSTONE_ERR_CAPACITY: the count needed), *n_nodes (host) = nodes of all trees and
+ * *iters (host, may be NULL) = f / g passes. Synchronises `stream`. */
+CSTONE_API int cstone_build_batched_result(const void* ws, int64_t n, int32_t n_sets, int64_t elem_cap,
+                                           int32_t max_iters, const int32_t* level_offsets, void* stream,
+                                           int64_t* n_elements, int64_t* n_nodes, int32_t* iters);
+
+/* ------------------------------------------------------------------------------------------
  * f and g as separate steps, for a leaf array whose counts are summed over several processes
  * (the global tree of Sec. 6: every rank counts its own particles, the counts are summed by an
  * allreduce, and every rank applies the same g to the summed counts).
@@ -364,6 +425,30 @@ CSTONE_API int cstone_rebalance_workspace_size(int64_t n_leaves, size_t* bytes);
 CSTONE_API int cstone_rebalance(const uint64_t* leaves, const uint32_t* counts, int64_t n_leaves, uint32_t ncrit,
                                 uint64_t* leaves_out, int64_t leaf_cap, int64_t* n_leaves_out, int32_t* changed,
                                 void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------------------------
+ * SFC domain decomposition (Sec. 6). A set spread over several processes takes the minimum of the
+ * per-axis minima and the maximum of the maxima of cstone_bounds over the processes, and
+ * cstone_cube_from_bounds turns them into the bounding cube of the union, with the arithmetic of
+ * cstone_bbox: lo = minima, side = largest extent (one IEEE subtraction per axis), side 1 when it is
+ * 0 or when there is no point (minima of +inf).
+ *   bounds [6] float64 device {min x, min y, min z, max x, max y, max z}; box [4] float64 device
+ *   output {lo_x, lo_y, lo_z, side}. Asynchronous.
+ *
+ * cstone_decompose cuts the globally replicated leaf array into n_ranks bins of consecutive
+ * leaves holding about N_tot / n_ranks particles each (the paper's "approximately"; this library's
+ * reading): cut r (0 < r < n_ranks) is the first leaf whose preceding leaves hold at least
+ * r N_tot / n_ranks particles, compared exactly in integers, n_leaves if no leaf qualifies;
+ * cuts[0] = 0, cuts[n_ranks] = n_leaves. Rank r owns leaves [cuts[r], cuts[r+1]), the key range
+ * [K[cuts[r]], K[cuts[r+1]]).
+ *   counts [n_leaves] uint32 device: the global leaf counts (summed over the processes); their sum
+ *          must stay below 2^64 / n_ranks.
+ *   n_ranks 1 .. 65536; cuts [n_ranks + 1] int64 device output. Asynchronous.
+ * ------------------------------------------------------------------------------------------ */
+CSTONE_API int cstone_cube_from_bounds(const double* bounds, double* box, void* stream);
+CSTONE_API int cstone_decompose_workspace_size(int64_t n_leaves, int32_t n_ranks, size_t* bytes);
+CSTONE_API int cstone_decompose(const uint32_t* counts, int64_t n_leaves, int32_t n_ranks, int64_t* cuts, void* ws,
+                                size_t ws_bytes, void* stream);
 
 /* Locally essential octree focused on the key range F = [f_start, f_end) (Sec. 7): one pass of
  * g1^LE, g2, g3 on the given counts. Inside F, and for a node overlapping F, the rule of

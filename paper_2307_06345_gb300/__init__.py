@@ -29,6 +29,8 @@ __all__ = [
     "cstone_leaves_result", "cstone_kernel_launches", "TimeStepper", "GraphTimeStepper", "cstone_leaf_counts",
     "cstone_rebalance", "cstone_bounds", "cstone_rebalance_focus", "build_focus_leaves", "LEVELS", "LEVELS30",
     "StreamedBuilder", "records_size", "cstone_keys_records", "cstone_upsweep_multipoles_records",
+    "cstone_cube_from_bounds", "cstone_decompose", "cstone_build_batched", "cstone_build_batched_result",
+    "BatchBuffers", "batched_capacity",
 ]
 
 MORTON, HILBERT = 0, 1
@@ -100,10 +102,17 @@ def load():
             "cstone_leaves_result": (ctypes.c_int, [P, i64, i32, P, pi64, pi32]),
             "cstone_leaf_counts": (ctypes.c_int, [P, i64, P, i64, P, P]),
             "cstone_bounds": (ctypes.c_int, [P, P, P, i64, P, P, sz, P]),
+            "cstone_cube_from_bounds": (ctypes.c_int, [P, P, P]),
+            "cstone_decompose_workspace_size": (ctypes.c_int, [i64, i32, psz]),
+            "cstone_decompose": (ctypes.c_int, [P, i64, i32, P, P, sz, P]),
             "cstone_rebalance_focus": (ctypes.c_int, [P, P, i64, u32, ctypes.c_uint64, ctypes.c_uint64,
                                                       ctypes.c_double, ctypes.c_int, P, i64, pi64, pi32, P, sz, P]),
             "cstone_rebalance_workspace_size": (ctypes.c_int, [i64, psz]),
             "cstone_rebalance": (ctypes.c_int, [P, P, i64, u32, P, i64, pi64, pi32, P, sz, P]),
+            "cstone_build_batched_workspace_size": (ctypes.c_int, [i64, i32, i64, i32, psz]),
+            "cstone_build_batched": (ctypes.c_int, [ctypes.POINTER(_BatchInput), ctypes.POINTER(_BatchParams),
+                                                    ctypes.POINTER(_BatchBuffers), P, sz, P]),
+            "cstone_build_batched_result": (ctypes.c_int, [P, i64, i32, i64, i32, P, P, pi64, pi64, pi32]),
             "cstone_records_size": (ctypes.c_int, [i64, psz]),
             "cstone_keys_records_workspace_size": (ctypes.c_int, [psz]),
             "cstone_keys_records": (ctypes.c_int, [P, P, P, P, i64, P, ctypes.c_int, P, P, P, sz, P]),
@@ -179,6 +188,25 @@ def _need(t: torch.Tensor, dtype, name):
         raise ValueError(f"{name} must be a contiguous CUDA tensor of {dtype}")
 
 
+class _BatchInput(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("z", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("set_offsets", ctypes.c_void_p), ("n_sets", ctypes.c_int32), ("boxes", ctypes.c_void_p)]
+
+
+class _BatchParams(ctypes.Structure):
+    _fields_ = [("curve", ctypes.c_int32), ("ncrit", ctypes.c_uint32), ("max_iters", ctypes.c_int32),
+                ("warm", ctypes.c_int32)]
+
+
+class _BatchBuffers(ctypes.Structure):
+    _fields_ = [("boxes_out", ctypes.c_void_p), ("keys", ctypes.c_void_p), ("sorted_keys", ctypes.c_void_p),
+                ("perm", ctypes.c_void_p), ("elements", ctypes.c_void_p), ("elem_cap", ctypes.c_int64),
+                ("element_offsets", ctypes.c_void_p), ("leaf_counts", ctypes.c_void_p),
+                ("leaf_offsets", ctypes.c_void_p), ("node_keys", ctypes.c_void_p), ("child", ctypes.c_void_p),
+                ("level_offsets", ctypes.c_void_p), ("leaf_to_node", ctypes.c_void_p),
+                ("node_counts", ctypes.c_void_p), ("node_cap", ctypes.c_int64)]
+
+
 # ------------------------------------------------------------------------- C entry points
 def _family(levels: int):
     """(C function, key dtype) picker for the key length: 21 levels -> cstone_*, int64 keys;
@@ -216,6 +244,29 @@ def cstone_bounds(x, y, z, bounds, ws: Workspace, stream=None):
     buf = ws.get(_size(lib.cstone_bbox_workspace_size, x.numel()))
     _check(lib.cstone_bounds(_ptr(x), _ptr(y), _ptr(z), x.numel(), _ptr(bounds), _ptr(buf), buf.numel(),
                              _stream(stream)), "cstone_bounds")
+
+
+def cstone_cube_from_bounds(bounds, box, stream=None):
+    """box[4] (float64 CUDA) = the bounding cube of the per-axis bounds[6] (minima, maxima) reduced
+    over several processes (Sec. 6)."""
+    _need(bounds, torch.float64, "bounds")
+    _need(box, torch.float64, "box")
+    if bounds.numel() < 6 or box.numel() < 4:
+        raise ValueError("bounds needs 6 entries and box 4")
+    _check(load().cstone_cube_from_bounds(_ptr(bounds), _ptr(box), _stream(stream)), "cstone_cube_from_bounds")
+
+
+def cstone_decompose(counts, n_leaves: int, n_ranks: int, cuts, ws: Workspace, stream=None):
+    """cuts[n_ranks + 1] (int64 CUDA) = the SFC domain decomposition of the global leaf counts
+    (Sec. 6): rank r owns leaves [cuts[r], cuts[r + 1])."""
+    lib = load()
+    _need(counts, torch.int32, "counts")
+    _need(cuts, torch.int64, "cuts")
+    if counts.numel() < n_leaves or cuts.numel() < n_ranks + 1:
+        raise ValueError("counts needs n_leaves entries and cuts n_ranks + 1")
+    buf = ws.get(_size(lib.cstone_decompose_workspace_size, n_leaves, n_ranks))
+    _check(lib.cstone_decompose(_ptr(counts), n_leaves, n_ranks, _ptr(cuts), _ptr(buf), buf.numel(),
+                                _stream(stream)), "cstone_decompose")
 
 
 def cstone_keys(x, y, z, box, curve: int, keys, stream=None, levels: int = LEVELS):
@@ -658,65 +709,150 @@ def cstone_upsweep_counts_batched(elem_counts, n_elements: int, leaf_to_node, ch
                                              _stream(stream)), "cstone_upsweep_counts_batched")
 
 
+def batched_capacity(n: int, n_sets: int, ncrit: int) -> int:
+    """Element capacity of a first batched build (grown if the trees need more)."""
+    return max(4 * n_sets, 16 * (n // (ncrit + 1)) + 2 * n_sets + 4096)
+
+
+@dataclass
+class BatchBuffers:
+    """Device buffers of cstone_build_batched at an element capacity (node capacity
+    elem_cap + elem_cap / 7 + S), reusable by later builds of the same sets."""
+    n: int
+    n_sets: int
+    elem_cap: int
+    node_cap: int
+    t: dict
+
+    @classmethod
+    def allocate(cls, n: int, n_sets: int, elem_cap: int, device, keep=None):
+        d = torch.device(device)
+        node_cap = elem_cap + elem_cap // 7 + n_sets
+        t = {} if keep is None else {k: keep.t[k] for k in ("boxes", "keys", "sorted_keys", "perm", "element_offsets",
+                                                             "LO")}
+        if keep is None:
+            t["boxes"] = torch.empty((n_sets, 4), dtype=torch.float64, device=d)
+            t["keys"] = torch.empty(max(n, 1), dtype=torch.int64, device=d)
+            t["sorted_keys"] = torch.empty(max(n, 1), dtype=torch.int64, device=d)
+            t["perm"] = torch.empty(max(n, 1), dtype=torch.int32, device=d)
+            t["element_offsets"] = torch.empty(n_sets + 1, dtype=torch.int64, device=d)
+            t["LO"] = torch.empty((n_sets, LEVELS + 2), dtype=torch.int32, device=d)
+        t["elements"] = torch.empty(elem_cap, dtype=torch.int64, device=d)
+        t["leaf_counts"] = torch.empty(elem_cap, dtype=torch.int32, device=d)
+        t["leaf_offsets"] = torch.empty(elem_cap, dtype=torch.int32, device=d)
+        t["leaf_to_node"] = torch.empty(elem_cap, dtype=torch.int32, device=d)
+        t["NK"] = torch.empty(node_cap, dtype=torch.int64, device=d)
+        t["CO"] = torch.empty(node_cap, dtype=torch.int32, device=d)
+        t["node_counts"] = torch.empty(node_cap, dtype=torch.int32, device=d)
+        return cls(n=n, n_sets=n_sets, elem_cap=elem_cap, node_cap=node_cap, t=t)
+
+    def c_struct(self) -> _BatchBuffers:
+        t = self.t
+        return _BatchBuffers(t["boxes"].data_ptr(), t["keys"].data_ptr(), t["sorted_keys"].data_ptr(),
+                             t["perm"].data_ptr(), t["elements"].data_ptr(), self.elem_cap,
+                             t["element_offsets"].data_ptr(), t["leaf_counts"].data_ptr(),
+                             t["leaf_offsets"].data_ptr(), t["NK"].data_ptr(), t["CO"].data_ptr(),
+                             t["LO"].data_ptr(), t["leaf_to_node"].data_ptr(), t["node_counts"].data_ptr(),
+                             self.node_cap)
+
+
+def cstone_build_batched(x, y, z, set_offsets, bufs: BatchBuffers, curve: int, ncrit: int, boxes=None,
+                         warm: bool = False, max_iters: int = 64, ws: Workspace | None = None, stream=None):
+    """The whole batched build in one C call (no host synchronisation; capturable in a CUDA graph).
+    ``boxes`` [S, 4] or None (bounding cubes into bufs.t["boxes"]); ``warm``: bufs' elements and
+    element offsets hold the previous arrays. Read the outcome with cstone_build_batched_result."""
+    lib = load()
+    for t, nm in ((x, "x"), (y, "y"), (z, "z")):
+        _need(t, torch.float64, nm)
+    _need(set_offsets, torch.int64, "set_offsets")
+    s = set_offsets.numel() - 1
+    if s != bufs.n_sets or x.numel() != bufs.n:
+        raise ValueError("the buffers were allocated for other sets")
+    if boxes is not None:
+        _need(boxes, torch.float64, "boxes")
+    ws = ws or Workspace(x.device)
+    buf = ws.get(_size(lib.cstone_build_batched_workspace_size, x.numel(), s, bufs.elem_cap, max_iters))
+    inp = _BatchInput(x.data_ptr(), y.data_ptr(), z.data_ptr(), x.numel(), set_offsets.data_ptr(), s,
+                      boxes.data_ptr() if boxes is not None else None)
+    prm = _BatchParams(curve, ncrit, max_iters, 1 if warm else 0)
+    out = bufs.c_struct()
+    _check(lib.cstone_build_batched(ctypes.byref(inp), ctypes.byref(prm), ctypes.byref(out), _ptr(buf), buf.numel(),
+                                    _stream(stream)), "cstone_build_batched")
+    return ws
+
+
+def cstone_build_batched_result(ws: Workspace, bufs: BatchBuffers, max_iters: int = 64, stream=None):
+    """(n_elements, n_nodes, iterations) of the last cstone_build_batched on ``ws``; raises
+    CstoneError (with ``required`` on a capacity overflow) if it failed."""
+    lib = load()
+    ne, nn, it = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int32(0)
+    rc = lib.cstone_build_batched_result(_ptr(ws.buf), bufs.n, bufs.n_sets, bufs.elem_cap, max_iters,
+                                         _ptr(bufs.t["LO"]), _stream(stream), ctypes.byref(ne), ctypes.byref(nn),
+                                         ctypes.byref(it))
+    if rc == ERR_CAPACITY:
+        err = CstoneError(rc, "cstone_build_batched", _detail())
+        err.required = int(ne.value)
+        raise err
+    _check(rc, "cstone_build_batched")
+    return int(ne.value), int(nn.value), int(it.value)
+
+
+def _batched_result(bufs: BatchBuffers, ne: int, nn: int, iters: int, ws) -> dict:
+    """Result dict of a batched build: device tensors cut to the built sizes, and host copies of the
+    element and node offsets (read from the device)."""
+    t = bufs.t
+    eo_host = t["element_offsets"].cpu().tolist()
+    node_offsets = t["LO"][:, 0].cpu().tolist() + [nn]
+    return {"boxes": t["boxes"], "keys": t["keys"][: bufs.n], "sorted_keys": t["sorted_keys"][: bufs.n],
+            "perm": t["perm"][: bufs.n], "elements": t["elements"][:ne], "n_elements": ne,
+            "element_offsets": t["element_offsets"], "element_offsets_host": eo_host,
+            "leaf_counts": t["leaf_counts"][:ne], "leaf_offsets": t["leaf_offsets"][:ne], "iters": iters,
+            "NK": t["NK"][:nn], "CO": t["CO"][:nn], "LO": t["LO"], "leaf_to_node": t["leaf_to_node"][:ne],
+            "node_counts": t["node_counts"][:nn], "node_offsets_host": node_offsets, "ws": ws, "buffers": bufs}
+
+
 def build_octrees_batched(x, y, z, set_offsets, curve: int = MORTON, ncrit: int = 32, boxes=None, warm=None,
-                          max_iters: int = 64, ws: Workspace | None = None, stream=None):
-    """Octrees of many independent sets stored back to back, one launch per phase for all sets.
+                          max_iters: int = 64, ws: Workspace | None = None, stream=None, buffers=None):
+    """Octrees of many independent sets stored back to back, one launch per phase for all sets
+    (the single C call cstone_build_batched, then one read of its outcome).
 
     ``set_offsets``: int64 CUDA tensor of S+1 particle offsets. ``boxes``: float64 CUDA tensor [S, 4]
     (bounding cubes are computed when None). ``warm``: a previous result of this function for the
-    same sets (its elements and element offsets warm-start the leaf loop). Returns a dict with the
-    concatenated per-set outputs and host copies of the element and node offsets."""
+    same sets (its elements and element offsets warm-start the leaf loop). ``buffers``: a
+    BatchBuffers to reuse. Returns a dict with the concatenated per-set outputs and host copies of
+    the element and node offsets."""
     dev = x.device
     n = x.numel()
     s = set_offsets.numel() - 1
     ws = ws or Workspace(dev)
-    if boxes is None:
-        boxes = torch.empty((s, 4), dtype=torch.float64, device=dev)
-        cstone_bbox_batched(x, y, z, set_offsets, boxes, stream)
-    keys = torch.empty(n, dtype=torch.int64, device=dev)
-    cstone_keys_batched(x, y, z, set_offsets, boxes, curve, keys, ws, stream)
-    sorted_keys = torch.empty_like(keys)
-    perm = torch.empty(n, dtype=torch.int32, device=dev)
-    cstone_sort_segmented(keys, sorted_keys, perm, set_offsets, ws, stream)
-    cap = max(4 * s, 16 * (n // (ncrit + 1)) + 2 * s + 4096)
+    cap = batched_capacity(n, s, ncrit)
     if warm is not None:
         cap = max(cap, 2 * warm["n_elements"])
+    bufs = buffers if (buffers is not None and buffers.n == n and buffers.n_sets == s and buffers.elem_cap >= cap) \
+        else BatchBuffers.allocate(n, s, cap, dev)
     while True:
-        elements = torch.empty(cap, dtype=torch.int64, device=dev)
-        element_offsets = torch.empty(s + 1, dtype=torch.int64, device=dev)
-        counts = torch.empty(cap, dtype=torch.int32, device=dev)
-        offsets = torch.empty(cap, dtype=torch.int32, device=dev)
-        ne0 = 0
         if warm is not None:
             ne0 = warm["n_elements"]
-            elements[:ne0].copy_(warm["elements"][:ne0])
-            element_offsets.copy_(warm["element_offsets"])
+            if warm["elements"].data_ptr() != bufs.t["elements"].data_ptr():
+                bufs.t["elements"][:ne0].copy_(warm["elements"][:ne0])
+            if warm["element_offsets"].data_ptr() != bufs.t["element_offsets"].data_ptr():
+                bufs.t["element_offsets"].copy_(warm["element_offsets"])
+        cstone_build_batched(x, y, z, set_offsets, bufs, curve, ncrit, boxes=boxes, warm=warm is not None,
+                             max_iters=max_iters, ws=ws, stream=stream)
         try:
-            ne, iters = cstone_build_leaves_batched(sorted_keys, set_offsets, ncrit, elements, element_offsets, counts,
-                                                    offsets, ne0, max_iters, ws, stream)
+            ne, nn, iters = cstone_build_batched_result(ws, bufs, max_iters, stream)
             break
         except CstoneError as e:
             if e.status != ERR_CAPACITY:
                 raise
-            cap = max(2 * cap, getattr(e, "required", 0) + 1024)
-    eo_host = element_offsets.cpu().tolist()
-    nl = [eo_host[i + 1] - eo_host[i] - 1 for i in range(s)]
-    nn = [v + (v - 1) // 7 for v in nl]
-    node_offsets = [0]
-    for v in nn:
-        node_offsets.append(node_offsets[-1] + v)
-    n_nodes = node_offsets[-1]
-    NK = torch.empty(n_nodes, dtype=torch.int64, device=dev)
-    CO = torch.empty(n_nodes, dtype=torch.int32, device=dev)
-    LO = torch.empty((s, LEVELS + 2), dtype=torch.int32, device=dev)
-    l2n = torch.empty(ne, dtype=torch.int32, device=dev)
-    cstone_link_tree_batched(elements, ne, element_offsets, n_nodes, NK, CO, LO, l2n, ws, stream)
-    node_counts = torch.empty(n_nodes, dtype=torch.int32, device=dev)
-    cstone_upsweep_counts_batched(counts, ne, l2n, CO, LO, s, node_counts, ws, stream)
-    return {"boxes": boxes, "keys": keys, "sorted_keys": sorted_keys, "perm": perm, "elements": elements[:ne],
-            "n_elements": ne, "element_offsets": element_offsets, "element_offsets_host": eo_host,
-            "leaf_counts": counts[:ne], "leaf_offsets": offsets[:ne], "iters": iters, "NK": NK, "CO": CO, "LO": LO,
-            "leaf_to_node": l2n, "node_counts": node_counts, "node_offsets_host": node_offsets, "ws": ws}
+            if warm is not None and warm["elements"].data_ptr() == bufs.t["elements"].data_ptr():
+                warm = None  # the failed loop left root arrays in place of the warm ones: start cold
+            bufs = BatchBuffers.allocate(n, s, max(2 * bufs.elem_cap, getattr(e, "required", 0) + 1024), dev,
+                                         keep=bufs)
+    out = _batched_result(bufs, ne, nn, iters, ws)
+    if boxes is not None:
+        out["boxes"] = boxes
+    return out
 
 
 def _grow(b: OctreeBuffers, want: int) -> OctreeBuffers:
@@ -849,24 +985,27 @@ class TimeStepper:
         self.last = None
 
     def rebuild(self, warm: bool = True):
+        prev = self.last
         out = build_octrees_batched(self.x, self.y, self.z, self.set_offsets, curve=self.curve, ncrit=self.ncrit,
-                                    boxes=self.boxes, warm=self.last if warm else None, ws=self.ws)
+                                    boxes=self.boxes, warm=prev if warm else None, ws=self.ws,
+                                    buffers=prev["buffers"] if prev is not None else None)
         self.last = out
         return out
 
 
 class GraphTimeStepper:
     """Time-step driver whose whole rebuild (keys, segmented sort, warm-started batched leaf loop,
-    linked octrees, node counts) is one CUDA graph, replayed once per step.
+    linked octrees, node counts: the one C call cstone_build_batched) is one CUDA graph, replayed
+    once per step.
 
     Every buffer is allocated at a capacity (``elem_cap`` elements over all runs; the node arrays
-    hold at most elem_cap + elem_cap / 7 + S nodes), the leaf loop takes its warm-start count from
-    the device, and the link and count phases run on capacities with the exact counts read on the
-    device, so no phase needs the host between the launches. After each replay the outcome is read
-    back (two synchronisations per step). The capacity is never below the batched builder's
-    first estimate (``elem_cap`` raises it, never lowers it). The first rebuild (cold, from the
-    roots) runs without the graph, with the synchronous leaf loop; the warm rebuild is captured on
-    its first use. A capacity overflow doubles the capacity, drops the graph and rebuilds cold."""
+    hold elem_cap + elem_cap / 7 + S nodes), the leaf loop takes its warm-start count from the
+    device, and the link and count phases run on the capacities with the exact counts on the
+    device, so no phase needs the host between the launches. After each replay one read-back
+    (cstone_build_batched_result) fetches the outcome. The capacity is never below the batched
+    builder's first estimate (``elem_cap`` raises it, never lowers it). The first rebuild (cold,
+    from the roots) runs without the graph; the warm rebuild is captured on its first use. A
+    capacity overflow grows the capacity, drops the graph and rebuilds cold."""
 
     def __init__(self, x, y, z, set_offsets, curve: int = HILBERT, ncrit: int = 64, pad: float = 0.1,
                  elem_cap: int | None = None, max_iters: int = 64):
@@ -880,98 +1019,53 @@ class GraphTimeStepper:
         cstone_bbox_batched(x, y, z, set_offsets, cube)
         self.boxes = padded_boxes(cube, pad)
         self.fixed_cap = elem_cap is not None
-        self.ws = {k: Workspace(dev) for k in ("keys", "sort", "leaves", "link", "counts")}
-        self.keys = torch.empty(n, dtype=torch.int64, device=dev)
-        self.sorted_keys = torch.empty_like(self.keys)
-        self.perm = torch.empty(n, dtype=torch.int32, device=dev)
-        self.element_offsets = torch.empty(s + 1, dtype=torch.int64, device=dev)
-        self.LO = torch.empty((s, LEVELS + 2), dtype=torch.int32, device=dev)
+        self.ws = Workspace(dev)
         # never below the estimate the batched builder starts from, so that a cold build does not
         # overflow its capacity in practice
-        self.min_cap = max(4 * s, 16 * (n // (ncrit + 1)) + 2 * s + 4096)
-        self._alloc(max(elem_cap or 0, self.min_cap))
+        self.min_cap = batched_capacity(n, s, ncrit)
+        self.bufs = BatchBuffers.allocate(n, s, max(elem_cap or 0, self.min_cap), dev)
+        self.graph = None
         self.have_arrays = False
 
-    def _alloc(self, cap: int, keep: int = 0):
-        """(Re)allocates the capacity-sized buffers; the first ``keep`` elements survive."""
-        dev, s = self.device, self.n_sets
-        old = getattr(self, "elements", None)
-        self.elem_cap = int(cap)
-        self.node_cap = self.elem_cap + self.elem_cap // 7 + s
-        self.elements = torch.empty(self.elem_cap, dtype=torch.int64, device=dev)
-        if keep:
-            self.elements[:keep].copy_(old[:keep])
-        self.counts = torch.empty(self.elem_cap, dtype=torch.int32, device=dev)
-        self.offsets = torch.empty(self.elem_cap, dtype=torch.int32, device=dev)
-        self.NK = torch.empty(self.node_cap, dtype=torch.int64, device=dev)
-        self.CO = torch.empty(self.node_cap, dtype=torch.int32, device=dev)
-        self.l2n = torch.empty(self.elem_cap, dtype=torch.int32, device=dev)
-        self.node_counts = torch.empty(self.node_cap, dtype=torch.int32, device=dev)
+    @property
+    def elem_cap(self) -> int:
+        return self.bufs.elem_cap
+
+    def _grow(self, cap: int):
+        self.bufs = BatchBuffers.allocate(self.n, self.n_sets, int(cap), self.device, keep=self.bufs)
         self.graph = None
 
     def _launch(self, warm: bool):
-        w = self.ws
-        cstone_keys_batched(self.x, self.y, self.z, self.set_offsets, self.boxes, self.curve, self.keys, w["keys"])
-        cstone_sort_segmented(self.keys, self.sorted_keys, self.perm, self.set_offsets, w["sort"])
-        cstone_build_leaves_batched_async(self.sorted_keys, self.set_offsets, self.ncrit, self.elements,
-                                          self.element_offsets, self.counts, self.offsets, warm, self.max_iters,
-                                          w["leaves"])
-        cstone_link_tree_batched(self.elements, self.elem_cap, self.element_offsets, self.node_cap, self.NK, self.CO,
-                                 self.LO, self.l2n, w["link"])
-        cstone_upsweep_counts_batched(self.counts, self.elem_cap, self.l2n, self.CO, self.LO, self.n_sets,
-                                      self.node_counts, w["counts"])
+        cstone_build_batched(self.x, self.y, self.z, self.set_offsets, self.bufs, self.curve, self.ncrit,
+                             boxes=self.boxes, warm=warm, max_iters=self.max_iters, ws=self.ws)
 
     def _result(self):
-        ne, iters = cstone_leaves_result(self.ws["leaves"], self.elem_cap, self.max_iters)
-        # error words of the phases that record device errors, the element offsets and the node
-        # count, in one read-back
-        names = ("sort", "link", "counts")
-        words = [self.ws[k].buf[:4].view(torch.int32).to(torch.int64) for k in names]
-        small = torch.cat(words + [self.element_offsets, self.LO[-1, -1:].to(torch.int64)]).cpu().tolist()
-        for k, st in zip(names, small[:3]):
-            if st != OK:
-                raise CstoneError(int(st), f"time step ({k})", "device error word")
-        eo_host = small[3: 4 + self.n_sets]
-        n_nodes = small[-1]
-        nl = [eo_host[i + 1] - eo_host[i] - 1 for i in range(self.n_sets)]
-        node_offsets = [0]
-        for v in nl:
-            node_offsets.append(node_offsets[-1] + v + (v - 1) // 7)
-        return {"boxes": self.boxes, "keys": self.keys, "sorted_keys": self.sorted_keys, "perm": self.perm,
-                "elements": self.elements[:ne], "n_elements": ne, "element_offsets": self.element_offsets,
-                "element_offsets_host": eo_host, "leaf_counts": self.counts[:ne], "leaf_offsets": self.offsets[:ne],
-                "iters": iters, "NK": self.NK[:n_nodes], "CO": self.CO[:n_nodes], "LO": self.LO,
-                "leaf_to_node": self.l2n[:ne], "node_counts": self.node_counts[:n_nodes],
-                "node_offsets_host": node_offsets}
+        ne, nn, iters = cstone_build_batched_result(self.ws, self.bufs, self.max_iters)
+        out = _batched_result(self.bufs, ne, nn, iters, self.ws)
+        out["boxes"] = self.boxes
+        return out
 
     def _cold(self):
-        # From the roots with the synchronous leaf loop: a capacity overflow is reported before the
-        # link and count phases run, and only the leaf loop is repeated at the grown capacity.
-        w = self.ws
-        if self.elem_cap < self.min_cap:
-            self._alloc(self.min_cap)
-        cstone_keys_batched(self.x, self.y, self.z, self.set_offsets, self.boxes, self.curve, self.keys, w["keys"])
-        cstone_sort_segmented(self.keys, self.sorted_keys, self.perm, self.set_offsets, w["sort"])
+        # from the roots, outside any graph; an overflow grows the capacity and starts again
         while True:
+            self._launch(False)
             try:
-                cstone_build_leaves_batched(self.sorted_keys, self.set_offsets, self.ncrit, self.elements,
-                                            self.element_offsets, self.counts, self.offsets, 0, self.max_iters,
-                                            w["leaves"])
+                out = self._result()
                 break
             except CstoneError as e:
                 if e.status != ERR_CAPACITY:
                     raise
-                self._alloc(max(2 * self.elem_cap, getattr(e, "required", 0) + 1024))
-        cstone_link_tree_batched(self.elements, self.elem_cap, self.element_offsets, self.node_cap, self.NK, self.CO,
-                                 self.LO, self.l2n, w["link"])
-        cstone_upsweep_counts_batched(self.counts, self.elem_cap, self.l2n, self.CO, self.LO, self.n_sets,
-                                      self.node_counts, w["counts"])
-        out = self._result()
+                self._grow(max(2 * self.elem_cap, getattr(e, "required", 0) + 1024))
         ne = out["n_elements"]
         tight = max(2 * ne + 64 * self.n_sets + 4096, self.min_cap)
         if not self.fixed_cap and tight < self.elem_cap:
-            self._alloc(tight, keep=ne)  # element offsets live outside the capacity buffers
-            out = dict(out, elements=self.elements[:ne])
+            old = self.bufs
+            self.bufs = BatchBuffers.allocate(self.n, self.n_sets, tight, self.device, keep=old)
+            self.bufs.t["elements"][:ne].copy_(old.t["elements"][:ne])  # the warm start of the next step
+            self.graph = None
+            # the tree outputs stay in the old buffers (returned as they are); the elements, which
+            # the next warm step reads in place, now live in the new ones
+            out = dict(out, elements=self.bufs.t["elements"][:ne])
         self.have_arrays = True
         return out
 
@@ -979,13 +1073,13 @@ class GraphTimeStepper:
         if not warm or not self.have_arrays:
             return self._cold()
         if self.graph is None:
-            self._launch(True)  # sizes every workspace before the capture
+            self._launch(True)  # sizes the workspace before the capture
             try:
                 self._result()
             except CstoneError as e:
                 if e.status != ERR_CAPACITY:
                     raise
-                self._alloc(max(2 * self.elem_cap, getattr(e, "required", 0) + 1024))
+                self._grow(max(2 * self.elem_cap, getattr(e, "required", 0) + 1024))
                 return self._cold()  # the failed pass left root arrays: start again from the roots
             self.graph = torch.cuda.CUDAGraph()
             with torch.cuda.graph(self.graph, capture_error_mode="thread_local"):
@@ -996,5 +1090,5 @@ class GraphTimeStepper:
         except CstoneError as e:
             if e.status != ERR_CAPACITY:
                 raise
-            self._alloc(max(2 * self.elem_cap, getattr(e, "required", 0) + 1024))
+            self._grow(max(2 * self.elem_cap, getattr(e, "required", 0) + 1024))
             return self._cold()

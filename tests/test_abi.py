@@ -88,3 +88,23 @@ def test_sort_bindings_reject_undersized_outputs(clib):
             fn(torch.zeros(100, dtype=torch.int64), torch.zeros(99, dtype=torch.int32))
         with pytest.raises(ValueError, match="at least 100"):
             fn(torch.zeros(50, dtype=torch.int64), torch.zeros(100, dtype=torch.int32))
+
+
+def test_one_call_batched_build_checks_its_capacities(clib):
+    """cstone_build_batched rejects an element capacity below 2 S and a node capacity below
+    elem_cap + elem_cap / 7 + S before any device work."""
+    import paper_2307_06345_gb300 as cs
+    inp = cs._BatchInput(256, 256, 256, 10, 256, 3, None)
+    prm = cs._BatchParams(0, 16, 64, 0)
+    small_elems = cs._BatchBuffers(*([256] * 5), 4, *([256] * 8), 100)
+    assert clib.cstone_build_batched(ctypes.byref(inp), ctypes.byref(prm), ctypes.byref(small_elems), None, 0,
+                                     None) == 1
+    small_nodes = cs._BatchBuffers(*([256] * 5), 70, *([256] * 8), 70 + 10 + 2)
+    assert clib.cstone_build_batched(ctypes.byref(inp), ctypes.byref(prm), ctypes.byref(small_nodes), None, 0,
+                                     None) == 1
+    buf = ctypes.create_string_buffer(512)
+    clib.cstone_last_error_detail(buf, 512)
+    assert b"node_cap" in buf.value
+    sz = ctypes.c_size_t()
+    assert clib.cstone_build_batched_workspace_size(1000, 3, 70, 64, ctypes.byref(sz)) == 0 and sz.value > 0
+    assert clib.cstone_build_batched_workspace_size(1000, 5000, 20000, 64, ctypes.byref(sz)) == 1  # > 4096 sets

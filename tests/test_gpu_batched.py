@@ -146,3 +146,44 @@ def test_batched_512_sets_sampled(lib, oracle):
     rng = np.random.default_rng(5)
     pick = sorted(set(rng.choice(512, 10, replace=False).tolist()) | {int(np.argmax(sizes)), int(np.argmin(sizes))})
     _check_batched_against_oracle(out, x, y, z, off, 0, 32, oracle, sets=pick, boxes=boxes.cpu().numpy())
+
+
+def test_one_call_batched_build_through_the_c_abi(lib, oracle):
+    """cstone_build_batched called directly through ctypes (one C call for the whole batched build,
+    then cstone_build_batched_result): cold from the roots with bounding cubes computed on the
+    device, then warm-started in place after the particles moved; every set against the oracle."""
+    import ctypes
+    sizes = [5000, 0, 1, 12_345, 777, 40_000]
+    x, y, z, off, kinds = _sets(sizes, 70)
+    s, n = len(sizes), x.size
+    X, Y, Z, OFF = dev(x), dev(y), dev(z), dev(off)
+    cap = lib.batched_capacity(n, s, 16)
+    bufs = lib.BatchBuffers.allocate(n, s, cap, "cuda")
+    clib = lib.load()
+    sz = ctypes.c_size_t()
+    assert clib.cstone_build_batched_workspace_size(n, s, cap, 64, ctypes.byref(sz)) == lib.OK
+    ws = torch.empty(sz.value, dtype=torch.uint8, device="cuda")
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for step, warm in enumerate((0, 1)):
+        if warm:  # small moves: the warm start needs few passes and reaches the same tree
+            rng = np.random.default_rng(5)
+            x, y, z = (c + 1e-4 * rng.standard_normal(c.size) for c in (x, y, z))
+            X.copy_(dev(x)), Y.copy_(dev(y)), Z.copy_(dev(z))
+        inp = lib._BatchInput(X.data_ptr(), Y.data_ptr(), Z.data_ptr(), n, OFF.data_ptr(), s, None)
+        prm = lib._BatchParams(lib.MORTON, 16, 64, warm)
+        out = bufs.c_struct()
+        rc = clib.cstone_build_batched(ctypes.byref(inp), ctypes.byref(prm), ctypes.byref(out),
+                                       ctypes.c_void_p(ws.data_ptr()), sz.value, stream)
+        assert rc == lib.OK
+        ne, nn, it = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        rc = clib.cstone_build_batched_result(ctypes.c_void_p(ws.data_ptr()), n, s, cap, 64,
+                                              ctypes.c_void_p(bufs.t["LO"].data_ptr()), stream, ctypes.byref(ne),
+                                              ctypes.byref(nn), ctypes.byref(it))
+        assert rc == lib.OK
+        res = lib._batched_result(bufs, ne.value, nn.value, it.value, None)
+        bx = res["boxes"].cpu().numpy()
+        if warm == 0:
+            for q in range(s):
+                a, b = off[q], off[q + 1]
+                assert np.array_equal(bx[q], oracle.bounding_cube(x[a:b], y[a:b], z[a:b]))
+        _check_batched_against_oracle(res, x, y, z, off, 0, 16, oracle, boxes=bx)

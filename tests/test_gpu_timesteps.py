@@ -179,3 +179,74 @@ def test_graph_time_stepper_capacity_floor(lib):
         torch.cuda.synchronize()
         _equal(a, b, ["elements", "element_offsets", "leaf_counts", "NK", "CO", "LO", "node_counts"])
     assert g.elem_cap == g.min_cap and g.graph is not None
+
+
+def _oracle_box(oracle, x, y, z, pad=0.1):
+    """The step-0 bounding cube of a run grown by `pad` of its side on every side, from the
+    oracle's bounding cube (the same two IEEE operations per component as the stepper's)."""
+    b = oracle.bounding_cube(x, y, z)
+    out = b.copy()
+    out[:3] = b[:3] - pad * b[3]
+    out[3] = b[3] * (1.0 + 2.0 * pad)
+    return out
+
+
+def test_time_steps_8x2p26_full_size_spot_checks(lib, oracle):
+    """The time-step workload at its full size, in the launch configuration bench.py times: 8 runs of
+    2^26 Plummer particles, 100 steps of Gaussian displacements of 1e-3 of the box (drawn on the
+    device), Hilbert keys, Ncrit 64, every rebuild one CUDA graph replay warm-started from the
+    previous step's leaves. Every step's warm rebuild equals a cold rebuild of the same
+    coordinates (the balanced tree is unique, Sec. 4); run 0 at steps 0, 1, 50 and 99 and every run
+    at step 99 equal the oracle's build from the raw coordinates (sorted keys, permutation, leaves,
+    leaf counts, NK, CO, LO, node counts)."""
+    from paper_2307_06345_gb300 import workloads as w
+    runs, n, steps = 8, 1 << 26, 100
+    oracle.set_threads(0)
+    d = torch.device("cuda")
+    parts = [w.plummer_device(n, w.BASE_SEED + 5 + r, d) for r in range(runs)]
+    X, Y, Z = (torch.cat([p[k] for p in parts]) for k in range(3))
+    del parts
+    OFF = torch.arange(runs + 1, dtype=torch.int64, device=d) * n
+    st = lib.GraphTimeStepper(X, Y, Z, OFF, curve=lib.HILBERT, ncrit=64)
+    boxes = st.boxes.cpu().numpy()
+    for r in range(runs):
+        sl = slice(r * n, (r + 1) * n)
+        assert np.array_equal(boxes[r], _oracle_box(oracle, X[sl].cpu().numpy(), Y[sl].cpu().numpy(),
+                                                    Z[sl].cpu().numpy()))
+    sigma = 1e-3 * float(boxes[0, 3]) / 1.2
+    g = torch.Generator(device=d)
+    g.manual_seed(w.BASE_SEED + 6)
+    ws = lib.Workspace()
+    keys = ["elements", "element_offsets", "leaf_counts", "NK", "CO", "LO", "node_counts"]
+    for step in range(steps):
+        if step > 0:
+            for c in (X, Y, Z):
+                c.add_(torch.randn(c.shape, dtype=torch.float64, device=d, generator=g), alpha=sigma)
+        warm = st.rebuild(warm=step > 0)
+        cold = lib.build_octrees_batched(X, Y, Z, OFF, curve=lib.HILBERT, ncrit=64, boxes=st.boxes, ws=ws)
+        torch.cuda.synchronize()
+        _equal(warm, cold, keys)
+        if step > 1:
+            assert warm["iters"] <= 4  # a slowly moving distribution needs few passes
+        check = range(runs) if step == steps - 1 else ([0] if step in (0, 1, 50) else [])
+        if not check:
+            continue
+        eo, no = warm["element_offsets_host"], warm["node_offsets_host"]
+        E, NK, CO, counts = u64(warm["elements"]), u64(warm["NK"]), i32(warm["CO"]), u32(warm["node_counts"])
+        LC, SK, PERM = u32(warm["leaf_counts"]), u64(warm["sorted_keys"]), u32(warm["perm"])
+        LO = i32(warm["LO"])
+        for r in check:
+            sl = slice(r * n, (r + 1) * n)
+            x, y, z = X[sl].cpu().numpy(), Y[sl].cpu().numpy(), Z[sl].cpu().numpy()
+            lo, side = boxes[r, :3], boxes[r, 3]
+            assert all(((c >= lo[k]) & (c < lo[k] + side)).all() for k, c in enumerate((x, y, z)))  # no clamping
+            ref = oracle.full_build(x, y, z, oracle.HILBERT, 64, box=boxes[r])
+            assert np.array_equal(SK[sl], ref["P"])
+            assert np.array_equal(PERM[sl].astype(np.int64) - r * n, ref["perm"].astype(np.int64))
+            assert np.array_equal(E[eo[r]: eo[r + 1]], ref["K"])
+            assert np.array_equal(LC[eo[r]: eo[r + 1] - 1], ref["N"])
+            assert np.array_equal(NK[no[r]: no[r + 1]], ref["NK"])
+            assert np.array_equal(CO[no[r]: no[r + 1]] - np.where(CO[no[r]: no[r + 1]] > 0, no[r], 0), ref["CO"])
+            assert np.array_equal(LO[r] - no[r], ref["LO"])
+            assert np.array_equal(counts[no[r]: no[r + 1]], ref["counts"])
+        del E, NK, CO, counts, LC, SK, PERM
