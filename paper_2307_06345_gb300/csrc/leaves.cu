@@ -13,13 +13,15 @@
 // once (batched sets): they are stored back to back, each ending with its own 8^L, and every
 // element carries its set id so that a merge never reaches across two sets.
 //
-// One pass (g1 + g2 + g3) is a single sweep over tiles of the elements: the threads decide O for
-// the tile's elements, the block scans the decisions, the tile's offset comes from decoupled
-// look-back over the preceding tiles (claimed in order through an atomic counter), and every
-// element is copied, split into 8 or dropped at its scanned position. A bounded grid barrier
-// closes the pass; all blocks then read the "changed" flag and either start the next pass or, once
-// a pass changed nothing, write the converged arrays out. The whole loop is one launch and needs
-// no host round trip.
+// One pass (g1 + g2 + g3) takes two sweeps over tiles of the elements (block b of the G co-resident
+// blocks takes tiles b, b + G, b + 2G, ...), so that no tile ever waits on another: the first sweep
+// decides O for every element of the tile (kept, one byte per element) and records the tile's op
+// total and split count; after a grid barrier the second sweep gives each tile its offsets as the
+// totals of all earlier tiles (each block adds them up itself), scans the tile, and copies, splits
+// or drops every element at its scanned position. A split takes its slot in the pass's split
+// queue with what the split phase needs (its particle range, its first child's position, the
+// child digit's shift). A pass in which g1 changes nothing ends after the first sweep: its input
+// is the converged array. The whole loop is one launch and needs no host round trip.
 #include "common.cuh"
 
 namespace CST_NS {
@@ -36,16 +38,14 @@ static_assert(kItems <= 8, "the staged tile (keys, positions, sets, ops, offsets
 constexpr int kMaxIters = 256;
 constexpr int kSplitChunks = 16;                 // keys per lane loaded at once when counting a split
 constexpr u32 kLinearSplit = 32 * kSplitChunks;  // split ranges up to this size are counted, not searched
-constexpr u64 kLookAggregate = 1ULL << 62;
-constexpr u64 kLookPrefix = 2ULL << 62;
-constexpr u64 kLookValue = (1ULL << 62) - 1ULL;
+// A tile's op total (low 32 bits) and split count (high 32 bits) in one word: a pass has at most 2^28
+// elements, so sums of op totals stay below 2^31 and never carry into the split count.
 
 struct LoopState {
     unsigned long long stamp[kMaxIters + 1];  // %globaltimer at the start of pass t (ns), for profiling
     u32 ne[kMaxIters + 1];        // elements entering pass t (ne[0] = initial)
     u32 changed[kMaxIters];       // pass t changed an array
-    u32 tile_counter[kMaxIters];  // tile dispenser of pass t
-    u32 nsplit[kMaxIters];        // splits queued in pass t
+    u32 nsplit[kMaxIters];        // splits queued in pass t (written by the pass's last tile)
     GridBarrier bar;
     u32 iters;                    // passes executed (set at convergence)
     u32 converged;
@@ -54,8 +54,10 @@ struct LoopState {
 };
 
 struct LeafBufs {
-    u32* split_elem;  // [ecap] element index of each queued split
-    u32* split_pos;   // [ecap] its first position in the new array
+    uint4* split_q;   // [ecap] queued splits: first particle, particle count, first child's position,
+                      // shift of the child digit
+    unsigned char* ops;  // [ecap] O of every element of the current pass
+    u64* tile_sum;       // [tiles] op total and split count of every tile of the current pass
     Key* K[2];
     u32* pos[2];   // lower bound of the element's key among its set's sorted keys (global index)
     u32* set[2];   // set of the element (batched builds only)
@@ -67,8 +69,6 @@ struct SetView {  // batched builds
     int n_sets;
 };
 
-__device__ __forceinline__ u64 ld_volatile64(const u64* p) { return *reinterpret_cast<const volatile u64*>(p); }
-__device__ __forceinline__ void st_volatile64(u64* p, u64 v) { *reinterpret_cast<volatile u64*>(p) = v; }
 
 // First position in P[lo, hi) whose key is >= key.
 __device__ __forceinline__ u32 lower_bound_in(const Key* __restrict__ P, u32 lo, u32 hi, Key key) {
@@ -136,17 +136,14 @@ __device__ void write_root_arrays(const Key* P, u32 n, SetView sv, u32 gtid, u32
 template <bool BATCH>
 __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const Key* __restrict__ P, u32 n, u32 ncrit,
                                                                LeafBufs b, u32 ecap, int max_iters, int warm,
-                                                               u32 ne_start, int fallback, u64* look, u32 max_tiles,
-                                                               LoopState* ls, WsHeader* hdr, SetView sv,
+                                                               u32 ne_start, int fallback, LoopState* ls, WsHeader* hdr, SetView sv,
                                                                Key* out_keys, u32* out_counts, u32* out_offsets) {
     __shared__ u32 s_warp[kThreads / 32];
     __shared__ unsigned char s_op[kTile];
-    __shared__ unsigned short s_split[kTile];
+    __shared__ u32 s_wsplit[kThreads / 32];
+    __shared__ u64 s_part[kThreads / 32];
     __shared__ u32 s_nsplit;
-    __shared__ u32 s_qbase;
     __shared__ u32 s_off[kTile];
-    __shared__ u32 s_tile;
-    __shared__ u64 s_prefix;
     __shared__ int s_any;
     // the tile's elements with a halo of kHalo on each side (the merge test reads up to 7 back
     // and 8 ahead, the split and count tests one ahead), staged once per tile
@@ -201,6 +198,7 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const Key* __rest
     grid_barrier(&ls->bar, hdr);
 
     int t = 0;
+    bool converged = false;
     for (; t < max_iters; ++t) {
         if (gtid == 0) {
             unsigned long long now;
@@ -216,22 +214,13 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const Key* __rest
         u32* setn = b.set[(t + 1) & 1];
         const u32 ne = ld_volatile(&ls->ne[t]);
         const u32 ntiles = (ne + kTile - 1) / kTile;
-        u64* look_t = look + (size_t)t * max_tiles;
+
+        // ---- g1 for every tile of this block: the decisions are kept (one byte per element), and
+        // each tile's op total and split count go to tile_sum
         int any_change = 0;
-
-        for (;;) {
-            if (tid == 0) {
-                s_tile = atomicAdd(&ls->tile_counter[t], 1u);
-                s_nsplit = 0;
-            }
-            __syncthreads();
-            const u32 tile = s_tile;
-            __syncthreads();
-            if (tile >= ntiles) break;
-
+        for (u32 tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
             // stage the tile's window (written by other blocks in the previous pass: read through
-            // L2, never through a read-only cache), then g1, striped: item j of the tile is element
-            // tile * kTile + j, handled by thread j % kThreads
+            // L2, never through a read-only cache)
             const u32 t0 = tile * kTile;
             const long long h0 = (long long)t0 - kHalo;
             for (int i = tid; i < kTile + 2 * kHalo; i += kThreads) {
@@ -243,17 +232,78 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const Key* __rest
                 }
             }
             __syncthreads();
+            // striped: item j of the tile is element tile * kTile + j, handled by thread j % kThreads
+            u32 sum = 0, nspl = 0;
 #pragma unroll
             for (int k = 0; k < kItems; ++k) {
                 const u32 j = k * kThreads + tid;
                 const u32 e = t0 + j;
-                const u32 o = (e < ne) ? decide<BATCH>(s_K, s_pos, s_set, e, ne, ncrit, h0) : 0u;
-                if (e < ne && o != 1u) any_change = 1;
-                s_op[j] = static_cast<unsigned char>(o);
+                if (e < ne) {
+                    const u32 o = decide<BATCH>(s_K, s_pos, s_set, e, ne, ncrit, h0);
+                    b.ops[e] = static_cast<unsigned char>(o);
+                    any_change |= o != 1u;
+                    sum += o;
+                    nspl += o == 8u ? 1u : 0u;
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                sum += __shfl_xor_sync(0xffffffffu, sum, o);
+                nspl += __shfl_xor_sync(0xffffffffu, nspl, o);
+            }
+            if (lane == 0) {
+                s_warp[warp] = sum;
+                s_wsplit[warp] = nspl;
             }
             __syncthreads();
-            // g2: exclusive scan of O over the tile (blocked runs of kItems per thread), then the
-            // tile's offset by decoupled look-back
+            if (tid == 0) {
+                u32 tot = 0, spl = 0;
+                for (int w = 0; w < kThreads / 32; ++w) {
+                    tot += s_warp[w];
+                    spl += s_wsplit[w];
+                }
+                b.tile_sum[tile] = (static_cast<u64>(spl) << 32) | tot;
+            }
+            __syncthreads();  // the staging arrays are rewritten by the next tile
+        }
+        if (tid == 0) s_any = 0;
+        __syncthreads();
+        if (any_change) s_any = 1;
+        __syncthreads();
+        if (tid == 0 && s_any) atomicOr(&ls->changed[t], 1u);
+        grid_barrier(&ls->bar, hdr);
+        if (ld_volatile(&hdr->err)) break;
+        if (ld_volatile(&ls->changed[t]) == 0u) {  // this pass confirms convergence: K is final
+            converged = true;
+            ++t;
+            break;
+        }
+
+        // ---- g2 + g3 for every tile of this block: the tile's offsets are the totals of all earlier
+        // tiles (each block adds the totals up itself: its tiles are blockIdx.x + k gridDim.x), then
+        // every element is copied, split into 8 or dropped at its scanned position. A split also
+        // takes its slot in the split queue, carrying what the split phase needs.
+        u64 prefix = 0;  // tile_sum over [0, done)
+        u32 done = 0;
+        for (u32 tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            u64 part = 0;
+            for (u32 q = done + tid; q < tile; q += kThreads) part += __ldcg(b.tile_sum + q);
+            for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+            if (lane == 0) s_part[warp] = part;
+            const u32 t0 = tile * kTile;
+            // the tile's elements, one more key and position (a split's gap and range end), its ops
+            for (int i = tid; i < kTile + 1; i += kThreads) {
+                const u32 e = t0 + i;
+                const bool ok = e < ne;
+                s_K[i] = ok ? __ldcg(K + e) : 0;
+                s_pos[i] = ok ? __ldcg(pos + e) : 0u;
+                if (BATCH) s_set[i] = ok ? __ldcg(set + e) : 0u;
+                if (i < kTile) s_op[i] = ok ? __ldcg(b.ops + e) : static_cast<unsigned char>(0);
+            }
+            if (tid == 0) s_nsplit = 0;
+            __syncthreads();
+            for (int w = 0; w < kThreads / 32; ++w) prefix += s_part[w];
+            done = tile + 1;
+            // exclusive scan of O over the tile (blocked runs of kItems per thread)
             u32 run[kItems];
             u32 sum = 0;
 #pragma unroll
@@ -262,75 +312,34 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const Key* __rest
                 sum += s_op[tid * kItems + k];
             }
             u32 incl = sum;
-            for (int s = 1; s < 32; s <<= 1) {
-                u32 v = __shfl_up_sync(0xffffffffu, incl, s);
-                if (lane >= s) incl += v;
+            for (int sft = 1; sft < 32; sft <<= 1) {
+                u32 v = __shfl_up_sync(0xffffffffu, incl, sft);
+                if (lane >= sft) incl += v;
             }
             if (lane == 31) s_warp[warp] = incl;
             __syncthreads();
-            u32 wpre = 0, total = 0;
-            for (int w = 0; w < kThreads / 32; ++w) {
-                u32 v = s_warp[w];
-                if (w < warp) wpre += v;
-                total += v;
-            }
+            u32 wpre = 0;
+            for (int w = 0; w < warp; ++w) wpre += s_warp[w];
             const u32 excl_in_tile = wpre + incl - sum;
 #pragma unroll
             for (int k = 0; k < kItems; ++k) s_off[tid * kItems + k] = excl_in_tile + run[k];
-
-            // decoupled look-back by warp 0: 32 predecessor descriptors per step
-            if (warp == 0) {
-                u64* mine = look_t + tile;
-                u64 prefix = 0;
-                if (tile == 0) {
-                    if (lane == 0) st_volatile64(mine, kLookPrefix | total);
-                } else {
-                    if (lane == 0) st_volatile64(mine, kLookAggregate | total);
-                    long long top = (long long)tile - 1;
-                    long long polls = 0;
-                    for (;;) {
-                        const long long jj = top - lane;
-                        const u64 v = jj >= 0 ? ld_volatile64(look_t + jj) : kLookPrefix;
-                        const u64 flag = v & ~kLookValue;
-                        const u32 pmask = __ballot_sync(0xffffffffu, flag == kLookPrefix);
-                        const u32 xmask = __ballot_sync(0xffffffffu, flag == 0ULL);
-                        const int first_p = pmask ? __ffs(pmask) - 1 : 32;
-                        const u32 before = first_p == 32 ? 0xffffffffu : ((1u << first_p) - 1u);
-                        if (xmask & before) {  // a nearer predecessor has not published yet
-                            __nanosleep(32);
-                            if (++polls > kSpinLimit || ld_volatile(&hdr->err) != 0u) {
-                                if (lane == 0) raise_error(hdr, CSTONE_ERR_TIMEOUT, 0x2000u);
-                                break;
-                            }
-                            continue;
-                        }
-                        u64 part = lane <= first_p ? (v & kLookValue) : 0ULL;
-                        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-                        prefix += part;
-                        if (first_p < 32) break;
-                        top -= 32;
-                    }
-                    if (lane == 0) st_volatile64(mine, kLookPrefix | (prefix + total));
-                }
-                if (lane == 0) s_prefix = prefix;
-            }
             __syncthreads();
-
-            // g3, striped: copy, split or drop each element at its scanned position. A split writes
-            // its 8 child keys and queues itself; the child particle offsets are found below.
-            const u64 prefix = s_prefix;
+            const u64 own = __ldcg(b.tile_sum + tile);
+            const u64 base_pos = prefix & 0xffffffffULL;
+            const u32 qbase = static_cast<u32>(prefix >> 32);
+            if (tile == ntiles - 1 && tid == 0) ls->nsplit[t] = static_cast<u32>((prefix + own) >> 32);
 #pragma unroll 1
             for (int k = 0; k < kItems; ++k) {
                 const u32 j = k * kThreads + tid;
                 const u32 e = t0 + j;
                 if (e >= ne) break;
-                const u64 o_pos = prefix + s_off[j];
+                const u64 o_pos = base_pos + s_off[j];
                 const u32 o = s_op[j];
                 if (o == 1u) {
                     if (o_pos < ecap) {
-                        Kn[o_pos] = s_K[j + kHalo];
-                        posn[o_pos] = s_pos[j + kHalo];
-                        if (BATCH) setn[o_pos] = s_set[j + kHalo];
+                        Kn[o_pos] = s_K[j];
+                        posn[o_pos] = s_pos[j];
+                        if (BATCH) setn[o_pos] = s_set[j];
                     }
                     if (e == ne - 1) {  // the last element is an end key: the new element count
                         const u64 ne_next = o_pos + 1;
@@ -341,51 +350,48 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const Key* __rest
                         }
                     }
                 } else if (o == 8u) {
-                    const Key ke = s_K[j + kHalo];
-                    const Key step = (s_K[j + kHalo + 1] - ke) >> 3;
+                    const Key ke = s_K[j];
+                    const Key delta = s_K[j + 1] - ke;
+                    const Key step = delta >> 3;
                     if (o_pos + 8 <= ecap) {
 #pragma unroll
                         for (int c = 0; c < 8; ++c) {
                             Kn[o_pos + c] = ke + static_cast<Key>(c) * step;
-                            if (BATCH) setn[o_pos + c] = s_set[j + kHalo];
+                            if (BATCH) setn[o_pos + c] = s_set[j];
                         }
-                        posn[o_pos] = s_pos[j + kHalo];
+                        posn[o_pos] = s_pos[j];
                     }
-                    s_split[atomicAdd(&s_nsplit, 1u)] = static_cast<unsigned short>(j);
+                    const u32 q = qbase + atomicAdd(&s_nsplit, 1u);
+                    if (q < ecap)  // always, unless a barrier timed out (then the error is recorded)
+                        b.split_q[q] = make_uint4(s_pos[j], s_pos[j + 1] - s_pos[j], static_cast<u32>(o_pos),
+                                              static_cast<u32>(key_ffs(delta) - 3));
                 }
             }
-            __syncthreads();
-            // queue the tile's splits for the grid-wide phase below (one reservation per tile)
-            if (tid == 0) s_qbase = s_nsplit ? atomicAdd(&ls->nsplit[t], s_nsplit) : 0u;
-            __syncthreads();
-            for (u32 q = tid; q < s_nsplit; q += kThreads) {
-                const u32 j = s_split[q];
-                b.split_elem[s_qbase + q] = t0 + j;
-                b.split_pos[s_qbase + q] = static_cast<u32>(prefix + s_off[j]);
-            }
-            __syncthreads();  // s_op / s_off are rewritten by the next tile
+            prefix += own;
+            __syncthreads();  // the staging arrays and s_nsplit are rewritten by the next tile
         }
         // particle offsets of the 7 inner children of every split leaf, one warp of the whole grid per
         // split (early passes have few leaves but long particle ranges): the child of a particle is
         // one octal digit of its key, so a short range is counted with ballots over coalesced
         // loads; a long range is narrowed by 32 probes at once and then binary-searched, one child
-        // boundary per lane
+        // boundary per lane. A warp loads its next queue entry before it works on the current one.
         grid_barrier(&ls->bar, hdr);
         {
             const u32 nsplit = ld_volatile(&ls->nsplit[t]);
             const u32 gwarp = gtid >> 5, nwarps = gthreads >> 5;
+            uint4 cur = gwarp < nsplit ? __ldcg(b.split_q + gwarp) : make_uint4(0, 0, 0, 0);
             for (u32 q = gwarp; q < nsplit; q += nwarps) {
-                const u32 e = b.split_elem[q];
-                const u32 o_pos = b.split_pos[q];
-                const Key ke = K[e];
-                const Key delta = K[e + 1] - ke;
-                const u32 lo = pos[e], cnt_all = pos[e + 1] - lo;
-                if (lo > n || cnt_all > n - lo) {  // self-check: a particle range outside P is never read
+                const u32 qn = q + nwarps;
+                const uint4 nxt = qn < nsplit ? __ldcg(b.split_q + qn) : make_uint4(0, 0, 0, 0);
+                const u32 lo = cur.x, cnt_all = cur.y, o_pos = cur.z;
+                const int child_shift = static_cast<int>(cur.w);
+                cur = nxt;
+                if (lo > n || cnt_all > n - lo || child_shift < 0 || child_shift > kKeyBits - 3) {
+                    // self-check: a particle range outside P is never read
                     if (lane == 0) raise_error(hdr, CSTONE_ERR_INVALID_ARG, 0x70000u);
                     continue;
                 }
-                const int child_shift = key_ffs(delta) - 3;
-                const bool room = static_cast<u64>(o_pos) + 8 <= ecap;
+                if (static_cast<u64>(o_pos) + 8 > ecap) continue;  // over capacity: reported, nothing to write
                 u32 below = 0;  // lane c in 1..7: particles whose child digit is < c
                 if (cnt_all <= kLinearSplit) {
                     // the child digits of the range do not decrease: the offset of child c is the first
@@ -397,7 +403,7 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const Key* __rest
                         const u32 jj = c * 32 + lane;
                         dg[c] = jj < cnt_all ? static_cast<u32>((__ldg(P + lo + jj) >> child_shift) & 7ULL) : 8u;
                     }
-                    if (lane >= 1 && lane < 8 && room) posn[o_pos + lane] = lo + cnt_all;
+                    if (lane >= 1 && lane < 8) posn[o_pos + lane] = lo + cnt_all;
                     __syncwarp();
                     u32 prev_last = 0;  // digit of the element before this chunk (0 before the first)
 #pragma unroll
@@ -406,76 +412,67 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const Key* __rest
                         const u32 up = __shfl_up_sync(0xffffffffu, dg[c], 1);
                         const u32 before_me = lane == 0 ? prev_last : up;
                         const u32 mine = dg[c] < 7u ? dg[c] : 7u;
-                        if (room)
-                            for (u32 d = before_me + 1; d <= mine; ++d) posn[o_pos + d] = lo + c * 32 + lane;
+                        for (u32 d = before_me + 1; d <= mine; ++d) posn[o_pos + d] = lo + c * 32 + lane;
                         prev_last = __shfl_sync(0xffffffffu, dg[c], 31);
                     }
                     continue;  // the boundaries are written
-                } else {
-                    // one round of 32 probes spread over the range: the child digits of the probes do
-                    // not decrease, so for child c the first n_c probes (digit < c) bound its offset to
-                    // (probe n_c - 1, probe n_c], about cnt_all / 33 particles; lane c then
-                    // binary-searches that interval
-                    const u32 qk = static_cast<u32>((static_cast<u64>(lane + 1) * cnt_all) / 33u);
-                    const u32 gk = static_cast<u32>((__ldg(P + lo + qk) >> child_shift) & 7ULL);
-                    u32 a = 0, hi = cnt_all;  // lane c in 1..7: its offset lies in [a, hi]
+                }
+                // one round of 32 probes spread over the range: the child digits of the probes do not
+                // decrease, so for child c the first n_c probes (digit < c) bound its offset to
+                // (probe n_c - 1, probe n_c], about cnt_all / 33 particles; lane c then
+                // binary-searches that interval for the first key >= the child's key. The parent's
+                // key is the first child's, written by g3 above.
+                const Key ke = __ldcg(Kn + o_pos);
+                const u32 qk = static_cast<u32>((static_cast<u64>(lane + 1) * cnt_all) / 33u);
+                const u32 gk = static_cast<u32>((__ldg(P + lo + qk) >> child_shift) & 7ULL);
+                u32 a = 0, hi = cnt_all;  // lane c in 1..7: its offset lies in [a, hi]
 #pragma unroll
-                    for (u32 d = 1; d < 8; ++d) {
-                        const u32 nc = __popc(__ballot_sync(0xffffffffu, gk < d));
-                        const u32 q_lo = __shfl_sync(0xffffffffu, qk, nc > 0 ? nc - 1 : 0);
-                        const u32 q_hi = __shfl_sync(0xffffffffu, qk, nc < 32 ? nc : 31);
-                        if (lane == d) {
-                            a = nc > 0 ? q_lo + 1 : 0;
-                            hi = nc < 32 ? q_hi : cnt_all;
-                        }
-                    }
-                    if (lane >= 1 && lane < 8) {
-                        const Key key = ke + static_cast<Key>(lane) * (delta >> 3);
-                        below = a;  // the particle before offset a (a probe of digit < c) is below key
-                        if (hi > a)
-                            for (u32 st = 1u << (31 - __clz(hi - a)); st > 0; st >>= 1) {
-                                const u32 probe = below + st;
-                                if (probe <= hi && __ldg(P + lo + probe - 1) < key) below = probe;
-                            }
+                for (u32 d = 1; d < 8; ++d) {
+                    const u32 nc = __popc(__ballot_sync(0xffffffffu, gk < d));
+                    const u32 q_lo = __shfl_sync(0xffffffffu, qk, nc > 0 ? nc - 1 : 0);
+                    const u32 q_hi = __shfl_sync(0xffffffffu, qk, nc < 32 ? nc : 31);
+                    if (lane == d) {
+                        a = nc > 0 ? q_lo + 1 : 0;
+                        hi = nc < 32 ? q_hi : cnt_all;
                     }
                 }
-                if (lane >= 1 && lane < 8 && room) posn[o_pos + lane] = lo + below;
+                if (lane >= 1 && lane < 8) {
+                    const Key key = ke + (static_cast<Key>(lane) << child_shift);
+                    below = a;  // the particle before offset a (a probe of digit < c) is below key
+                    if (hi > a)
+                        for (u32 st = 1u << (31 - __clz(hi - a)); st > 0; st >>= 1) {
+                            const u32 probe = below + st;
+                            if (probe <= hi && __ldg(P + lo + probe - 1) < key) below = probe;
+                        }
+                    posn[o_pos + lane] = lo + below;
+                }
             }
         }
-        if (tid == 0) s_any = 0;
-        __syncthreads();
-        if (any_change) s_any = 1;
-        __syncthreads();
-        if (tid == 0 && s_any) atomicOr(&ls->changed[t], 1u);
         grid_barrier(&ls->bar, hdr);
-        if (ld_volatile(&hdr->err)) break;
-        if (ld_volatile(&ls->changed[t]) == 0u) {
-            ++t;  // this pass confirmed convergence; its output equals its input
-            break;
-        }
     }
 
     if (ld_volatile(&hdr->err)) {
         if (fallback) write_root_arrays<BATCH>(P, n, sv, gtid, gthreads, out_keys, out_counts, out_offsets);
         return;
     }
-    const bool converged = (t <= max_iters) && ld_volatile(&ls->changed[t - 1]) == 0u;
+    // converged: the last pass (t - 1) changed nothing, so its input arrays are the result
+    const int last = t - 1;
     if (gtid == 0) {
         unsigned long long now;
         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
         ls->stamp[t] = now;
         ls->iters = static_cast<u32>(t);
         ls->converged = converged ? 1u : 0u;
-        ls->final_buf = static_cast<u32>(t & 1);
+        ls->final_buf = static_cast<u32>(last & 1);
     }
     if (!converged) {
         if (fallback) write_root_arrays<BATCH>(P, n, sv, gtid, gthreads, out_keys, out_counts, out_offsets);
         return;
     }
-    const u32 ne = ld_volatile(&ls->ne[t]);
-    const Key* K = b.K[t & 1];
-    const u32* pos = b.pos[t & 1];
-    const u32* set = b.set[t & 1];
+    const u32 ne = ld_volatile(&ls->ne[last]);
+    const Key* K = b.K[last & 1];
+    const u32* pos = b.pos[last & 1];
+    const u32* set = b.set[last & 1];
     for (u32 e = gtid; e < ne; e += gthreads) {
         const Key k = K[e];
         out_keys[e] = k;
@@ -493,24 +490,22 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const Key* __rest
 struct LeavesLayout {
     LoopState* ls;
     LeafBufs bufs;
-    u64* look;
-    u32 max_tiles;
     size_t bytes;
 };
 
 LeavesLayout leaves_layout(void* ws, long long ecap, int max_iters, bool batch) {
+    (void)max_iters;
     LeavesLayout l;
     Carver c(ws);
     l.ls = c.take<LoopState>(1);
-    l.bufs.split_elem = c.take<u32>((size_t)ecap);
-    l.bufs.split_pos = c.take<u32>((size_t)ecap);
+    l.bufs.split_q = c.take<uint4>((size_t)ecap);
+    l.bufs.ops = c.take<unsigned char>((size_t)ecap);
+    l.bufs.tile_sum = c.take<u64>((size_t)((ecap + kTile - 1) / kTile));
     for (int k = 0; k < 2; ++k) {
         l.bufs.K[k] = c.take<Key>((size_t)ecap);
         l.bufs.pos[k] = c.take<u32>((size_t)ecap);
         l.bufs.set[k] = batch ? c.take<u32>((size_t)ecap) : nullptr;
     }
-    l.max_tiles = static_cast<u32>((ecap + kTile - 1) / kTile);
-    l.look = c.take<u64>((size_t)l.max_tiles * (size_t)max_iters);
     l.bytes = c.size();
     return l;
 }
@@ -537,7 +532,7 @@ int read_leaves_result(void* ws, cudaStream_t st, long long ecap, int max_iters,
     }
     if (h.err) return fail(static_cast<int>(h.err), "%s: device error %u (info 0x%x)", who, h.err, h.err_info);
     if (!s.converged) return fail(CSTONE_ERR_NOT_CONVERGED, "%s: not converged after %d passes", who, max_iters);
-    *ne_out = s.ne[s.iters];
+    *ne_out = s.ne[s.iters - 1];  // the last pass changed nothing: its input is the result
     return CSTONE_OK;
 }
 
@@ -553,22 +548,20 @@ int run_leaves(const Key* P, long long n, u32 ncrit, Key* leaves, long long ecap
     WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
     CST_CUDA(cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st));
     CST_CUDA(cudaMemsetAsync(l.ls, 0, sizeof(LoopState), st));
-    CST_CUDA(cudaMemsetAsync(l.look, 0, (size_t)l.max_tiles * max_iters * sizeof(u64), st));
     int warm = ne0 != 0 ? 1 : 0;
     u32 ne_start = ne0 < 0 ? kDeviceCount : static_cast<u32>(ne0);
     int fallback = sync ? 0 : 1;
 
     const Key* P_ = P;
-    u32 n_ = static_cast<u32>(n), ncrit_ = ncrit, ecap_ = static_cast<u32>(ecap), max_tiles = l.max_tiles;
+    u32 n_ = static_cast<u32>(n), ncrit_ = ncrit, ecap_ = static_cast<u32>(ecap);
     int max_iters_ = max_iters;
     LeafBufs bufs = l.bufs;
-    u64* look = l.look;
     LoopState* ls = l.ls;
     Key* out_keys = leaves;
     u32* out_counts = counts;
     u32* out_offsets = offsets;
     void* args[] = {&P_,       &n_,   &ncrit_,    &bufs, &ecap_, &max_iters_, &warm,     &ne_start,   &fallback,
-                    &look,     &max_tiles, &ls,   &hdr,  &sv,    &out_keys,   &out_counts, &out_offsets};
+                    &ls,       &hdr,  &sv,    &out_keys,   &out_counts, &out_offsets};
     CST_COOP(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(leaves_loop_kernel<BATCH>), dim3(leaves_grid<BATCH>()),
                                          dim3(kThreads), args, 0, st));
     if (!sync) return CSTONE_OK;
