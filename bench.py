@@ -7,8 +7,8 @@ keys, radix sort with permutation, cornerstone leaf loop, linked octree, node-co
 the FP32 compensated monopole/quadrupole upsweep. Inputs (3.5 GB) are larger than the 129 MB L2,
 so no explicit flush is needed between steps.
 
-``--impl reference`` times the plain CPU oracle instead (single thread, bounded sample of the
-same workload); under torchrun only rank 0 runs it.
+``--impl reference`` times the plain CPU oracle instead (on every host core, bounded sample of
+the same workload); under torchrun only rank 0 runs it.
 """
 from __future__ import annotations
 
@@ -28,7 +28,8 @@ NCRIT = 64
 SEED = 20230626 + 2
 METRIC = "particles/s full octree build (keys->sort->leaves->tree) @1 GB300, % HBM roofline"
 WORKLOAD = "2^27 Gaussian clumps + 20% uniform, Hilbert keys, Ncrit=64, with count + multipole upsweep"
-CPU_SAMPLE = 1 << 21
+CPU_SAMPLE = 1 << 23
+REF_SAMPLE = 1 << 22  # per step of the reference arm (its --steps K --warmup W run stays within minutes)
 
 
 def parse():
@@ -46,6 +47,7 @@ def parse():
     p.add_argument("--no-table1", action="store_true")
     p.add_argument("--no-keys30", action="store_true")
     p.add_argument("--no-focus", action="store_true")
+    p.add_argument("--no-configs", action="store_true")
     return p.parse_args()
 
 
@@ -290,6 +292,8 @@ def run_ours(args, rank, world, local):
         extra["focused_tree"] = measure_focus(b, n_leaves)
     if rank == 0 and not args.no_keys30:
         extra["keys30_same_workload"] = measure_keys30(X, Y, Z, M, K=max(3, min(K, 10)))
+    if rank == 0 and not args.no_configs:
+        extra["other_configs"] = measure_configs(dev, X, Y, Z, M, K=max(3, min(K, 10)))
     if rank == 0 and not args.no_batched:
         extra["batched_512_sets"] = measure_batched(dev)
     if rank == 0 and (not args.no_timesteps and args.ts_steps > 0 or not args.no_table1):
@@ -338,6 +342,124 @@ def run_ours(args, rank, world, local):
     return line
 
 
+def run_global(args, rank, world, local):
+    """N > 1 processes, one per GPU (Sec. 6): every rank holds 2^27 clump particles of its own; a step
+    builds the global octree of all ranks' particles (global bounding cube from bounds reduced over
+    the ranks, local keys and sort, then f on the rank's own keys, one allreduce(SUM) of the leaf
+    counts over NCCL and the same g on every rank, per pass), cuts it into one SFC domain per rank,
+    sends every particle (and its mass) to the rank owning its key (all_to_all), and builds the
+    rank's full local octree with node counts and multipoles in the global frame. Weak scaling:
+    value = all ranks' particles / the slowest rank's step time."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2307_06345_gb300 as cs
+    from paper_2307_06345_gb300 import distributed as D
+
+    os.environ.setdefault("NCCL_DEBUG", "INFO")  # NCCL's communicator lines name the ranks and devices
+    os.environ.setdefault("NCCL_NVLS_ENABLE", "0")
+    cs.load()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist.init_process_group("nccl", device_id=dev)
+    n = args.n
+    x, y, z, m = workload(n, rank)
+    X, Y, Z, M = (torch.from_numpy(a).to(dev) for a in (x, y, z, m))
+    ops = D.DeviceOps(dev)
+    stream = torch.cuda.current_stream()
+    state = {}
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        t = D.build_global_tree(X, Y, Z, curve=cs.HILBERT, ncrit=NCRIT, ops=ops)
+        cuts = D.decompose(ops, t["N_global"], world)
+        if ev:
+            ev[1].record(stream)
+        rx, ry, rz, rm = D.exchange(ops, X, Y, Z, t["P"], t["perm"], t["K"], cuts, extra=(M,))
+        if ev:
+            ev[2].record(stream)
+        out = cs.build_octree(rx, ry, rz, curve=cs.HILBERT, ncrit=NCRIT, box=t["box"], masses=rm,
+                              buffers=state.get("buffers") if state.get("n") == rx.numel() else None)
+        state["buffers"], state["n"] = out["buffers"], rx.numel()
+        if ev:
+            ev[3].record(stream)
+        return t, out
+
+    for _ in range(max(args.warmup, 1)):
+        t, out = step()
+    torch.cuda.synchronize()
+    K = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    dist.barrier()
+    torch.cuda.synchronize()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        launches0 = cs.cstone_kernel_launches()
+        start.record(stream)
+        for k in range(K):
+            t, out = step(evs[k])
+        stop.record(stream)
+        launches = cs.cstone_kernel_launches() - launches0
+        torch.cuda.synchronize()
+    dist.barrier()
+    torch.cuda.synchronize()
+    ms_per_step = max_over_ranks(start.elapsed_time(stop), dist, dev) / K
+    phase = {name: float(np.mean([e[i].elapsed_time(e[i + 1]) for e in evs]))
+             for i, name in enumerate(("global_tree", "exchange", "local_build"))}
+    n_local = out["perm"].numel()
+    # end to end: the same step with this rank's inputs copied in from pinned host memory and its
+    # local tree's leaves and node counts copied out, every step
+    hx, hy, hz, hm = (torch.from_numpy(a).pin_memory() for a in (x, y, z, m))
+    ke = max(2, min(K, 5))
+    dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h2d = d2h = 0
+    e0.record(stream)
+    for _ in range(ke):
+        for dst, src in zip((X, Y, Z, M), (hx, hy, hz, hm)):
+            dst.copy_(src, non_blocking=True)
+            h2d += src.numel() * src.element_size()
+        t, out = step()
+        for key in ("leaves", "node_counts"):
+            host = out[key].cpu()
+            d2h += host.numel() * host.element_size()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / ke, dist, dev)
+    hbm, peak_kind = peaks()
+    nl_local = out["n_leaves"]
+    local_bytes = sum(v for k2, v in algorithmic_bytes(n_local, nl_local, int(nl_local * 1.3),
+                                                        cs.n_nodes(nl_local)).items() if k2 != "bbox")
+    line = None
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": world * n / (ms_per_step * 1e-3), "unit": "particles/s", "n_gpus": world,
+            "steps": K, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + f", {n} particles per rank", "n_particles_per_rank": n,
+                       "ncrit": NCRIT, "curve": "hilbert", "l2_flush": "inputs (3.5 GB per rank) larger than L2",
+                       "parallelism": f"global octree over {world} ranks (Sec. 6): allreduce(SUM) of the leaf counts "
+                                      "per f/g pass over NCCL, SFC decomposition, all_to_all exchange, local build",
+                       "global_leaves": int(t["n_leaves"]), "global_passes": int(t["passes"]),
+                       "rank0_local_particles": n_local, "rank0_local_leaves": out["n_leaves"]},
+            "phase_ms": phase,
+            "roofline": {"bound": "hbm", "kernel": "local_build", "achieved": local_bytes / (phase["local_build"] * 1e-3)
+                         / 1e9, "peak": hbm, "unit": "GB/s", "peak_source": peak_kind,
+                         "frac": local_bytes / (phase["local_build"] * 1e-3) / 1e9 / hbm, "traffic": None},
+            "cpu_baseline": None,
+            "e2e": {"value": world * n / (e2e_ms * 1e-3), "unit": "particles/s", "h2d_bytes_per_step": h2d // ke,
+                    "d2h_bytes_per_step": d2h // ke, "ms_per_step": e2e_ms, "steps": ke},
+            "clocks": clocks.summary(),
+            "gpu_launches": launches,
+        }
+    dist.barrier()
+    dist.destroy_process_group()
+    return line
+
+
 def measure_focus(b, n_leaves: int, reps: int = 5):
     """The locally essential tree of Sec. 7 on the benchmark workload: focus on the key range of the
     5th of 8 equal-count domains (the domain an 8-rank decomposition gives rank 4), minimum-distance
@@ -350,8 +472,8 @@ def measure_focus(b, n_leaves: int, reps: int = 5):
     Kg = b.leaves[: n_leaves + 1].clone()
     N = torch.empty(n_leaves, dtype=torch.int32, device=Kg.device)
     cs.cstone_leaf_counts(b.sorted_keys, Kg, n_leaves, N)
-    cuts = D.decompose(N, 8)
-    f = [int(v) for v in Kg[torch.tensor([cuts[4], cuts[5]], device=Kg.device)].cpu().tolist()]
+    cuts = D.decompose(D.DeviceOps(Kg.device), N, 8)
+    f = [int(v) for v in Kg[cuts[4:6]].cpu().tolist()]
     f = [v + (1 << 64) if v < 0 else v for v in f]
     ws = cs.Workspace(Kg.device)
     out = cs.build_focus_leaves(b.sorted_keys, NCRIT, f[0], f[1], 0.5, cs.HILBERT, warm_leaves=Kg, ws=ws)
@@ -365,7 +487,8 @@ def measure_focus(b, n_leaves: int, reps: int = 5):
         torch.cuda.synchronize()
         ts.append(e0.elapsed_time(e1))
     K, Nf, passes = out
-    inside = int(N[cuts[4]: cuts[5]].sum().item())
+    c4, c5 = (int(v) for v in cuts[4:6].cpu().tolist())
+    inside = int(N[c4: c5].sum().item())
     return {"focus_keys": f, "theta": 0.5, "ncrit": NCRIT, "ms": sorted(ts)[len(ts) // 2], "passes": passes,
             "n_leaves_focused": K.numel() - 1, "n_leaves_global": n_leaves, "particles_in_focus": inside,
             "start": "balanced tree of all particles"}
@@ -419,6 +542,60 @@ def measure_keys30(X, Y, Z, M, K: int = 10):
             "n_leaves": nl, "leaf_iterations": it,
             "max_leaf_count": int(b.counts[:nl].max().item()), "root_count": int(counts[0].item()),
             "sort_algorithmic_bytes_per_key": 12 + 3 * 16}
+
+
+def _timed_builds(X, Y, Z, M, curve, ncrit, box, K, masses=True):
+    """ms per full build (CUDA events over K builds after two warm-ups) and the built tree."""
+    import torch
+
+    import paper_2307_06345_gb300 as cs
+
+    kw = dict(curve=curve, ncrit=ncrit, box=box, masses=M if masses else None)
+    out = cs.build_octree(X, Y, Z, **kw)
+    b = out["buffers"]
+    out = cs.build_octree(X, Y, Z, buffers=b, **kw)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(K):
+        out = cs.build_octree(X, Y, Z, buffers=b, **kw)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / K, out
+
+
+def measure_configs(dev, X, Y, Z, M, K: int = 10):
+    """Throughput of the other single-set workloads: 65,536 uniform particles (unit cube, Morton,
+    Ncrit 64), 2^25 Plummer particles (bounding cube, Hilbert, Ncrit 64), and the benchmark workload
+    at Ncrit 16; full builds with the count upsweep (and multipoles for the clump workload), CUDA
+    events around K back-to-back builds (each build synchronises once for its leaf count)."""
+    import numpy as np
+    import torch
+
+    import paper_2307_06345_gb300 as cs
+    from paper_2307_06345_gb300 import workloads as w
+
+    res = {}
+    n1 = 65_536
+    x, y, z = w.uniform(n1, w.BASE_SEED)
+    to = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    unit = torch.tensor([0.0, 0.0, 0.0, 1.0], dtype=torch.float64, device=dev)
+    ms, out = _timed_builds(to(x), to(y), to(z), None, cs.MORTON, 64, unit, max(K, 20), masses=False)
+    res["uniform_65536_morton_ncrit64"] = {"ms": ms, "particles_per_s": n1 / (ms * 1e-3), "n_leaves": out["n_leaves"]}
+    n2 = 1 << 25
+    x, y, z = w.plummer(n2, w.BASE_SEED + 1)
+    ms, out = _timed_builds(to(x), to(y), to(z), None, cs.HILBERT, 64, None, K, masses=False)
+    res["plummer_2p25_hilbert_ncrit64"] = {"ms": ms, "particles_per_s": n2 / (ms * 1e-3), "n_leaves": out["n_leaves"],
+                                           "iters": out["iters"]}
+    del x, y, z, out
+    ms, out = _timed_builds(X, Y, Z, M, cs.HILBERT, 16, None, K)
+    res["clumps_2p27_hilbert_ncrit16_multipoles"] = {"ms": ms, "particles_per_s": X.numel() / (ms * 1e-3),
+                                                     "n_leaves": out["n_leaves"], "iters": out["iters"]}
+    del out
+    torch.cuda.empty_cache()
+    res["note"] = ("full builds through build_octree (bounding cube unless given, keys, sort, leaves, link, node "
+                   "counts; multipoles where named); the uniform set is latency bound (n_l = 4096)")
+    return res
 
 
 def measure_batched(dev, reps: int = 5):
@@ -625,19 +802,48 @@ def measure_table1(dev):
     return res
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (from /proc/cpuinfo or lscpu)."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu model")):
+                    return ln.split(":", 1)[1].strip()
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def _oracle_step(oracle, x, y, z, m):
+    t0 = time.perf_counter()
+    ref = oracle.full_build(x, y, z, oracle.HILBERT, NCRIT)
+    oracle.multipoles(x, y, z, m, ref["P"], ref["perm"], ref["NK"])
+    return time.perf_counter() - t0
+
+
 def cpu_baseline(sample: int, rank_seed: int = 0):
-    """The oracle as it stands, single-threaded, on a bounded sample of the same workload."""
+    """The oracle as it stands on a bounded sample of the same workload: on every host core (its
+    parallel loops over particles, leaves and nodes), and single-threaded on a quarter of the sample."""
     import oracle
 
     oracle.build()
     x, y, z, m = workload(sample, rank_seed)
-    t0 = time.perf_counter()
-    ref = oracle.full_build(x, y, z, oracle.HILBERT, NCRIT)
-    oracle.multipoles(x, y, z, m, ref["P"], ref["perm"], ref["NK"])
-    dt = time.perf_counter() - t0
-    return {"value": sample / dt, "unit": "particles/s", "cores": 1, "kind": "oracle",
+    cores = oracle.set_threads(0)
+    dt = _oracle_step(oracle, x, y, z, m)
+    s1 = sample // 4
+    oracle.set_threads(1)
+    dt1 = _oracle_step(oracle, x[:s1], y[:s1], z[:s1], m[:s1])
+    oracle.set_threads(0)
+    return {"value": sample / dt, "unit": "particles/s", "cores": cores, "kind": "oracle",
+            "cpu_model": cpu_model(),
             "sample": f"{sample} particles of the same clump distribution, full path incl. multipoles, "
-                      f"{dt:.1f} s single-threaded"}
+                      f"{dt:.1f} s on {cores} threads",
+            "single_thread": {"value": s1 / dt1, "unit": "particles/s", "cores": 1,
+                              "sample": f"the first {s1} of those particles, {dt1:.1f} s"}}
 
 
 def run_reference(args, rank, world):
@@ -646,24 +852,22 @@ def run_reference(args, rank, world):
     import oracle
 
     oracle.build()
-    sample = CPU_SAMPLE
+    sample = REF_SAMPLE
     x, y, z, m = workload(sample)
+    cores = oracle.set_threads(0)
     for _ in range(args.warmup):
         pass  # the oracle has no warm state; warm-up steps would only repeat the timed work
-    times = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        ref = oracle.full_build(x, y, z, oracle.HILBERT, NCRIT)
-        oracle.multipoles(x, y, z, m, ref["P"], ref["perm"], ref["NK"])
-        times.append(time.perf_counter() - t0)
+    times = [_oracle_step(oracle, x, y, z, m) for _ in range(args.steps)]
     dt = sum(times) / len(times)
     value = sample / dt
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64/u64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_particles": sample, "ncrit": NCRIT, "curve": "hilbert"},
-            "cpu_baseline": {"value": value, "unit": "particles/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{sample} particles per step of the same clump distribution"},
+            "cpu_baseline": {"value": value, "unit": "particles/s", "cores": cores, "kind": "oracle",
+                             "cpu_model": cpu_model(),
+                             "sample": f"{sample} particles per step of the same clump distribution, "
+                                       f"{cores} threads"},
             "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -672,6 +876,8 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         line = run_reference(args, rank, world)
+    elif world > 1:
+        line = run_global(args, rank, world, local)
     else:
         line = run_ours(args, rank, world, local)
     if rank == 0 and line is not None:
