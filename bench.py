@@ -145,7 +145,7 @@ class ClockSampler:
 # measured with ncu (dram__bytes_read.sum + dram__bytes_write.sum over the phase's launches) on
 # 2^24 particles of the same workload and scaled by the particle count (these phases stream or
 # gather per particle, so traffic grows with n).
-MEASURED_DRAM_BYTES_PER_PARTICLE = {"bbox": 24.2, "keys": 64.2, "sort": 232.2, "multipoles": 135.4}
+MEASURED_DRAM_BYTES_PER_PARTICLE = {"bbox": 24.2, "keys": 64.4, "sort": 235.1, "multipoles": 139.8}
 
 
 def algorithmic_bytes(n: int, n_leaves: int, iter_leaves: int, n_nodes: int):
@@ -320,6 +320,8 @@ def run_ours(args, rank, world, local):
             "phase_ms": phase_ms,
             "step_algorithmic_bytes": step_bytes,
             "step_hbm_frac": step_bytes / (ms_per_step * 1e-3) / 1e9 / hbm,
+            "build_hbm_frac_without_multipoles": (step_bytes - algo["multipoles"]) /
+                                                 ((ms_per_step - phase_ms["multipoles"]) * 1e-3) / 1e9 / hbm,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "peak_source": peak_kind,
                          "traffic": (MEASURED_DRAM_BYTES_PER_PARTICLE[dom] * n

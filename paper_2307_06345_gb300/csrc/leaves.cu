@@ -51,6 +51,7 @@ struct LoopState {
     u32 converged;
     u32 required;                 // elements needed when the capacity was exceeded
     u32 final_buf;                // buffer holding the converged arrays
+    unsigned long long phase_stamp[kMaxIters][2];  // %globaltimer after pass t's first and second sweep
 };
 
 struct LeafBufs {
@@ -69,6 +70,31 @@ struct SetView {  // batched builds
     int n_sets;
 };
 
+
+// Asynchronous 16-byte copy from global (through L2 only) to shared memory: src_bytes (0..16) are
+// copied and the rest of the 16 bytes is zero-filled.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Stages elements [e_first, e_first + count) of a device array into shared memory (element e_first
+// + i at dst[i]) with 16-byte copies; elements outside [0, ne) read as zero. e_first and the array
+// start must be 16-byte aligned in bytes.
+template <class T>
+__device__ __forceinline__ void stage_async(T* dst, const T* src, long long e_first, int count, u32 ne, int tid) {
+    constexpr int kPer = 16 / static_cast<int>(sizeof(T));
+    const int chunks = (count + kPer - 1) / kPer;
+    for (int c = tid; c < chunks; c += kThreads) {
+        const long long e0 = e_first + (long long)c * kPer;
+        long long valid = (long long)ne - e0;
+        valid = valid < 0 ? 0 : (valid > kPer ? kPer : valid);
+        const bool inside = e0 >= 0 && valid > 0;
+        cp_async16(dst + c * kPer, inside ? static_cast<const void*>(src + e0) : static_cast<const void*>(src),
+                   inside ? static_cast<int>(valid * sizeof(T)) : 0);
+    }
+}
 
 // First position in P[lo, hi) whose key is >= key.
 __device__ __forceinline__ u32 lower_bound_in(const Key* __restrict__ P, u32 lo, u32 hi, Key key) {
@@ -139,7 +165,7 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const Key* __rest
                                                                u32 ne_start, int fallback, LoopState* ls, WsHeader* hdr, SetView sv,
                                                                Key* out_keys, u32* out_counts, u32* out_offsets) {
     __shared__ u32 s_warp[kThreads / 32];
-    __shared__ unsigned char s_op[kTile];
+    __shared__ __align__(16) unsigned char s_op[kTile];
     __shared__ u32 s_wsplit[kThreads / 32];
     __shared__ u64 s_part[kThreads / 32];
     __shared__ u32 s_nsplit;
@@ -148,9 +174,9 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const Key* __rest
     // the tile's elements with a halo of kHalo on each side (the merge test reads up to 7 back
     // and 8 ahead, the split and count tests one ahead), staged once per tile
     constexpr int kHalo = 8;
-    __shared__ Key s_K[kTile + 2 * kHalo];
-    __shared__ u32 s_pos[kTile + 2 * kHalo];
-    __shared__ u32 s_set[BATCH ? kTile + 2 * kHalo : 1];
+    __shared__ __align__(16) Key s_K[kTile + 2 * kHalo];
+    __shared__ __align__(16) u32 s_pos[kTile + 2 * kHalo];
+    __shared__ __align__(16) u32 s_set[BATCH ? kTile + 2 * kHalo : 4];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const u32 gtid = blockIdx.x * kThreads + tid, gthreads = gridDim.x * kThreads;
 
@@ -223,14 +249,10 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const Key* __rest
             // L2, never through a read-only cache)
             const u32 t0 = tile * kTile;
             const long long h0 = (long long)t0 - kHalo;
-            for (int i = tid; i < kTile + 2 * kHalo; i += kThreads) {
-                const long long e = h0 + i;
-                if (e >= 0 && e < ne) {
-                    s_K[i] = __ldcg(K + e);
-                    s_pos[i] = __ldcg(pos + e);
-                    if (BATCH) s_set[i] = __ldcg(set + e);
-                }
-            }
+            stage_async(s_K, K, h0, kTile + 2 * kHalo, ne, tid);
+            stage_async(s_pos, pos, h0, kTile + 2 * kHalo, ne, tid);
+            if (BATCH) stage_async(s_set, set, h0, kTile + 2 * kHalo, ne, tid);
+            cp_async_wait_all();
             __syncthreads();
             // striped: item j of the tile is element tile * kTile + j, handled by thread j % kThreads
             u32 sum = 0, nspl = 0;
@@ -271,6 +293,11 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const Key* __rest
         __syncthreads();
         if (tid == 0 && s_any) atomicOr(&ls->changed[t], 1u);
         grid_barrier(&ls->bar, hdr);
+        if (gtid == 0) {
+            unsigned long long now;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+            ls->phase_stamp[t][0] = now;
+        }
         if (ld_volatile(&hdr->err)) break;
         if (ld_volatile(&ls->changed[t]) == 0u) {  // this pass confirms convergence: K is final
             converged = true;
@@ -291,15 +318,12 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const Key* __rest
             if (lane == 0) s_part[warp] = part;
             const u32 t0 = tile * kTile;
             // the tile's elements, one more key and position (a split's gap and range end), its ops
-            for (int i = tid; i < kTile + 1; i += kThreads) {
-                const u32 e = t0 + i;
-                const bool ok = e < ne;
-                s_K[i] = ok ? __ldcg(K + e) : 0;
-                s_pos[i] = ok ? __ldcg(pos + e) : 0u;
-                if (BATCH) s_set[i] = ok ? __ldcg(set + e) : 0u;
-                if (i < kTile) s_op[i] = ok ? __ldcg(b.ops + e) : static_cast<unsigned char>(0);
-            }
+            stage_async(s_K, K, t0, kTile + 1, ne, tid);
+            stage_async(s_pos, pos, t0, kTile + 1, ne, tid);
+            if (BATCH) stage_async(s_set, set, t0, kTile + 1, ne, tid);
+            stage_async(s_op, b.ops, t0, kTile, ne, tid);
             if (tid == 0) s_nsplit = 0;
+            cp_async_wait_all();
             __syncthreads();
             for (int w = 0; w < kThreads / 32; ++w) prefix += s_part[w];
             done = tile + 1;
@@ -376,6 +400,11 @@ __global__ void __launch_bounds__(kThreads) leaves_loop_kernel(const Key* __rest
         // loads; a long range is narrowed by 32 probes at once and then binary-searched, one child
         // boundary per lane. A warp loads its next queue entry before it works on the current one.
         grid_barrier(&ls->bar, hdr);
+        if (gtid == 0) {
+            unsigned long long now;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+            ls->phase_stamp[t][1] = now;
+        }
         {
             const u32 nsplit = ld_volatile(&ls->nsplit[t]);
             const u32 gwarp = gtid >> 5, nwarps = gthreads >> 5;
