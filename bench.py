@@ -28,7 +28,7 @@ NCRIT = 64
 SEED = 20230626 + 2
 METRIC = "particles/s full octree build (keys->sort->leaves->tree) @1 GB300, % HBM roofline"
 WORKLOAD = "2^27 Gaussian clumps + 20% uniform, Hilbert keys, Ncrit=64, with count + multipole upsweep"
-CPU_SAMPLE = 1 << 23
+CPU_SAMPLE = 1 << 25  # about 8 s of the oracle on 16 Arm cores, plus 5 s single-threaded on a quarter
 REF_SAMPLE = 1 << 22  # per step of the reference arm (its --steps K --warmup W run stays within minutes)
 
 
@@ -827,15 +827,48 @@ def _oracle_step(oracle, x, y, z, m):
     return time.perf_counter() - t0
 
 
+def multipole_errors_on_sample(oracle, x, y, z, m):
+    """The library's multipoles of the sample's full build against the oracle's FP64 moments of the
+    oracle's own tree (equal to the library's, which the tests check), over every non-empty node:
+    mass |dM| / M, centre max-norm |d com| / node side, quadrupole max_ab |dQ_ab| / max_ab |Q_ab|."""
+    import numpy as np
+    import torch
+
+    import paper_2307_06345_gb300 as cs
+
+    ref = oracle.full_build(x, y, z, oracle.HILBERT, NCRIT)
+    M_ref, c_ref, q_ref = oracle.multipoles(x, y, z, m, ref["P"], ref["perm"], ref["NK"])
+    to = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    out = cs.build_octree(to(x), to(y), to(z), curve=cs.HILBERT, ncrit=NCRIT, masses=to(m))
+    torch.cuda.synchronize()
+    if out["NK"].numel() != ref["NK"].size or not np.array_equal(out["NK"].cpu().numpy().view(np.uint64), ref["NK"]):
+        return {"error": "trees differ"}
+    M = out["mass"].cpu().numpy().astype(np.float64)
+    com = out["com"].cpu().numpy().T
+    q = out["quad"].cpu().numpy().T.astype(np.float64)
+    lev = np.zeros(ref["NK"].size, np.int64)
+    for lv in range(1, 22):
+        lev += ref["NK"] >= np.uint64(1 << (3 * lv))
+    side = ref["box"][3] * 2.0 ** (-lev.astype(np.float64))
+    nz = M_ref > 0
+    qn = np.maximum(np.max(np.abs(q_ref), axis=1), 1e-12 * M_ref * side ** 2)
+    return {"mass": float(np.max(np.abs(M[nz] - M_ref[nz]) / M_ref[nz])),
+            "com": float(np.max(np.max(np.abs(com[nz] - c_ref[nz]), axis=1) / side[nz])),
+            "quad": float(np.max(np.max(np.abs(q[nz] - q_ref[nz]), axis=1) / qn[nz])),
+            "nodes": int(nz.sum()), "tolerance": 1e-6}
+
+
 def cpu_baseline(sample: int, rank_seed: int = 0):
     """The oracle as it stands on a bounded sample of the same workload: on every host core (its
-    parallel loops over particles, leaves and nodes), and single-threaded on a quarter of the sample."""
+    parallel loops over particles, leaves and nodes), and single-threaded on a quarter of the sample.
+    Also the multipole errors of the library's build of that sample against the oracle."""
     import oracle
 
     oracle.build()
     x, y, z, m = workload(sample, rank_seed)
     cores = oracle.set_threads(0)
     dt = _oracle_step(oracle, x, y, z, m)
+    errors = multipole_errors_on_sample(oracle, x, y, z, m)
     s1 = sample // 4
     oracle.set_threads(1)
     dt1 = _oracle_step(oracle, x[:s1], y[:s1], z[:s1], m[:s1])
@@ -845,7 +878,8 @@ def cpu_baseline(sample: int, rank_seed: int = 0):
             "sample": f"{sample} particles of the same clump distribution, full path incl. multipoles, "
                       f"{dt:.1f} s on {cores} threads",
             "single_thread": {"value": s1 / dt1, "unit": "particles/s", "cores": 1,
-                              "sample": f"the first {s1} of those particles, {dt1:.1f} s"}}
+                              "sample": f"the first {s1} of those particles, {dt1:.1f} s"},
+            "multipole_max_errors_on_sample": errors}
 
 
 def run_reference(args, rank, world):
