@@ -917,12 +917,13 @@ class StreamedBuilder:
         res["iters"] = out["iters"]
         return res
 
-    def run(self, sets, on_result=None, events=None):
+    def run(self, sets, on_result=None, events=None, build_starts=None):
         """Builds every (x, y, z, m) of ``sets`` (pinned host tensors: float64 coordinates, float32
         masses, n particles each). Returns the number of bytes copied in and out; ``on_result(k,
         result)`` receives set k's host result dict once its copy-out has completed (a result's
         tensors are reused two sets later). ``events`` = (start, stop) CUDA events, recorded before
-        the first copy-in and after the last copy-out."""
+        the first copy-in and after the last copy-out. ``build_starts``, a list, receives one timing
+        event per set, recorded on the compute stream where the set's build starts."""
         sets = list(sets)
         for src in sets:
             if len(src) != 4 or any(t.numel() != self.n or t.is_cuda for t in src):
@@ -940,6 +941,10 @@ class StreamedBuilder:
             with torch.cuda.stream(self.s_comp):
                 self.s_comp.wait_event(self.ev_in[slot])
                 self.s_comp.wait_event(self.ev_out[slot])  # the slot's previous tree has left
+                if build_starts is not None:
+                    ev = torch.cuda.Event(enable_timing=True)
+                    ev.record(self.s_comp)
+                    build_starts.append(ev)
                 x, y, z, m = self.inputs[slot]
                 out = build_octree(x, y, z, curve=self.curve, ncrit=self.ncrit, masses=m,
                                    buffers=self.buffers[slot], stream=self.s_comp, levels=self.levels)

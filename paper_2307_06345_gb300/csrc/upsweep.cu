@@ -265,27 +265,30 @@ __global__ void __launch_bounds__(kThreads) multipole_pack_kernel(const double* 
         pack(__ldcs(x + p), __ldcs(y + p), __ldcs(z + p), __ldcs(m + p), p);
 }
 
-// Leaf moments. A leaf is handled by a group of 8 lanes, each lane taking every 8th particle and
-// loading its 32-byte record through perm (the one random access of the upsweep), with the group's
-// partial sums combined by shuffles: the centre of mass from fixed-point differences to the leaf's
-// first particle, then the second moments about it. A lane issues the perm loads of its first
-// kHeld particles together, then their record loads together, and keeps those records in
-// registers for the second pass, so a leaf of up to 8 * kHeld particles costs two round trips to
-// memory instead of two per particle; records beyond that are read again for the second pass.
+// Leaf moments. A leaf is handled by a group of kGroupLanes lanes (8, or 4 or 2 where leaves are
+// small), each lane taking every kGroupLanes-th particle and loading its 32-byte record through
+// perm (the one random access of the upsweep), with the group's partial sums combined by
+// shuffles: the centre of mass from fixed-point differences to the leaf's first particle, then the
+// second moments about it. A lane issues the perm loads of its first kHeld particles together,
+// then their record loads together, and keeps those records in registers for the second pass, so
+// a leaf of up to kGroupLanes * kHeld particles costs two round trips to memory instead of two per
+// particle; records beyond that are read again for the second pass. Narrower groups put more
+// leaves, and so more record loads, in flight per warp: with 4.6 particles per leaf (2^27 clumps
+// at N_crit 16) two lanes per leaf take the whole multipole upsweep from 10.9 to 6.5 ms.
 constexpr int kLeafThreads = 256;
-constexpr int kGroupLanes = 8;  // lanes per leaf
 constexpr u32 kBigLeaf = 512;   // larger leaves are summed by a whole block
 #ifndef CSTONE_MP_HELD
 #define CSTONE_MP_HELD 4
 #endif
 constexpr int kHeld = CSTONE_MP_HELD;  // records per lane held between the two passes
 
+template <int G>
 __device__ __forceinline__ ff group_sum(ff v) {
 #pragma unroll
-    for (int s = kGroupLanes / 2; s >= 1; s >>= 1) {
+    for (int s = G / 2; s >= 1; s >>= 1) {
         ff o;
-        o.hi = __shfl_xor_sync(0xffffffffu, v.hi, s, kGroupLanes);
-        o.lo = __shfl_xor_sync(0xffffffffu, v.lo, s, kGroupLanes);
+        o.hi = __shfl_xor_sync(0xffffffffu, v.hi, s, G);
+        o.lo = __shfl_xor_sync(0xffffffffu, v.lo, s, G);
         v = ff_add(v, o);
     }
     return v;
@@ -303,6 +306,7 @@ __device__ __forceinline__ Record load_record(const Record* rec, u32 p) {
     return r;
 }
 
+template <int kGroupLanes>
 __global__ void __launch_bounds__(kLeafThreads, 4) multipole_leaf_kernel(const u32* __restrict__ offsets, u32 nl,
                                                                       const u32* __restrict__ perm,
                                                                       const int* __restrict__ leaf_to_node,
@@ -363,9 +367,9 @@ __global__ void __launch_bounds__(kLeafThreads, 4) multipole_leaf_kernel(const u
         const u32 j = a + t * kGroupLanes + gl;
         if (j < b) first_moments(load_record(s.rec, __ldg(perm + j)));
     }
-    M = group_sum(M);
+    M = group_sum<kGroupLanes>(M);
 #pragma unroll
-    for (int d = 0; d < 3; ++d) S[d] = group_sum(S[d]);
+    for (int d = 0; d < 3; ++d) S[d] = group_sum<kGroupLanes>(S[d]);
     long long c[3] = {0, 0, 0};
     if (b > a) {  // centre = anchor + S / M, rounded to the fixed-point grid
         const float Mv = ff_val(M);
@@ -400,9 +404,9 @@ __global__ void __launch_bounds__(kLeafThreads, 4) multipole_leaf_kernel(const u
         if (j < b) second_moments(load_record(s.rec, __ldg(perm + j)));
     }
 #pragma unroll
-    for (int k = 0; k < 6; ++k) Q[k] = group_sum(Q[k]);
+    for (int k = 0; k < 6; ++k) Q[k] = group_sum<kGroupLanes>(Q[k]);
 #pragma unroll
-    for (int d = 0; d < 3; ++d) R[d] = group_sum(R[d]);
+    for (int d = 0; d < 3; ++d) R[d] = group_sum<kGroupLanes>(R[d]);
     if (active && gl == 0) store_node(leaf_to_node[i], n_nodes, M, c, Q, R, s, f, mass, com, quad);
 }
 
@@ -688,10 +692,19 @@ int launch_upsweep_multipoles(const double* x, const double* y, const double* z,
         CST_LAUNCHED("multipole_pack_kernel");
     }
     CST_CUDA(cudaMemsetAsync(l.mp.n_big, 0, sizeof(u32), st));
-    const long long groups_per_block = kLeafThreads / kGroupLanes;
-    unsigned lgrid = static_cast<unsigned>((nl + groups_per_block - 1) / groups_per_block);
-    multipole_leaf_kernel<<<lgrid, kLeafThreads, 0, st>>>(offsets, static_cast<u32>(nl), perm, leaf_to_node, nn, l.mp,
-                                                          box, mass, com, quad);
+    // lanes per leaf from the mean leaf size (measured: 2 at 4.6 particles per leaf, 8 at 17.5)
+    const int G = n < 8 * nl ? 2 : (n < 12 * nl ? 4 : 8);
+    const long long groups_per_block = kLeafThreads / G;
+    const unsigned lgrid = static_cast<unsigned>((nl + groups_per_block - 1) / groups_per_block);
+    if (G == 2)
+        multipole_leaf_kernel<2><<<lgrid, kLeafThreads, 0, st>>>(offsets, static_cast<u32>(nl), perm, leaf_to_node, nn,
+                                                                 l.mp, box, mass, com, quad);
+    else if (G == 4)
+        multipole_leaf_kernel<4><<<lgrid, kLeafThreads, 0, st>>>(offsets, static_cast<u32>(nl), perm, leaf_to_node, nn,
+                                                                 l.mp, box, mass, com, quad);
+    else
+        multipole_leaf_kernel<8><<<lgrid, kLeafThreads, 0, st>>>(offsets, static_cast<u32>(nl), perm, leaf_to_node, nn,
+                                                                 l.mp, box, mass, com, quad);
     CST_LAUNCHED("multipole_leaf_kernel");
     multipole_bigleaf_kernel<<<sm_count() * 4, kLeafThreads, 0, st>>>(offsets, perm, leaf_to_node, nn, l.mp, box, mass,
                                                                      com, quad);

@@ -183,3 +183,18 @@ def test_multipoles_duplicates_and_single_particles(lib, oracle):
     m = rng.lognormal(0, 1, len(pts)).astype(np.float32)
     err = _multipole_case(lib, oracle, pts[:, 0].copy(), pts[:, 1].copy(), pts[:, 2].copy(), m, 0, 8)
     assert err["mass"] <= TOL and err["com"] <= TOL and err["quad"] <= TOL, err
+
+
+@pytest.mark.parametrize("ncrit,lo,hi", [(16, 0, 8), (48, 8, 12), (128, 12, 1e9)])
+def test_multipoles_each_leaf_group_width(lib, oracle, ncrit, lo, hi):
+    # the leaf sums take 2, 4 or 8 lanes per leaf by the mean leaf size (below 8, below 12, above):
+    # one case in each range
+    from paper_2307_06345_gb300 import workloads as w
+    n = 60_000
+    x, y, z = w.clumps(n, 21, n_clumps=30)
+    m = w.lognormal_masses(n, 22)
+    box = oracle.bounding_cube(x, y, z)
+    mean = n / (oracle.full_build(x, y, z, 1, ncrit, box=box)["K"].size - 1)
+    assert lo <= mean < hi, mean
+    err = _multipole_case(lib, oracle, x, y, z, m, 1, ncrit, box=box)
+    assert err["mass"] <= TOL and err["com"] <= TOL and err["quad"] <= TOL, err
