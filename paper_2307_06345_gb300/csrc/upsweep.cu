@@ -31,6 +31,8 @@ namespace CST_NS {
 namespace {
 
 constexpr int kThreads = 256;
+// Levels with at most this many internal nodes are combined by one block (see the level loops).
+constexpr u32 kSmallLevel = 2 * kThreads;
 
 // ---------------------------------------------------------------------------- counts
 constexpr int kNumLevels = kLevels + 1;
@@ -82,23 +84,38 @@ __global__ void __launch_bounds__(kThreads) upsweep_counts_kernel(const u32* __r
     }
     list_internal(child, n_nodes, n_int, internal, gtid, gthreads, hdr);
     grid_barrier(bar, hdr);
+    auto combine = [&](u32 g) {
+        const u32 c = 8u * g + 1u;  // c + 7 <= 8 n_int = n_nodes - 1
+        const int x = internal[g];
+        u32 sum = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) sum += __ldcg(node_counts + c + k);
+        if (x < 0 || static_cast<u32>(x) >= n_nodes || static_cast<u32>(child[x]) != c) {
+            raise_error(hdr, CSTONE_ERR_INVALID_ARG, 0x73000u);
+            return;
+        }
+        node_counts[x] = sum;
+    };
+    // A level of at most kSmallLevel internal nodes is summed by block 0 alone, followed by a block
+    // barrier instead of a grid barrier (the top levels and the deepest levels of a clustered tree
+    // are small); a grid barrier precedes the next level that the whole grid sums.
+    bool pending = false;  // block 0 wrote levels since the last grid barrier (the same in every block)
     for (int l = kLevels - 1; l >= 0; --l) {
         if (s_lo[l + 2] == s_lo[l + 1]) continue;  // no internal node at level l
         u32 g0, g1;
         internal_range(s_lo, l, n_int, g0, g1);
-        for (u32 g = g0 + gtid; g < g1; g += gthreads) {
-            const u32 c = 8u * g + 1u;  // c + 7 <= 8 n_int = n_nodes - 1
-            const int x = internal[g];
-            u32 sum = 0;
-#pragma unroll
-            for (int k = 0; k < 8; ++k) sum += __ldcg(node_counts + c + k);
-            if (x < 0 || static_cast<u32>(x) >= n_nodes || static_cast<u32>(child[x]) != c) {
-                raise_error(hdr, CSTONE_ERR_INVALID_ARG, 0x73000u);
-                continue;
+        if (g1 <= g0 + kSmallLevel) {
+            if (blockIdx.x == 0) {
+                for (u32 g = g0 + threadIdx.x; g < g1; g += kThreads) combine(g);
+                __syncthreads();
             }
-            node_counts[x] = sum;
+            pending = true;
+            continue;
         }
+        if (pending) grid_barrier(bar, hdr);
+        for (u32 g = g0 + gtid; g < g1; g += gthreads) combine(g);
         grid_barrier(bar, hdr);
+        pending = false;
     }
 }
 
@@ -499,7 +516,7 @@ __global__ void __launch_bounds__(kLeafThreads) multipole_bigleaf_kernel(const u
 
 // Internal nodes, level by level from the deepest: every internal node of a level combines its 8
 // children (in child order) with the parallel-axis shift; a grid barrier separates the levels.
-__global__ void __launch_bounds__(kThreads) multipole_level_kernel(const int* __restrict__ child,
+__global__ void __launch_bounds__(kThreads, 2) multipole_level_kernel(const int* __restrict__ child,
                                                                    const int* __restrict__ level_offsets, u32 n_nodes,
                                                                    MpScratch s, const double* __restrict__ box,
                                                                    float* __restrict__ mass, double* __restrict__ com,
@@ -515,96 +532,109 @@ __global__ void __launch_bounds__(kThreads) multipole_level_kernel(const int* __
     const u32 n_int = (n_nodes - 1) / 8;
     list_internal(child, n_nodes, n_int, s.internal, gtid, gthreads, hdr);
     grid_barrier(bar, hdr);
+    auto combine = [&](u32 g) {
+        const int c0 = static_cast<int>(8u * g + 1u);  // c0 + 7 <= 8 n_int = n_nodes - 1
+        const int x = s.internal[g];
+        ff Mc[8];
+        long long cc[8][3];
+        int anchor = -1;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const float2 mm = __ldcg(reinterpret_cast<const float2*>(s.mass) + c0 + k);
+            Mc[k] = {mm.x, mm.y};
+            if (anchor < 0 && (mm.x != 0.f || mm.y != 0.f)) anchor = k;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) cc[k][d] = __ldcg(s.cfix + (size_t)d * n_nodes + c0 + k);
+        }
+        ff Mp = ff_zero(), Sp[3] = {ff_zero(), ff_zero(), ff_zero()}, Qp[6], Rp[3] = {ff_zero(), ff_zero(), ff_zero()};
+#pragma unroll
+        for (int k = 0; k < 6; ++k) Qp[k] = ff_zero();
+        long long cp[3] = {0, 0, 0};
+        if (anchor >= 0) {
+            long long ca[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                ca[d] = cc[0][d];
+#pragma unroll
+                for (int k = 1; k < 8; ++k)
+                    if (k == anchor) ca[d] = cc[k][d];
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                Mp = ff_add(Mp, Mc[k]);
+                const float mk = ff_val(Mc[k]);
+#pragma unroll
+                for (int d = 0; d < 3; ++d)
+                    Sp[d] = ff_add(Sp[d], __fmul_rn(mk, fixed_diff(cc[k][d], ca[d], f)));
+            }
+            const float Mv = ff_val(Mp);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const float off = __fdiv_rn(ff_val(Sp[d]), Mv);
+                cp[d] = ca[d] + float_to_int64(__fmul_rn(__fmul_rn(off, 1.0f / f.s1), 1.0f / f.s2));
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                float e[3];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) e[d] = fixed_diff(cc[k][d], cp[d], f);
+                const float mk = ff_val(Mc[k]);
+                const float me0 = __fmul_rn(mk, e[0]), me1 = __fmul_rn(mk, e[1]), me2 = __fmul_rn(mk, e[2]);
+                const float shift[6] = {__fmul_rn(me0, e[0]), __fmul_rn(me0, e[1]), __fmul_rn(me0, e[2]),
+                                        __fmul_rn(me1, e[1]), __fmul_rn(me1, e[2]), __fmul_rn(me2, e[2])};
+                // the child's residual first moment about its own centre: cross terms r e^T + e r^T
+                ff rk[3];
+                float rv[3];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    const float2 rr = __ldcg(reinterpret_cast<const float2*>(s.res + (size_t)d * n_nodes) + c0 + k);
+                    rk[d] = ff{rr.x, rr.y};
+                    rv[d] = ff_val(rk[d]);
+                }
+                const float cross[6] = {
+                    __fmul_rn(2.0f, __fmul_rn(rv[0], e[0])), __fadd_rn(__fmul_rn(rv[0], e[1]), __fmul_rn(rv[1], e[0])),
+                    __fadd_rn(__fmul_rn(rv[0], e[2]), __fmul_rn(rv[2], e[0])), __fmul_rn(2.0f, __fmul_rn(rv[1], e[1])),
+                    __fadd_rn(__fmul_rn(rv[1], e[2]), __fmul_rn(rv[2], e[1])), __fmul_rn(2.0f, __fmul_rn(rv[2], e[2]))};
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                    const float2 qq =
+                        __ldcg(reinterpret_cast<const float2*>(s.quad + (size_t)q * n_nodes) + c0 + k);
+                    Qp[q] = ff_add(Qp[q], ff{qq.x, qq.y});
+                    Qp[q] = ff_add(Qp[q], shift[q]);
+                    Qp[q] = ff_add(Qp[q], cross[q]);
+                }
+                const float me[3] = {me0, me1, me2};
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    Rp[d] = ff_add(Rp[d], rk[d]);
+                    Rp[d] = ff_add(Rp[d], me[d]);
+                }
+            }
+        }
+        if (x < 0 || static_cast<u32>(x) >= n_nodes || child[x] != c0) {
+            raise_error(hdr, CSTONE_ERR_INVALID_ARG, 0x75000u);
+            return;
+        }
+        store_node(x, n_nodes, Mp, cp, Qp, Rp, s, f, mass, com, quad);
+    };
+    // small levels by block 0 alone, as in the count upsweep
+    bool pending = false;
     for (int l = kLevels - 1; l >= 0; --l) {
         if (s_lo[l + 2] == s_lo[l + 1]) continue;  // no internal node at level l
         u32 g0, g1;
         internal_range(s_lo, l, n_int, g0, g1);
-        for (u32 g = g0 + gtid; g < g1; g += gthreads) {
-            const int c0 = static_cast<int>(8u * g + 1u);  // c0 + 7 <= 8 n_int = n_nodes - 1
-            const int x = s.internal[g];
-            ff Mc[8];
-            long long cc[8][3];
-            int anchor = -1;
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const float2 mm = __ldcg(reinterpret_cast<const float2*>(s.mass) + c0 + k);
-                Mc[k] = {mm.x, mm.y};
-                if (anchor < 0 && (mm.x != 0.f || mm.y != 0.f)) anchor = k;
-#pragma unroll
-                for (int d = 0; d < 3; ++d) cc[k][d] = __ldcg(s.cfix + (size_t)d * n_nodes + c0 + k);
+        if (g1 <= g0 + kSmallLevel) {
+            if (blockIdx.x == 0) {
+                for (u32 g = g0 + threadIdx.x; g < g1; g += kThreads) combine(g);
+                __syncthreads();
             }
-            ff Mp = ff_zero(), Sp[3] = {ff_zero(), ff_zero(), ff_zero()}, Qp[6], Rp[3] = {ff_zero(), ff_zero(), ff_zero()};
-#pragma unroll
-            for (int k = 0; k < 6; ++k) Qp[k] = ff_zero();
-            long long cp[3] = {0, 0, 0};
-            if (anchor >= 0) {
-                long long ca[3];
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    ca[d] = cc[0][d];
-#pragma unroll
-                    for (int k = 1; k < 8; ++k)
-                        if (k == anchor) ca[d] = cc[k][d];
-                }
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    Mp = ff_add(Mp, Mc[k]);
-                    const float mk = ff_val(Mc[k]);
-#pragma unroll
-                    for (int d = 0; d < 3; ++d)
-                        Sp[d] = ff_add(Sp[d], __fmul_rn(mk, fixed_diff(cc[k][d], ca[d], f)));
-                }
-                const float Mv = ff_val(Mp);
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    const float off = __fdiv_rn(ff_val(Sp[d]), Mv);
-                    cp[d] = ca[d] + float_to_int64(__fmul_rn(__fmul_rn(off, 1.0f / f.s1), 1.0f / f.s2));
-                }
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    float e[3];
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) e[d] = fixed_diff(cc[k][d], cp[d], f);
-                    const float mk = ff_val(Mc[k]);
-                    const float me0 = __fmul_rn(mk, e[0]), me1 = __fmul_rn(mk, e[1]), me2 = __fmul_rn(mk, e[2]);
-                    const float shift[6] = {__fmul_rn(me0, e[0]), __fmul_rn(me0, e[1]), __fmul_rn(me0, e[2]),
-                                            __fmul_rn(me1, e[1]), __fmul_rn(me1, e[2]), __fmul_rn(me2, e[2])};
-                    // the child's residual first moment about its own centre: cross terms r e^T + e r^T
-                    ff rk[3];
-                    float rv[3];
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) {
-                        const float2 rr = __ldcg(reinterpret_cast<const float2*>(s.res + (size_t)d * n_nodes) + c0 + k);
-                        rk[d] = ff{rr.x, rr.y};
-                        rv[d] = ff_val(rk[d]);
-                    }
-                    const float cross[6] = {
-                        __fmul_rn(2.0f, __fmul_rn(rv[0], e[0])), __fadd_rn(__fmul_rn(rv[0], e[1]), __fmul_rn(rv[1], e[0])),
-                        __fadd_rn(__fmul_rn(rv[0], e[2]), __fmul_rn(rv[2], e[0])), __fmul_rn(2.0f, __fmul_rn(rv[1], e[1])),
-                        __fadd_rn(__fmul_rn(rv[1], e[2]), __fmul_rn(rv[2], e[1])), __fmul_rn(2.0f, __fmul_rn(rv[2], e[2]))};
-#pragma unroll
-                    for (int q = 0; q < 6; ++q) {
-                        const float2 qq =
-                            __ldcg(reinterpret_cast<const float2*>(s.quad + (size_t)q * n_nodes) + c0 + k);
-                        Qp[q] = ff_add(Qp[q], ff{qq.x, qq.y});
-                        Qp[q] = ff_add(Qp[q], shift[q]);
-                        Qp[q] = ff_add(Qp[q], cross[q]);
-                    }
-                    const float me[3] = {me0, me1, me2};
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) {
-                        Rp[d] = ff_add(Rp[d], rk[d]);
-                        Rp[d] = ff_add(Rp[d], me[d]);
-                    }
-                }
-            }
-            if (x < 0 || static_cast<u32>(x) >= n_nodes || child[x] != c0) {
-                raise_error(hdr, CSTONE_ERR_INVALID_ARG, 0x75000u);
-                continue;
-            }
-            store_node(x, n_nodes, Mp, cp, Qp, Rp, s, f, mass, com, quad);
+            pending = true;
+            continue;
         }
+        if (pending) grid_barrier(bar, hdr);
+        for (u32 g = g0 + gtid; g < g1; g += gthreads) combine(g);
         grid_barrier(bar, hdr);
+        pending = false;
     }
 }
 
