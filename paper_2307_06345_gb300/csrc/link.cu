@@ -14,8 +14,13 @@
 // is the same. The partition is a counting sort with L + 1 buckets: per-tile level counts, one scan
 // over (level, tile), and a scatter that ranks items stably inside each tile.
 //
-// Step 5: the first child of an internal node is found by binary search for its key << 3 within
-// the next level's range of NK; the same pass fills the parent of every sibling group.
+// Step 5: the first child of an internal node. In this layout every internal node has its 8
+// children together and the sibling groups follow their parents' breadth-first order, so the
+// children of the g-th internal node (counting internal nodes only, in breadth-first order) are
+// the nodes 8 g + 1 .. 8 g + 8: the child index that the paper's search for the key << 3 in the
+// next level finds. The scatter ranks every internal node among the internal nodes with a second
+// counting sort of the pairs alone and writes CO (and the parent of every sibling group) directly.
+// Batched sets still search (link_b_child_kernel).
 #include "common.cuh"
 
 namespace CST_NS {
@@ -41,15 +46,15 @@ __device__ __forceinline__ Key placeholder(Key key, int level) {
 }
 
 __global__ void __launch_bounds__(kThreads) link_count_kernel(const Key* __restrict__ K, u32 nl, u32 ntiles,
-                                                              u32* __restrict__ counts) {
-    __shared__ u32 s_cnt[kNumLevels];
-    if (threadIdx.x < kNumLevels) s_cnt[threadIdx.x] = 0;
+                                                              u32* __restrict__ counts, u32* __restrict__ pair_counts) {
+    __shared__ u32 s_cnt[2][kNumLevels];
+    if (threadIdx.x < 2 * kNumLevels) (&s_cnt[0][0])[threadIdx.x] = 0;
     __syncthreads();
     const u32 tile = blockIdx.x;
     const u32 i0 = tile * kTile + threadIdx.x * kItems;
-    u32 local[kNumLevels];
+    u32 local[kNumLevels], plocal[kNumLevels];
 #pragma unroll
-    for (int l = 0; l < kNumLevels; ++l) local[l] = 0;
+    for (int l = 0; l < kNumLevels; ++l) local[l] = plocal[l] = 0;
 #pragma unroll
     for (int k = 0; k < kItems; ++k) {
         u32 i = i0 + k;
@@ -61,17 +66,27 @@ __global__ void __launch_bounds__(kThreads) link_count_kernel(const Key* __restr
         if (i + 1 < nl) {
             int pl = pair_level(a, b);
 #pragma unroll
-            for (int l = 0; l < kNumLevels; ++l) local[l] += (l == pl);
+            for (int l = 0; l < kNumLevels; ++l) {
+                local[l] += (l == pl);
+                if (pair_counts) plocal[l] += (l == pl);
+            }
         }
     }
 #pragma unroll
     for (int l = 0; l < kNumLevels; ++l) {
-        u32 v = local[l];
-        for (int s = 16; s > 0; s >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s);
-        if ((threadIdx.x & 31) == 0 && v) atomicAdd(&s_cnt[l], v);
+        u32 v = local[l], w = plocal[l];
+        for (int s = 16; s > 0; s >>= 1) {
+            v += __shfl_xor_sync(0xffffffffu, v, s);
+            w += __shfl_xor_sync(0xffffffffu, w, s);
+        }
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(&s_cnt[0][l], v);
+        if ((threadIdx.x & 31) == 0 && w) atomicAdd(&s_cnt[1][l], w);
     }
     __syncthreads();
-    if (threadIdx.x < kNumLevels) counts[(size_t)threadIdx.x * ntiles + tile] = s_cnt[threadIdx.x];
+    if (threadIdx.x < kNumLevels) {
+        counts[(size_t)threadIdx.x * ntiles + tile] = s_cnt[0][threadIdx.x];
+        if (pair_counts) pair_counts[(size_t)threadIdx.x * ntiles + tile] = s_cnt[1][threadIdx.x];
+    }
 }
 
 // Exclusive scan of the level-major (level, tile) counts in one block; LO[l] = offset of (l, 0),
@@ -110,15 +125,116 @@ __global__ void __launch_bounds__(1024) link_scan_kernel(u32* __restrict__ count
     }
 }
 
+// Exclusive scans of the level-major (level, tile) counts of all nodes (half 0) and of the internal
+// nodes alone (half 1), each of `len` entries, in chunks of kScanChunk: block (c, h) sums chunk c
+// of half h, then block (c, h) adds the sums of the chunks before it and scans its chunk. LO comes
+// from half 0 (LO[l] = offset of (l, 0), LO[22] = total); a total of all nodes different from
+// n_expected, or of internal nodes different from (n_expected - 1) / 8, means the input was not a
+// cornerstone array.
+constexpr u32 kScanThreads = 1024;
+constexpr u32 kScanPer = 4;
+constexpr u32 kScanChunk = kScanThreads * kScanPer;
+
+__global__ void __launch_bounds__(kScanThreads) link_scan_reduce_kernel(const u32* __restrict__ counts, u32 len,
+                                                                        u32* __restrict__ partial) {
+    __shared__ u32 s_warp[kScanThreads / 32];
+    const u32 h = blockIdx.y, c = blockIdx.x;
+    const u32* a = counts + (size_t)h * len;
+    u32 sum = 0;
+#pragma unroll
+    for (u32 j = 0; j < kScanPer; ++j) {
+        const u32 i = c * kScanChunk + j * kScanThreads + threadIdx.x;  // coalesced
+        if (i < len) sum += a[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if ((threadIdx.x & 31) == 0) s_warp[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        u32 v = s_warp[threadIdx.x];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) partial[h * gridDim.x + c] = v;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) link_scan_apply_kernel(u32* __restrict__ counts, u32 len, u32 ntiles,
+                                                                       const u32* __restrict__ partial,
+                                                                       int* __restrict__ LO, u32 n_expected,
+                                                                       WsHeader* hdr) {
+    __shared__ u32 s_warp[kScanThreads / 32];
+    __shared__ u32 s_carry;
+    const u32 h = blockIdx.y, c = blockIdx.x, nchunks = gridDim.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp == 0) {  // sums of the chunks before this one (and of all chunks, for the total)
+        u32 before = 0, all = 0;
+        for (u32 k = lane; k < nchunks; k += 32) {
+            const u32 v = partial[h * nchunks + k];
+            all += v;
+            if (k < c) before += v;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            before += __shfl_xor_sync(0xffffffffu, before, o);
+            all += __shfl_xor_sync(0xffffffffu, all, o);
+        }
+        if (lane == 0) {
+            s_carry = before;
+            if (c == nchunks - 1) {
+                const u32 want = h == 0 ? n_expected : (n_expected - 1) / 8;
+                if (h == 0) LO[kNumLevels] = static_cast<int>(all);
+                if (all != want) raise_error(hdr, CSTONE_ERR_INVALID_ARG, all);
+            }
+        }
+    }
+    __syncthreads();
+    u32* a = counts + (size_t)h * len;
+    // thread t takes the kScanPer consecutive entries c * kScanChunk + t * kScanPer + j
+    const u32 i0 = c * kScanChunk + threadIdx.x * kScanPer;
+    u32 v[kScanPer], sum = 0;
+#pragma unroll
+    for (u32 j = 0; j < kScanPer; ++j) {
+        v[j] = i0 + j < len ? a[i0 + j] : 0u;
+        sum += v[j];
+    }
+    u32 incl = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+        const u32 t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        u32 w = s_warp[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const u32 t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        s_warp[lane] = w;
+    }
+    __syncthreads();
+    u32 run = s_carry + (warp > 0 ? s_warp[warp - 1] : 0u) + incl - sum;
+#pragma unroll
+    for (u32 j = 0; j < kScanPer; ++j) {
+        const u32 i = i0 + j;
+        if (i < len) {
+            a[i] = run;
+            if (h == 0 && i % ntiles == 0) LO[i / ntiles] = static_cast<int>(run);
+        }
+        run += v[j];
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) link_scatter_kernel(const Key* __restrict__ K, u32 nl, u32 ntiles,
-                                                                const u32* __restrict__ offsets, u32 n_nodes,
-                                                                Key* __restrict__ NK, int* __restrict__ leaf_to_node) {
-    __shared__ u32 s_rank[kNumLevels][kThreads];  // per-thread counts, then per-thread slots
+                                                                const u32* __restrict__ offsets,
+                                                                const u32* __restrict__ pair_offsets, u32 n_nodes,
+                                                                Key* __restrict__ NK, int* __restrict__ leaf_to_node,
+                                                                int* __restrict__ CO, int* __restrict__ parent) {
+    __shared__ u32 s_rank[kNumLevels][kThreads];   // per-thread counts, then per-thread slots
+    __shared__ u32 s_prank[kNumLevels][kThreads];  // the same for internal nodes only
     const int tid = threadIdx.x;
     const u32 tile = blockIdx.x;
     const u32 i0 = tile * kTile + tid * kItems;
+    const u32 n_int = (n_nodes - 1) / 8;
 #pragma unroll
-    for (int l = 0; l < kNumLevels; ++l) s_rank[l][tid] = 0;
+    for (int l = 0; l < kNumLevels; ++l) s_rank[l][tid] = s_prank[l][tid] = 0;
     // count this thread's items per level (own column, no conflicts)
     for (int k = 0; k < kItems; ++k) {
         u32 i = i0 + k;
@@ -127,18 +243,24 @@ __global__ void __launch_bounds__(kThreads) link_scatter_kernel(const Key* __res
         s_rank[leaf_level(b - a)][tid] += 1;
         if (i + 1 < nl) {
             int pl = pair_level(a, b);
-            if (pl >= 0) s_rank[pl][tid] += 1;
+            if (pl >= 0) {
+                s_rank[pl][tid] += 1;
+                s_prank[pl][tid] += 1;
+            }
         }
     }
     __syncthreads();
     // exclusive scan of every level row across the threads, plus the tile's global offset
     const int lane = tid & 31, warp = tid >> 5;
-    for (int l = warp; l < kNumLevels; l += kThreads / 32) {
+    for (int r = warp; r < 2 * kNumLevels; r += kThreads / 32) {
+        const int l = r % kNumLevels;
+        u32* row = r < kNumLevels ? s_rank[l] : s_prank[l];
+        const u32* off = r < kNumLevels ? offsets : pair_offsets;
         u32 v[kThreads / 32];
         u32 sum = 0;
 #pragma unroll
         for (int q = 0; q < kThreads / 32; ++q) {
-            v[q] = s_rank[l][lane * (kThreads / 32) + q];
+            v[q] = row[lane * (kThreads / 32) + q];
             sum += v[q];
         }
         u32 incl = sum;
@@ -146,15 +268,16 @@ __global__ void __launch_bounds__(kThreads) link_scatter_kernel(const Key* __res
             u32 t = __shfl_up_sync(0xffffffffu, incl, s);
             if (lane >= s) incl += t;
         }
-        u32 run = offsets[(size_t)l * ntiles + tile] + incl - sum;
+        u32 run = off[(size_t)l * ntiles + tile] + incl - sum;
 #pragma unroll
         for (int q = 0; q < kThreads / 32; ++q) {
-            s_rank[l][lane * (kThreads / 32) + q] = run;
+            row[lane * (kThreads / 32) + q] = run;
             run += v[q];
         }
     }
     __syncthreads();
-    // emit in in-order sequence: leaf i, then the internal node of pair i
+    // emit in in-order sequence: leaf i, then the internal node of pair i; the g-th internal node
+    // has its children at 8 g + 1
     for (int k = 0; k < kItems; ++k) {
         u32 i = i0 + k;
         if (i >= nl) break;
@@ -163,50 +286,29 @@ __global__ void __launch_bounds__(kThreads) link_scatter_kernel(const Key* __res
         u32 x = s_rank[ll][tid]++;
         if (x < n_nodes) {
             NK[x] = placeholder(a, ll);
+            CO[x] = 0;
             leaf_to_node[i] = static_cast<int>(x);
         }
         if (i + 1 < nl) {
             int pl = pair_level(a, b);
             if (pl >= 0) {
                 u32 y = s_rank[pl][tid]++;
-                if (y < n_nodes) NK[y] = placeholder(a, pl);
+                u32 g = s_prank[pl][tid]++;
+                if (y < n_nodes) {
+                    NK[y] = placeholder(a, pl);
+                    CO[y] = g < n_int ? static_cast<int>(8u * g + 1u) : 0;
+                    if (parent && g < n_int) parent[g] = static_cast<int>(y);
+                }
             }
         }
-    }
-}
-
-__global__ void __launch_bounds__(kThreads) link_child_kernel(const Key* __restrict__ NK, u32 n_nodes,
-                                                              const int* __restrict__ LO, int* __restrict__ CO,
-                                                              int* __restrict__ parent) {
-    __shared__ int s_lo[kNumLevels + 1];
-    if (threadIdx.x <= kNumLevels) s_lo[threadIdx.x] = LO[threadIdx.x];
-    __syncthreads();
-    for (u32 x = blockIdx.x * kThreads + threadIdx.x; x < n_nodes; x += gridDim.x * kThreads) {
-        Key k = NK[x];
-        int level = (kWordBits - 1 - key_clz(k)) / 3;
-        int c = 0;
-        if (level < kLevels) {
-            Key want = k << 3;
-            u32 lo = min(static_cast<u32>(s_lo[level + 1]), n_nodes);
-            u32 hi = min(static_cast<u32>(s_lo[level + 2]), n_nodes);
-            const u32 end = hi;
-            while (lo < hi) {
-                u32 mid = lo + ((hi - lo) >> 1);
-                if (NK[mid] < want)
-                    lo = mid + 1;
-                else
-                    hi = mid;
-            }
-            if (lo < end && NK[lo] == want) c = static_cast<int>(lo);
-        }
-        CO[x] = c;
-        if (c > 0 && parent) parent[(c - 1) >> 3] = static_cast<int>(x);
     }
 }
 
 struct LinkLayout {
-    u32* counts;
+    u32* counts;   // [2][ntiles * 22]: all nodes, then internal nodes, per (level, tile)
+    u32* partial;  // [2][chunks] chunk sums of the scans
     u32 ntiles;
+    u32 chunks;    // scan chunks per half
     size_t bytes;
 };
 
@@ -215,7 +317,10 @@ LinkLayout link_layout(void* ws, long long nl) {
     Carver c(ws);
     l.ntiles = static_cast<u32>((nl + kTile - 1) / kTile);
     if (l.ntiles == 0) l.ntiles = 1;
-    l.counts = c.take<u32>((size_t)l.ntiles * kNumLevels + 1);
+    const u32 len = l.ntiles * kNumLevels;
+    l.chunks = (len + kScanChunk - 1) / kScanChunk;
+    l.counts = c.take<u32>((size_t)2 * len);
+    l.partial = c.take<u32>((size_t)2 * l.chunks);
     l.bytes = c.size();
     return l;
 }
@@ -525,17 +630,18 @@ int launch_link(const Key* K, long long nl, Key* NK, int* CO, int* LO, int* leaf
     WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
     CST_CUDA(cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st));
     const u32 n_nodes = static_cast<u32>(nl + (nl - 1) / 7);
-    link_count_kernel<<<l.ntiles, kThreads, 0, st>>>(K, static_cast<u32>(nl), l.ntiles, l.counts);
+    const u32 len = l.ntiles * kNumLevels;
+    u32* pair_counts = l.counts + len;
+    link_count_kernel<<<l.ntiles, kThreads, 0, st>>>(K, static_cast<u32>(nl), l.ntiles, l.counts, pair_counts);
     CST_LAUNCHED("link_count_kernel");
-    link_scan_kernel<<<1, 1024, 0, st>>>(l.counts, l.ntiles, LO, n_nodes, hdr);
-    CST_LAUNCHED("link_scan_kernel");
-    link_scatter_kernel<<<l.ntiles, kThreads, 0, st>>>(K, static_cast<u32>(nl), l.ntiles, l.counts, n_nodes, NK,
-                                                       leaf_to_node);
+    link_scan_reduce_kernel<<<dim3(l.chunks, 2), kScanThreads, 0, st>>>(l.counts, len, l.partial);
+    CST_LAUNCHED("link_scan_reduce_kernel");
+    link_scan_apply_kernel<<<dim3(l.chunks, 2), kScanThreads, 0, st>>>(l.counts, len, l.ntiles, l.partial, LO, n_nodes,
+                                                                        hdr);
+    CST_LAUNCHED("link_scan_apply_kernel");
+    link_scatter_kernel<<<l.ntiles, kThreads, 0, st>>>(K, static_cast<u32>(nl), l.ntiles, l.counts, pair_counts,
+                                                       n_nodes, NK, leaf_to_node, CO, parent);
     CST_LAUNCHED("link_scatter_kernel");
-    long long want = (n_nodes + kThreads - 1) / kThreads;
-    int grid = static_cast<int>(want < (long long)sm_count() * 8 ? want : (long long)sm_count() * 8);
-    link_child_kernel<<<grid, kThreads, 0, st>>>(NK, n_nodes, LO, CO, parent);
-    CST_LAUNCHED("link_child_kernel");
     return CSTONE_OK;
 }
 
