@@ -334,7 +334,7 @@ constexpr int kChunkTiles = 32;  // tiles per chunk of the two-level scan
 // segmented sort count nothing).
 template <bool SEG>
 __global__ void __launch_bounds__(kThreads) tile_count_kernel(const Key* __restrict__ kin, long long n, int shift,
-                                                              u32* __restrict__ counts, SegTiles seg) {
+                                                              unsigned short* __restrict__ counts, SegTiles seg) {
     __shared__ u32 wh[kWarps][kRadix];
     const int tid = threadIdx.x, warp = tid >> 5;
     for (int i = tid; i < kWarps * kRadix; i += kThreads) (&wh[0][0])[i] = 0;
@@ -368,12 +368,12 @@ __global__ void __launch_bounds__(kThreads) tile_count_kernel(const Key* __restr
         u32 c = 0;
 #pragma unroll
         for (int w = 0; w < kWarps; ++w) c += wh[w][dd];
-        counts[(size_t)blockIdx.x * kRadix + dd] = c;
+        counts[(size_t)blockIdx.x * kRadix + dd] = static_cast<unsigned short>(c);
     }
 }
 
 // Per chunk of kChunkTiles tiles: the keys of every digit (thread = digit).
-__global__ void __launch_bounds__(kRadix) chunk_sum_kernel(const u32* __restrict__ counts, long long tiles,
+__global__ void __launch_bounds__(kRadix) chunk_sum_kernel(const unsigned short* __restrict__ counts, long long tiles,
                                                            u32* __restrict__ chunk) {
     const int d = threadIdx.x;
     const long long t0 = (long long)blockIdx.x * kChunkTiles;
@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(1024) chunk_scan_kernel(u32* __restrict__ chun
 // Output position of every tile's first key of every digit (thread = digit): the digit's first
 // position in the pass (the keys of all smaller digits: an exclusive scan of totals over the digits,
 // done by every block; 0 when totals is NULL) plus the digit's keys in all earlier tiles.
-__global__ void __launch_bounds__(kRadix) tile_offsets_kernel(const u32* __restrict__ counts, long long tiles,
+__global__ void __launch_bounds__(kRadix) tile_offsets_kernel(const unsigned short* __restrict__ counts, long long tiles,
                                                               const u32* __restrict__ chunk,
                                                               const u32* __restrict__ totals,
                                                               u32* __restrict__ offsets) {
@@ -541,19 +541,22 @@ int run_passes(const Key* keys_in, Key* keys_out, u32* perm, long long n, long l
     const Key* ksrc = keys_in;
     const u32* vsrc = nullptr;
     const long long nchunks = (tiles + kChunkTiles - 1) / kChunkTiles;
+    // tile counts as 16-bit words (a tile holds fewer than 2^16 keys) in the counts buffer
+    unsigned short* counts16 = reinterpret_cast<unsigned short*>(counts);
+    static_assert(kTile < 65536, "16-bit tile counts");
     static_assert(kPasses % 2 == 0, "the last pass must write the output buffers");
     for (int p = 0; p < kPasses; ++p) {
         Key* kdst = (p % 2 == 0) ? keys_alt : keys_out;
         u32* vdst = (p % 2 == 0) ? vals_alt : perm;
-        tile_count_kernel<SEG><<<(unsigned)tiles, kThreads, 0, st>>>(ksrc, n, p * kRadixBits, counts, seg);
+        tile_count_kernel<SEG><<<(unsigned)tiles, kThreads, 0, st>>>(ksrc, n, p * kRadixBits, counts16, seg);
         CST_LAUNCHED("tile_count_kernel");
-        chunk_sum_kernel<<<(unsigned)nchunks, kRadix, 0, st>>>(counts, tiles, chunk);
+        chunk_sum_kernel<<<(unsigned)nchunks, kRadix, 0, st>>>(counts16, tiles, chunk);
         CST_LAUNCHED("chunk_sum_kernel");
         // a segmented sort scans all tiles from 0 and places the digits per segment; each tile
         // subtracts its segment's first tile
         chunk_scan_kernel<<<kRadix, 1024, 0, st>>>(chunk, nchunks, SEG ? nullptr : totals);
         CST_LAUNCHED("chunk_scan_kernel");
-        tile_offsets_kernel<<<(unsigned)nchunks, kRadix, 0, st>>>(counts, tiles, chunk, SEG ? nullptr : totals,
+        tile_offsets_kernel<<<(unsigned)nchunks, kRadix, 0, st>>>(counts16, tiles, chunk, SEG ? nullptr : totals,
                                                                   tile_pos);
         CST_LAUNCHED("tile_offsets_kernel");
         if (p == 0)
