@@ -47,45 +47,40 @@ __device__ __forceinline__ Key placeholder(Key key, int level) {
 
 __global__ void __launch_bounds__(kThreads) link_count_kernel(const Key* __restrict__ K, u32 nl, u32 ntiles,
                                                               u32* __restrict__ counts, u32* __restrict__ pair_counts) {
-    __shared__ u32 s_cnt[2][kNumLevels];
-    if (threadIdx.x < 2 * kNumLevels) (&s_cnt[0][0])[threadIdx.x] = 0;
-    __syncthreads();
+    // per-thread counts per level (own column, no conflicts): all nodes, then internal nodes
+    __shared__ u32 s_c[2][kNumLevels][kThreads];
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int l = 0; l < kNumLevels; ++l) s_c[0][l][tid] = s_c[1][l][tid] = 0;
     const u32 tile = blockIdx.x;
-    const u32 i0 = tile * kTile + threadIdx.x * kItems;
-    u32 local[kNumLevels], plocal[kNumLevels];
-#pragma unroll
-    for (int l = 0; l < kNumLevels; ++l) local[l] = plocal[l] = 0;
-#pragma unroll
+    const u32 i0 = tile * kTile + tid * kItems;
     for (int k = 0; k < kItems; ++k) {
         u32 i = i0 + k;
         if (i >= nl) break;
         Key a = K[i], b = K[i + 1];
-        int ll = leaf_level(b - a);
-#pragma unroll
-        for (int l = 0; l < kNumLevels; ++l) local[l] += (l == ll);
+        s_c[0][leaf_level(b - a)][tid] += 1;
         if (i + 1 < nl) {
             int pl = pair_level(a, b);
-#pragma unroll
-            for (int l = 0; l < kNumLevels; ++l) {
-                local[l] += (l == pl);
-                if (pair_counts) plocal[l] += (l == pl);
+            if (pl >= 0) {
+                s_c[0][pl][tid] += 1;
+                s_c[1][pl][tid] += 1;
             }
         }
     }
-#pragma unroll
-    for (int l = 0; l < kNumLevels; ++l) {
-        u32 v = local[l], w = plocal[l];
-        for (int s = 16; s > 0; s >>= 1) {
-            v += __shfl_xor_sync(0xffffffffu, v, s);
-            w += __shfl_xor_sync(0xffffffffu, w, s);
-        }
-        if ((threadIdx.x & 31) == 0 && v) atomicAdd(&s_cnt[0][l], v);
-        if ((threadIdx.x & 31) == 0 && w) atomicAdd(&s_cnt[1][l], w);
-    }
     __syncthreads();
-    if (threadIdx.x < kNumLevels) {
-        counts[(size_t)threadIdx.x * ntiles + tile] = s_cnt[0][threadIdx.x];
-        if (pair_counts) pair_counts[(size_t)threadIdx.x * ntiles + tile] = s_cnt[1][threadIdx.x];
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int r = warp; r < 2 * kNumLevels; r += kThreads / 32) {
+        const u32* row = &s_c[r / kNumLevels][r % kNumLevels][0];
+        u32 v = 0;
+#pragma unroll
+        for (int q = 0; q < kThreads / 32; ++q) v += row[q * 32 + lane];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) {
+            if (r < kNumLevels)
+                counts[(size_t)r * ntiles + tile] = v;
+            else if (pair_counts)
+                pair_counts[(size_t)(r - kNumLevels) * ntiles + tile] = v;
+        }
     }
 }
 
