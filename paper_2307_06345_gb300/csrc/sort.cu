@@ -5,9 +5,10 @@
 //
 // Each digit pass reads a tile of keys (and values), ranks them within the tile (the lanes of a warp
 // holding the same digit are found with one ballot per digit bit, which measured much cheaper than
-// a warp match instruction), stages the tile in shared memory in digit order and writes each
-// digit's run contiguously at the tile's output position for that digit; the first pass generates
-// the identity values instead of reading them. Ahead of every pass, a count of every tile's digits
+// a warp match instruction), stages the tile in shared memory in digit order (the keys, then the
+// values, through one buffer) and writes each digit's run contiguously at the tile's output
+// position for that digit; the first pass generates the identity values instead of reading them.
+// Ahead of every pass, a count of every tile's digits
 // and a two-level scan of the counts give each tile its output positions, so no tile waits on
 // another (a decoupled look-back between tiles, measured first, spent a third of the sort's time
 // waiting on predecessors); the same counts give the digits' totals, whose scan over the digits
@@ -177,8 +178,11 @@ __device__ __forceinline__ u32 match_digit(u32 v) {
 }
 
 struct PassSmem {
-    Key keys[kTile];
-    u32 vals[kTile];
+    union {  // the tile in digit order: its keys, then (once they are written out) its values
+        Key keys[kTile];
+        u32 vals[kTile];
+    } stage;
+    unsigned char dig[kTile];  // digit of every staged key
     u32 warp_hist[kWarps][kRadix];  // per-warp digit counts, then each warp's first staging slot
     u32 delta[kRadix];              // output position minus staging slot, per digit
     u32 scan_tmp[kWarps];
@@ -302,26 +306,39 @@ __global__ void __launch_bounds__(kThreads, CSTONE_SORT_MIN_BLOCKS)
     }
     __syncthreads();
 
-    // ---- stage in digit order
+    // ---- stage the keys in digit order and write each digit's run contiguously, then the same for
+    // the values in the same buffer (one staging buffer instead of two leaves more of the SM's
+    // L1 for the loads in flight: about 1 % faster on clustered keys)
+    u32 slot2[kItems / 2];  // staging slot of every item (0xffff: none), two per register
 #pragma unroll
     for (int it = 0; it < kItems; ++it) {
         const u32 dd = digit_of(it);
+        u32 slot = 0xffffu;
         if (dd < kRadix) {
             const u32 r = (rank2[it >> 1] >> ((it & 1) * 16)) & 0xffffu;
-            const u32 slot = sm.warp_hist[warp][dd] + r;
-            sm.keys[slot] = key[it];
-            sm.vals[slot] = val[it];
+            slot = sm.warp_hist[warp][dd] + r;
+            sm.stage.keys[slot] = key[it];
         }
+        if (it & 1)
+            slot2[it >> 1] |= slot << 16;
+        else
+            slot2[it >> 1] = slot;
     }
     __syncthreads();
-
-    // ---- write each digit's run contiguously
     for (u32 s = tid; s < count; s += kThreads) {
-        const Key k = sm.keys[s];
-        const u32 pos = sm.delta[static_cast<u32>(k >> shift) & (kRadix - 1)] + s;
-        kout[pos] = k;
-        vout[pos] = sm.vals[s];
+        const Key k = sm.stage.keys[s];
+        const u32 dk = static_cast<u32>(k >> shift) & (kRadix - 1);
+        sm.dig[s] = static_cast<unsigned char>(dk);
+        kout[sm.delta[dk] + s] = k;
     }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < kItems; ++it) {
+        const u32 slot = (slot2[it >> 1] >> ((it & 1) * 16)) & 0xffffu;
+        if (slot != 0xffffu) sm.stage.vals[slot] = val[it];
+    }
+    __syncthreads();
+    for (u32 s = tid; s < count; s += kThreads) vout[sm.delta[sm.dig[s]] + s] = sm.stage.vals[s];
 }
 
 // ---- output offsets of every tile, ahead of a pass (single-set sorts). A tile's output position
