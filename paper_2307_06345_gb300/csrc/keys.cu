@@ -74,8 +74,8 @@ __global__ void __launch_bounds__(256) bbox_reduce_kernel(const double* __restri
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 const double2* p = reinterpret_cast<const double2*>(c[d]) + 2 * q;
-                v[d][0] = __ldcs(p);
-                v[d][1] = __ldcs(p + 1);
+                v[d][0] = __ldcg(p);
+                v[d][1] = __ldcg(p + 1);
             }
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(256) keys_kernel(const double* __restrict__ x,
 
     if (!VEC) {
         for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-            keys[i] = encode(__ldcs(x + i), __ldcs(y + i), __ldcs(z + i));
+            keys[i] = encode(__ldcg(x + i), __ldcg(y + i), __ldcg(z + i));
         return;
     }
     const long long pairs = n >> 1;
@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(256) keys_kernel(const double* __restrict__ x,
     const double2* y2 = reinterpret_cast<const double2*>(y);
     const double2* z2 = reinterpret_cast<const double2*>(z);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < pairs; i += (long long)gridDim.x * blockDim.x) {
-        double2 a = __ldcs(x2 + i), b = __ldcs(y2 + i), c = __ldcs(z2 + i);
+        double2 a = __ldcg(x2 + i), b = __ldcg(y2 + i), c = __ldcg(z2 + i);
         const Key k0 = encode(a.x, b.x, c.x), k1 = encode(a.y, b.y, c.y);
         if constexpr (sizeof(Key) == 8)
             __stcs(reinterpret_cast<ulonglong2*>(keys) + i, make_ulonglong2(k0, k1));
@@ -407,15 +407,15 @@ __global__ void __launch_bounds__(256, CSTONE_KEYS_REC_MIN_BLOCKS)
         const long long i0 = base + lane, i1 = base + 32 + lane;
         if (i0 >= n) break;
         const bool ok1 = i1 < n;
-        const double ax = __ldcs(x + i0), ay = __ldcs(y + i0), az = __ldcs(z + i0);
-        const float am = __ldcs(m + i0);
+        const double ax = __ldcg(x + i0), ay = __ldcg(y + i0), az = __ldcg(z + i0);
+        const float am = __ldcg(m + i0);
         double bx = 0.0, by = 0.0, bz = 0.0;
         float bm = 0.f;
         if (ok1) {
-            bx = __ldcs(x + i1);
-            by = __ldcs(y + i1);
-            bz = __ldcs(z + i1);
-            bm = __ldcs(m + i1);
+            bx = __ldcg(x + i1);
+            by = __ldcg(y + i1);
+            bz = __ldcg(z + i1);
+            bm = __ldcg(m + i1);
         }
         keys[i0] = one(i0, ax, ay, az, am);
         if (ok1) keys[i1] = one(i1, bx, by, bz, bm);
@@ -578,7 +578,7 @@ __global__ void __launch_bounds__(256) keys_batched_kernel(const double* __restr
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const int sidx = set_of(set_offsets, n_sets, i);
         const FixedGrid* g = grids + 3 * sidx;
-        const double px = __ldcs(x + i), py = __ldcs(y + i), pz = __ldcs(z + i);
+        const double px = __ldcg(x + i), py = __ldcg(y + i), pz = __ldcg(z + i);
         u32 c[3];
         const double pc[3] = {px, py, pz};
 #pragma unroll

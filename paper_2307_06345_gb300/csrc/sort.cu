@@ -224,11 +224,11 @@ __global__ void __launch_bounds__(kThreads, CSTONE_SORT_MIN_BLOCKS)
     for (int it = 0; it < kItems; ++it) {
         const u32 o = woff + it * 32;
         const bool ok = o < count;
-        key[it] = ok ? __ldcs(tkeys + o) : ~static_cast<Key>(0);
+        key[it] = ok ? __ldcg(tkeys + o) : ~static_cast<Key>(0);
         if (FIRST)
             val[it] = base + o;
         else
-            val[it] = ok ? __ldcs(vin + base + o) : 0u;
+            val[it] = ok ? __ldcg(vin + base + o) : 0u;
     }
     auto digit_of = [&](int it) -> u32 {
         return (woff + it * 32 < count) ? static_cast<u32>((key[it] >> shift) & (kRadix - 1)) : static_cast<u32>(kRadix);
@@ -373,7 +373,7 @@ __global__ void __launch_bounds__(kThreads) tile_count_kernel(const Key* __restr
 #pragma unroll
     for (int it = 0; it < kItems; ++it) {
         const u32 o = woff + it * 32;
-        kk[it] = o < count ? __ldcs(tkeys + o) : ~static_cast<Key>(0);
+        kk[it] = o < count ? __ldcg(tkeys + o) : ~static_cast<Key>(0);
     }
 #pragma unroll
     for (int it = 0; it < kItems; ++it) {

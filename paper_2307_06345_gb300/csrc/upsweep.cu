@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(kThreads) multipole_pack_kernel(const double* 
     // one particle per thread and step: 8-byte coalesced loads, and a warp's two 16-byte stores
     // cover 1 KB of records contiguously
     for (u32 p = blockIdx.x * kThreads + threadIdx.x; p < n; p += gridDim.x * kThreads)
-        pack(__ldcs(x + p), __ldcs(y + p), __ldcs(z + p), __ldcs(m + p), p);
+        pack(__ldcg(x + p), __ldcg(y + p), __ldcg(z + p), __ldcg(m + p), p);
 }
 
 // Leaf moments. A leaf is handled by a group of kGroupLanes lanes (8, or 4 or 2 where leaves are
