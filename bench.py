@@ -145,7 +145,7 @@ class ClockSampler:
 # measured with ncu (dram__bytes_read.sum + dram__bytes_write.sum over the phase's launches) on
 # 2^24 particles of the same workload and scaled by the particle count (these phases stream or
 # gather per particle, so traffic grows with n).
-MEASURED_DRAM_BYTES_PER_PARTICLE = {"bbox": 24.2, "keys": 64.4, "sort": 235.1, "multipoles": 139.8}
+MEASURED_DRAM_BYTES_PER_PARTICLE = {"bbox": 24.2, "keys": 64.7, "sort": 233.5, "multipoles": 139.8}
 
 
 def algorithmic_bytes(n: int, n_leaves: int, iter_leaves: int, n_nodes: int):
