@@ -26,7 +26,7 @@ import torch
 from . import _build
 
 SORT_CANDIDATES = [{"threads": 256, "items": i, "min_blocks": b}
-                   for i, b in ((8, 5), (10, 4), (12, 4), (14, 3), (16, 3))]
+                   for i, b in ((8, 5), (8, 6), (10, 4), (10, 5), (12, 4), (14, 3), (14, 4), (16, 3), (16, 4))]
 # the leaf loop stages a tile of elements in shared memory: more than 8 per thread exceeds 48 KB
 LEAVES_CANDIDATES = [{"items": i} for i in (4, 6, 8)]
 
