@@ -246,9 +246,10 @@ def run_ours(args, rank, world, local):
     achieved = algo[dom] / (phase_ms[dom] * 1e-3) / 1e9
     step_bytes = sum(algo.values())
 
-    # end to end through the public API with host buffers: every step copies its inputs in from
-    # pinned host memory and its tree out to pinned host memory (StreamedBuilder: copy-in of the
-    # next step, the build and copy-out of the previous step overlap on three streams)
+    # end to end through the C entry points that take host buffers (cstone_host_stage,
+    # cstone_host_build, driven by StreamedBuilder): every step copies its inputs in from pinned host
+    # memory and its tree out to pinned host memory; the copy-in of the next step, the build and
+    # the copy-out of the previous step overlap on three streams
     e2e = None
     if not args.no_e2e:
         hx, hy, hz, hm = (torch.from_numpy(a).pin_memory() for a in (x, y, z, m))
@@ -293,10 +294,10 @@ def run_ours(args, rank, world, local):
         e2e = {"value": world * n / (e2e_ms * 1e-3), "unit": "particles/s", "h2d_bytes_per_step": h2d // ke,
                "d2h_bytes_per_step": d2h // ke, "ms_per_step": e2e_ms, "steps": ke,
                "runs_ms_per_step": [r[0] for r in runs],
-               "method": "StreamedBuilder: per step H2D of x, y, z, m from pinned memory, full build with "
-                         "multipoles, D2H of leaves, counts, NK, CO, LO, node counts, mass, com, quad; copies "
-                         "overlapped with the neighbouring steps' builds; the median of three runs of "
-                         f"{ke} steps",
+               "method": "C ABI cstone_host_stage + cstone_host_build (StreamedBuilder): per step H2D of x, y, "
+                         "z, m from pinned host memory, full build with multipoles, D2H of leaves, counts, NK, CO, "
+                         "LO, node counts, mass, com, quad to pinned host memory; copies overlapped with the "
+                         f"neighbouring steps' builds; the median of three runs of {ke} steps",
                "host_link": link, "steady_ms_per_step": period_ms,
                "copy_in_floor_ms": copy_in_ms,
                "note": "the host link carries about 210 GB/s host to device whether one copy, several "

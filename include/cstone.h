@@ -406,6 +406,69 @@ CSTONE_API int cstone_build_batched_result(const void* ws, int64_t n, int32_t n_
                                            int64_t* n_elements, int64_t* n_nodes, int32_t* iters);
 
 /* ------------------------------------------------------------------------------------------
+ * Full build from host memory (end to end): a particle set's coordinates and masses are copied in
+ * from host buffers, the tree is built on the device as by the single-set calls above (bounding
+ * cube, keys and multipole records, sort, cornerstone leaves of Sec. 4, linked octree and node
+ * counts of Sec. 5, multipoles), and the tree is copied out to host buffers. Two calls per set,
+ * so that consecutive sets overlap on the GPU:
+ *   cstone_host_stage  copies a set into a device slot (on copy_in_stream);
+ *   cstone_host_build  builds a staged slot (on compute_stream) and copies its tree out (on
+ *                      copy_out_stream).
+ * With two slots, the order stage(0, set 0); for k: { stage((k+1) % 2, set k+1); build(k % 2) }
+ * copies set k+1 in while set k builds and set k-1's tree goes out. Host buffers must be pinned
+ * (cudaHostAlloc / cudaHostRegister) for the copies to be asynchronous.
+ *
+ * A slot is caller-owned: a device workspace of cstone_host_workspace_size bytes (256-byte
+ * aligned; it holds the staged inputs, every intermediate and output array, and the phases'
+ * scratch) and four CUDA events (cudaEvent_t passed as void*, created by the caller, timing may
+ * be disabled) through which the calls order the slot's reuse: staged (the set is on the
+ * device), inputs_read (the build has read the inputs: the next stage may overwrite them), built
+ * (the tree is complete) and copied_out (the tree is on the host: the next build may overwrite
+ * it; the caller waits on this event before reading the host tree). A slot must not be staged or
+ * built from two host threads at once.
+ *
+ * cstone_host_build synchronises compute_stream once, after the leaf loop, for the number of
+ * leaves; it returns CSTONE_ERR_CAPACITY (with out->n_leaves = the leaves needed) when leaf_cap
+ * is too small, and then copies nothing out. Device errors of the phases after the leaf loop are
+ * read by cstone_host_status (synchronises compute_stream). n, leaf_cap and with_masses must be
+ * the values the workspace was sized for.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct {
+    void* ws;             /* device workspace, cstone_host_workspace_size bytes */
+    size_t ws_bytes;
+    void* staged;         /* cudaEvent_t */
+    void* inputs_read;    /* cudaEvent_t */
+    void* built;          /* cudaEvent_t */
+    void* copied_out;     /* cudaEvent_t */
+} cstone_host_slot;
+
+typedef struct {              /* host arrays (pinned), owned by the caller; node_cap = leaf_cap + (leaf_cap - 1) / 7 */
+    uint64_t* leaves;         /* [leaf_cap + 1] cornerstone array K */
+    uint32_t* leaf_counts;    /* [leaf_cap] N_i */
+    uint64_t* node_keys;      /* [node_cap] NK */
+    int32_t* child;           /* [node_cap] CO */
+    int32_t* level_offsets;   /* [23] LO */
+    uint32_t* node_counts;    /* [node_cap] */
+    float* mass;              /* [node_cap], or NULL without masses */
+    double* com;              /* [3 * node_cap]: com[d * n_nodes + i], or NULL */
+    float* quad;              /* [6 * node_cap]: quad[q * n_nodes + i] (xx xy xz yy yz zz), or NULL */
+    int64_t n_leaves;         /* out (host, set by cstone_host_build) */
+    int64_t n_nodes;          /* out */
+    int32_t iters;            /* out: f / g passes */
+} cstone_host_tree;
+
+CSTONE_API int cstone_host_workspace_size(int64_t n, int64_t leaf_cap, int32_t with_masses, size_t* bytes);
+/* hx, hy, hz [n] float64 host; hm [n] float32 host, NULL without masses (then with_masses = 0). */
+CSTONE_API int cstone_host_stage(const double* hx, const double* hy, const double* hz, const float* hm, int64_t n,
+                                 int64_t leaf_cap, const cstone_host_slot* slot, void* copy_in_stream);
+CSTONE_API int cstone_host_build(int64_t n, int64_t leaf_cap, int32_t with_masses, int32_t curve, uint32_t ncrit,
+                                 int32_t max_iters, const cstone_host_slot* slot, cstone_host_tree* out,
+                                 void* compute_stream, void* copy_out_stream);
+/* First device error recorded by the last cstone_host_build on the slot (CSTONE_OK if none). */
+CSTONE_API int cstone_host_status(int64_t n, int64_t leaf_cap, int32_t with_masses, const cstone_host_slot* slot,
+                                  void* compute_stream);
+
+/* ------------------------------------------------------------------------------------------
  * f and g as separate steps, for a leaf array whose counts are summed over several processes
  * (the global tree of Sec. 6: every rank counts its own particles, the counts are summed by an
  * allreduce, and every rank applies the same g to the summed counts).

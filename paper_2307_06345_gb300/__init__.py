@@ -117,6 +117,11 @@ def load():
             "cstone_keys_records_workspace_size": (ctypes.c_int, [psz]),
             "cstone_keys_records": (ctypes.c_int, [P, P, P, P, i64, P, ctypes.c_int, P, P, P, sz, P]),
             "cstone_upsweep_multipoles_records": (ctypes.c_int, [P, P, i64, P, i64, P, P, P, P, P, P, P, P, sz, P]),
+            "cstone_host_workspace_size": (ctypes.c_int, [i64, i64, i32, psz]),
+            "cstone_host_stage": (ctypes.c_int, [P, P, P, P, i64, i64, ctypes.POINTER(_HostSlot), P]),
+            "cstone_host_build": (ctypes.c_int, [i64, i64, i32, i32, u32, i32, ctypes.POINTER(_HostSlot),
+                                                 ctypes.POINTER(_HostTree), P, P]),
+            "cstone_host_status": (ctypes.c_int, [i64, i64, i32, ctypes.POINTER(_HostSlot), P]),
         }
         for name in ("keys", "sort_workspace_size", "sort", "leaves_workspace_size", "build_leaves",
                      "link_workspace_size", "link_tree", "upsweep_workspace_size", "upsweep_counts",
@@ -205,6 +210,18 @@ class _BatchBuffers(ctypes.Structure):
                 ("leaf_offsets", ctypes.c_void_p), ("node_keys", ctypes.c_void_p), ("child", ctypes.c_void_p),
                 ("level_offsets", ctypes.c_void_p), ("leaf_to_node", ctypes.c_void_p),
                 ("node_counts", ctypes.c_void_p), ("node_cap", ctypes.c_int64)]
+
+
+class _HostSlot(ctypes.Structure):
+    _fields_ = [("ws", ctypes.c_void_p), ("ws_bytes", ctypes.c_size_t), ("staged", ctypes.c_void_p),
+                ("inputs_read", ctypes.c_void_p), ("built", ctypes.c_void_p), ("copied_out", ctypes.c_void_p)]
+
+
+class _HostTree(ctypes.Structure):
+    _fields_ = [("leaves", ctypes.c_void_p), ("leaf_counts", ctypes.c_void_p), ("node_keys", ctypes.c_void_p),
+                ("child", ctypes.c_void_p), ("level_offsets", ctypes.c_void_p), ("node_counts", ctypes.c_void_p),
+                ("mass", ctypes.c_void_p), ("com", ctypes.c_void_p), ("quad", ctypes.c_void_p),
+                ("n_leaves", ctypes.c_int64), ("n_nodes", ctypes.c_int64), ("iters", ctypes.c_int32)]
 
 
 # ------------------------------------------------------------------------- C entry points
@@ -866,56 +883,77 @@ def _grow(b: OctreeBuffers, want: int) -> OctreeBuffers:
 # ------------------------------------------------------------------------- host-resident input
 class StreamedBuilder:
     """Full builds (as ``build_octree``, with multipoles) of a sequence of particle sets held in
-    pinned host memory, with the host<->device transfers overlapped with the builds.
-
-    Three CUDA streams and two slots of device inputs and output buffers: while set k is built on
-    the compute stream, set k+1's coordinates and masses are copied in on a copy-in stream and set
-    k-1's tree is copied out on a copy-out stream (the link carries both directions at once).
-    Events order every reuse of a slot: a copy-in waits until the build that read the slot is done,
-    and a build waits until the copy-out of the slot's previous tree is done. The results are
-    pinned host tensors, valid once ``run`` returns (or, for set k, once its event has completed).
+    pinned host memory, with the host<->device transfers overlapped with the builds: the C entry
+    points cstone_host_stage (copy-in) and cstone_host_build (build and copy-out) on two device
+    slots and three CUDA streams. While set k is built on the compute stream, set k+1 is copied in
+    on the copy-in stream and set k-1's tree is copied out on the copy-out stream (the link carries
+    both directions at once); the slots' events order every reuse of their memory. The results are
+    pinned host tensors, valid once ``run`` returns (or, for set k, once its copy-out event has
+    completed). 63-bit keys.
     """
 
     OUT = ("leaves", "leaf_counts", "NK", "CO", "LO", "node_counts", "mass", "com", "quad")
 
-    def __init__(self, n: int, device="cuda", curve: int = HILBERT, ncrit: int = 64, levels: int = LEVELS):
-        self.n, self.curve, self.ncrit, self.levels = n, curve, ncrit, levels
+    def __init__(self, n: int, device="cuda", curve: int = HILBERT, ncrit: int = 64, levels: int = LEVELS,
+                 leaf_cap: int | None = None, max_iters: int = 64):
+        if levels != LEVELS:
+            raise ValueError("StreamedBuilder builds 63-bit keys (levels = 21)")
+        lib = load()
+        self.n, self.curve, self.ncrit, self.levels, self.max_iters = n, curve, ncrit, levels, max_iters
         self.device = torch.device(device)
+        self.cap = leaf_cap if leaf_cap is not None else leaf_capacity(n, ncrit)
+        self.node_cap = self.cap + (self.cap - 1) // 7
         self.s_comp = torch.cuda.Stream(self.device)
         self.s_in = torch.cuda.Stream(self.device)
         self.s_out = torch.cuda.Stream(self.device)
-        f64, f32 = torch.float64, torch.float32
-        self.inputs = [tuple(torch.empty(n, dtype=dt, device=self.device) for dt in (f64, f64, f64, f32))
-                       for _ in range(2)]
-        self.buffers = [None, None]
-        self.host = [{}, {}]
-        self.ev_in = [torch.cuda.Event() for _ in range(2)]     # slot's inputs copied in
-        self.ev_used = [torch.cuda.Event() for _ in range(2)]   # slot's build finished
-        self.ev_out = [torch.cuda.Event() for _ in range(2)]    # slot's tree copied out
+        nbytes = _size(lib.cstone_host_workspace_size, n, self.cap, 1)
+        self.slots, self.events, self.ws, self.host = [], [], [], []
+        for _ in range(2):
+            ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
+            evs = [torch.cuda.Event() for _ in range(4)]  # staged, inputs_read, built, copied_out
+            for e in evs:  # creates the events (completed) so that their handles exist
+                e.record(self.s_comp)
+            self.ws.append(ws)
+            self.events.append(evs)
+            self.slots.append(_HostSlot(ws.data_ptr(), nbytes, *(e.cuda_event for e in evs)))
+            cap, nc = self.cap, self.node_cap
+            pin = lambda k, dt: torch.empty(max(k, 1), dtype=dt, pin_memory=True)  # noqa: E731
+            self.host.append({"leaves": pin(cap + 1, torch.int64), "leaf_counts": pin(cap, torch.int32),
+                              "NK": pin(nc, torch.int64), "CO": pin(nc, torch.int32),
+                              "LO": pin(LEVELS + 2, torch.int32), "node_counts": pin(nc, torch.int32),
+                              "mass": pin(nc, torch.float32), "com": pin(3 * nc, torch.float64),
+                              "quad": pin(6 * nc, torch.float32)})
+        self.s_comp.synchronize()
 
-    def _copy_in(self, slot: int, src):
-        with torch.cuda.stream(self.s_in):
-            self.s_in.wait_event(self.ev_used[slot])
-            for dst, h in zip(self.inputs[slot], src):
-                dst.copy_(h, non_blocking=True)
-            self.ev_in[slot].record(self.s_in)
+    def _tree(self, slot: int) -> _HostTree:
+        h = self.host[slot]
+        return _HostTree(*(h[k].data_ptr() for k in self.OUT), 0, 0, 0)
 
-    def _copy_out(self, slot: int, out: dict):
-        host = self.host[slot]
-        res = {}
-        with torch.cuda.stream(self.s_out):
-            self.s_out.wait_event(self.ev_used[slot])
-            for k in self.OUT:
-                t = out[k].reshape(-1)
-                h = host.get(k)
-                if h is None or h.numel() < t.numel():
-                    h = host[k] = torch.empty(max(t.numel(), 1), dtype=t.dtype, pin_memory=True)
-                h[: t.numel()].copy_(t, non_blocking=True)
-                res[k] = h[: t.numel()]
-            self.ev_out[slot].record(self.s_out)
-        res["n_leaves"] = out["n_leaves"]
-        res["iters"] = out["iters"]
+    def _stage(self, slot: int, src):
+        x, y, z, m = src
+        _check(load().cstone_host_stage(_ptr(x), _ptr(y), _ptr(z), _ptr(m), self.n, self.cap,
+                                        ctypes.byref(self.slots[slot]), _stream(self.s_in)), "cstone_host_stage")
+
+    def _build(self, slot: int) -> dict:
+        lib = load()
+        tree = self._tree(slot)
+        rc = lib.cstone_host_build(self.n, self.cap, 1, self.curve, self.ncrit, self.max_iters,
+                                   ctypes.byref(self.slots[slot]), ctypes.byref(tree), _stream(self.s_comp),
+                                   _stream(self.s_out))
+        _check(rc, "cstone_host_build")
+        nl, nn = int(tree.n_leaves), int(tree.n_nodes)
+        h = self.host[slot]
+        sizes = {"leaves": nl + 1, "leaf_counts": nl, "NK": nn, "CO": nn, "LO": LEVELS + 2, "node_counts": nn,
+                 "mass": nn, "com": 3 * nn, "quad": 6 * nn}
+        res = {k: h[k][: sizes[k]] for k in self.OUT}
+        res["n_leaves"], res["iters"] = nl, int(tree.iters)
         return res
+
+    def status(self, slot: int) -> int:
+        """Device errors recorded by the last build on ``slot`` (raises CstoneError)."""
+        _check(load().cstone_host_status(self.n, self.cap, 1, ctypes.byref(self.slots[slot]), _stream(self.s_comp)),
+               "cstone_host_status")
+        return 0
 
     def run(self, sets, on_result=None, events=None, build_starts=None):
         """Builds every (x, y, z, m) of ``sets`` (pinned host tensors: float64 coordinates, float32
@@ -923,34 +961,28 @@ class StreamedBuilder:
         result)`` receives set k's host result dict once its copy-out has completed (a result's
         tensors are reused two sets later). ``events`` = (start, stop) CUDA events, recorded before
         the first copy-in and after the last copy-out. ``build_starts``, a list, receives one timing
-        event per set, recorded on the compute stream where the set's build starts."""
+        event per set, recorded on the compute stream ahead of the set's build."""
         sets = list(sets)
         for src in sets:
-            if len(src) != 4 or any(t.numel() != self.n or t.is_cuda for t in src):
-                raise ValueError("every set is (x, y, z, m) host tensors of n particles")
+            if (len(src) != 4 or any(t.numel() != self.n or t.is_cuda or not t.is_contiguous() for t in src)
+                    or any(t.dtype != torch.float64 for t in src[:3]) or src[3].dtype != torch.float32):
+                raise ValueError("every set is (x, y, z, m) contiguous host tensors of n particles "
+                                 "(float64 coordinates, float32 masses)")
         h2d = d2h = 0
         pending = []
         if events is not None:
             events[0].record(self.s_in)
         if sets:
-            self._copy_in(0, sets[0])
+            self._stage(0, sets[0])
         for k in range(len(sets)):
             slot = k % 2
             if k + 1 < len(sets):
-                self._copy_in((k + 1) % 2, sets[k + 1])  # queued before this build's host syncs
-            with torch.cuda.stream(self.s_comp):
-                self.s_comp.wait_event(self.ev_in[slot])
-                self.s_comp.wait_event(self.ev_out[slot])  # the slot's previous tree has left
-                if build_starts is not None:
-                    ev = torch.cuda.Event(enable_timing=True)
-                    ev.record(self.s_comp)
-                    build_starts.append(ev)
-                x, y, z, m = self.inputs[slot]
-                out = build_octree(x, y, z, curve=self.curve, ncrit=self.ncrit, masses=m,
-                                   buffers=self.buffers[slot], stream=self.s_comp, levels=self.levels)
-                self.buffers[slot] = out["buffers"]
-                self.ev_used[slot].record(self.s_comp)
-            res = self._copy_out(slot, out)
+                self._stage((k + 1) % 2, sets[k + 1])  # queued before this build's host synchronisation
+            if build_starts is not None:
+                ev = torch.cuda.Event(enable_timing=True)
+                ev.record(self.s_comp)
+                build_starts.append(ev)
+            res = self._build(slot)
             if events is not None and k + 1 == len(sets):
                 events[1].record(self.s_out)
             h2d += sum(t.numel() * t.element_size() for t in sets[k])
@@ -958,7 +990,7 @@ class StreamedBuilder:
             pending.append((k, slot, res))
             while pending and (len(pending) > 1 or k + 1 == len(sets)):
                 kk, sl, r = pending.pop(0)
-                self.ev_out[sl].synchronize()
+                self.events[sl][3].synchronize()  # the slot's tree is on the host
                 if on_result is not None:
                     on_result(kk, r)
         return h2d, d2h

@@ -61,3 +61,46 @@ def test_streamed_short_sequences(lib, count):
     for k, (x, y, z, m) in enumerate(sets):
         ref = lib.build_octree(x.cuda(), y.cuda(), z.cuda(), curve=1, ncrit=16, masses=m.cuda())
         assert torch.equal(got[k], ref["NK"].cpu())
+
+
+def test_host_build_through_c_abi(lib):
+    # one set through cstone_host_stage and cstone_host_build directly: the host tree equals
+    # build_octree on a device copy; then a leaf capacity too small is reported with a count above it
+    import ctypes
+    n = 70_001
+    (x, y, z, m), = _sets(n, 1)
+    L = lib.load()
+    ref = lib.build_octree(x.cuda(), y.cuda(), z.cuda(), curve=1, ncrit=24, masses=m.cuda())
+    torch.cuda.synchronize()
+    for cap, ok in ((lib.leaf_capacity(n, 24), True), (ref["n_leaves"] - 7, False)):
+        nbytes = ctypes.c_size_t()
+        assert L.cstone_host_workspace_size(n, cap, 1, ctypes.byref(nbytes)) == 0
+        ws = torch.empty(nbytes.value, dtype=torch.uint8, device="cuda")
+        evs = [torch.cuda.Event() for _ in range(4)]
+        for e in evs:
+            e.record()
+        slot = lib._HostSlot(ws.data_ptr(), nbytes.value, *(e.cuda_event for e in evs))
+        nc = cap + (cap - 1) // 7
+        host = [torch.empty(k, dtype=dt, pin_memory=True) for k, dt in
+                ((cap + 1, torch.int64), (cap, torch.int32), (nc, torch.int64), (nc, torch.int32), (23, torch.int32),
+                 (nc, torch.int32), (nc, torch.float32), (3 * nc, torch.float64), (6 * nc, torch.float32))]
+        tree = lib._HostTree(*(t.data_ptr() for t in host), 0, 0, 0)
+        s_in, s_c, s_o = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+        P = ctypes.c_void_p
+        assert L.cstone_host_stage(P(x.data_ptr()), P(y.data_ptr()), P(z.data_ptr()), P(m.data_ptr()), n, cap,
+                                   ctypes.byref(slot), P(s_in.cuda_stream)) == 0
+        rc = L.cstone_host_build(n, cap, 1, 1, 24, 64, ctypes.byref(slot), ctypes.byref(tree), P(s_c.cuda_stream),
+                                 P(s_o.cuda_stream))
+        if not ok:
+            assert rc == lib.ERR_CAPACITY and tree.n_leaves > cap
+            continue
+        assert rc == 0
+        evs[3].synchronize()
+        assert L.cstone_host_status(n, cap, 1, ctypes.byref(slot), P(s_c.cuda_stream)) == 0
+        nl, nn = tree.n_leaves, tree.n_nodes
+        assert nl == ref["n_leaves"] and nn == ref["NK"].numel() and tree.iters == ref["iters"]
+        got = dict(zip(lib.StreamedBuilder.OUT, (host[0][: nl + 1], host[1][:nl], host[2][:nn], host[3][:nn],
+                                                 host[4], host[5][:nn], host[6][:nn], host[7][: 3 * nn],
+                                                 host[8][: 6 * nn])))
+        for name, t in got.items():
+            assert torch.equal(t, ref[name].reshape(-1).cpu()), name
