@@ -34,7 +34,7 @@ int host_layout(int64_t n, int64_t cap, bool masses, HostLayout* l) {
     const size_t NC = static_cast<size_t>(nc);
     size_t len[kParts] = {};
     len[kX] = len[kY] = len[kZ] = 8 * N;
-    len[kM] = masses ? 4 * N : 0;
+    len[kM] = 4 * N;  // reserved with or without masses: the staged inputs sit at the same offsets either way
     len[kBox] = 4 * sizeof(double);
     len[kKeys] = len[kSorted] = 8 * N;
     len[kPerm] = 4 * N;
