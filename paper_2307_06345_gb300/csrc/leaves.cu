@@ -159,8 +159,11 @@ __device__ void write_root_arrays(const Key* P, u32 n, SetView sv, u32 gtid, u32
     }
 }
 
+#ifndef CSTONE_LEAVES_MIN_BLOCKS
+#define CSTONE_LEAVES_MIN_BLOCKS 5
+#endif
 template <bool BATCH>
-__global__ void __launch_bounds__(kThreads, 5) leaves_loop_kernel(const Key* __restrict__ P, u32 n, u32 ncrit,
+__global__ void __launch_bounds__(kThreads, CSTONE_LEAVES_MIN_BLOCKS) leaves_loop_kernel(const Key* __restrict__ P, u32 n, u32 ncrit,
                                                                LeafBufs b, u32 ecap, int max_iters, int warm,
                                                                u32 ne_start, int fallback, LoopState* ls, WsHeader* hdr, SetView sv,
                                                                Key* out_keys, u32* out_counts, u32* out_offsets) {
