@@ -213,7 +213,8 @@ int cstone_host_status(int64_t n, int64_t leaf_cap, int32_t with_masses, const c
     if (int rc = cst::host_layout(n, leaf_cap, with_masses != 0, &l)) return rc;
     if (int rc = cst::check_ws(slot->ws, slot->ws_bytes, l.bytes, "cstone_host_status")) return rc;
     const char* base = static_cast<const char*>(slot->ws);
-    const int parts[] = {cst::kWsBbox, cst::kWsRec, cst::kWsSort, cst::kWsLink, cst::kWsCounts, cst::kWsMp};
+    // the phases that record device errors in their workspace header (the bounding cube records none)
+    const int parts[] = {cst::kWsRec, cst::kWsSort, cst::kWsLink, cst::kWsCounts, cst::kWsMp};
     for (int k : parts) {
         if (l.len[k] == 0) continue;
         int status = 0;

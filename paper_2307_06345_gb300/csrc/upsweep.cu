@@ -516,7 +516,7 @@ __global__ void __launch_bounds__(kLeafThreads) multipole_bigleaf_kernel(const u
 
 // Internal nodes, level by level from the deepest: every internal node of a level combines its 8
 // children (in child order) with the parallel-axis shift; a grid barrier separates the levels.
-__global__ void __launch_bounds__(kThreads, 2) multipole_level_kernel(const int* __restrict__ child,
+__global__ void __launch_bounds__(kThreads, 4) multipole_level_kernel(const int* __restrict__ child,
                                                                    const int* __restrict__ level_offsets, u32 n_nodes,
                                                                    MpScratch s, const double* __restrict__ box,
                                                                    float* __restrict__ mass, double* __restrict__ com,
@@ -532,92 +532,95 @@ __global__ void __launch_bounds__(kThreads, 2) multipole_level_kernel(const int*
     const u32 n_int = (n_nodes - 1) / 8;
     list_internal(child, n_nodes, n_int, s.internal, gtid, gthreads, hdr);
     grid_barrier(bar, hdr);
-    auto combine = [&](u32 g) {
-        const int c0 = static_cast<int>(8u * g + 1u);  // c0 + 7 <= 8 n_int = n_nodes - 1
-        const int x = s.internal[g];
-        ff Mc[8];
-        long long cc[8][3];
-        int anchor = -1;
+    // One internal node per group of 8 lanes, lane k taking child k: the node's sums are shuffle
+    // reductions over the group (compensated adds, pairwise order).
+    auto group_ff = [](ff v) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const float2 mm = __ldcg(reinterpret_cast<const float2*>(s.mass) + c0 + k);
-            Mc[k] = {mm.x, mm.y};
-            if (anchor < 0 && (mm.x != 0.f || mm.y != 0.f)) anchor = k;
-#pragma unroll
-            for (int d = 0; d < 3; ++d) cc[k][d] = __ldcg(s.cfix + (size_t)d * n_nodes + c0 + k);
+        for (int s_ = 4; s_ >= 1; s_ >>= 1) {
+            ff o;
+            o.hi = __shfl_xor_sync(0xffffffffu, v.hi, s_, 8);
+            o.lo = __shfl_xor_sync(0xffffffffu, v.lo, s_, 8);
+            v = ff_add(v, o);
         }
-        ff Mp = ff_zero(), Sp[3] = {ff_zero(), ff_zero(), ff_zero()}, Qp[6], Rp[3] = {ff_zero(), ff_zero(), ff_zero()};
+        return v;
+    };
+    auto combine8 = [&](u32 g, bool active) {  // every lane of the warp calls it (shuffles)
+        const int lane8 = threadIdx.x & 7;
+        const int gbase = (threadIdx.x & 31) & ~7;
+        const int c0 = static_cast<int>(8u * (active ? g : 0u) + 1u);
+        const int ck = c0 + lane8;
+        ff Mk = ff_zero();
+        long long cc[3] = {0, 0, 0};
+        ff rk[3] = {ff_zero(), ff_zero(), ff_zero()}, qk[6];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) Qp[k] = ff_zero();
-        long long cp[3] = {0, 0, 0};
-        if (anchor >= 0) {
-            long long ca[3];
+        for (int q = 0; q < 6; ++q) qk[q] = ff_zero();
+        if (active) {
+            const float2 mm = __ldcg(reinterpret_cast<const float2*>(s.mass) + ck);
+            Mk = {mm.x, mm.y};
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                ca[d] = cc[0][d];
-#pragma unroll
-                for (int k = 1; k < 8; ++k)
-                    if (k == anchor) ca[d] = cc[k][d];
+                cc[d] = __ldcg(s.cfix + (size_t)d * n_nodes + ck);
+                const float2 rr = __ldcg(reinterpret_cast<const float2*>(s.res + (size_t)d * n_nodes) + ck);
+                rk[d] = ff{rr.x, rr.y};
             }
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                Mp = ff_add(Mp, Mc[k]);
-                const float mk = ff_val(Mc[k]);
-#pragma unroll
-                for (int d = 0; d < 3; ++d)
-                    Sp[d] = ff_add(Sp[d], __fmul_rn(mk, fixed_diff(cc[k][d], ca[d], f)));
+            for (int q = 0; q < 6; ++q) {
+                const float2 qq = __ldcg(reinterpret_cast<const float2*>(s.quad + (size_t)q * n_nodes) + ck);
+                qk[q] = ff{qq.x, qq.y};
             }
+        }
+        const u32 nz = (__ballot_sync(0xffffffffu, active && (Mk.hi != 0.f || Mk.lo != 0.f)) >> gbase) & 0xffu;
+        const int anchor = nz ? __ffs(nz) - 1 : 0;
+        long long ca[3], cp[3] = {0, 0, 0};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) ca[d] = __shfl_sync(0xffffffffu, cc[d], anchor, 8);
+        ff Mp = group_ff(Mk), Qp[6], Rp[3];
+        const float mk = ff_val(Mk);
+        ff Sp[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) Sp[d] = group_ff(ff{nz ? __fmul_rn(mk, fixed_diff(cc[d], ca[d], f)) : 0.f, 0.f});
+        if (nz) {
             const float Mv = ff_val(Mp);
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 const float off = __fdiv_rn(ff_val(Sp[d]), Mv);
                 cp[d] = ca[d] + float_to_int64(__fmul_rn(__fmul_rn(off, 1.0f / f.s1), 1.0f / f.s2));
             }
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                float e[3];
-#pragma unroll
-                for (int d = 0; d < 3; ++d) e[d] = fixed_diff(cc[k][d], cp[d], f);
-                const float mk = ff_val(Mc[k]);
-                const float me0 = __fmul_rn(mk, e[0]), me1 = __fmul_rn(mk, e[1]), me2 = __fmul_rn(mk, e[2]);
-                const float shift[6] = {__fmul_rn(me0, e[0]), __fmul_rn(me0, e[1]), __fmul_rn(me0, e[2]),
-                                        __fmul_rn(me1, e[1]), __fmul_rn(me1, e[2]), __fmul_rn(me2, e[2])};
-                // the child's residual first moment about its own centre: cross terms r e^T + e r^T
-                ff rk[3];
-                float rv[3];
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    const float2 rr = __ldcg(reinterpret_cast<const float2*>(s.res + (size_t)d * n_nodes) + c0 + k);
-                    rk[d] = ff{rr.x, rr.y};
-                    rv[d] = ff_val(rk[d]);
-                }
-                const float cross[6] = {
-                    __fmul_rn(2.0f, __fmul_rn(rv[0], e[0])), __fadd_rn(__fmul_rn(rv[0], e[1]), __fmul_rn(rv[1], e[0])),
-                    __fadd_rn(__fmul_rn(rv[0], e[2]), __fmul_rn(rv[2], e[0])), __fmul_rn(2.0f, __fmul_rn(rv[1], e[1])),
-                    __fadd_rn(__fmul_rn(rv[1], e[2]), __fmul_rn(rv[2], e[1])), __fmul_rn(2.0f, __fmul_rn(rv[2], e[2]))};
-#pragma unroll
-                for (int q = 0; q < 6; ++q) {
-                    const float2 qq =
-                        __ldcg(reinterpret_cast<const float2*>(s.quad + (size_t)q * n_nodes) + c0 + k);
-                    Qp[q] = ff_add(Qp[q], ff{qq.x, qq.y});
-                    Qp[q] = ff_add(Qp[q], shift[q]);
-                    Qp[q] = ff_add(Qp[q], cross[q]);
-                }
-                const float me[3] = {me0, me1, me2};
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    Rp[d] = ff_add(Rp[d], rk[d]);
-                    Rp[d] = ff_add(Rp[d], me[d]);
-                }
-            }
         }
+        float e[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) e[d] = nz ? fixed_diff(cc[d], cp[d], f) : 0.f;
+        const float me0 = __fmul_rn(mk, e[0]), me1 = __fmul_rn(mk, e[1]), me2 = __fmul_rn(mk, e[2]);
+        const float shift[6] = {__fmul_rn(me0, e[0]), __fmul_rn(me0, e[1]), __fmul_rn(me0, e[2]),
+                                __fmul_rn(me1, e[1]), __fmul_rn(me1, e[2]), __fmul_rn(me2, e[2])};
+        float rv[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) rv[d] = ff_val(rk[d]);
+        const float cross[6] = {
+            __fmul_rn(2.0f, __fmul_rn(rv[0], e[0])), __fadd_rn(__fmul_rn(rv[0], e[1]), __fmul_rn(rv[1], e[0])),
+            __fadd_rn(__fmul_rn(rv[0], e[2]), __fmul_rn(rv[2], e[0])), __fmul_rn(2.0f, __fmul_rn(rv[1], e[1])),
+            __fadd_rn(__fmul_rn(rv[1], e[2]), __fmul_rn(rv[2], e[1])), __fmul_rn(2.0f, __fmul_rn(rv[2], e[2]))};
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            ff t = ff_add(qk[q], shift[q]);
+            t = ff_add(t, cross[q]);
+            Qp[q] = group_ff(nz ? t : ff_zero());
+        }
+        const float me[3] = {me0, me1, me2};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) Rp[d] = group_ff(nz ? ff_add(rk[d], me[d]) : ff_zero());
+        if (!active || lane8 != 0) return;
+        const int x = s.internal[g];
         if (x < 0 || static_cast<u32>(x) >= n_nodes || child[x] != c0) {
             raise_error(hdr, CSTONE_ERR_INVALID_ARG, 0x75000u);
             return;
         }
         store_node(x, n_nodes, Mp, cp, Qp, Rp, s, f, mass, com, quad);
     };
-    // small levels by block 0 alone, as in the count upsweep
+    // small levels by block 0 alone, as in the count upsweep; 8 lanes per node, the loop bounds
+    // the same in every lane of a warp
+    constexpr u32 kGroups = kThreads / 8;
+    const u32 gw = (blockIdx.x * kThreads + threadIdx.x) / 32, nw = gridDim.x * (kThreads / 32);
     bool pending = false;
     for (int l = kLevels - 1; l >= 0; --l) {
         if (s_lo[l + 2] == s_lo[l + 1]) continue;  // no internal node at level l
@@ -625,14 +628,20 @@ __global__ void __launch_bounds__(kThreads, 2) multipole_level_kernel(const int*
         internal_range(s_lo, l, n_int, g0, g1);
         if (g1 <= g0 + kSmallLevel) {
             if (blockIdx.x == 0) {
-                for (u32 g = g0 + threadIdx.x; g < g1; g += kThreads) combine(g);
+                for (u32 b0 = g0; b0 < g1; b0 += kGroups) {  // uniform trip count in the block
+                    const u32 g = b0 + threadIdx.x / 8;
+                    combine8(g, g < g1);
+                }
                 __syncthreads();
             }
             pending = true;
             continue;
         }
         if (pending) grid_barrier(bar, hdr);
-        for (u32 g = g0 + gtid; g < g1; g += gthreads) combine(g);
+        for (u32 b0 = g0 + 4 * gw; b0 < g1; b0 += 4 * nw) {  // a warp takes 4 nodes, b0 the same in its lanes
+            const u32 g = b0 + (threadIdx.x & 31) / 8;
+            combine8(g, g < g1);
+        }
         grid_barrier(bar, hdr);
         pending = false;
     }
