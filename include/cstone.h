@@ -430,8 +430,8 @@ CSTONE_API int cstone_build_batched_result(const void* ws, int64_t n, int32_t n_
  * cstone_host_build synchronises compute_stream once, after the leaf loop, for the number of
  * leaves; it returns CSTONE_ERR_CAPACITY (with out->n_leaves = the leaves needed) when leaf_cap
  * is too small, and then copies nothing out. Device errors of the phases after the leaf loop are
- * read by cstone_host_status (synchronises compute_stream). n, leaf_cap and with_masses must be
- * the values the workspace was sized for.
+ * read by cstone_host_status (synchronises compute_stream). n (at least 1), leaf_cap and
+ * with_masses must be the values the workspace was sized for.
  * ------------------------------------------------------------------------------------------ */
 typedef struct {
     void* ws;             /* device workspace, cstone_host_workspace_size bytes */

@@ -889,7 +889,8 @@ class StreamedBuilder:
     on the copy-in stream and set k-1's tree is copied out on the copy-out stream (the link carries
     both directions at once); the slots' events order every reuse of their memory. The results are
     pinned host tensors, valid once ``run`` returns (or, for set k, once its copy-out event has
-    completed). 63-bit keys.
+    completed). 63-bit keys. ``leaf_cap`` (default: the bound of ``leaf_capacity``) sizes the slots;
+    a tree that needs more leaves raises CstoneError (ERR_CAPACITY) from ``run``.
     """
 
     OUT = ("leaves", "leaf_counts", "NK", "CO", "LO", "node_counts", "mass", "com", "quad")
