@@ -108,3 +108,25 @@ def test_one_call_batched_build_checks_its_capacities(clib):
     sz = ctypes.c_size_t()
     assert clib.cstone_build_batched_workspace_size(1000, 3, 70, 64, ctypes.byref(sz)) == 0 and sz.value > 0
     assert clib.cstone_build_batched_workspace_size(1000, 5000, 20000, 64, ctypes.byref(sz)) == 1  # > 4096 sets
+
+
+def test_host_build_queries_and_argument_checks(clib):
+    # the end-to-end entry points: workspace sizing and the checks made before any CUDA call
+    import paper_2307_06345_gb300 as cs
+    sz, sz_m = ctypes.c_size_t(), ctypes.c_size_t()
+    n, cap = 100_000, cs.leaf_capacity(100_000, 64)
+    assert clib.cstone_host_workspace_size(n, cap, 0, ctypes.byref(sz)) == 0
+    assert clib.cstone_host_workspace_size(n, cap, 1, ctypes.byref(sz_m)) == 0
+    # inputs (28 bytes per particle), keys, sorted keys and permutation at least; masses add the
+    # 32-byte records and the node multipoles
+    assert sz.value >= 48 * n and sz_m.value >= sz.value + 32 * n
+    assert clib.cstone_host_workspace_size(0, cap, 1, ctypes.byref(sz)) == 1
+    assert clib.cstone_host_workspace_size(n, 0, 1, ctypes.byref(sz)) == 1
+    dummy = ctypes.c_void_p(256)
+    slot = cs._HostSlot(256, sz_m.value, 0, 0, 0, 0)  # events missing
+    assert clib.cstone_host_stage(dummy, dummy, dummy, None, n, cap, ctypes.byref(slot), None) == 1
+    slot = cs._HostSlot(256, 1024, 8, 8, 8, 8)  # workspace too small
+    assert clib.cstone_host_stage(dummy, dummy, dummy, None, n, cap, ctypes.byref(slot), None) == 1
+    tree = cs._HostTree()
+    assert clib.cstone_host_build(n, cap, 1, 1, 64, 64, ctypes.byref(slot), ctypes.byref(tree), None, None) == 1
+    assert clib.cstone_host_build(n, cap, 1, 1, 64, 64, None, ctypes.byref(tree), None, None) == 1
