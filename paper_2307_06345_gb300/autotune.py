@@ -6,9 +6,9 @@ with CUDA events on the two workloads the shapes matter for, checked bit for bit
 library's current output, and the fastest shape per knob group is written to ``tuning.json``,
 which the in-tree build turns into compile definitions.
 
-Workloads: the single-set build of 2^27 clump particles (Hilbert keys, Ncrit 64) and the batched
-build of 512 sets of log-uniform size in [2^10, 2^20) (Morton keys, Ncrit 32). A candidate's score
-is the sum of its median times on both.
+Workloads: the single-set build of 2^27 clump particles (Hilbert keys, Ncrit 64; the leaf loop also
+at Ncrit 16) and the batched build of 512 sets of log-uniform size in [2^10, 2^20) (Morton keys,
+Ncrit 32). A candidate's score is the sum of its median times on all of them.
 """
 from __future__ import annotations
 
@@ -100,6 +100,11 @@ class Inputs:
         self.counts = torch.empty(cap, dtype=torch.int32, device=dev)
         self.n_leaves, _ = cs.cstone_build_leaves(self.sorted, 64, self.leaves, self.counts, None, 0, 64, ws)
         self.ref_leaves = self.leaves[: self.n_leaves + 1].clone()
+        cap16 = cs.leaf_capacity(n_single, 16)  # the same keys at Ncrit 16 (the benchmark's other Ncrit)
+        self.leaves16 = torch.empty(cap16 + 1, dtype=torch.int64, device=dev)
+        self.counts16 = torch.empty(cap16, dtype=torch.int32, device=dev)
+        self.n_leaves16, _ = cs.cstone_build_leaves(self.sorted, 16, self.leaves16, self.counts16, None, 0, 64, ws)
+        self.ref_leaves16 = self.leaves16[: self.n_leaves16 + 1].clone()
 
         sets = w.batched_sets(512, w.BASE_SEED + 3)
         sizes = np.array([len(s[0]) for s in sets], np.int64)
@@ -176,6 +181,19 @@ def time_leaves(L, inp: Inputs, reps: int):
 
     single = _median_ms(single_run, reps)
     ok = nl.value == inp.n_leaves and torch.equal(leaves[: nl.value + 1], inp.ref_leaves)
+    cap16 = inp.counts16.numel()
+    ws16 = _ws(L, "cstone_leaves_workspace_size", n, cap16, 64)
+    leaves16, counts16 = torch.empty_like(inp.leaves16), torch.empty_like(inp.counts16)
+
+    def single16_run():
+        nl.value = 0
+        rc = L.cstone_build_leaves(_ptr(inp.sorted), n, 16, _ptr(leaves16), cap16, ctypes.byref(nl), _ptr(counts16),
+                                   None, 64, ctypes.byref(it), _ptr(ws16), ws16.numel(), _stream())
+        if rc != 0:
+            raise RuntimeError(f"cstone_build_leaves failed ({rc})")
+
+    single16 = _median_ms(single16_run, reps)
+    ok = ok and nl.value == inp.n_leaves16 and torch.equal(leaves16[: nl.value + 1], inp.ref_leaves16)
     nb = inp.bsorted.numel()
     bws = _ws(L, "cstone_leaves_batched_workspace_size", inp.belem_cap, 64)
     elements, eo, bcounts = torch.empty_like(inp.belements), torch.empty_like(inp.beo), torch.empty_like(inp.bcounts)
@@ -191,7 +209,8 @@ def time_leaves(L, inp: Inputs, reps: int):
 
     batched = _median_ms(batched_run, reps)
     ok = ok and ne.value == inp.bne and torch.equal(elements[: ne.value], inp.ref_belements)
-    return {"single_ms": single, "batched_ms": batched, "score_ms": single + batched, "bit_exact": bool(ok)}
+    return {"single_ms": single, "single16_ms": single16, "batched_ms": batched,
+            "score_ms": single + single16 + batched, "bit_exact": bool(ok)}
 
 
 def tune(n_single: int = 1 << 27, reps: int = 5, out: str = _build.TUNING, verbose: bool = True) -> dict:
@@ -226,7 +245,7 @@ def tune(n_single: int = 1 << 27, reps: int = 5, out: str = _build.TUNING, verbo
             raise RuntimeError(f"no {group} candidate reproduced the reference output")
         choice[group] = min(good, key=lambda r: r["score_ms"])["candidate"]
     doc = {"device": torch.cuda.get_device_name(dev), "choice": choice, "measurements": results,
-           "workloads": {"single": f"{n_single} clump particles, Hilbert keys, Ncrit 64",
+           "workloads": {"single": f"{n_single} clump particles, Hilbert keys, Ncrit 64 (leaf loop also at 16)",
                          "batched": "512 sets, sizes log-uniform in [2^10, 2^20), Morton keys, Ncrit 32"},
            "reps": reps, "seconds": round(time.time() - t0, 1)}
     with open(out, "w") as f:
