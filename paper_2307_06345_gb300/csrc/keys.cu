@@ -17,8 +17,12 @@
 // in shared memory, so a 21-level key takes 7 lookups.
 #include <mutex>
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "records.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace CST_NS {
 
@@ -504,16 +508,25 @@ __device__ __forceinline__ int set_of(const long long* __restrict__ set_offsets,
     return lo;
 }
 
-// Bounding cube of every set, one block per set.
-__global__ void __launch_bounds__(256) bbox_batched_kernel(const double* __restrict__ x, const double* __restrict__ y,
-                                                           const double* __restrict__ z,
-                                                           const long long* __restrict__ set_offsets,
-                                                           double* __restrict__ boxes) {
-    __shared__ long long s_lo[8][3], s_hi[8][3];
-    const long long a = set_offsets[blockIdx.x], b = set_offsets[blockIdx.x + 1];
+// Bounding cube of every set: one cluster of kBoxCluster blocks per set (a large set is read by
+// kBoxCluster SMs, not one); each block reduces its share of the set, and the cluster's first block
+// combines the blocks' results from their shared memory (distributed shared memory of the cluster).
+constexpr int kBoxCluster = 16;  // a non-portable cluster size, allowed per kernel at launch
+constexpr int kBoxThreads = 256;
+
+__global__ void __cluster_dims__(kBoxCluster, 1, 1) __launch_bounds__(kBoxThreads)
+    bbox_batched_kernel(const double* __restrict__ x, const double* __restrict__ y, const double* __restrict__ z,
+                        const long long* __restrict__ set_offsets, double* __restrict__ boxes) {
+    __shared__ long long s_lo[kBoxThreads / 32][3], s_hi[kBoxThreads / 32][3];
+    __shared__ long long s_blo[3], s_bhi[3];  // this block's result, read by the cluster's first block
+    cg::cluster_group cluster = cg::this_cluster();
+    const unsigned rank = cluster.block_rank();
+    const int set = static_cast<int>(blockIdx.x / kBoxCluster);
+    const long long a = set_offsets[set], b = set_offsets[set + 1];
     long long lo[3] = {kOrderedMax, kOrderedMax, kOrderedMax}, hi[3] = {kOrderedMin, kOrderedMin, kOrderedMin};
     const double* c[3] = {x, y, z};
-    for (long long i = a + threadIdx.x; i < b; i += blockDim.x) {
+    for (long long i = a + static_cast<long long>(rank) * kBoxThreads + threadIdx.x; i < b;
+         i += static_cast<long long>(kBoxCluster) * kBoxThreads) {
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             const long long o = ordered_bits(__ldg(c[d] + i));
@@ -535,26 +548,39 @@ __global__ void __launch_bounds__(256) bbox_batched_kernel(const double* __restr
             s_hi[warp][d] = hi[d];
         }
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    double* box = boxes + 4 * blockIdx.x;
-    if (b <= a) {
-        box[0] = box[1] = box[2] = 0.0;
-        box[3] = 1.0;
-        return;
-    }
-    double side = 0.0;
-    for (int d = 0; d < 3; ++d) {
+    if (threadIdx.x < 3) {
+        const int d = threadIdx.x;
         long long l = s_lo[0][d], h = s_hi[0][d];
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+        for (int w = 1; w < kBoxThreads / 32; ++w) {
             l = min(l, s_lo[w][d]);
             h = max(h, s_hi[w][d]);
         }
-        const double lod = from_ordered(l), hid = from_ordered(h);
-        box[d] = lod;
-        const double ext = __dsub_rn(hid, lod);
-        side = ext > side ? ext : side;
+        s_blo[d] = l;
+        s_bhi[d] = h;
     }
-    box[3] = side > 0.0 ? side : 1.0;
+    cluster.sync();  // every block's result is in its shared memory
+    if (rank == 0 && threadIdx.x == 0) {
+        double* box = boxes + 4 * set;
+        if (b <= a) {
+            box[0] = box[1] = box[2] = 0.0;
+            box[3] = 1.0;
+        } else {
+            double side = 0.0;
+            for (int d = 0; d < 3; ++d) {
+                long long l = s_blo[d], h = s_bhi[d];
+                for (unsigned r = 1; r < kBoxCluster; ++r) {
+                    l = min(l, cluster.map_shared_rank(s_blo, r)[d]);
+                    h = max(h, cluster.map_shared_rank(s_bhi, r)[d]);
+                }
+                const double lod = from_ordered(l), hid = from_ordered(h);
+                box[d] = lod;
+                const double ext = __dsub_rn(hid, lod);
+                side = ext > side ? ext : side;
+            }
+            box[3] = side > 0.0 ? side : 1.0;
+        }
+    }
+    cluster.sync();  // the other blocks keep their shared memory until it has been read
 }
 
 __global__ void keys_batched_setup_kernel(const double* __restrict__ boxes, int n_sets, FixedGrid* grids) {
@@ -614,7 +640,8 @@ size_t keys_batched_ws_bytes(int n_sets) {
 
 int launch_bbox_batched(const double* x, const double* y, const double* z, const long long* set_offsets, int n_sets,
                         double* boxes, cudaStream_t st) {
-    bbox_batched_kernel<<<n_sets, 256, 0, st>>>(x, y, z, set_offsets, boxes);
+    CST_CUDA(cudaFuncSetAttribute(bbox_batched_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    bbox_batched_kernel<<<n_sets * kBoxCluster, kBoxThreads, 0, st>>>(x, y, z, set_offsets, boxes);
     CST_LAUNCHED("bbox_batched_kernel");
     return CSTONE_OK;
 }
