@@ -84,48 +84,13 @@ __global__ void __launch_bounds__(kThreads) link_count_kernel(const Key* __restr
     }
 }
 
-// Exclusive scan of the level-major (level, tile) counts in one block; LO[l] = offset of (l, 0),
-// LO[22] = total. A total different from n_expected means the input was not a cornerstone array.
-__global__ void __launch_bounds__(1024) link_scan_kernel(u32* __restrict__ counts, u32 ntiles, int* __restrict__ LO,
-                                                         u32 n_expected, WsHeader* hdr) {
-    __shared__ u32 s_part[1024];
-    const u32 total_len = ntiles * kNumLevels;
-    const u32 per = (total_len + 1023) / 1024;
-    const u32 begin = threadIdx.x * per;
-    const u32 end = min(begin + per, total_len);
-    u32 sum = 0;
-    for (u32 i = begin; i < end; ++i) sum += counts[i];
-    s_part[threadIdx.x] = sum;
-    __syncthreads();
-    for (int s = 1; s < 1024; s <<= 1) {
-        u32 v = threadIdx.x >= (unsigned)s ? s_part[threadIdx.x - s] : 0u;
-        __syncthreads();
-        s_part[threadIdx.x] += v;
-        __syncthreads();
-    }
-    u32 run = s_part[threadIdx.x] - sum;
-    for (u32 i = begin; i < end; ++i) {
-        u32 c = counts[i];
-        counts[i] = run;
-        if (LO && i % ntiles == 0) LO[i / ntiles] = static_cast<int>(run);
-        run += c;
-    }
-    if (threadIdx.x == 1023) {
-        u32 total = s_part[1023];
-        counts[total_len] = total;
-        if (LO) {
-            LO[kNumLevels] = static_cast<int>(total);
-            if (total != n_expected) raise_error(hdr, CSTONE_ERR_INVALID_ARG, total);
-        }
-    }
-}
-
 // Exclusive scans of the level-major (level, tile) counts of all nodes (half 0) and of the internal
 // nodes alone (half 1), each of `len` entries, in chunks of kScanChunk: block (c, h) sums chunk c
 // of half h, then block (c, h) adds the sums of the chunks before it and scans its chunk. LO comes
 // from half 0 (LO[l] = offset of (l, 0), LO[22] = total); a total of all nodes different from
 // n_expected, or of internal nodes different from (n_expected - 1) / 8, means the input was not a
-// cornerstone array.
+// cornerstone array. Without LO (the batched (set, level, tile) counts, one half) the total goes
+// to the entry after the scanned ones.
 constexpr u32 kScanThreads = 1024;
 constexpr u32 kScanPer = 4;
 constexpr u32 kScanChunk = kScanThreads * kScanPer;
@@ -173,9 +138,13 @@ __global__ void __launch_bounds__(kScanThreads) link_scan_apply_kernel(u32* __re
         if (lane == 0) {
             s_carry = before;
             if (c == nchunks - 1) {
-                const u32 want = h == 0 ? n_expected : (n_expected - 1) / 8;
-                if (h == 0) LO[kNumLevels] = static_cast<int>(all);
-                if (all != want) raise_error(hdr, CSTONE_ERR_INVALID_ARG, all);
+                if (LO) {
+                    const u32 want = h == 0 ? n_expected : (n_expected - 1) / 8;
+                    if (h == 0) LO[kNumLevels] = static_cast<int>(all);
+                    if (all != want) raise_error(hdr, CSTONE_ERR_INVALID_ARG, all);
+                } else {
+                    counts[(size_t)h * len + len] = all;  // without LO (batched sets): the total after the scan
+                }
             }
         }
     }
@@ -211,7 +180,7 @@ __global__ void __launch_bounds__(kScanThreads) link_scan_apply_kernel(u32* __re
         const u32 i = i0 + j;
         if (i < len) {
             a[i] = run;
-            if (h == 0 && i % ntiles == 0) LO[i / ntiles] = static_cast<int>(run);
+            if (LO && h == 0 && i % ntiles == 0) LO[i / ntiles] = static_cast<int>(run);
         }
         run += v[j];
     }
@@ -557,8 +526,10 @@ __global__ void __launch_bounds__(kThreads) link_b_child_kernel(const Key* __res
 
 struct LinkBLayout {
     LinkSets ls;
-    u32* counts;
+    u32* counts;   // [max_tiles * 22 + 1]: (set, level, tile) counts, their exclusive scan, the total
+    u32* partial;  // [chunks] chunk sums of the scan
     u32 max_tiles;
+    u32 chunks;
     size_t bytes;
 };
 
@@ -575,6 +546,8 @@ LinkBLayout link_b_layout(void* ws, long long n_elements, int n_sets) {
     l.ls.n_sets = n_sets;
     l.ls.elem_offsets = nullptr;
     l.counts = c.take<u32>((size_t)l.max_tiles * kNumLevels + 1);
+    l.chunks = static_cast<u32>(((size_t)l.max_tiles * kNumLevels + kScanChunk - 1) / kScanChunk);
+    l.partial = c.take<u32>(l.chunks);
     l.bytes = c.size();
     return l;
 }
@@ -599,8 +572,11 @@ int launch_link_batched(const Key* K, long long n_elements, const long long* ele
     link_b_count_kernel<<<l.max_tiles, kThreads, 0, st>>>(K, l.ls, l.counts);
     CST_LAUNCHED("link_b_count_kernel");
     // one exclusive scan over all (set, level, tile) counts; unused tail entries are zero
-    link_scan_kernel<<<1, 1024, 0, st>>>(l.counts, l.max_tiles, nullptr, 0u, hdr);
-    CST_LAUNCHED("link_scan_kernel");
+    const u32 len = l.max_tiles * kNumLevels;
+    link_scan_reduce_kernel<<<dim3(l.chunks, 1), kScanThreads, 0, st>>>(l.counts, len, l.partial);
+    CST_LAUNCHED("link_scan_reduce_kernel");
+    link_scan_apply_kernel<<<dim3(l.chunks, 1), kScanThreads, 0, st>>>(l.counts, len, 1u, l.partial, nullptr, 0u, hdr);
+    CST_LAUNCHED("link_scan_apply_kernel");
     const int lo_threads = n_sets * (kNumLevels + 1);
     link_b_lo_kernel<<<(lo_threads + 255) / 256, 256, 0, st>>>(l.counts, l.ls, LO, leaf_to_node, hdr);
     CST_LAUNCHED("link_b_lo_kernel");
